@@ -1,0 +1,421 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these tests compares the oracle with itself: they check published
+known-answer vectors, closed forms, exact Boltzmann enumeration, limits
+(T = 0, T = infinity), exact invariants (gauge covariance, energy bookkeeping)
+and brute-force loops on tiny lattices.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as ora
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors
+# ----------------------------------------------------------------------------------
+def _kat_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            rows.append([int(v, 16) for v in line.split()])
+    return rows
+
+
+def test_philox_known_answers():
+    rows = _kat_rows()
+    assert len(rows) == 3
+    for r in rows:
+        out = ora.philox4x32_10(r[0:4], r[4:6])
+        assert [int(v) for v in out] == r[6:10]
+
+
+# ----------------------------------------------------------------------------------
+# geometry of the random-number mapping
+# ----------------------------------------------------------------------------------
+def _geometry_table():
+    tab = {}
+    with open(os.path.join(GOLDEN, "geometry_lanes.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                L, kx, ky, kz = (int(v) for v in line.split())
+                tab[L] = (kx, ky, kz)
+    return tab
+
+
+def test_geometry_table():
+    for L, k in _geometry_table().items():
+        g = ora.geometry(L)
+        assert g[:3] == k
+        assert g[3:] == (L // k[0], L // k[1], L // k[2])
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 12, 16, 24])
+def test_geometry_bijection_and_colour(L):
+    kx, ky, kz, Lx, Ly, Lz = ora.geometry(L)
+    lanes = kx * ky * kz
+    seen = {}
+    for z, y, x in itertools.product(range(L), repeat=3):
+        w, b = ora.site_to_word(L, x, y, z)
+        assert 0 <= w < Lx * Ly * Lz and 0 <= b < lanes
+        assert (w, b) not in seen
+        seen[(w, b)] = (x, y, z)
+    assert len(seen) == L ** 3
+    # every site of a word-site has the same checkerboard colour
+    colours = {}
+    for (w, b), (x, y, z) in seen.items():
+        colours.setdefault(w, set()).add((x + y + z) & 1)
+    assert all(len(c) == 1 for c in colours.values())
+
+
+def test_geometry_rejects_bad_sizes():
+    for L in [0, 1, 3, 7, 1025, -2]:
+        with pytest.raises(ValueError):
+            ora.geometry(L)
+
+
+# ----------------------------------------------------------------------------------
+# acceptance thresholds (Eq. 9 and the heat-bath rule)
+# ----------------------------------------------------------------------------------
+TWO64 = 2.0 ** 64
+
+
+def test_metropolis_thresholds_closed_form_limits():
+    thr, alw = ora.thresholds(0.7, 0)
+    # dE = -12..0 always accepted, dE > 0 not
+    assert list(alw) == [1, 1, 1, 1, 0, 0, 0]
+    # exact values at T = 4/ln 2: exp(-4/T) = 1/2, so dE = 4, 8, 12 give 2^63, 2^62, 2^61
+    T = 4.0 / math.log(2.0)
+    thr, alw = ora.thresholds(T, 0)
+    for k, e in [(4, 63), (5, 62), (6, 61)]:
+        assert abs(int(thr[k]) - 2 ** e) <= 2 ** (e - 48)
+    # T = 0: no uphill move; T = infinity: every move
+    thr, alw = ora.thresholds(0.0, 0)
+    assert list(alw) == [1, 1, 1, 1, 0, 0, 0] and list(thr[4:]) == [0, 0, 0]
+    thr, alw = ora.thresholds(float("inf"), 0)
+    assert list(alw) == [1] * 7
+
+
+def test_thresholds_sign_and_scale():
+    # the probability falls with dE and with 1/T; at T = 1, dE = 4: e^-4
+    thr, _ = ora.thresholds(1.0, 0)
+    assert abs(int(thr[4]) / TWO64 - math.exp(-4.0)) < 1e-15
+    assert abs(int(thr[6]) / TWO64 - math.exp(-12.0)) < 1e-15
+    assert int(thr[4]) > int(thr[5]) > int(thr[6]) > 0
+    # T = 0.5, dE = 12 has probability e^-24 ~ 3.8e-11, below 2^-32, still positive
+    thr, _ = ora.thresholds(0.5, 0)
+    # floor() loses less than one unit of 2^-64
+    assert int(thr[6]) > 0 and abs(int(thr[6]) - math.ldexp(math.exp(-24.0), 64)) <= 1.0
+
+
+def test_heatbath_thresholds():
+    thr, alw = ora.thresholds(1.3, 1)
+    assert not any(alw)
+    assert int(thr[3]) == 2 ** 63  # dE = 0: probability 1/2 exactly
+    for k in range(7):
+        # p(dE) + p(-dE) = 1
+        assert abs(int(thr[k]) + int(thr[6 - k]) - 2 ** 64) <= 2 ** 12
+    assert abs(int(thr[4]) / TWO64 - 1.0 / (1.0 + math.exp(4.0 / 1.3))) < 1e-15
+    thr, alw = ora.thresholds(0.0, 1)
+    assert list(alw) == [1, 1, 1, 0, 0, 0, 0] and int(thr[3]) == 2 ** 63
+    assert list(thr[4:]) == [0, 0, 0]
+    thr, alw = ora.thresholds(float("inf"), 1)
+    assert all(int(v) == 2 ** 63 for v in thr)
+
+
+def test_thresholds_reject_bad_args():
+    for T, rule in [(-1.0, 0), (float("nan"), 0), (1.0, 2)]:
+        with pytest.raises(ValueError):
+            ora.thresholds(T, rule)
+
+
+# ----------------------------------------------------------------------------------
+# random numbers and initial state
+# ----------------------------------------------------------------------------------
+def test_random64_uniform_top_bits():
+    L = 8
+    vals = []
+    for t in range(4):
+        for z, y, x in itertools.product(range(L), repeat=3):
+            vals.append(ora.random64(L, 12345, 3, t & 1, x, y, z, t) >> 60)
+    counts = np.bincount(np.array(vals), minlength=16)
+    n = len(vals)
+    chi2 = float(np.sum((counts - n / 16.0) ** 2 / (n / 16.0)))
+    assert chi2 < 45.0  # 15 dof, p ~ 1e-4
+
+
+def test_random64_depends_on_every_key_part():
+    base = ora.random64(16, 7, 2, 0, 3, 4, 5, 11)
+    assert base != ora.random64(16, 8, 2, 0, 3, 4, 5, 11)  # seed
+    assert base != ora.random64(16, 7, 3, 0, 3, 4, 5, 11)  # sample
+    assert base != ora.random64(16, 7, 2, 1, 3, 4, 5, 11)  # replica
+    assert base != ora.random64(16, 7, 2, 0, 4, 4, 5, 11)  # site
+    assert base != ora.random64(16, 7, 2, 0, 3, 4, 5, 12)  # sweep
+    assert base != ora.random64(16, 7, 2, 0, 3, 4, 5, 11 + (1 << 32))  # high sweep bits
+
+
+def test_couplings_bimodal_fraction():
+    L = 16
+    assert np.all(ora.init_couplings(L, 0.0, 5, 0) == 1)
+    assert np.all(ora.init_couplings(L, 1.0, 5, 0) == -1)
+    J = ora.init_couplings(L, 0.3, 5, 1)
+    n = J.size
+    frac = float(np.mean(J == -1))
+    assert abs(frac - 0.3) < 5 * math.sqrt(0.3 * 0.7 / n)
+    assert set(np.unique(J)) == {-1, 1}
+    # different samples get different disorder
+    assert np.any(ora.init_couplings(L, 0.5, 5, 0) != ora.init_couplings(L, 0.5, 5, 1))
+
+
+def test_spins_uniform_start():
+    S = ora.init_spins(16, 9, 0)
+    n = S.size
+    assert abs(float(np.mean(S == -1)) - 0.5) < 5 * math.sqrt(0.25 / n)
+    assert np.any(S[0] != S[1])  # the replicas start from different states
+
+
+# ----------------------------------------------------------------------------------
+# exact enumeration of the Boltzmann distribution at L = 2
+# ----------------------------------------------------------------------------------
+def _energy_table_L2(J):
+    """Energy of all 256 states of the 2^3 lattice; state bit i = site i is -1."""
+    E = np.zeros(256)
+    for st in range(256):
+        s = np.array([-1 if (st >> i) & 1 else 1 for i in range(8)], dtype=np.int8)
+        S = np.stack([s.reshape(2, 2, 2), s.reshape(2, 2, 2)])
+        E[st] = ora.energy(S, J)[0]
+    return E
+
+
+def _state_index(S_a):
+    flat = S_a.reshape(-1)
+    return int(sum(1 << i for i in range(8) if flat[i] == -1))
+
+
+def _chain_histogram(J, T, rule, seed, n_sweeps, burn=200):
+    L = 2
+    S = ora.init_spins(L, seed, 0)
+    hist = np.zeros(256)
+    ora.sweeps(L, seed, 0, S, J, T, rule, 0, burn)
+    for t in range(burn, burn + n_sweeps):
+        ora.sweeps(L, seed, 0, S, J, T, rule, t, 1)
+        hist[_state_index(S[0])] += 1
+        hist[_state_index(S[1])] += 1
+    return hist
+
+
+def _chi2(hist, E, T):
+    w = np.exp(-(E - E.min()) / T)
+    p = w / w.sum()
+    n = hist.sum()
+    exp_ = n * p
+    return float(np.sum((hist - exp_) ** 2 / exp_))
+
+
+@pytest.mark.parametrize("p_neg,T,rule,seed", [(0.0, 3.0, 0, 1), (0.5, 2.0, 0, 2),
+                                               (0.5, 2.0, 1, 3), (0.25, 2.5, 0, 4)])
+def test_L2_chain_samples_boltzmann(p_neg, T, rule, seed):
+    J = ora.init_couplings(2, p_neg, 100 + seed, 0)
+    E = _energy_table_L2(J)
+    hist = _chain_histogram(J, T, rule, seed, 60000)
+    chi2 = _chi2(hist, E, T)
+    dof = 255
+    # samples are correlated in time (chi2/dof falls towards 1 as the run grows,
+    # where a biased chain would make it grow); a 2x allowance is still far below
+    # the value for a wrong temperature or a wrong sign of dE
+    assert chi2 / dof < 2.0, chi2 / dof
+    assert _chi2(hist, E, 0.7 * T) / dof > 6.0
+    assert _chi2(hist, -E, T) / dof > 6.0
+
+
+# ----------------------------------------------------------------------------------
+# limits and invariants of the dynamics
+# ----------------------------------------------------------------------------------
+def test_infinite_temperature_flips_every_spin_every_sweep():
+    L = 6
+    J = ora.init_couplings(L, 0.5, 3, 0)
+    S0 = ora.init_spins(L, 3, 0)
+    S = S0.copy()
+    E0 = ora.energy(S0, J)
+    for t in range(5):
+        ora.sweeps(L, 3, 0, S, J, float("inf"), 0, t, 1)
+        assert np.array_equal(S, S0 if t % 2 else -S0)
+        # C(t_w, t) = (-1)^t exactly and E(t) = E(0)
+        assert np.all(ora.autocorr_sum(S0, S) == (-1) ** (t + 1) * L ** 3)
+        assert np.array_equal(ora.energy(S, J), E0)
+
+
+def test_zero_temperature_ferromagnet():
+    L = 8
+    J = ora.init_couplings(L, 0.0, 4, 0)
+    # the all-up state is absorbing
+    S = np.ones((2, L, L, L), dtype=np.int8)
+    ora.sweeps(L, 4, 0, S, J, 0.0, 0, 0, 5)
+    assert np.all(S == 1)
+    # from a random start the energy never rises
+    S = ora.init_spins(L, 4, 0)
+    prev = ora.energy(S, J)
+    for t in range(30):
+        ora.sweeps(L, 4, 0, S, J, 0.0, 0, t, 1)
+        e = ora.energy(S, J)
+        assert np.all(e <= prev)
+        prev = e
+    assert np.all(prev < 0)
+
+
+@pytest.mark.parametrize("L,p_neg,T,rule", [(4, 0.5, 0.7, 0), (6, 0.3, 1.1, 0),
+                                            (8, 0.5, 0.8, 1), (2, 0.5, 1.0, 0)])
+def test_energy_bookkeeping(L, p_neg, T, rule):
+    """Sum of accepted dE equals the change of the energy computed from scratch."""
+    J = ora.init_couplings(L, p_neg, 21, 2)
+    S = ora.init_spins(L, 21, 2)
+    E0 = ora.energy(S, J)
+    acc = np.zeros(2, dtype=np.int64)
+    for t in range(0, 40, 5):
+        acc += ora.sweeps(L, 21, 2, S, J, T, rule, t, 5)
+        assert np.array_equal(ora.energy(S, J) - E0, acc)
+
+
+@pytest.mark.parametrize("L,rule", [(4, 0), (6, 0), (8, 1), (12, 0)])
+def test_gauge_covariance(L, rule):
+    """J'_ij = e_i e_j J_ij and S'(0) = e S(0) give S'(t) = e S(t) with the same randoms."""
+    rng = np.random.default_rng(L)
+    eps = rng.choice(np.array([-1, 1], dtype=np.int8), size=(L, L, L))
+    J = ora.init_couplings(L, 0.5, 77, 1)
+    S = ora.init_spins(L, 77, 1)
+    Jg = np.empty_like(J)
+    for d, ax in ((0, 2), (1, 1), (2, 0)):
+        Jg[d] = J[d] * eps * np.roll(eps, -1, axis=ax)
+    Sg = (S * eps[None]).astype(np.int8)
+    ora.sweeps(L, 77, 1, S, J, 0.8, rule, 0, 12)
+    ora.sweeps(L, 77, 1, Sg, Jg, 0.8, rule, 0, 12)
+    assert np.array_equal(Sg, S * eps[None])
+    assert ora.overlap_sum(Sg) == ora.overlap_sum(S)
+    assert np.array_equal(ora.c4_sums(Sg), ora.c4_sums(S))
+    assert np.array_equal(ora.energy(Sg, Jg), ora.energy(S, J))
+
+
+def test_mattis_disorder_is_a_ferromagnet():
+    """J_ij = e_i e_j has an unfrustrated ground state S = e with E = -3N."""
+    L = 6
+    eps = np.random.default_rng(3).choice(np.array([-1, 1], dtype=np.int8), size=(L, L, L))
+    J = np.empty((3, L, L, L), dtype=np.int8)
+    for d, ax in ((0, 2), (1, 1), (2, 0)):
+        J[d] = eps * np.roll(eps, -1, axis=ax)
+    S = np.stack([eps, eps]).astype(np.int8)
+    assert np.all(ora.energy(S, J) == -3 * L ** 3)
+    ora.sweeps(L, 1, 0, S, J, 0.0, 0, 0, 4)
+    assert np.array_equal(S[0], eps) and np.array_equal(S[1], eps)
+
+
+def test_acceptance_rate_matches_threshold():
+    """At T = infinity for heat bath every move has probability 1/2."""
+    L = 16
+    J = ora.init_couplings(L, 0.5, 8, 0)
+    S = ora.init_spins(L, 8, 0)
+    S0 = S.copy()
+    ora.sweeps(L, 8, 0, S, J, float("inf"), 1, 0, 1)
+    n = S.size
+    frac = float(np.mean(S != S0))
+    assert abs(frac - 0.5) < 5 * math.sqrt(0.25 / n)
+
+
+# ----------------------------------------------------------------------------------
+# observables: brute-force loops on tiny lattices
+# ----------------------------------------------------------------------------------
+def _brute(S, J):
+    L = S.shape[1]
+    N = L ** 3
+    Q = 0
+    G = np.zeros((3, L), dtype=np.int64)
+    E = [0, 0]
+    for z in range(L):
+        for y in range(L):
+            for x in range(L):
+                q = int(S[0, z, y, x]) * int(S[1, z, y, x])
+                Q += q
+                for r in range(L):
+                    G[0, r] += q * int(S[0, z, y, (x + r) % L]) * int(S[1, z, y, (x + r) % L])
+                    G[1, r] += q * int(S[0, z, (y + r) % L, x]) * int(S[1, z, (y + r) % L, x])
+                    G[2, r] += q * int(S[0, (z + r) % L, y, x]) * int(S[1, (z + r) % L, y, x])
+                for a in range(2):
+                    s = int(S[a, z, y, x])
+                    E[a] -= int(J[0, z, y, x]) * s * int(S[a, z, y, (x + 1) % L])
+                    E[a] -= int(J[1, z, y, x]) * s * int(S[a, z, (y + 1) % L, x])
+                    E[a] -= int(J[2, z, y, x]) * s * int(S[a, (z + 1) % L, y, x])
+    return Q, G, E, N
+
+
+@pytest.mark.parametrize("L", [2, 4, 6])
+def test_observables_brute_force(L):
+    J = ora.init_couplings(L, 0.4, 31, 0)
+    S = ora.init_spins(L, 31, 0)
+    ora.sweeps(L, 31, 0, S, J, 0.9, 0, 0, 3)
+    Q, G, E, N = _brute(S, J)
+    assert ora.overlap_sum(S) == Q
+    assert np.array_equal(ora.c4_sums(S), G[:, : L // 2 + 1])
+    assert list(ora.energy(S, J)) == E
+    # C4(0) = 1 and the periodic symmetry C4(r) = C4(L - r)
+    assert np.all(G[:, 0] == N)
+    for r in range(1, L):
+        assert np.array_equal(G[:, r], G[:, L - r])
+    # C(t_w, t_w) = 1
+    assert np.all(ora.autocorr_sum(S, S) == N)
+
+
+def test_run_job_schedule():
+    out = ora.run_job(4, 0.5, 5, 2, 0.7, 0, t_w=[0, 2], t=[0, 1, 3], n_sweeps=5)
+    N = 64
+    assert set(out["A"]) == {(0, 0), (0, 1), (0, 3), (2, 0), (2, 1), (2, 3)}
+    assert np.all(out["A"][(0, 0)] == N) and np.all(out["A"][(2, 0)] == N)
+    assert set(out["G"]) == {0, 2}
+    assert sorted(out["Q"]) == [0, 1, 2, 3, 5]
+    for tw in (0, 2):
+        assert np.all(out["G"][tw][:, :, 0] == N)
+    # energy bookkeeping across the whole run
+    E5 = out["E"][5]
+    E0 = out["E"][0]
+    assert np.array_equal(E5 - E0, out["dE"])
+
+
+# ----------------------------------------------------------------------------------
+# FP64 derived quantities (Eqs. 5-6)
+# ----------------------------------------------------------------------------------
+def test_xi1_closed_forms():
+    for n in (4, 8, 64):
+        c4 = np.full(n + 1, 0.37)
+        assert ora.xi1(c4, n) == pytest.approx((2 * n + 1) / 3.0, rel=1e-14)
+    # a cut at r_c = 4 keeps r = 1..4: sum r^2 / sum r = 30 / 10
+    assert ora.xi1(np.full(9, 1.0), 4) == pytest.approx(3.0, rel=1e-15)
+    assert math.isnan(ora.xi1(np.zeros(9), 8))
+    assert math.isnan(ora.xi1(np.full(9, 1.0), 0))
+
+
+def test_cutoff_rule():
+    c4 = np.array([1.0, 0.5, 0.3, 0.1, 0.02, 0.01])
+    sem = np.array([0.0, 0.01, 0.01, 0.01, 0.01, 0.01])
+    assert ora.cutoff(c4, sem) == 3  # first r with C4 < 3 sem is r = 4
+    assert ora.cutoff(c4, np.zeros(6)) == 5
+    assert ora.cutoff(c4, np.full(6, np.nan)) == 5
+    assert ora.cutoff(np.array([1.0, -0.1, 0.5]), np.array([0, 0.01, 0.01])) == 0
+
+
+def test_c4_curve_average_and_sem():
+    N = 8
+    G = np.zeros((2, 3, 2), dtype=np.int64)
+    G[:, :, 0] = N
+    G[0, :, 1] = [8, 4, 0]   # sample 0: mean over axes 4/8 = 0.5
+    G[1, :, 1] = [0, 0, 0]   # sample 1: 0
+    c4, sem = ora.c4_curve(G, N)
+    assert c4[0] == 1.0 and c4[1] == 0.25
+    assert sem[1] == pytest.approx(0.25, rel=1e-15)  # std([0.5, 0]) / sqrt(2)
