@@ -1,0 +1,352 @@
+"""Throughput benchmark: checkerboard Metropolis sweeps of the 3D +-J EA model.
+
+Workload (paper scale): L = 128 (N = 2,097,152), five jobs with p_neg in
+{0.5, 0.4, 0.3, 0.2, 0.1} of 16 samples each, two replicas per sample, T = 0.7,
+logarithmic measurement schedule.  A step is one window of sweeps over all 80
+samples (both replicas), with the scheduled measurements that fall inside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank runs its own
+independent copy of the workload (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin flips/ns (ps/flip) at L=128 + % of roofline; batched vs plain; p50/p99"
+UNIT = "flips/ns"
+
+
+# ----------------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------------
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ----------------------------------------------------------------------------------
+def cpu_oracle_sample(n_sweeps=4, L=128):
+    """Oracle on sample 0 of the first side-128 job: flips/ns on one host thread."""
+    import oracle as ora
+    from paper_1411_5512_gb300 import workloads
+
+    w = workloads.PAPER_SCALE[0]
+    J = ora.init_couplings(L, w["p_neg"], w["seed"], 0)
+    S = ora.init_spins(L, w["seed"], 0)
+    ora.sweeps(L, w["seed"], 0, S, J, w["T"], 0, 0, 1)  # warm the library
+    t0 = time.perf_counter()
+    ora.sweeps(L, w["seed"], 0, S, J, w["T"], 0, 1, n_sweeps)
+    dt = time.perf_counter() - t0
+    flips = n_sweeps * 2 * L ** 3
+    return {"value": flips / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "sample 0 of the L=128 p_neg=0.5 job, %d sweeps x 2 replicas "
+                      "(%.3g flips, %.1f s), one host thread" % (n_sweeps, flips, dt)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    per_step = max(1, args.ref_sweeps)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(1)
+    times = []
+    flips = 0
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(per_step)
+        times.append(per_step * 2 * 128 ** 3 / (r["value"] * 1e9))
+        flips += per_step * 2 * 128 ** 3
+    tot = sum(times)
+    value = flips / (tot * 1e9)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "L128_p0.5-0.1_S16x5_T0.7 (CPU oracle, bounded sample)",
+                       "L": 128, "samples": 1, "sweeps_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d steps x sample 0 of the L=128 p_neg=0.5 job x %d "
+                                       "sweeps x 2 replicas" % (args.steps, per_step)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1411_5512_gb300 import job, workloads
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    job.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    specs = workloads.PAPER_SCALE
+    L = specs[0]["L"]
+    N = L ** 3
+    sweeps_per_step = args.sweeps_per_step
+    total_sweeps = (args.warmup + args.steps) * sweeps_per_step
+    t_w = workloads.pow2_times(total_sweeps)
+    t_lag = workloads.pow2_times(total_sweeps)
+
+    def make_jobs():
+        jobs = []
+        for w in specs:
+            j = job.EAJob(w["L"], w["p_neg"], w["seed"] + 1000 * rank, w["n_samples"],
+                          stream=stream)
+            j.set_schedule(t_w, t_lag)
+            j.quench(w["T"])
+            jobs.append(j)
+        return jobs
+
+    jobs = make_jobs()
+    samples = sum(w["n_samples"] for w in specs)
+    flips_per_step = sweeps_per_step * samples * 2 * N
+    # L2 flush buffer (larger than the 126 MB L2), written between steps
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step():
+        for j in jobs:
+            j.sweep(sweeps_per_step)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * flips_per_step * args.steps / (t_ms * 1e6)
+    launches = args.steps * sweeps_per_step * 2 * len(specs)
+    kernel_ms = t_ms / launches  # per half-step launch, incl. the rare observable kernels
+    flips_per_launch = samples // len(specs) * N  # one half-step of one job: N per sample
+
+    pk, pk_kind = peaks()
+    # memory roofline of the half-step form: per flip read 1 word of the updated
+    # area, 1 of the neighbour area, 3 coupling bits per 2 flips... counted per
+    # site-update: spins read 2 bits + write 1 bit, couplings 3 bits = 6 bits
+    bytes_per_flip = 6.0 / 8.0
+    achieved_gbs = flips_per_launch * bytes_per_flip / (kernel_ms * 1e6)
+    roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved_gbs / pk["hbm_gbs"], "traffic": None,
+            "peak_kind": pk_kind, "kernel": "halfstep_kernel<0>",
+            "kernel_us_per_launch": kernel_ms * 1e3}
+
+    # end to end through the public API: job lifecycle per step on host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, job, workloads, stream, rank, world)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_sample(args.cpu_sweeps)
+
+    for j in jobs:
+        j.close()
+    clocks = sampler.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "ps_per_flip": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "L128_p0.5-0.1_S16x5_T0.7", "L": L,
+                       "jobs": [w["p_neg"] for w in specs], "samples": samples, "replicas": 2,
+                       "sweeps_per_step": sweeps_per_step, "rule": "metropolis", "rng_group": 1,
+                       "path": "plain (per-job half-step launches)",
+                       "l2": "flushed between steps (256 MiB write); the 105 MB state is "
+                             "L2-sized, so sweeps inside a step see it cache-warm"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+            "wall_s": wall}
+    if e2e is not None:
+        line["e2e"] = e2e
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, job, workloads, stream, rank, world):
+    """Whole jobs through the public API: create (couplings from the seed), schedule
+    (host arrays), quench, sweeps, and every scheduled observable read back to host."""
+    import numpy as np
+    import torch
+
+    specs = workloads.PAPER_SCALE
+    n = args.e2e_sweeps
+    t_w = workloads.pow2_times(n)
+    t_lag = workloads.pow2_times(n)
+    h2d = 8 * (len(t_w) + len(t_lag)) * len(specs)
+    d2h = 0
+
+    def one():
+        nonlocal d2h
+        d2h = 0
+        jobs = []
+        for w in specs:
+            j = job.EAJob(w["L"], w["p_neg"], w["seed"] + 7 + 1000 * rank, w["n_samples"],
+                          stream=stream)
+            j.set_schedule(t_w, t_lag)
+            j.quench(w["T"])
+            j.sweep(n)
+            jobs.append(j)
+        for j in jobs:
+            for a in t_w:
+                for b in t_lag:
+                    if a + b <= n:
+                        m = j.measure(a, b)
+                        d2h += sum(m[k].nbytes for k in ("A", "Q", "E", "G"))
+            j.close()
+
+    one()  # warm
+    torch.cuda.synchronize()
+    reps = max(1, args.e2e_steps)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        one()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    samples = sum(w["n_samples"] for w in specs)
+    flips = reps * n * samples * 2 * 128 ** 3
+    return {"value": world * flips / (dt * 1e9), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "sweeps_per_step": n, "steps": reps,
+            "includes": "create+couplings, schedule H2D, quench, sweeps, all observables D2H, "
+                        "destroy"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps-per-step", type=int, default=64)
+    ap.add_argument("--e2e-sweeps", type=int, default=1024)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--ref-sweeps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * ea_ageing.h -- C ABI of the GB300 (sm_103a) library for the non-equilibrium
+ * ageing simulation of the three-dimensional +-J Edwards-Anderson model of
+ * Manssen & Hartmann, "Ageing at the Spin-Glass/Ferromagnet Transition: Monte
+ * Carlo Simulation using GPUs" (arXiv 1411.5512).
+ *
+ * One context ("job") holds n_samples disorder samples of an L^3 periodic
+ * lattice, each with two replicas that share the couplings (Sec. II, Eq. 2),
+ * quenched from a random start (Sec. II) and evolved by single-spin-flip
+ * Metropolis sweeps in checkerboard order (Sec. III, Eq. 9).  Measurements of
+ * the autocorrelation C(t, t_w) (Eq. 7), the replica overlap q (Eq. 2), the
+ * four-point correlation C4(r, t_w) (Eq. 3) along the lattice axes and the
+ * integral estimator xi_1 (Eqs. 5-6) are taken on the device at the times of a
+ * schedule.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status: EA_OK (0) or a negative EA_ERR_*.
+ *     No call aborts the process or throws across the ABI.  After an error on
+ *     a context, ea_last_error(ctx) describes it.
+ *   - Host pointers are plain C arrays owned by the caller; the library never
+ *     keeps them after the call returns.  Device memory is owned by the context
+ *     and released by ea_destroy.
+ *   - p_neg is the fraction of NEGATIVE (antiferromagnetic) couplings, i.e.
+ *     1 - p in the paper's P(J) = p delta(J - 1) + (1 - p) delta(J + 1)
+ *     (Sec. II).  p_neg = 0.5 is the spin glass, p_neg = 0 the ferromagnet.
+ *   - Spins are reported as int8 +-1 in the order [z][y][x] (x fastest); the
+ *     coupling array J[d][z][y][x] (d = x, y, z) holds the bond between a site
+ *     and its +e_d neighbour, with periodic boundaries (Sec. II).
+ *   - L must be even (a checkerboard on a periodic lattice), 2 <= L <= 1024.
+ *   - Sweep t (t = 0, 1, ...) updates, in half-step h = 0 then h = 1, every
+ *     site of colour (x + y + z) mod 2 == h XOR a of replica a, so replica 1
+ *     runs the opposite colour order (the interlaced layout of Fig. 1).  After
+ *     n sweeps the context time is n; measurements at time m see the state
+ *     after m sweeps.
+ *   - Results are bit-identical to the CPU oracle on the same arguments: the
+ *     random numbers depend only on (seed, sample, replica, site, sweep).
+ */
+#ifndef EA_AGEING_H
+#define EA_AGEING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define EA_OK 0
+#define EA_ERR_INVALID_ARG (-1) /* argument out of range (odd L, p outside [0,1], ...) */
+#define EA_ERR_OOM (-2)         /* device or host allocation failed */
+#define EA_ERR_NO_SNAPSHOT (-3) /* (t_w, t) not scheduled or not reached yet */
+#define EA_ERR_STATE (-4)       /* call out of order (e.g. sweep before quench) */
+#define EA_ERR_TIMEOUT (-5)     /* a bounded device wait ran out */
+#define EA_ERR_CUDA (-6)        /* a CUDA runtime call failed */
+#define EA_ERR_IO (-7)          /* checkpoint file could not be written or read */
+
+/* ---- update rules ------------------------------------------------------- */
+#define EA_RULE_METROPOLIS 0 /* p = min(1, exp(-dE/T))      (Sec. III, Eq. 9) */
+#define EA_RULE_HEATBATH 1   /* p = 1 / (1 + exp(dE/T))     (variant)         */
+
+typedef struct ea_ctx ea_ctx;
+
+/* Observables of one (t_w, t) pair, filled by ea_measure.  Every array pointer
+ * may be NULL (then it is skipped); non-NULL arrays are caller-owned host
+ * memory of the stated sizes.  S = n_samples, R = L/2 + 1. */
+typedef struct ea_obs {
+    int64_t *A;      /* [S][2]  sum_i S_i(t_w) S_i(t_w + t) per replica     (Eq. 7 x N) */
+    int64_t *Q;      /* [S]     sum_i S^0_i S^1_i at time t_w + t          (Eq. 2 x N) */
+    int64_t *E;      /* [S][2]  H = -sum_<ij> J_ij S_i S_j at t_w + t       (Eq. 1)     */
+    int64_t *G;      /* [S][3][R] sum_i q_i q_{i + r e_d}, d = x,y,z, at t_w (Eq. 3 x N) */
+    double *C4;      /* [R]     C4(r, t_w), averaged over axes and samples            */
+    double *C4_sem;  /* [R]     standard error of C4 over samples (NaN if S < 2)       */
+    double C;        /* C(t, t_w), averaged over replicas and samples     (Eq. 7)     */
+    double q_mean;   /* sample mean of q at time t_w + t                  (Eq. 2)     */
+    double xi1;      /* xi_1(t_w) = I_2 / I_1 over r = 1..r_cut (Eqs. 5-6); NaN if empty */
+    int r_cut;       /* last r before C4 first drops below 3 * C4_sem (L/2 if never)   */
+} ea_obs;
+
+/* ---- host-only helpers (no GPU needed) ---------------------------------- */
+
+/* Human-readable name of a status code.  Never NULL. */
+const char *ea_status_string(int status);
+
+/* Geometry of the random-number mapping for lattice side L (Sec. III's
+ * multi-part packing, over three axes): out = {kx, ky, kz, L/kx, L/ky, L/kz}.
+ * The lattice is cut into kx*ky*kz <= 32 blocks of even side and the sites at
+ * the same position in every block form one 32-bit word.  Rule: h = L/2,
+ * p2 = largest power of two dividing h, kz = min(32, p2), ky = min(32/kz, p2),
+ * kx = min(32/(kz*ky), p2).  EA_ERR_INVALID_ARG for odd L or L outside [2,1024]. */
+int ea_geometry(int L, int out[6]);
+
+/* Acceptance thresholds for dE = 4k - 12, k = 0..6.  A move is accepted when
+ * always[k] != 0 or when the 64-bit uniform random number r < thr[k], so with
+ * probability floor(2^64 P(dE)) / 2^64, where P is min(1, exp(-dE/T)) for
+ * EA_RULE_METROPOLIS (Eq. 9) and 1/(1 + exp(dE/T)) for EA_RULE_HEATBATH;
+ * P = 1 sets always[k].  T = 0 and T = +inf give the limits.  Both arrays are
+ * caller-owned.  EA_ERR_INVALID_ARG for T < 0, NaN T or an unknown rule. */
+int ea_thresholds(double T, int rule, uint64_t thr[7], uint8_t always[7]);
+
+/* Device bytes a context with this shape and schedule will hold (spins,
+ * couplings, snapshots and results).  Host-only arithmetic. */
+int ea_footprint(int L, int n_samples, int n_tw, int n_t, size_t *bytes);
+
+/* ---- device memory hook -------------------------------------------------- */
+
+/* Route the library's device allocations through the caller (for example a
+ * framework's caching allocator).  alloc(bytes, stream, user) returns a device
+ * pointer or NULL; release(ptr, bytes, stream, user) frees it.  Passing NULL
+ * for both restores cudaMalloc / cudaFree.  Process-wide; call it while no
+ * context exists. */
+typedef void *(*ea_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*ea_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+int ea_set_allocator(ea_alloc_fn alloc, ea_free_fn release, void *user);
+
+/* ---- job lifecycle ------------------------------------------------------- */
+
+/* Create a job of n_samples samples of side L and generate their couplings on
+ * the device: J = -1 with probability p_neg, independently per bond (Sec. II,
+ * Eq. 1's bimodal P(J)).  rng_group_G >= 1 samples share each sweep random
+ * number (the paper shares one number across the samples of a word, Sec. III;
+ * G = 1 gives every sample its own); disorder and start stay per sample.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream); every device
+ * call of the job is enqueued on it.  *out receives the new context.
+ * Errors: EA_ERR_INVALID_ARG (odd L, L out of range, p_neg outside [0,1],
+ * n_samples < 1, G < 1), EA_ERR_OOM, EA_ERR_CUDA. */
+int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_samples,
+                      int rng_group_G, void *cuda_stream);
+
+/* Set the measurement schedule: waiting times t_w[0..n_tw) and time lags
+ * t[0..n_t) (Sec. II: C(t, t_w) and C4(r, t_w) are measured at waiting times
+ * counted in sweeps from the quench).  At every t_w the state is snapshotted
+ * and Q, E and the four-point sums G are taken; at every t_w + t the
+ * autocorrelation against the t_w snapshot and Q, E are taken.  Duplicates
+ * are ignored.  Must precede ea_quench.  Arrays are caller-owned.
+ * Errors: EA_ERR_INVALID_ARG (n < 0, more than 4096 entries, time >= 2^48),
+ * EA_ERR_STATE (after quench), EA_ERR_OOM. */
+int ea_set_schedule(ea_ctx *ctx, const uint64_t *t_w, int n_tw, const uint64_t *t, int n_t);
+
+/* Quench: draw uniform random initial spins for both replicas of every
+ * sample (Sec. II, start from infinite temperature), set the thresholds for
+ * temperature T and the update rule, reset the time to 0 and take the time-0
+ * measurements of the schedule.  May be called again to restart.
+ * Errors: EA_ERR_INVALID_ARG (T < 0, NaN, unknown rule), EA_ERR_CUDA. */
+int ea_quench(ea_ctx *ctx, double T, int rule);
+
+/* Run n sweeps (Sec. III: one sweep = both checkerboard half-steps), firing
+ * the scheduled snapshots and measurements on the way.  Asynchronous: work is
+ * enqueued on the job's stream.  Errors: EA_ERR_STATE (before ea_quench),
+ * EA_ERR_INVALID_ARG (time would pass 2^48), EA_ERR_CUDA. */
+int ea_sweep(ea_ctx *ctx, uint64_t n);
+
+/* Current time (sweeps done since the quench). */
+int ea_time(const ea_ctx *ctx, uint64_t *t);
+
+/* Read back the observables of the pair (t_w, t) into *out and derive the
+ * FP64 quantities (C, q, C4, its error, r_cut, xi_1; Eqs. 2, 3, 5-7).
+ * Synchronises the job's stream.  Errors: EA_ERR_NO_SNAPSHOT when t_w is not
+ * a scheduled waiting time, t not a scheduled lag, or t_w + t not reached. */
+int ea_measure(ea_ctx *ctx, uint64_t t_w, uint64_t t, ea_obs *out);
+
+/* Copy spins of sample s, replica a into out[L^3] (int8 +-1, [z][y][x]).
+ * Synchronous.  Errors: EA_ERR_INVALID_ARG, EA_ERR_STATE (before quench). */
+int ea_get_spins(ea_ctx *ctx, int s, int a, int8_t *out);
+
+/* Copy couplings of sample s into out[3][L^3] (int8 +-1, [d][z][y][x]). */
+int ea_get_couplings(ea_ctx *ctx, int s, int8_t *out);
+
+/* Load a configuration (the paper stores whole configurations at its
+ * measurement points, Sec. IV): replace the spins of sample s, replica a by
+ * in[L^3] (int8 +-1, [z][y][x]), or its couplings by in[3][L^3] ([d][z][y][x]),
+ * and set the time counter with ea_set_time (sweep t then draws the random
+ * numbers of sweep t).  Snapshots and results already taken are kept.
+ * Synchronous.  Errors: EA_ERR_INVALID_ARG (a value other than +-1, bad
+ * index, time >= 2^48), EA_ERR_STATE (spins or time before ea_quench). */
+int ea_set_spins(ea_ctx *ctx, int s, int a, const int8_t *in);
+int ea_set_couplings(ea_ctx *ctx, int s, const int8_t *in);
+int ea_set_time(ea_ctx *ctx, uint64_t t);
+
+/* Thresholds in use (as ea_thresholds).  EA_ERR_STATE before ea_quench. */
+int ea_get_thresholds(const ea_ctx *ctx, uint64_t thr[7], uint8_t always[7]);
+
+/* Write the whole job (parameters, time, schedule, spins, couplings,
+ * snapshots, results) to a file; ea_restore rebuilds it on cuda_stream.  The
+ * random numbers are counter-based, so a restored job continues bit-identically.
+ * Errors: EA_ERR_IO, EA_ERR_STATE (before quench), EA_ERR_CUDA, EA_ERR_OOM. */
+int ea_checkpoint(ea_ctx *ctx, const char *path);
+int ea_restore(ea_ctx **out, const char *path, void *cuda_stream);
+
+/* Release the job and its device memory.  NULL is accepted. */
+int ea_destroy(ea_ctx *ctx);
+
+/* Text of the last error on ctx (empty string if none).  Never NULL. */
+const char *ea_last_error(const ea_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EA_AGEING_H */

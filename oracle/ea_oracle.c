@@ -277,6 +277,8 @@ int ora_init_spins(int L, uint64_t seed, uint32_t s, int8_t *S)
 /* k = (dE + 12) / 4.  Sites of one colour do not neighbour each other, so  */
 /* this site-by-site loop equals the simultaneous update of a colour.       */
 /* dE_acc[a] accumulates the energy change of accepted flips of replica a.  */
+/* s keys the random numbers (counter word 3): the sample index, or the     */
+/* sample index divided by G when G samples share their random numbers.     */
 /* ------------------------------------------------------------------------ */
 int ora_sweep(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, const uint64_t thr[7],
               const uint8_t always[7], uint64_t t, int64_t dE_acc[2])

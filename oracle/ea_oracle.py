@@ -134,7 +134,11 @@ def init_spins(L, seed, s):
 
 
 def sweeps(L, seed, s, S, J, T, rule, t0, n):
-    """Run sweeps t0 .. t0+n-1 in place on S; return the accepted dE per replica."""
+    """Run sweeps t0 .. t0+n-1 in place on S; return the accepted dE per replica.
+
+    ``s`` keys the sweep random numbers: the sample index, or sample // G when
+    G samples share their random numbers.
+    """
     assert S.dtype == np.int8 and S.shape == (2, L, L, L) and S.flags.c_contiguous
     J = np.ascontiguousarray(J, dtype=np.int8)
     thr, alw = thresholds(T, rule)
@@ -248,7 +252,7 @@ def measurement_times(t_w, t, n_sweeps):
 
 
 def run_job(L, p_neg, seed, n_samples, T, rule, t_w, t, n_sweeps, samples=None,
-            keep_spins=False):
+            keep_spins=False, rng_group=1):
     """Run one job and return its integer observables.
 
     Returns a dict with
@@ -258,7 +262,9 @@ def run_job(L, p_neg, seed, n_samples, T, rule, t_w, t, n_sweeps, samples=None,
       'G'  {t_w: int64 [S][3][L/2+1]}   four-point sums at each t_w
       'dE' int64 [S][2]                 accepted energy changes over the run
       'spins' int8 [S][2][L][L][L]      final spins (if keep_spins)
-    ``samples`` selects a subset of the sample indices 0..n_samples-1.
+    ``samples`` selects a subset of the sample indices 0..n_samples-1.  Samples
+    s and s' with s // rng_group == s' // rng_group share their sweep random
+    numbers (disorder and initial spins stay per sample).
     """
     t_w = sorted(set(int(x) for x in t_w))
     t = sorted(set(int(x) for x in t))
@@ -284,7 +290,7 @@ def run_job(L, p_neg, seed, n_samples, T, rule, t_w, t, n_sweeps, samples=None,
         now = 0
         for m in times + [n_sweeps]:
             if m > now:
-                out["dE"][si] += sweeps(L, seed, s, S, J, T, rule, now, m - now)
+                out["dE"][si] += sweeps(L, seed, s // rng_group, S, J, T, rule, now, m - now)
                 now = m
             if m not in out["Q"]:
                 continue

@@ -1,0 +1,107 @@
+"""ctypes binding of the C ABI in include/ea_ageing.h (argument marshalling only).
+
+Every function of the header is exposed under its own name with its C
+signature.  Loading fails loudly when the compiled library is missing: there is
+no CPU fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libea_gb300.so")
+
+EA_OK = 0
+EA_ERR_INVALID_ARG = -1
+EA_ERR_OOM = -2
+EA_ERR_NO_SNAPSHOT = -3
+EA_ERR_STATE = -4
+EA_ERR_TIMEOUT = -5
+EA_ERR_CUDA = -6
+EA_ERR_IO = -7
+
+EA_RULE_METROPOLIS = 0
+EA_RULE_HEATBATH = 1
+
+i64p = ctypes.POINTER(ctypes.c_int64)
+u64p = ctypes.POINTER(ctypes.c_uint64)
+u8p = ctypes.POINTER(ctypes.c_uint8)
+i8p = ctypes.POINTER(ctypes.c_int8)
+u32p = ctypes.POINTER(ctypes.c_uint32)
+dblp = ctypes.POINTER(ctypes.c_double)
+intp = ctypes.POINTER(ctypes.c_int)
+vp = ctypes.c_void_p
+
+
+class EaObs(ctypes.Structure):
+    _fields_ = [("A", i64p), ("Q", i64p), ("E", i64p), ("G", i64p),
+                ("C4", dblp), ("C4_sem", dblp),
+                ("C", ctypes.c_double), ("q_mean", ctypes.c_double),
+                ("xi1", ctypes.c_double), ("r_cut", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(vp, ctypes.c_size_t, vp, vp)
+FREE_FN = ctypes.CFUNCTYPE(None, vp, ctypes.c_size_t, vp, vp)
+
+# name -> (restype, argtypes), in header order
+SIGNATURES = {
+    "ea_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ea_geometry": (ctypes.c_int, [ctypes.c_int, intp]),
+    "ea_thresholds": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, u64p, u8p]),
+    "ea_footprint": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_size_t)]),
+    "ea_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, vp]),
+    "ea_create_samples": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp]),
+    "ea_set_schedule": (ctypes.c_int, [vp, u64p, ctypes.c_int, u64p, ctypes.c_int]),
+    "ea_quench": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
+    "ea_sweep": (ctypes.c_int, [vp, ctypes.c_uint64]),
+    "ea_time": (ctypes.c_int, [vp, u64p]),
+    "ea_measure": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint64,
+                                  ctypes.POINTER(EaObs)]),
+    "ea_get_spins": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, i8p]),
+    "ea_get_couplings": (ctypes.c_int, [vp, ctypes.c_int, i8p]),
+    "ea_set_spins": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, i8p]),
+    "ea_set_couplings": (ctypes.c_int, [vp, ctypes.c_int, i8p]),
+    "ea_set_time": (ctypes.c_int, [vp, ctypes.c_uint64]),
+    "ea_get_thresholds": (ctypes.c_int, [vp, u64p, u8p]),
+    "ea_checkpoint": (ctypes.c_int, [vp, ctypes.c_char_p]),
+    "ea_restore": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_char_p, vp]),
+    "ea_destroy": (ctypes.c_int, [vp]),
+    "ea_last_error": (ctypes.c_char_p, [vp]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the compiled library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "libea_gb300.so is not built (%s); run __graft_entry__.build() or "
+            "python -m paper_1411_5512_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class EAError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = load().ea_status_string(status).decode()
+        super().__init__("%s%s" % (name, (": " + msg) if msg else ""))
+
+
+def check(status, ctx=None):
+    if status != EA_OK:
+        msg = ""
+        if ctx is not None:
+            msg = (load().ea_last_error(ctx) or b"").decode()
+        raise EAError(status, msg)
+    return status

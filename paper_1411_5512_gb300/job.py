@@ -1,0 +1,188 @@
+"""Pythonic wrapper of one EA ageing job (a context of the C ABI).
+
+Only argument marshalling happens here: every step of the simulation and of
+the observables runs in the CUDA library.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+_torch_alloc_refs = None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _torch_alloc_refs
+    import torch
+
+    lib = _lib.load()
+    if _torch_alloc_refs is not None:
+        return
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = _lib.ALLOC_FN(_alloc)
+    f = _lib.FREE_FN(_free)
+    _lib.check(lib.ea_set_allocator(a, f, None))
+    _torch_alloc_refs = (a, f)
+
+
+def use_cuda_allocator():
+    """Back to the library's own cudaMalloc / cudaFree."""
+    global _torch_alloc_refs
+    lib = _lib.load()
+    _lib.check(lib.ea_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None))
+    _torch_alloc_refs = None
+
+
+def geometry(L):
+    out = (ctypes.c_int * 6)()
+    _lib.check(_lib.load().ea_geometry(L, out))
+    return tuple(out)
+
+
+def thresholds(T, rule=0):
+    thr = np.zeros(7, dtype=np.uint64)
+    alw = np.zeros(7, dtype=np.uint8)
+    _lib.check(_lib.load().ea_thresholds(float(T), int(rule),
+                                         thr.ctypes.data_as(_lib.u64p),
+                                         alw.ctypes.data_as(_lib.u8p)))
+    return thr, alw
+
+
+def footprint(L, n_samples, n_tw, n_t):
+    b = ctypes.c_size_t()
+    _lib.check(_lib.load().ea_footprint(L, n_samples, n_tw, n_t, ctypes.byref(b)))
+    return b.value
+
+
+class EAJob:
+    """n_samples disorder samples x 2 replicas of an L^3 +-J EA lattice."""
+
+    def __init__(self, L, p_neg, seed, n_samples, rng_group=1, stream=None, _handle=None):
+        self.lib = _lib.load()
+        self.L = int(L)
+        self.n_samples = int(n_samples)
+        self._stream = stream
+        if _handle is not None:
+            self.h = _handle
+            return
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.ea_create_samples(ctypes.byref(h), self.L, float(p_neg),
+                                              int(seed), self.n_samples, int(rng_group),
+                                              _stream_handle(stream)))
+        self.h = h
+
+    # -- lifecycle ---------------------------------------------------------------
+    def set_schedule(self, t_w, t):
+        tw = np.ascontiguousarray(np.array(list(t_w), dtype=np.uint64))
+        tt = np.ascontiguousarray(np.array(list(t), dtype=np.uint64))
+        _lib.check(self.lib.ea_set_schedule(self.h, tw.ctypes.data_as(_lib.u64p), len(tw),
+                                            tt.ctypes.data_as(_lib.u64p), len(tt)), self.h)
+
+    def quench(self, T, rule=0):
+        _lib.check(self.lib.ea_quench(self.h, float(T), int(rule)), self.h)
+
+    def sweep(self, n):
+        _lib.check(self.lib.ea_sweep(self.h, int(n)), self.h)
+
+    @property
+    def time(self):
+        t = ctypes.c_uint64()
+        _lib.check(self.lib.ea_time(self.h, ctypes.byref(t)), self.h)
+        return t.value
+
+    def measure(self, t_w, t):
+        S, R = self.n_samples, self.L // 2 + 1
+        A = np.zeros((S, 2), dtype=np.int64)
+        Q = np.zeros(S, dtype=np.int64)
+        E = np.zeros((S, 2), dtype=np.int64)
+        G = np.zeros((S, 3, R), dtype=np.int64)
+        C4 = np.zeros(R, dtype=np.float64)
+        sem = np.zeros(R, dtype=np.float64)
+        obs = _lib.EaObs(A.ctypes.data_as(_lib.i64p), Q.ctypes.data_as(_lib.i64p),
+                         E.ctypes.data_as(_lib.i64p), G.ctypes.data_as(_lib.i64p),
+                         C4.ctypes.data_as(_lib.dblp), sem.ctypes.data_as(_lib.dblp),
+                         0.0, 0.0, 0.0, 0)
+        _lib.check(self.lib.ea_measure(self.h, int(t_w), int(t), ctypes.byref(obs)), self.h)
+        return {"A": A, "Q": Q, "E": E, "G": G, "C4": C4, "C4_sem": sem, "C": obs.C,
+                "q_mean": obs.q_mean, "xi1": obs.xi1, "r_cut": obs.r_cut}
+
+    def spins(self, s, a):
+        out = np.zeros((self.L,) * 3, dtype=np.int8)
+        _lib.check(self.lib.ea_get_spins(self.h, int(s), int(a), out.ctypes.data_as(_lib.i8p)),
+                   self.h)
+        return out
+
+    def all_spins(self, s):
+        return np.stack([self.spins(s, 0), self.spins(s, 1)])
+
+    def couplings(self, s):
+        out = np.zeros((3,) + (self.L,) * 3, dtype=np.int8)
+        _lib.check(self.lib.ea_get_couplings(self.h, int(s), out.ctypes.data_as(_lib.i8p)),
+                   self.h)
+        return out
+
+    def set_spins(self, s, a, spins):
+        arr = np.ascontiguousarray(spins, dtype=np.int8)
+        assert arr.shape == (self.L,) * 3
+        _lib.check(self.lib.ea_set_spins(self.h, int(s), int(a), arr.ctypes.data_as(_lib.i8p)),
+                   self.h)
+
+    def set_couplings(self, s, J):
+        arr = np.ascontiguousarray(J, dtype=np.int8)
+        assert arr.shape == (3,) + (self.L,) * 3
+        _lib.check(self.lib.ea_set_couplings(self.h, int(s), arr.ctypes.data_as(_lib.i8p)),
+                   self.h)
+
+    def set_time(self, t):
+        _lib.check(self.lib.ea_set_time(self.h, int(t)), self.h)
+
+    def thresholds(self):
+        thr = np.zeros(7, dtype=np.uint64)
+        alw = np.zeros(7, dtype=np.uint8)
+        _lib.check(self.lib.ea_get_thresholds(self.h, thr.ctypes.data_as(_lib.u64p),
+                                              alw.ctypes.data_as(_lib.u8p)), self.h)
+        return thr, alw
+
+    def checkpoint(self, path):
+        _lib.check(self.lib.ea_checkpoint(self.h, str(path).encode()), self.h)
+
+    @classmethod
+    def restore(cls, path, stream=None):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(lib.ea_restore(ctypes.byref(h), str(path).encode(), _stream_handle(stream)))
+        # read back shape from the file header: L and S are the 2nd and 3rd int32
+        with open(path, "rb") as f:
+            head = f.read(16)
+        L, S = np.frombuffer(head[8:16], dtype=np.int32)
+        return cls(int(L), 0.0, 0, int(S), stream=stream, _handle=h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h:
+            self.lib.ea_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,310 @@
+"""GPU parity: the CUDA library against the CPU oracle on the same seeded inputs.
+
+Spins, couplings and every integer observable must match bit for bit; the FP64
+derived quantities (C, q, C4 and its error, xi_1) within 1e-12 relative.  All
+calls go through the C ABI (ctypes binding).
+"""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as ora
+from paper_1411_5512_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def J():
+    from paper_1411_5512_gb300 import build, job
+    build.build()
+    return job
+
+
+def close(a, b, rel=REL):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    both_nan = np.isnan(a) & np.isnan(b)
+    ok = both_nan | (np.abs(a - b) <= rel * np.maximum(np.abs(b), 1e-300)) | (a == b)
+    return bool(np.all(ok))
+
+
+def gpu_run(jm, L, p_neg, seed, S, T, rule, t_w, t, n, G=1):
+    j = jm.EAJob(L, p_neg, seed, S, rng_group=G)
+    j.set_schedule(t_w, t)
+    j.quench(T, rule)
+    j.sweep(n)
+    return j
+
+
+def compare_job(j, out, L, S_idx, t_w, t, n):
+    """Integer sums of every scheduled pair and derived values against the oracle."""
+    N = L ** 3
+    for tw in t_w:
+        for lag in t:
+            if tw + lag > n:
+                continue
+            g = j.measure(tw, lag)
+            assert np.array_equal(g["A"][S_idx], out["A"][(tw, lag)]), (tw, lag)
+            assert np.array_equal(g["Q"][S_idx], out["Q"][tw + lag]), (tw, lag)
+            assert np.array_equal(g["E"][S_idx], out["E"][tw + lag]), (tw, lag)
+            assert np.array_equal(g["G"][S_idx], out["G"][tw]), tw
+            if len(S_idx) == j.n_samples:
+                d = ora.derived(out, L, tw, lag)
+                assert close(g["C"], d["C"]) and close(g["q_mean"], np.mean(d["q"]))
+                assert close(g["C4"], d["C4"]) and close(g["C4_sem"], d["C4_sem"])
+                assert g["r_cut"] == d["r_cut"]
+                assert close(g["xi1"], d["xi1"])
+    return True
+
+
+# ----------------------------------------------------------------------------------
+# initial state
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("L,p_neg", [(2, 0.5), (4, 0.5), (6, 0.3), (8, 0.5), (12, 0.0),
+                                     (16, 1.0), (24, 0.25), (32, 0.5), (48, 0.1)])
+def test_initial_state_bit_exact(J, L, p_neg):
+    S = 3
+    j = J.EAJob(L, p_neg, 1000 + L, S)
+    j.quench(0.7)
+    for s in range(S):
+        assert np.array_equal(j.couplings(s), ora.init_couplings(L, p_neg, 1000 + L, s))
+        assert np.array_equal(j.all_spins(s), ora.init_spins(L, 1000 + L, s))
+    j.close()
+
+
+# ----------------------------------------------------------------------------------
+# sweeps: final spins of every sample and replica
+# ----------------------------------------------------------------------------------
+SWEEP_CASES = [
+    # L, p_neg, T, rule, G, S, sweeps
+    (2, 0.5, 0.7, 0, 1, 2, 40),
+    (4, 0.5, 0.7, 0, 1, 2, 30),
+    (6, 0.5, 0.7, 0, 1, 2, 25),   # one site per word (L/2 odd)
+    (8, 0.4, 0.9, 0, 1, 2, 25),
+    (12, 0.5, 0.7, 0, 1, 2, 20),
+    (16, 0.5, 0.7, 0, 1, 3, 30),
+    (16, 0.5, 1.3, 1, 1, 2, 20),  # heat bath
+    (16, 0.5, 0.7, 0, 2, 4, 20),  # pairs of samples share random numbers
+    (16, 0.0, 0.0, 0, 1, 2, 10),  # T = 0 ferromagnet
+    (16, 0.5, float("inf"), 0, 1, 2, 3),
+    (16, 0.5, 0.0, 1, 1, 2, 8),   # heat bath at T = 0: dE = 0 flips with 1/2
+    (16, 1.0, 0.5, 0, 1, 2, 10),
+    (24, 0.3, 0.9, 0, 1, 2, 15),
+    (32, 0.5, 0.6, 0, 1, 2, 12),
+    (48, 0.2, 0.7, 0, 1, 1, 4),
+    (64, 0.5, 0.7, 0, 1, 1, 3),
+    (96, 0.5, 0.7, 0, 1, 1, 2),
+]
+
+
+@pytest.mark.parametrize("L,p_neg,T,rule,G,S,n", SWEEP_CASES)
+def test_sweeps_bit_exact(J, L, p_neg, T, rule, G, S, n):
+    seed = 7 + L
+    j = gpu_run(J, L, p_neg, seed, S, T, rule, [], [], n, G=G)
+    ref = ora.run_job(L, p_neg, seed, S, T, rule, [], [], n, keep_spins=True, rng_group=G)
+    for s in range(S):
+        assert np.array_equal(j.all_spins(s), ref["spins"][s]), s
+    j.close()
+
+
+# ----------------------------------------------------------------------------------
+# scheduled observables
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("L,p_neg,T,S", [(16, 0.5, 0.7, 4), (8, 0.2, 0.6, 3), (12, 0.5, 1.0, 2)])
+def test_observables_match_oracle(J, L, p_neg, T, S):
+    t_w, t, n = [0, 1, 2, 4, 8], [0, 1, 2, 4, 8, 16], 30
+    j = gpu_run(J, L, p_neg, 5, S, T, 0, t_w, t, n)
+    out = ora.run_job(L, p_neg, 5, S, T, 0, t_w, t, n)
+    compare_job(j, out, L, list(range(S)), t_w, t, n)
+    j.close()
+
+
+def test_tiny_workload_full_length(J):
+    w = workloads.TINY
+    j = gpu_run(J, w["L"], w["p_neg"], w["seed"], w["n_samples"], w["T"], 0, w["t_w"], w["t"],
+                w["sweeps"])
+    out = ora.run_job(w["L"], w["p_neg"], w["seed"], w["n_samples"], w["T"], 0, w["t_w"],
+                      w["t"], w["sweeps"], keep_spins=True)
+    compare_job(j, out, w["L"], [0], w["t_w"], w["t"], w["sweeps"])
+    assert np.array_equal(j.all_spins(0), out["spins"][0])
+    # C(t_w, t_w) = 1
+    assert j.measure(8, 0)["C"] == 1.0
+    j.close()
+
+
+def test_small_workload_sampled(J):
+    """Side 32, 64 samples: the GPU runs all samples, the oracle three of them."""
+    w = workloads.SMALL[0]
+    n = 16
+    t_w, t = [0, 2, 8], [0, 1, 4, 8]
+    j = gpu_run(J, w["L"], w["p_neg"], w["seed"], w["n_samples"], w["T"], 0, t_w, t, n)
+    pick = [0, 31, 63]
+    out = ora.run_job(w["L"], w["p_neg"], w["seed"], w["n_samples"], w["T"], 0, t_w, t, n,
+                      samples=pick, keep_spins=True)
+    compare_job(j, out, w["L"], pick, t_w, t, n)
+    for i, s in enumerate(pick):
+        assert np.array_equal(j.all_spins(s), out["spins"][i])
+    j.close()
+
+
+# ----------------------------------------------------------------------------------
+# late times and the high bits of the sweep counter, from oracle-made states
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("L,t0", [(16, (1 << 32) - 2), (24, (1 << 40) + 12345), (32, 999_983)])
+def test_late_time_from_oracle_state(J, L, t0):
+    seed, p_neg, T = 31, 0.5, 0.7
+    Jc = ora.init_couplings(L, p_neg, seed, 0)
+    S0 = ora.init_spins(L, seed, 0)
+    ora.sweeps(L, seed, 0, S0, Jc, T, 0, 0, 5)  # an oracle-made, non-trivial state
+    ref = S0.copy()
+    ora.sweeps(L, seed, 0, ref, Jc, T, 0, t0, 4)
+    j = J.EAJob(L, p_neg, seed, 1)
+    j.quench(T)
+    j.set_couplings(0, Jc)
+    j.set_spins(0, 0, S0[0])
+    j.set_spins(0, 1, S0[1])
+    j.set_time(t0)
+    j.sweep(4)
+    assert j.time == t0 + 4
+    assert np.array_equal(j.all_spins(0), ref)
+    j.close()
+
+
+# ----------------------------------------------------------------------------------
+# full size (side 128, the benchmark's launch configuration), sampled
+# ----------------------------------------------------------------------------------
+def test_paper_scale_sampled(J):
+    """All 80 samples of the five p_neg jobs run on the GPU; the oracle runs sample 0
+    of the first and last job for three sweeps."""
+    jobs = workloads.PAPER_SCALE
+    n = 3
+    handles = []
+    for w in jobs:
+        j = J.EAJob(w["L"], w["p_neg"], w["seed"], w["n_samples"])
+        j.quench(w["T"])
+        handles.append(j)
+    for j in handles:
+        j.sweep(n)
+    for k in (0, len(jobs) - 1):
+        w = jobs[k]
+        out = ora.run_job(w["L"], w["p_neg"], w["seed"], w["n_samples"], w["T"], 0, [], [], n,
+                          samples=[0], keep_spins=True)
+        assert np.array_equal(handles[k].all_spins(0), out["spins"][0])
+    for j in handles:
+        j.close()
+
+
+def test_gauge_covariance_full_size(J):
+    """Property at any size: J' = e_i e_j J, S'(0) = e S(0) gives S'(t) = e S(t)."""
+    L, seed = 128, 3
+    rng = np.random.default_rng(9)
+    eps = rng.choice(np.array([-1, 1], dtype=np.int8), size=(L, L, L))
+    Jc = ora.init_couplings(L, 0.5, seed, 0)
+    S0 = ora.init_spins(L, seed, 0)
+    Jg = np.empty_like(Jc)
+    for d, ax in ((0, 2), (1, 1), (2, 0)):
+        Jg[d] = Jc[d] * eps * np.roll(eps, -1, axis=ax)
+    a = J.EAJob(L, 0.5, seed, 1)
+    b = J.EAJob(L, 0.5, seed, 1)
+    for j, JJ, SS in ((a, Jc, S0), (b, Jg, (S0 * eps[None]).astype(np.int8))):
+        j.quench(0.7)
+        j.set_couplings(0, JJ)
+        j.set_spins(0, 0, SS[0])
+        j.set_spins(0, 1, SS[1])
+        j.sweep(50)
+    assert np.array_equal(b.all_spins(0), a.all_spins(0) * eps[None])
+    a.close()
+    b.close()
+
+
+def test_infinite_temperature_full_size(J):
+    L = 128
+    j = J.EAJob(L, 0.5, 4, 2)
+    j.quench(float("inf"))
+    s0 = [j.all_spins(s) for s in range(2)]
+    j.sweep(3)
+    for s in range(2):
+        assert np.array_equal(j.all_spins(s), -s0[s])
+    j.close()
+
+
+# ----------------------------------------------------------------------------------
+# state handling and errors
+# ----------------------------------------------------------------------------------
+def test_checkpoint_restore_continues_bit_exact(J, tmp_path):
+    L, S = 16, 2
+    t_w, t = [0, 4, 8], [0, 2, 8]
+    a = gpu_run(J, L, 0.5, 12, S, 0.7, 0, t_w, t, 10)
+    path = str(tmp_path / "job.ckpt")
+    a.checkpoint(path)
+    a.sweep(9)
+    b = J.EAJob.restore(path)
+    assert b.time == 10
+    b.sweep(9)
+    for s in range(S):
+        assert np.array_equal(a.all_spins(s), b.all_spins(s))
+    for tw in t_w:
+        for lag in t:
+            ma, mb = a.measure(tw, lag), b.measure(tw, lag)
+            for k in ("A", "Q", "E", "G"):
+                assert np.array_equal(ma[k], mb[k])
+    a.close()
+    b.close()
+
+
+def test_thresholds_in_use_match_oracle(J):
+    j = J.EAJob(8, 0.5, 1, 1)
+    j.quench(0.55, 1)
+    thr, alw = j.thresholds()
+    t2, a2 = ora.thresholds(0.55, 1)
+    assert np.array_equal(thr, t2) and np.array_equal(alw, a2)
+    j.close()
+
+
+def test_error_statuses(J):
+    from paper_1411_5512_gb300 import _lib
+    j = J.EAJob(8, 0.5, 1, 2)
+    with pytest.raises(_lib.EAError) as e:
+        j.sweep(1)
+    assert e.value.status == _lib.EA_ERR_STATE
+    j.set_schedule([0, 2], [0, 1])
+    j.quench(0.7)
+    with pytest.raises(_lib.EAError) as e:
+        j.set_schedule([0], [0])
+    assert e.value.status == _lib.EA_ERR_STATE
+    with pytest.raises(_lib.EAError) as e:
+        j.measure(2, 1)  # not reached yet
+    assert e.value.status == _lib.EA_ERR_NO_SNAPSHOT
+    j.sweep(3)
+    j.measure(2, 1)
+    with pytest.raises(_lib.EAError) as e:
+        j.measure(1, 1)  # 1 is not a waiting time
+    assert e.value.status == _lib.EA_ERR_NO_SNAPSHOT
+    with pytest.raises(_lib.EAError) as e:
+        j.spins(2, 0)
+    assert e.value.status == _lib.EA_ERR_INVALID_ARG
+    bad = np.zeros((8, 8, 8), dtype=np.int8)
+    with pytest.raises(_lib.EAError):
+        j.set_spins(0, 0, bad)
+    j.close()
+
+
+def test_torch_allocator_route(J):
+    import torch
+    J.use_torch_allocator()
+    try:
+        before = torch.cuda.memory_allocated()
+        j = gpu_run(J, 16, 0.5, 2, 2, 0.7, 0, [0, 1], [0, 1], 3)
+        assert torch.cuda.memory_allocated() > before
+        ref = ora.run_job(16, 0.5, 2, 2, 0.7, 0, [0, 1], [0, 1], 3, keep_spins=True)
+        assert np.array_equal(j.all_spins(1), ref["spins"][1])
+        j.close()
+        assert torch.cuda.memory_allocated() == before
+    finally:
+        J.use_cuda_allocator()
