@@ -156,8 +156,38 @@ def run_reference(args, world, rank):
 # ----------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------
+# integer ops per word update of the Metropolis sweep:
+# 6 LOP3 bond bits + 8 LOP3 count + 4 accept/flip/store + 5 class masks
+# + 3 class tests x (popc, table load, compare, branch)
+OPS_FIXED_PER_WORD = 35
+OPS_PER_PHILOX = 60        # 10 rounds x (2 mul.lo + 2 mul.hi + 2 three-input XOR)
+INT_LANES_PER_SM = 128     # int32-capable lanes per SM (4 SMSP x 32)
+N_SM = 152
+
+
+def timed_steps(stream, n_steps, step_fn, flush):
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
+    for k in range(n_steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            step_fn()
+            ends[k].record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    i = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[i]
+
+
 def run_ours(args, world, rank, local):
-    import numpy as np
     import torch
 
     from paper_1411_5512_gb300 import job, workloads
@@ -171,79 +201,96 @@ def run_ours(args, world, rank, local):
     specs = workloads.PAPER_SCALE
     L = specs[0]["L"]
     N = L ** 3
-    sweeps_per_step = args.sweeps_per_step
-    total_sweeps = (args.warmup + args.steps) * sweeps_per_step
+    sps = args.sweeps_per_step
+    total_sweeps = (2 * args.warmup + 2 * args.steps + 64) * sps
     t_w = workloads.pow2_times(total_sweeps)
     t_lag = workloads.pow2_times(total_sweeps)
 
-    def make_jobs():
-        jobs = []
-        for w in specs:
-            j = job.EAJob(w["L"], w["p_neg"], w["seed"] + 1000 * rank, w["n_samples"],
-                          stream=stream)
-            j.set_schedule(t_w, t_lag)
-            j.quench(w["T"])
-            jobs.append(j)
-        return jobs
-
-    jobs = make_jobs()
+    jobs = []
+    for w in specs:
+        j = job.EAJob(w["L"], w["p_neg"], w["seed"] + 1000 * rank, w["n_samples"], stream=stream)
+        j.set_schedule(t_w, t_lag)
+        j.quench(w["T"])
+        jobs.append(j)
     samples = sum(w["n_samples"] for w in specs)
-    flips_per_step = sweeps_per_step * samples * 2 * N
+    flips_per_step = sps * samples * 2 * N
     # L2 flush buffer (larger than the 126 MB L2), written between steps
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    def step():
+    def plain_step():
         for j in jobs:
-            j.sweep(sweeps_per_step)
+            j.sweep(sps)
+
+    batch = job.EABatch(stream=stream)
+    for j in jobs:
+        batch.add(j)
+    batch_cfg = batch.autotune(trial_sweeps=8)
+
+    def batched_step():
+        batch.sweep(sps)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step()
+            batched_step()
     stream.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
     wall0 = time.perf_counter()
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-            starts[k].record(stream)
-            step()
-            ends[k].record(stream)
-    stream.synchronize()
+    step_ms = timed_steps(stream, args.steps, batched_step, flush)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if world > 1:
         torch.distributed.barrier()
     sampler.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_ms = sum(step_ms)
     if world > 1:
         tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_ms = float(tt.item())
     value = world * flips_per_step * args.steps / (t_ms * 1e6)
-    launches = args.steps * sweeps_per_step * 2 * len(specs)
-    kernel_ms = t_ms / launches  # per half-step launch, incl. the rare observable kernels
-    flips_per_launch = samples // len(specs) * N  # one half-step of one job: N per sample
+    launches_per_step = 2 * sps  # one launch per half-step covers all 80 samples
+    launches = args.steps * launches_per_step
+    kernel_ms = t_ms / launches  # incl. the rare observable and time-advance kernels
+
+    # plain: the same work as separate per-job launch sequences (the paper's two
+    # launches per sweep, one job at a time)
+    batch.close()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plain_step()
+    plain_ms = timed_steps(stream, args.steps, plain_step, flush)
+    plain_value = flips_per_step * args.steps / (sum(plain_ms) * 1e6)
+
+    # algorithmic integer work of the update, counted on the live state
+    batch = job.EABatch(stream=stream)
+    for j in jobs:
+        batch.add(j)
+    prof = batch.profile(sweeps=4)
+    batch.close()
+    words = max(1, prof["words"])
+    ops_per_word = OPS_FIXED_PER_WORD + OPS_PER_PHILOX * prof["philox_calls"] / words
+    # word updates and flips are both counted over the same sweeps (32 sites per word)
+    ops_per_flip = ops_per_word * words / prof["flips"]
 
     pk, pk_kind = peaks()
-    # memory roofline of the half-step form: per flip read 1 word of the updated
-    # area, 1 of the neighbour area, 3 coupling bits per 2 flips... counted per
-    # site-update: spins read 2 bits + write 1 bit, couplings 3 bits = 6 bits
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    peak_tops = N_SM * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    flips_per_launch = samples * N  # one half-step updates every site of one replica
+    achieved_tops = flips_per_launch * ops_per_flip / (kernel_ms * 1e-3) / 1e12
     bytes_per_flip = 6.0 / 8.0
     achieved_gbs = flips_per_launch * bytes_per_flip / (kernel_ms * 1e6)
-    roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved_gbs / pk["hbm_gbs"], "traffic": None,
-            "peak_kind": pk_kind, "kernel": "halfstep_kernel<0>",
-            "kernel_us_per_launch": kernel_ms * 1e3}
+    roof = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+            "frac": achieved_tops / peak_tops, "traffic": None,
+            "peak_basis": "152 SMs x 128 int32 lanes x %.0f MHz (max SM clock)" % sm_mhz,
+            "kernel": "sweep_kernel<0,false>", "kernel_us_per_launch": kernel_ms * 1e3,
+            "ops_per_flip": ops_per_flip, "philox_calls_per_word": prof["philox_calls"] / words,
+            "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": pk["hbm_gbs"],
+                    "frac": achieved_gbs / pk["hbm_gbs"], "bytes_per_flip": bytes_per_flip,
+                    "peak_kind": pk_kind}}
 
-    # end to end through the public API: job lifecycle per step on host buffers
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, job, workloads, stream, rank, world)
@@ -261,12 +308,18 @@ def run_ours(args, world, rank, local):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "L128_p0.5-0.1_S16x5_T0.7", "L": L,
                        "jobs": [w["p_neg"] for w in specs], "samples": samples, "replicas": 2,
-                       "sweeps_per_step": sweeps_per_step, "rule": "metropolis", "rng_group": 1,
-                       "path": "plain (per-job half-step launches)",
+                       "sweeps_per_step": sps, "rule": "metropolis", "rng_group": 1,
+                       "path": "batched (one launch per half-step for all 5 jobs)",
+                       "batch_config": {"cols_per_thread": batch_cfg[0],
+                                        "graph_sweeps": batch_cfg[1]},
                        "l2": "flushed between steps (256 MiB write); the 105 MB state is "
                              "L2-sized, so sweeps inside a step see it cache-warm"},
-            "roofline": roof, "clocks": clocks, "gpu_launches": launches,
-            "wall_s": wall}
+            "step_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99)},
+            "plain": {"value": plain_value, "unit": UNIT,
+                      "path": "per-job launches, 2 per sweep per job",
+                      "step_ms": {"p50": pct(plain_ms, 50), "p99": pct(plain_ms, 99)}},
+            "batched_over_plain": value / plain_value,
+            "roofline": roof, "clocks": clocks, "gpu_launches": launches, "wall_s": wall}
     if e2e is not None:
         line["e2e"] = e2e
     if cpu is not None:

@@ -98,6 +98,15 @@ int ea_geometry(int L, int out[6]);
  * caller-owned.  EA_ERR_INVALID_ARG for T < 0, NaN T or an unknown rule. */
 int ea_thresholds(double T, int rule, uint64_t thr[7], uint8_t always[7]);
 
+/* Geometric-gap table of the Metropolis update: C[g] = floor(2^64 (1 - (1 -
+ * p)^g)) for g = 0..32 (clamped to 2^64 - 1), computed as floor(ldexp(-expm1(g
+ * log1p(-p)), 64)).  Among the n sites of one word-site with the same dE > 0,
+ * each flipping independently with p = exp(-dE/T) (Eq. 9), a 64-bit uniform V
+ * gives no flip when V >= C[n], else a first flip at rank min{g : V < C[g+1]}
+ * in increasing lane order; the sites after it start a fresh gap with the next
+ * draw.  EA_ERR_INVALID_ARG unless 0 < p < 1.  Host-only. */
+int ea_geo_table(double p, uint64_t C[33]);
+
 /* Device bytes a context with this shape and schedule will hold (spins,
  * couplings, snapshots and results).  Host-only arithmetic. */
 int ea_footprint(int L, int n_samples, int n_tw, int n_t, size_t *bytes);
@@ -192,6 +201,137 @@ int ea_destroy(ea_ctx *ctx);
 
 /* Text of the last error on ctx (empty string if none).  Never NULL. */
 const char *ea_last_error(const ea_ctx *ctx);
+
+/* ---- batching: many jobs, one launch per half-step ------------------------
+ *
+ * A batch sweeps many quenched jobs together: every half-step of every
+ * member, whatever its L, p_neg, T, rule or sample count, is one kernel launch
+ * over a table of jobs (Sec. III: one launch per half-step keeps the global
+ * synchronisation of the checkerboard).  With graph_sweeps > 0 the launches of
+ * graph_sweeps sweeps are captured once into a CUDA graph and replayed.  Each
+ * member keeps its own time, schedule and random stream, so a job gives
+ * bit-identical results alone and in any batch.
+ *
+ * While a job is a member, its work (sweeps and measurements) is enqueued on
+ * the batch's stream; ea_measure and the other per-job calls stay valid.  The
+ * batch does not own its members: remove (or destroy the batch) before
+ * ea_destroy on a member. */
+typedef struct ea_batch ea_batch;
+
+/* New empty batch on cuda_stream (NULL = legacy stream; graphs then stay off).
+ * Errors: EA_ERR_OOM. */
+int ea_batch_create(ea_batch **out, void *cuda_stream);
+
+/* Add / remove a quenched job.  Errors: EA_ERR_INVALID_ARG (NULL, already a
+ * member / not a member), EA_ERR_STATE (job not quenched). */
+int ea_batch_add(ea_batch *b, ea_ctx *job);
+int ea_batch_remove(ea_batch *b, ea_ctx *job);
+
+/* Number of member jobs. */
+int ea_batch_size(const ea_batch *b, int *n_jobs);
+
+/* Launch shape used by ea_batch_sweep: word columns per thread of the sweep
+ * kernel (1, 2 or 4; 0 = per-job default) and sweeps per captured graph
+ * (0 = direct launches).  Neither changes any result. */
+int ea_batch_configure(ea_batch *b, int cols_per_thread, int graph_sweeps);
+int ea_batch_get_config(const ea_batch *b, int *cols_per_thread, int *graph_sweeps);
+
+/* Try the launch shapes on the members' current state for trial_sweeps sweeps
+ * each, keep the fastest and put the state back as it was (time, spins): the
+ * tuning leaves every result unchanged.  Synchronises the batch stream. */
+int ea_batch_autotune(ea_batch *b, int trial_sweeps);
+
+/* Work counts of the update, for the integer-op roofline: runs `sweeps`
+ * sweeps of every member with a counting variant of the sweep kernel and
+ * then puts the members' state back (time, spins), so no result changes.
+ * out = {word updates, Philox4x32-10 calls, calls that took the general
+ * (non-zero threshold) plane path, attempted spin flips}.  The call count is
+ * per word with per-word early exit, i.e. what the algorithm needs, not what a
+ * SIMT warp issues.  Synchronises the batch stream. */
+int ea_batch_profile(ea_batch *b, int sweeps, uint64_t out[4]);
+
+/* Run n sweeps of every member, firing each member's scheduled measurements
+ * at its own times.  Asynchronous on the batch stream.
+ * Errors: EA_ERR_INVALID_ARG (a member's time would pass 2^48), EA_ERR_CUDA. */
+int ea_batch_sweep(ea_batch *b, uint64_t n);
+
+/* Destroy the batch; members return to their own streams.  NULL is accepted. */
+int ea_batch_destroy(ea_batch *b);
+const char *ea_batch_last_error(const ea_batch *b);
+
+/* ---- serving: continuous batching of ageing jobs ---------------------------
+ *
+ * A server keeps a queue of submitted jobs and a batch of running ones.  Each
+ * ea_server_step (1) admits queued jobs in submission order that fit, by
+ * device footprint (ea_footprint) within the byte budget and by the slot
+ * limit, skipping ones that do not fit yet; (2) advances every running job by
+ * up to chunk_sweeps sweeps in the batch's launches, each job stopping at its
+ * own sweep count; (3) retires finished jobs.  Jobs that arrive while others
+ * are on the GPU join at the next step, so their work overlaps on the device.
+ * A job's results depend only on its own spec (seed, sample index, time),
+ * never on what else ran with it.  Finished jobs keep their device memory,
+ * and their budget share, until ea_server_release. */
+typedef struct ea_server ea_server;
+
+typedef struct ea_job_spec {
+    int L;
+    double p_neg;
+    uint64_t seed;
+    int n_samples;
+    int rng_group_G;
+    double T;
+    int rule;
+    uint64_t sweeps;           /* the job is done after this many sweeps */
+    const uint64_t *t_w;       /* measurement schedule, as ea_set_schedule */
+    int n_tw;
+    const uint64_t *t;
+    int n_t;
+} ea_job_spec;
+
+#define EA_JOB_QUEUED 0
+#define EA_JOB_RUNNING 1
+#define EA_JOB_DONE 2
+
+typedef struct ea_server_stats {
+    int queued, running, done;
+    size_t bytes_in_use;       /* footprint of running and unreleased jobs */
+    uint64_t flips;            /* attempted spin flips run so far */
+    uint64_t steps;
+} ea_server_stats;
+
+/* New server.  budget_bytes: device bytes its jobs may hold; max_running:
+ * slots; chunk_sweeps: sweeps per step (> 0).  Errors: EA_ERR_INVALID_ARG,
+ * EA_ERR_OOM. */
+int ea_server_create(ea_server **out, size_t budget_bytes, int max_running, uint64_t chunk_sweeps,
+                     void *cuda_stream);
+
+/* Queue a job (copies the spec and its schedule arrays).  *job_id receives
+ * its id.  Errors: EA_ERR_INVALID_ARG (bad spec, or a footprint above the
+ * whole budget). */
+int ea_server_submit(ea_server *srv, const ea_job_spec *spec, int64_t *job_id);
+
+/* One round: admit, run one chunk, retire.  *n_finished (may be NULL)
+ * receives the number of jobs retired in this round.  Asynchronous apart from
+ * the admission of new jobs; a retired job's results are read with
+ * ea_measure on its context (ea_server_job), which synchronises. */
+int ea_server_step(ea_server *srv, int *n_finished);
+
+/* State (EA_JOB_*) and time of a job. */
+int ea_server_job_state(const ea_server *srv, int64_t job_id, int *state, uint64_t *time);
+
+/* The job's context (owned by the server; valid until ea_server_release),
+ * for ea_measure / ea_get_spins.  EA_ERR_STATE while the job is queued. */
+int ea_server_job(ea_server *srv, int64_t job_id, ea_ctx **job);
+
+/* Free a finished job's device memory and its budget share.
+ * EA_ERR_STATE unless the job is done. */
+int ea_server_release(ea_server *srv, int64_t job_id);
+
+int ea_server_get_stats(const ea_server *srv, ea_server_stats *out);
+
+/* Destroy the server and every job it still holds.  NULL is accepted. */
+int ea_server_destroy(ea_server *srv);
+const char *ea_server_last_error(const ea_server *srv);
 
 #ifdef __cplusplus
 }

@@ -133,8 +133,8 @@ int ora_site_to_word(int L, int x, int y, int z, uint32_t *widx, int *lane)
 }
 
 /* ------------------------------------------------------------------------ */
-/* The 64-bit uniform number r(seed, s, a, site, t) used by the update of    */
-/* replica a of sample s at the given site during sweep t (t = 0, 1, ...).  */
+/* The 64-bit uniform number r(seed, s, a, site, t) used by the heat-bath    */
+/* update of replica a of sample s at the given site during sweep t.        */
 /*                                                                          */
 /* Bit (63 - k) of r, k = 0..63, is bit `lane` of plane k, where plane k is */
 /* output word (k mod 4) of Philox4x32-10 with key (lo32(seed), hi32(seed)) */
@@ -270,69 +270,212 @@ int ora_init_spins(int L, uint64_t seed, uint32_t s, int8_t *S)
 }
 
 /* ------------------------------------------------------------------------ */
-/* One sweep t of both replicas of one sample (Sec. III).                   */
-/* Half-step h = 0, 1: replica a updates every site of colour (x+y+z) mod 2 */
-/* equal to h XOR a.  Each update computes dE = 2 S_i sum_j J_ij S_j over    */
-/* the six neighbours (Eq. 9) and flips S_i when always[k] or r < thr[k],    */
-/* k = (dE + 12) / 4.  Sites of one colour do not neighbour each other, so  */
-/* this site-by-site loop equals the simultaneous update of a colour.       */
+/* Metropolis acceptance by geometric gaps.                                 */
+/*                                                                          */
+/* Among the sites of one word-site that share the energy change dE > 0     */
+/* (class u = (12 - dE) / 4 unsatisfied bonds, u = 0, 1, 2), each must flip  */
+/* independently with probability p_u = exp(-dE/T) (Eq. 9).  Taken in       */
+/* increasing lane order, they form a Bernoulli(p_u) sequence, and the      */
+/* number G of rejections before the first acceptance is geometric:         */
+/* P(G >= g) = (1 - p_u)^g.  One 64-bit uniform V decides the first         */
+/* acceptance among n remaining sites: none if V >= C_u[n], else the site   */
+/* of rank G = min{g : V < C_u[g+1]}, with                                  */
+/*   C_u[g] = floor(2^64 (1 - (1 - p_u)^g)),  computed as                   */
+/*   floor(ldexp(-expm1(g * log1p(-p_u)), 64)), clamped to 2^64 - 1.         */
+/* The sites after an acceptance start a fresh gap with the next draw.      */
+/*                                                                          */
+/* Draw d of class u (64 bits) of the word-site update.  Call 0 holds the   */
+/* draws a word-site usually needs: output 0 = draw 0 and output 1 = draw 1 */
+/* of class 2 (dE = 4), output 2 = draw 0 of class 1, output 3 = draw 0 of   */
+/* class 0.  Draw d >= f_u (f = 1, 1, 2 for u = 0, 1, 2) is output e mod 4   */
+/* of call 1 + u + 3 (e div 4), e = d - f_u.  The high word of a draw is that */
+/* output; its low word is the same output of call (that call + 64).  Calls  */
+/* use counter                                                               */
+/*   c0 = widx, c1 = lo32(t),                                               */
+/*   c2 = (3 << 30) | (bits 32..47 of t) << 12 | a << 11 | call,            */
+/*   c3 = s (sample index, or sample index / G).                            */
+/* ------------------------------------------------------------------------ */
+#define STREAM_METROPOLIS 3u
+
+int ora_geo_table(double p, uint64_t C[33])
+{
+    if (!(p > 0.0 && p < 1.0))
+        return ORA_BAD_ARG;
+    C[0] = 0;
+    for (int g = 1; g <= 32; g++) {
+        double q = -expm1((double)g * log1p(-p)); /* 1 - (1 - p)^g */
+        double v = ldexp(q, 64);
+        C[g] = (v >= 18446744073709551615.0) ? UINT64_MAX : (uint64_t)floor(v);
+    }
+    return ORA_OK;
+}
+
+static uint64_t metro_draw(uint32_t widx, uint64_t seed, uint32_t s, int a, uint64_t t, int u, int d)
+{
+    static const int first_out[3][2] = {{3, -1}, {2, -1}, {0, 1}}; /* [u][d] in call 0 */
+    static const int n_first[3] = {1, 1, 2};
+    int call, out;
+    if (d < n_first[u]) {
+        call = 0;
+        out = first_out[u][d];
+    } else {
+        int e = d - n_first[u];
+        call = 1 + u + 3 * (e / 4);
+        out = e % 4;
+    }
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t c2 = (STREAM_METROPOLIS << 30) | ((uint32_t)((t >> 32) & 0xFFFFu) << 12) |
+                  ((uint32_t)a << 11);
+    uint32_t hi_ctr[4] = {widx, (uint32_t)t, c2 | (uint32_t)call, s};
+    uint32_t lo_ctr[4] = {widx, (uint32_t)t, c2 | (uint32_t)(call + 64), s};
+    uint32_t hi[4], lo[4];
+    ora_philox4x32_10(hi_ctr, key, hi);
+    ora_philox4x32_10(lo_ctr, key, lo);
+    return ((uint64_t)hi[out] << 32) | (uint64_t)lo[out];
+}
+
+/* Flip decisions of the lanes lane_list[0..n) (increasing lane order) of one
+   class: sets flip[lane] = 1 for the accepted ones. */
+static void metro_class(const uint64_t C[33], const int *lane_list, int n, uint32_t widx,
+                        uint64_t seed, uint32_t s, int a, uint64_t t, int u, uint8_t *flip)
+{
+    int start = 0, d = 0;
+    while (n - start > 0) {
+        uint64_t V = metro_draw(widx, seed, s, a, t, u, d);
+        d++;
+        int rem = n - start;
+        if (V >= C[rem])
+            break; /* no acceptance among the remaining sites */
+        int G = 0;
+        while (!(V < C[G + 1]))
+            G++;
+        flip[lane_list[start + G]] = 1;
+        start += G + 1;
+    }
+}
+
+/* Local field dE = 2 S_i sum_j J_ij S_j at site (x, y, z) of replica Sa. */
+static int delta_E(int L, const int8_t *Sa, const int8_t *J, int x, int y, int z)
+{
+    int64_t N = (int64_t)L * L * L;
+    int64_t i = x + (int64_t)L * (y + (int64_t)L * z);
+    int xp = (x + 1) % L, xm = (x + L - 1) % L;
+    int yp = (y + 1) % L, ym = (y + L - 1) % L;
+    int zp = (z + 1) % L, zm = (z + L - 1) % L;
+    int64_t ixp = xp + (int64_t)L * (y + (int64_t)L * z);
+    int64_t ixm = xm + (int64_t)L * (y + (int64_t)L * z);
+    int64_t iyp = x + (int64_t)L * (yp + (int64_t)L * z);
+    int64_t iym = x + (int64_t)L * (ym + (int64_t)L * z);
+    int64_t izp = x + (int64_t)L * (y + (int64_t)L * zp);
+    int64_t izm = x + (int64_t)L * (y + (int64_t)L * zm);
+    /* forward bonds are stored at i, backward bonds at the neighbour i - e_d */
+    int h_loc = J[0 * N + i] * Sa[ixp] + J[0 * N + ixm] * Sa[ixm] + J[1 * N + i] * Sa[iyp] +
+                J[1 * N + iym] * Sa[iym] + J[2 * N + i] * Sa[izp] + J[2 * N + izm] * Sa[izm];
+    return 2 * Sa[i] * h_loc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Half-step h of sweep t of both replicas of one sample (Sec. III): replica */
+/* a updates every site of colour (x+y+z) mod 2 equal to h XOR a.  Sites of  */
+/* one colour do not neighbour each other, so the sites of a colour are     */
+/* decided from the same configuration and may be taken in any order; here  */
+/* they are taken word-site by word-site.  Each site gets dE = 2 S_i sum_j  */
+/* J_ij S_j (Eq. 9), k = (dE + 12) / 4, and flips when always[k];           */
+/*   rule 0 (Metropolis): the other sites of a word-site are decided per    */
+/*     class by geometric gaps (above); a class with threshold 0 never flips */
+/*   rule 1 (heat bath): a site flips when its uniform r < thr[k]           */
+/*     (ora_random64).                                                      */
 /* dE_acc[a] accumulates the energy change of accepted flips of replica a.  */
 /* s keys the random numbers (counter word 3): the sample index, or the     */
 /* sample index divided by G when G samples share their random numbers.     */
 /* ------------------------------------------------------------------------ */
-int ora_sweep(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, const uint64_t thr[7],
-              const uint8_t always[7], uint64_t t, int64_t dE_acc[2])
+int ora_half_step(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, double T, int rule,
+                  uint64_t t, int h, int64_t dE_acc[2])
 {
-    if (L < 2 || L > 1024 || (L & 1) || t >= ((uint64_t)1 << 48))
+    uint64_t thr[7];
+    uint8_t always[7];
+    if (L < 2 || L > 1024 || (L & 1) || t >= ((uint64_t)1 << 48) || (h != 0 && h != 1) ||
+        ora_thresholds(T, rule, thr, always) != ORA_OK)
         return ORA_BAD_ARG;
-    int64_t N = (int64_t)L * L * L;
-    for (int h = 0; h < 2; h++) {
-        for (int a = 0; a < 2; a++) {
-            int8_t *Sa = S + a * N;
-            for (int z = 0; z < L; z++)
-                for (int y = 0; y < L; y++)
-                    for (int x = 0; x < L; x++) {
-                        if (((x + y + z) & 1) != (h ^ a))
-                            continue;
-                        int64_t i = x + (int64_t)L * (y + (int64_t)L * z);
-                        int xp = (x + 1) % L, xm = (x + L - 1) % L;
-                        int yp = (y + 1) % L, ym = (y + L - 1) % L;
-                        int zp = (z + 1) % L, zm = (z + L - 1) % L;
-                        int64_t ixp = xp + (int64_t)L * (y + (int64_t)L * z);
-                        int64_t ixm = xm + (int64_t)L * (y + (int64_t)L * z);
-                        int64_t iyp = x + (int64_t)L * (yp + (int64_t)L * z);
-                        int64_t iym = x + (int64_t)L * (ym + (int64_t)L * z);
-                        int64_t izp = x + (int64_t)L * (y + (int64_t)L * zp);
-                        int64_t izm = x + (int64_t)L * (y + (int64_t)L * zm);
-                        /* local field sum_j J_ij S_j: forward bonds are stored at i,
-                           backward bonds at the neighbour i - e_d */
-                        int h_loc = J[0 * N + i] * Sa[ixp] + J[0 * N + ixm] * Sa[ixm] +
-                                    J[1 * N + i] * Sa[iyp] + J[1 * N + iym] * Sa[iym] +
-                                    J[2 * N + i] * Sa[izp] + J[2 * N + izm] * Sa[izm];
-                        int dE = 2 * Sa[i] * h_loc;
-                        int k = (dE + 12) / 4;
-                        int flip;
-                        if (always[k]) {
-                            flip = 1;
-                        } else {
-                            flip = random_below(L, seed, s, a, x, y, z, t, thr[k]);
-                        }
-                        if (flip) {
-                            Sa[i] = (int8_t)-Sa[i];
-                            dE_acc[a] += dE;
-                        }
-                    }
+    uint64_t C[3][33];
+    int live[3] = {0, 0, 0};
+    if (rule == 0) {
+        for (int u = 0; u < 3; u++) {
+            int k = 6 - u;
+            if (!always[k] && thr[k] > 0) {
+                live[u] = 1;
+                ora_geo_table(exp(-(double)(12 - 4 * u) / T), C[u]);
+            }
         }
+    }
+    int g[6];
+    ora_geometry(L, g);
+    int kx = g[0], ky = g[1], kz = g[2], Lx = g[3], Ly = g[4], Lz = g[5];
+    int lanes = kx * ky * kz;
+    int64_t N = (int64_t)L * L * L;
+    for (int a = 0; a < 2; a++) {
+        int8_t *Sa = S + a * N;
+        for (int zw = 0; zw < Lz; zw++)
+            for (int yw = 0; yw < Ly; yw++)
+                for (int xw = 0; xw < Lx; xw++) {
+                    if (((xw + yw + zw) & 1) != (h ^ a))
+                        continue;
+                    uint32_t widx = (uint32_t)(xw + Lx * (yw + Ly * zw));
+                    int dE[32], sx[32], sy[32], sz[32];
+                    uint8_t flip[32];
+                    for (int b = 0; b < lanes; b++) {
+                        sx[b] = (b % kx) * Lx + xw;
+                        sy[b] = ((b / kx) % ky) * Ly + yw;
+                        sz[b] = (b / (kx * ky)) * Lz + zw;
+                        dE[b] = delta_E(L, Sa, J, sx[b], sy[b], sz[b]);
+                        flip[b] = always[(dE[b] + 12) / 4];
+                    }
+                    if (rule == 0) {
+                        for (int u = 0; u < 3; u++) {
+                            if (!live[u])
+                                continue;
+                            int list[32], n = 0;
+                            for (int b = 0; b < lanes; b++)
+                                if (dE[b] == 12 - 4 * u)
+                                    list[n++] = b;
+                            if (n > 0)
+                                metro_class(C[u], list, n, widx, seed, s, a, t, u, flip);
+                        }
+                    } else {
+                        for (int b = 0; b < lanes; b++)
+                            if (!flip[b])
+                                flip[b] = (uint8_t)random_below(L, seed, s, a, sx[b], sy[b],
+                                                                sz[b], t, thr[(dE[b] + 12) / 4]);
+                    }
+                    for (int b = 0; b < lanes; b++)
+                        if (flip[b]) {
+                            int64_t i = sx[b] + (int64_t)L * (sy[b] + (int64_t)L * sz[b]);
+                            Sa[i] = (int8_t)-Sa[i];
+                            dE_acc[a] += dE[b];
+                        }
+                }
+    }
+    return ORA_OK;
+}
+
+/* One sweep t: half-step 0, then half-step 1. */
+int ora_sweep(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, double T, int rule,
+              uint64_t t, int64_t dE_acc[2])
+{
+    for (int h = 0; h < 2; h++) {
+        int rc = ora_half_step(L, seed, s, S, J, T, rule, t, h, dE_acc);
+        if (rc != ORA_OK)
+            return rc;
     }
     return ORA_OK;
 }
 
 /* Several sweeps t0, t0+1, ..., t0+n-1 in a row. */
-int ora_sweeps(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, const uint64_t thr[7],
-               const uint8_t always[7], uint64_t t0, uint64_t n, int64_t dE_acc[2])
+int ora_sweeps(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, double T, int rule,
+               uint64_t t0, uint64_t n, int64_t dE_acc[2])
 {
     for (uint64_t k = 0; k < n; k++) {
-        int rc = ora_sweep(L, seed, s, S, J, thr, always, t0 + k, dE_acc);
+        int rc = ora_sweep(L, seed, s, S, J, T, rule, t0 + k, dE_acc);
         if (rc != ORA_OK)
             return rc;
     }

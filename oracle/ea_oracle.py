@@ -65,9 +65,16 @@ def lib():
         L.ora_init_couplings.restype = ctypes.c_int
         L.ora_init_spins.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, i8p]
         L.ora_init_spins.restype = ctypes.c_int
-        L.ora_sweeps.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, i8p, i8p, u64p,
-                                 u8p, ctypes.c_uint64, ctypes.c_uint64, i64p]
+        L.ora_sweeps.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, i8p, i8p,
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                 i64p]
         L.ora_sweeps.restype = ctypes.c_int
+        L.ora_half_step.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, i8p, i8p,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                    i64p]
+        L.ora_half_step.restype = ctypes.c_int
+        L.ora_geo_table.argtypes = [ctypes.c_double, u64p]
+        L.ora_geo_table.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -141,12 +148,27 @@ def sweeps(L, seed, s, S, J, T, rule, t0, n):
     """
     assert S.dtype == np.int8 and S.shape == (2, L, L, L) and S.flags.c_contiguous
     J = np.ascontiguousarray(J, dtype=np.int8)
-    thr, alw = thresholds(T, rule)
     dE = np.zeros(2, dtype=np.int64)
     _check(lib().ora_sweeps(L, seed, s, _ptr(S, ctypes.c_int8), _ptr(J, ctypes.c_int8),
-                            _ptr(thr, ctypes.c_uint64), _ptr(alw, ctypes.c_uint8), t0, n,
-                            _ptr(dE, ctypes.c_int64)), "sweeps")
+                            float(T), int(rule), t0, n, _ptr(dE, ctypes.c_int64)), "sweeps")
     return dE
+
+
+def half_step(L, seed, s, S, J, T, rule, t, h):
+    """Half-step h of sweep t in place on S; return the accepted dE per replica."""
+    assert S.dtype == np.int8 and S.shape == (2, L, L, L) and S.flags.c_contiguous
+    J = np.ascontiguousarray(J, dtype=np.int8)
+    dE = np.zeros(2, dtype=np.int64)
+    _check(lib().ora_half_step(L, seed, s, _ptr(S, ctypes.c_int8), _ptr(J, ctypes.c_int8),
+                               float(T), int(rule), t, h, _ptr(dE, ctypes.c_int64)), "half_step")
+    return dE
+
+
+def geo_table(p):
+    """C[g] = floor(2^64 (1 - (1 - p)^g)), g = 0..32: the geometric-gap table."""
+    C = np.zeros(33, dtype=np.uint64)
+    _check(lib().ora_geo_table(float(p), _ptr(C, ctypes.c_uint64)), "geo_table(p=%r)" % p)
+    return C
 
 
 # ----------------------------------------------------------------------------------

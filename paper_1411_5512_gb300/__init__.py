@@ -9,7 +9,7 @@ from . import _lib  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("EAJob", "geometry", "thresholds", "footprint", "use_torch_allocator",
+    if name in ("EAJob", "EABatch", "EAServer", "geometry", "thresholds", "footprint", "use_torch_allocator",
                 "use_cuda_allocator"):
         from . import job
         return getattr(job, name)

@@ -39,6 +39,23 @@ class EaObs(ctypes.Structure):
                 ("xi1", ctypes.c_double), ("r_cut", ctypes.c_int)]
 
 
+class EaJobSpec(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("p_neg", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("n_samples", ctypes.c_int), ("rng_group_G", ctypes.c_int),
+                ("T", ctypes.c_double), ("rule", ctypes.c_int), ("sweeps", ctypes.c_uint64),
+                ("t_w", u64p), ("n_tw", ctypes.c_int), ("t", u64p), ("n_t", ctypes.c_int)]
+
+
+class EaServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("running", ctypes.c_int), ("done", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t), ("flips", ctypes.c_uint64),
+                ("steps", ctypes.c_uint64)]
+
+
+EA_JOB_QUEUED = 0
+EA_JOB_RUNNING = 1
+EA_JOB_DONE = 2
+
 ALLOC_FN = ctypes.CFUNCTYPE(vp, ctypes.c_size_t, vp, vp)
 FREE_FN = ctypes.CFUNCTYPE(None, vp, ctypes.c_size_t, vp, vp)
 
@@ -47,6 +64,7 @@ SIGNATURES = {
     "ea_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ea_geometry": (ctypes.c_int, [ctypes.c_int, intp]),
     "ea_thresholds": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, u64p, u8p]),
+    "ea_geo_table": (ctypes.c_int, [ctypes.c_double, u64p]),
     "ea_footprint": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_size_t)]),
     "ea_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, vp]),
@@ -68,6 +86,28 @@ SIGNATURES = {
     "ea_restore": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_char_p, vp]),
     "ea_destroy": (ctypes.c_int, [vp]),
     "ea_last_error": (ctypes.c_char_p, [vp]),
+    "ea_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), vp]),
+    "ea_batch_add": (ctypes.c_int, [vp, vp]),
+    "ea_batch_remove": (ctypes.c_int, [vp, vp]),
+    "ea_batch_size": (ctypes.c_int, [vp, intp]),
+    "ea_batch_configure": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+    "ea_batch_get_config": (ctypes.c_int, [vp, intp, intp]),
+    "ea_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ea_batch_profile": (ctypes.c_int, [vp, ctypes.c_int, u64p]),
+    "ea_batch_sweep": (ctypes.c_int, [vp, ctypes.c_uint64]),
+    "ea_batch_destroy": (ctypes.c_int, [vp]),
+    "ea_batch_last_error": (ctypes.c_char_p, [vp]),
+    "ea_server_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_size_t, ctypes.c_int,
+                                        ctypes.c_uint64, vp]),
+    "ea_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(EaJobSpec),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "ea_server_step": (ctypes.c_int, [vp, intp]),
+    "ea_server_job_state": (ctypes.c_int, [vp, ctypes.c_int64, intp, u64p]),
+    "ea_server_job": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.POINTER(vp)]),
+    "ea_server_release": (ctypes.c_int, [vp, ctypes.c_int64]),
+    "ea_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(EaServerStats)]),
+    "ea_server_destroy": (ctypes.c_int, [vp]),
+    "ea_server_last_error": (ctypes.c_char_p, [vp]),
 }
 
 _lib = None
@@ -98,10 +138,14 @@ class EAError(RuntimeError):
         super().__init__("%s%s" % (name, (": " + msg) if msg else ""))
 
 
-def check(status, ctx=None):
+def check(status, ctx=None, batch=None, server=None):
     if status != EA_OK:
         msg = ""
         if ctx is not None:
             msg = (load().ea_last_error(ctx) or b"").decode()
+        if batch is not None:
+            msg = (load().ea_batch_last_error(batch) or b"").decode()
+        if server is not None:
+            msg = (load().ea_server_last_error(server) or b"").decode()
         raise EAError(status, msg)
     return status

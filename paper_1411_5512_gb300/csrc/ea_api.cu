@@ -8,6 +8,8 @@
 // half-step gives the global synchronisation), measurements are enqueued
 // in between, and nothing synchronises until results are read back.
 #include <algorithm>
+#include <deque>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -104,6 +106,20 @@ int make_geo(int L, Geo *g)
     return 0;
 }
 
+int geo_table(double p, uint64_t C[33])
+{
+    if (!(p > 0.0 && p < 1.0))
+        return -1;
+    C[0] = 0;
+    for (int g = 1; g <= 32; ++g) {
+        // 1 - (1 - p)^g, accurate for tiny p
+        const double q = -std::expm1((double)g * std::log1p(-p));
+        const double v = std::ldexp(q, 64);
+        C[g] = v >= 18446744073709551615.0 ? UINT64_MAX : (uint64_t)std::floor(v);
+    }
+    return 0;
+}
+
 }  // namespace ea
 
 // ---------------------------------------------------------------------------
@@ -141,11 +157,21 @@ static int compute_thresholds(double T, int rule, uint64_t thr[7], uint8_t alway
     return EA_OK;
 }
 
-static ea::Thr make_thr(int rule, const uint64_t thr_k[7], const uint8_t always_k[7])
+static ea::Thr make_thr(int rule, double T, const uint64_t thr_k[7], const uint8_t always_k[7])
 {
     ea::Thr t;
     std::memset(&t, 0, sizeof(t));
     t.rule = rule;
+    if (rule == EA_RULE_METROPOLIS) {
+        // classes u = 0, 1, 2 (dE = 12, 8, 4) decided by geometric gaps
+        for (int u = 0; u < 3; ++u) {
+            const int k = 6 - u;
+            if (!always_k[k] && thr_k[k] > 0) {
+                t.geo_live |= 1u << u;
+                ea::geo_table(std::exp(-(double)(12 - 4 * u) / T), t.geoC[u]);
+            }
+        }
+    }
     int n_always = 0;
     for (int u = 0; u < 7; ++u) {
         // u unsatisfied bonds <=> dE = 12 - 4u <=> k = 6 - u
@@ -175,6 +201,8 @@ static ea::Thr make_thr(int rule, const uint64_t thr_k[7], const uint8_t always_
     for (int u = 0; u < nu; ++u)
         if (!((t.always_u >> u) & 1u) && t.thr_u[u] != 0)
             any_nonzero = true;
+    if (rule == EA_RULE_METROPOLIS)
+        any_nonzero = t.geo_live != 0;
     t.zero_calls = zero_calls;
     // with every needed threshold 0 no lane can accept: skip the random numbers
     t.none_random = !any_nonzero;
@@ -196,6 +224,10 @@ struct ea_ctx {
     uint32_t *spins = nullptr;
     uint32_t *J = nullptr;
     uint32_t *snaps = nullptr;
+    ea::JobDev jd;                 // host copy of the job's sweep-table entry
+    ea::JobDev *jd_dev = nullptr;  // one-entry table for the plain path
+    int *bb_dev = nullptr;         // its block_begin = {0, blocks}
+    int blocks = 0;
     unsigned long long *res = nullptr;
     size_t spins_bytes = 0, J_bytes = 0, snaps_bytes = 0, res_bytes = 0;
 
@@ -209,6 +241,9 @@ struct ea_ctx {
     uint8_t always_k[7] = {0};
     ea::Thr thr;
     uint64_t t = 0;
+
+    ea_batch *batch = nullptr;          // batch this job belongs to, if any
+    cudaStream_t own_stream = nullptr;  // the job's stream outside a batch
 
     std::string err;
 
@@ -306,18 +341,35 @@ int build_schedule(ea_ctx *c, std::vector<uint64_t> tw, std::vector<uint64_t> tt
     return EA_OK;
 }
 
-ea::SweepLaunch sweep_args(const ea_ctx *c)
+int upload_job(ea_ctx *c)
 {
-    ea::SweepLaunch p;
-    p.spins = c->spins;
-    p.J = c->J;
-    p.geo = c->geo;
-    p.thr = c->thr;
-    p.key0 = (uint32_t)c->seed;
-    p.key1 = (uint32_t)(c->seed >> 32);
-    p.n_samples = c->S;
-    p.rng_group = c->G;
-    return p;
+    c->jd.t = c->t;
+    c->jd.t_end = c->t;
+    EA_CUDA(c, cudaMemcpyAsync(c->jd_dev, &c->jd, sizeof(ea::JobDev), cudaMemcpyHostToDevice,
+                               c->stream));
+    return EA_OK;
+}
+
+// The plain path's table entry runs sweeps t .. t_end-1 of the next chunk.
+int upload_time(ea_ctx *c, uint64_t t_end)
+{
+    static_assert(offsetof(ea::JobDev, t_end) == offsetof(ea::JobDev, t) + sizeof(uint64_t),
+                  "t and t_end are uploaded together");
+    c->jd.t = c->t;
+    c->jd.t_end = t_end;
+    EA_CUDA(c, cudaMemcpyAsync(&c->jd_dev->t, &c->jd.t, 2 * sizeof(uint64_t),
+                               cudaMemcpyHostToDevice, c->stream));
+    return EA_OK;
+}
+
+int launch_plain(ea_ctx *c, uint64_t n)
+{
+    const bool heat = c->rule == EA_RULE_HEATBATH;
+    EA_CUDA(c, ea::launch_sweep_table(heat ? nullptr : c->jd_dev, heat ? nullptr : c->bb_dev,
+                                      heat ? 0 : 1, heat ? 0 : c->blocks,
+                                      heat ? c->jd_dev : nullptr, heat ? c->bb_dev : nullptr,
+                                      heat ? 1 : 0, heat ? c->blocks : 0, n, c->stream));
+    return EA_OK;
 }
 
 // Measurements due at the current time c->t (if it is a scheduled time).
@@ -349,6 +401,18 @@ int fire_measurements(ea_ctx *c)
 }
 
 int check_ctx(const ea_ctx *c) { return c ? EA_OK : EA_ERR_INVALID_ARG; }
+
+}  // namespace
+
+// Columns per thread of the sweep kernel: enough blocks to fill the GPU a
+// few times over for one job, fewer per-thread set-ups for large lattices.
+static int default_cols_per_thread(const Geo &g)
+{
+    const int cols = g.n[0] * g.n[1];
+    return cols >= 8192 ? 2 : 1;
+}
+
+namespace {
 
 }  // namespace
 
@@ -389,6 +453,13 @@ int ea_thresholds(double T, int rule, uint64_t thr[7], uint8_t always[7])
     if (!thr || !always)
         return EA_ERR_INVALID_ARG;
     return compute_thresholds(T, rule, thr, always);
+}
+
+int ea_geo_table(double p, uint64_t C[33])
+{
+    if (!C)
+        return EA_ERR_INVALID_ARG;
+    return ea::geo_table(p, C) == 0 ? EA_OK : EA_ERR_INVALID_ARG;
 }
 
 int ea_footprint(int L, int n_samples, int n_tw, int n_t, size_t *bytes)
@@ -433,14 +504,34 @@ int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_sa
     c->S = n_samples;
     c->G = rng_group_G;
     c->stream = (cudaStream_t)cuda_stream;
+    c->own_stream = c->stream;
     c->geo = g;
     c->spins_bytes = c->area_words() * sizeof(uint32_t);
     c->J_bytes = (size_t)n_samples * 3 * g.words * sizeof(uint32_t);
     c->spins = (uint32_t *)dev_alloc(c->spins_bytes, c->stream);
     c->J = (uint32_t *)dev_alloc(c->J_bytes, c->stream);
-    if (!c->spins || !c->J) {
+    c->jd_dev = (ea::JobDev *)dev_alloc(sizeof(ea::JobDev), c->stream);
+    c->bb_dev = (int *)dev_alloc(2 * sizeof(int), c->stream);
+    if (!c->spins || !c->J || !c->jd_dev || !c->bb_dev) {
         ea_destroy(c);
         return EA_ERR_OOM;
+    }
+    std::memset(&c->jd, 0, sizeof(c->jd));
+    c->jd.spins = c->spins;
+    c->jd.J = c->J;
+    c->jd.geo = g;
+    c->jd.n_samples = n_samples;
+    c->jd.rng_group = (uint32_t)rng_group_G;
+    ea::fill_job_keys(&c->jd, seed);
+    ea::fill_job_layout(&c->jd, default_cols_per_thread(g));
+    c->blocks = n_samples * c->jd.blocks_per_sample;
+    {
+        const int bb[2] = {0, c->blocks};
+        if (cudaMemcpy(c->bb_dev, bb, sizeof(bb), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            ea_destroy(c);
+            return EA_ERR_CUDA;
+        }
     }
     cudaError_t e = ea::launch_init_couplings(c->J, g, n_samples, p_neg, seed, c->stream);
     if (e == cudaSuccess)
@@ -484,12 +575,16 @@ int ea_quench(ea_ctx *c, double T, int rule)
     c->rule = rule;
     std::memcpy(c->thr_k, thr, sizeof(thr));
     std::memcpy(c->always_k, alw, sizeof(alw));
-    c->thr = make_thr(rule, thr, alw);
+    c->thr = make_thr(rule, T, thr, alw);
+    ea::fill_job_thresholds(&c->jd, c->thr);
     EA_CUDA(c, ea::launch_init_spins(c->spins, c->geo, c->S, c->seed, c->stream));
     if (c->res)
         EA_CUDA(c, cudaMemsetAsync(c->res, 0, c->res_bytes, c->stream));
     c->t = 0;
     c->quenched = true;
+    int rc = upload_job(c);
+    if (rc != EA_OK)
+        return rc;
     return fire_measurements(c);
 }
 
@@ -502,11 +597,15 @@ int ea_sweep(ea_ctx *c, uint64_t n)
     if (n > ea::kMaxTime || c->t + n > ea::kMaxTime)
         return fail(c, EA_ERR_INVALID_ARG, "time would pass 2^48");
     const uint64_t target = c->t + n;
-    const ea::SweepLaunch p = sweep_args(c);
     while (c->t < target) {
         auto it = std::upper_bound(c->meas.begin(), c->meas.end(), c->t);
         const uint64_t stop = (it == c->meas.end()) ? target : std::min(target, *it);
-        EA_CUDA(c, ea::launch_sweeps(p, c->t, stop - c->t, c->stream));
+        int rc0 = upload_time(c, stop);
+        if (rc0 != EA_OK)
+            return rc0;
+        rc0 = launch_plain(c, stop - c->t);
+        if (rc0 != EA_OK)
+            return rc0;
         c->t = stop;
         const int rc = fire_measurements(c);
         if (rc != EA_OK)
@@ -881,7 +980,8 @@ int ea_restore(ea_ctx **out, const char *path, void *cuda_stream)
             c->rule = h.rule;
             std::memcpy(c->thr_k, thr, sizeof(thr));
             std::memcpy(c->always_k, alw, sizeof(alw));
-            c->thr = make_thr(h.rule, thr, alw);
+            c->thr = make_thr(h.rule, h.T, thr, alw);
+            ea::fill_job_thresholds(&c->jd, c->thr);
         }
     }
     if (rc == EA_OK) {
@@ -899,6 +999,11 @@ int ea_restore(ea_ctx **out, const char *path, void *cuda_stream)
     }
     c->t = h.t;
     c->quenched = true;
+    rc = upload_job(c);
+    if (rc != EA_OK) {
+        ea_destroy(c);
+        return rc;
+    }
     *out = c;
     return EA_OK;
 }
@@ -907,11 +1012,15 @@ int ea_destroy(ea_ctx *c)
 {
     if (!c)
         return EA_OK;
-    if (c->spins || c->J || c->snaps || c->res)
+    if (c->batch)
+        ea_batch_remove(c->batch, c);
+    if (c->spins || c->J || c->snaps || c->res || c->jd_dev)
         cudaStreamSynchronize(c->stream);
     release_schedule(c);
     dev_free(c->spins, c->spins_bytes, c->stream);
     dev_free(c->J, c->J_bytes, c->stream);
+    dev_free(c->jd_dev, sizeof(ea::JobDev), c->stream);
+    dev_free(c->bb_dev, 2 * sizeof(int), c->stream);
     delete c;
     return EA_OK;
 }
@@ -922,5 +1031,727 @@ const char *ea_last_error(const ea_ctx *c)
         return "";
     return c->err.c_str();
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct ea_batch {
+    cudaStream_t stream = nullptr;
+    std::vector<ea_ctx *> members;
+    int cpt = 0;           // word columns per thread (0 = per-job default)
+    int graph_sweeps = 0;  // sweeps per captured graph (0 = direct launches)
+    // device job tables, one per update rule
+    ea::JobDev *tab_dev[2] = {nullptr, nullptr};
+    int *bb_dev[2] = {nullptr, nullptr};
+    size_t cap[2] = {0, 0};
+    int n_jobs[2] = {0, 0};
+    int blocks[2] = {0, 0};
+    std::vector<ea::JobDev> tab_host[2];
+    std::vector<int> bb_host[2];
+    // captured graph of graph_sweeps sweeps over the current tables
+    cudaGraphExec_t graph = nullptr;
+    int graph_K = 0;
+    const void *graph_key[2] = {nullptr, nullptr};
+    int graph_blocks[2] = {0, 0};
+    std::string err;
+};
+
+namespace {
+
+int bfail(ea_batch *b, int code, const std::string &msg)
+{
+    if (b)
+        b->err = msg;
+    return code;
+}
+
+#define EA_BCUDA(b, call)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            cudaGetLastError();                                                        \
+            return bfail((b), EA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                              \
+    } while (0)
+
+void drop_graph(ea_batch *b)
+{
+    if (b->graph)
+        cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_K = 0;
+}
+
+// Rebuild both rule tables from the members' current state and upload them;
+// member i may run up to min(n, limits[i]) more sweeps (limits may be NULL).
+int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits = nullptr)
+{
+    size_t mi = 0;
+    for (int r = 0; r < 2; ++r) {
+        b->tab_host[r].clear();
+        b->bb_host[r].assign(1, 0);
+    }
+    for (ea_ctx *m : b->members) {
+        const int r = m->rule == EA_RULE_HEATBATH ? 1 : 0;
+        ea::JobDev jd = m->jd;
+        jd.t = m->t;
+        uint64_t allow = std::min<uint64_t>(n, ea::kMaxTime - m->t);
+        if (limits)
+            allow = std::min<uint64_t>(allow, (*limits)[mi]);
+        ++mi;
+        jd.t_end = m->t + allow;
+        if (b->cpt > 0)
+            ea::fill_job_layout(&jd, b->cpt);
+        b->tab_host[r].push_back(jd);
+        b->bb_host[r].push_back(b->bb_host[r].back() + m->S * jd.blocks_per_sample);
+    }
+    for (int r = 0; r < 2; ++r) {
+        const size_t n = b->tab_host[r].size();
+        b->n_jobs[r] = (int)n;
+        b->blocks[r] = b->bb_host[r].back();
+        if (n == 0)
+            continue;
+        if (n > b->cap[r]) {
+            size_t cap = std::max<size_t>(n, 2 * b->cap[r]);
+            dev_free(b->tab_dev[r], b->cap[r] * sizeof(ea::JobDev), b->stream);
+            dev_free(b->bb_dev[r], (b->cap[r] + 1) * sizeof(int), b->stream);
+            b->tab_dev[r] = (ea::JobDev *)dev_alloc(cap * sizeof(ea::JobDev), b->stream);
+            b->bb_dev[r] = (int *)dev_alloc((cap + 1) * sizeof(int), b->stream);
+            b->cap[r] = cap;
+            if (!b->tab_dev[r] || !b->bb_dev[r])
+                return bfail(b, EA_ERR_OOM, "batch table allocation failed");
+        }
+        EA_BCUDA(b, cudaMemcpyAsync(b->tab_dev[r], b->tab_host[r].data(), n * sizeof(ea::JobDev),
+                                    cudaMemcpyHostToDevice, b->stream));
+        EA_BCUDA(b, cudaMemcpyAsync(b->bb_dev[r], b->bb_host[r].data(), (n + 1) * sizeof(int),
+                                    cudaMemcpyHostToDevice, b->stream));
+    }
+    return EA_OK;
+}
+
+int enqueue_direct(ea_batch *b, uint64_t n, unsigned long long *counters = nullptr)
+{
+    EA_BCUDA(b, ea::launch_sweep_table(b->tab_dev[0], b->bb_dev[0], b->n_jobs[0], b->blocks[0],
+                                       b->tab_dev[1], b->bb_dev[1], b->n_jobs[1], b->blocks[1], n,
+                                       b->stream, counters));
+    for (int r = 0; r < 2; ++r)
+        EA_BCUDA(b, ea::launch_advance_time(b->tab_dev[r], b->n_jobs[r], n, b->stream));
+    return EA_OK;
+}
+
+int ensure_graph(ea_batch *b)
+{
+    const int K = b->graph_sweeps;
+    if (b->graph && b->graph_K == K && b->graph_key[0] == b->tab_dev[0] &&
+        b->graph_key[1] == b->tab_dev[1] && b->graph_blocks[0] == b->blocks[0] &&
+        b->graph_blocks[1] == b->blocks[1])
+        return EA_OK;
+    drop_graph(b);
+    cudaGraph_t g = nullptr;
+    EA_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_direct(b, (uint64_t)K);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc != EA_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        if (g)
+            cudaGraphDestroy(g);
+        return bfail(b, EA_ERR_CUDA, "graph capture failed");
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph = nullptr;
+        return bfail(b, EA_ERR_CUDA, "graph instantiation failed");
+    }
+    b->graph_K = K;
+    b->graph_key[0] = b->tab_dev[0];
+    b->graph_key[1] = b->tab_dev[1];
+    b->graph_blocks[0] = b->blocks[0];
+    b->graph_blocks[1] = b->blocks[1];
+    return EA_OK;
+}
+
+// n sweeps of every member on the tables as uploaded (no measurements).
+int run_sweeps(ea_batch *b, uint64_t n)
+{
+    if (n == 0 || (b->blocks[0] == 0 && b->blocks[1] == 0))
+        return EA_OK;
+    uint64_t rem = n;
+    if (b->graph_sweeps > 0 && b->stream != nullptr && n >= (uint64_t)b->graph_sweeps) {
+        int rc = ensure_graph(b);
+        if (rc != EA_OK)
+            return rc;
+        const uint64_t full = n / (uint64_t)b->graph_sweeps;
+        for (uint64_t i = 0; i < full; ++i)
+            EA_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+        rem = n - full * (uint64_t)b->graph_sweeps;
+    }
+    if (rem)
+        return enqueue_direct(b, rem);
+    return EA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ea_batch_create(ea_batch **out, void *cuda_stream)
+{
+    if (!out)
+        return EA_ERR_INVALID_ARG;
+    ea_batch *b = new (std::nothrow) ea_batch();
+    if (!b)
+        return EA_ERR_OOM;
+    b->stream = (cudaStream_t)cuda_stream;
+    *out = b;
+    return EA_OK;
+}
+
+int ea_batch_add(ea_batch *b, ea_ctx *job)
+{
+    if (!b || !job || job->batch)
+        return b ? bfail(b, EA_ERR_INVALID_ARG, "job is NULL or already in a batch")
+                 : EA_ERR_INVALID_ARG;
+    if (!job->quenched)
+        return bfail(b, EA_ERR_STATE, "job not quenched");
+    // work already queued on the job's own stream must come first
+    if (job->stream != b->stream)
+        EA_BCUDA(b, cudaStreamSynchronize(job->stream));
+    job->batch = b;
+    job->stream = b->stream;
+    b->members.push_back(job);
+    return EA_OK;
+}
+
+int ea_batch_remove(ea_batch *b, ea_ctx *job)
+{
+    if (!b || !job)
+        return EA_ERR_INVALID_ARG;
+    auto it = std::find(b->members.begin(), b->members.end(), job);
+    if (it == b->members.end())
+        return bfail(b, EA_ERR_INVALID_ARG, "job is not a member");
+    if (job->own_stream != b->stream)
+        EA_BCUDA(b, cudaStreamSynchronize(b->stream));
+    b->members.erase(it);
+    job->batch = nullptr;
+    job->stream = job->own_stream;
+    return EA_OK;
+}
+
+int ea_batch_size(const ea_batch *b, int *n_jobs)
+{
+    if (!b || !n_jobs)
+        return EA_ERR_INVALID_ARG;
+    *n_jobs = (int)b->members.size();
+    return EA_OK;
+}
+
+int ea_batch_configure(ea_batch *b, int cols_per_thread, int graph_sweeps)
+{
+    if (!b || !(cols_per_thread == 0 || cols_per_thread == 1 || cols_per_thread == 2 ||
+                cols_per_thread == 4) ||
+        graph_sweeps < 0 || graph_sweeps > 4096)
+        return EA_ERR_INVALID_ARG;
+    b->cpt = cols_per_thread;
+    b->graph_sweeps = graph_sweeps;
+    return EA_OK;
+}
+
+int ea_batch_get_config(const ea_batch *b, int *cols_per_thread, int *graph_sweeps)
+{
+    if (!b || !cols_per_thread || !graph_sweeps)
+        return EA_ERR_INVALID_ARG;
+    *cols_per_thread = b->cpt;
+    *graph_sweeps = b->graph_sweeps;
+    return EA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// n sweeps of every member, member i stopping after limits[i] of them (all n
+// when limits is NULL); scheduled measurements fire at each member's times.
+int batch_sweep_impl(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits)
+{
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        ea_ctx *m = b->members[i];
+        const uint64_t want = limits ? std::min<uint64_t>(n, (*limits)[i]) : n;
+        if (want > ea::kMaxTime || m->t + want > ea::kMaxTime)
+            return bfail(b, EA_ERR_INVALID_ARG, "a member's time would pass 2^48");
+    }
+    if (b->members.empty() || n == 0)
+        return EA_OK;
+    std::vector<uint64_t> end(b->members.size());
+    for (size_t i = 0; i < b->members.size(); ++i)
+        end[i] = b->members[i]->t + (limits ? std::min<uint64_t>(n, (*limits)[i]) : n);
+    int rc = upload_tables(b, n, limits);
+    if (rc != EA_OK)
+        return rc;
+    uint64_t remaining = n;
+    while (remaining > 0) {
+        uint64_t step = remaining;
+        bool any = false;
+        for (size_t i = 0; i < b->members.size(); ++i) {
+            ea_ctx *m = b->members[i];
+            if (m->t >= end[i])
+                continue;
+            any = true;
+            step = std::min<uint64_t>(step, end[i] - m->t);
+            auto it = std::upper_bound(m->meas.begin(), m->meas.end(), m->t);
+            if (it != m->meas.end())
+                step = std::min<uint64_t>(step, *it - m->t);
+        }
+        if (!any)
+            break;
+        rc = run_sweeps(b, step);
+        if (rc != EA_OK)
+            return rc;
+        for (size_t i = 0; i < b->members.size(); ++i) {
+            ea_ctx *m = b->members[i];
+            const uint64_t adv = std::min<uint64_t>(step, end[i] - m->t);
+            if (adv == 0)
+                continue;
+            m->t += adv;
+            rc = fire_measurements(m);
+            if (rc != EA_OK)
+                return bfail(b, rc, "measurement failed: " + m->err);
+        }
+        remaining -= step;
+    }
+    return EA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ea_batch_sweep(ea_batch *b, uint64_t n)
+{
+    if (!b)
+        return EA_ERR_INVALID_ARG;
+    return batch_sweep_impl(b, n, nullptr);
+}
+
+namespace {
+
+// Copies of the members' spins and times, so that trial sweeps (tuning,
+// profiling) leave the jobs exactly as they were.
+struct SavedState {
+    std::vector<uint32_t *> spins;
+    std::vector<uint64_t> times;
+};
+
+int save_state(ea_batch *b, SavedState &st)
+{
+    st.spins.assign(b->members.size(), nullptr);
+    st.times.assign(b->members.size(), 0);
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        ea_ctx *m = b->members[i];
+        st.times[i] = m->t;
+        st.spins[i] = (uint32_t *)dev_alloc(m->spins_bytes, b->stream);
+        if (!st.spins[i])
+            return bfail(b, EA_ERR_OOM, "scratch allocation failed");
+        EA_BCUDA(b, cudaMemcpyAsync(st.spins[i], m->spins, m->spins_bytes,
+                                    cudaMemcpyDeviceToDevice, b->stream));
+    }
+    return EA_OK;
+}
+
+int restore_state(ea_batch *b, SavedState &st, int rc)
+{
+    for (size_t i = 0; i < st.spins.size(); ++i) {
+        ea_ctx *m = b->members[i];
+        m->t = st.times[i];
+        if (st.spins[i] &&
+            cudaMemcpyAsync(m->spins, st.spins[i], m->spins_bytes, cudaMemcpyDeviceToDevice,
+                            b->stream) != cudaSuccess &&
+            rc == EA_OK)
+            rc = bfail(b, EA_ERR_CUDA, "state restore failed");
+    }
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess && rc == EA_OK)
+        rc = bfail(b, EA_ERR_CUDA, "stream synchronisation failed");
+    for (size_t i = 0; i < st.spins.size(); ++i)
+        dev_free(st.spins[i], b->members[i]->spins_bytes, b->stream);
+    st.spins.clear();
+    return rc;
+}
+
+}  // namespace
+
+int ea_batch_profile(ea_batch *b, int sweeps, uint64_t out[4])
+{
+    if (!b || !out || sweeps < 1)
+        return EA_ERR_INVALID_ARG;
+    std::memset(out, 0, 4 * sizeof(uint64_t));
+    if (b->members.empty())
+        return EA_OK;
+    SavedState st;
+    int rc = save_state(b, st);
+    unsigned long long *ctr = nullptr;
+    if (rc == EA_OK) {
+        ctr = (unsigned long long *)dev_alloc(4 * sizeof(unsigned long long), b->stream);
+        if (!ctr)
+            rc = bfail(b, EA_ERR_OOM, "counter allocation failed");
+        else if (cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), b->stream) != cudaSuccess)
+            rc = bfail(b, EA_ERR_CUDA, "counter reset failed");
+    }
+    if (rc == EA_OK)
+        rc = upload_tables(b, (uint64_t)sweeps);
+    if (rc == EA_OK)
+        rc = enqueue_direct(b, (uint64_t)sweeps, ctr);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (rc == EA_OK &&
+        (cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+         cudaStreamSynchronize(b->stream) != cudaSuccess))
+        rc = bfail(b, EA_ERR_CUDA, "counter read-back failed");
+    rc = restore_state(b, st, rc);
+    dev_free(ctr, 4 * sizeof(unsigned long long), b->stream);
+    if (rc != EA_OK)
+        return rc;
+    uint64_t flips = 0;
+    for (ea_ctx *m : b->members)
+        flips += (uint64_t)sweeps * 2ull * (uint64_t)m->S * (uint64_t)m->L * m->L * m->L;
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = h[2];
+    out[3] = flips;
+    return EA_OK;
+}
+
+int ea_batch_autotune(ea_batch *b, int trial_sweeps)
+{
+    if (!b || trial_sweeps < 1)
+        return EA_ERR_INVALID_ARG;
+    if (b->members.empty())
+        return EA_OK;
+    // tuning runs on the members' state and puts it back
+    SavedState st;
+    int rc = save_state(b, st);
+    const int cpts[3] = {1, 2, 4};
+    const int graphs[2] = {0, 16};
+    float best = 1e30f;
+    int best_cpt = b->cpt, best_graph = b->graph_sweeps;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == EA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = bfail(b, EA_ERR_CUDA, "event creation failed");
+    for (int ci = 0; ci < 3 && rc == EA_OK; ++ci) {
+        for (int gi = 0; gi < 2 && rc == EA_OK; ++gi) {
+            if (graphs[gi] > 0 && b->stream == nullptr)
+                continue;
+            b->cpt = cpts[ci];
+            b->graph_sweeps = graphs[gi] > 0 ? std::min(graphs[gi], trial_sweeps) : 0;
+            rc = upload_tables(b, ea::kMaxTime);
+            if (rc == EA_OK)
+                rc = run_sweeps(b, (uint64_t)b->graph_sweeps > 0 ? b->graph_sweeps : 1);  // warm
+            if (rc != EA_OK)
+                break;
+            cudaEventRecord(e0, b->stream);
+            rc = run_sweeps(b, (uint64_t)trial_sweeps);
+            cudaEventRecord(e1, b->stream);
+            if (rc != EA_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = rc != EA_OK ? rc : bfail(b, EA_ERR_CUDA, "autotune timing failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_cpt = b->cpt;
+                best_graph = b->graph_sweeps;
+            }
+        }
+    }
+    rc = restore_state(b, st, rc);
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    b->cpt = best_cpt;
+    b->graph_sweeps = best_graph;
+    drop_graph(b);
+    return rc;
+}
+
+int ea_batch_destroy(ea_batch *b)
+{
+    if (!b)
+        return EA_OK;
+    cudaStreamSynchronize(b->stream);
+    for (ea_ctx *m : b->members) {
+        m->batch = nullptr;
+        m->stream = m->own_stream;
+    }
+    drop_graph(b);
+    for (int r = 0; r < 2; ++r) {
+        dev_free(b->tab_dev[r], b->cap[r] * sizeof(ea::JobDev), b->stream);
+        dev_free(b->bb_dev[r], (b->cap[r] + 1) * sizeof(int), b->stream);
+    }
+    delete b;
+    return EA_OK;
+}
+
+const char *ea_batch_last_error(const ea_batch *b) { return b ? b->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// serving
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ServerJob {
+    int64_t id = 0;
+    ea_job_spec spec;
+    std::vector<uint64_t> tw, tt;
+    int state = EA_JOB_QUEUED;
+    ea_ctx *ctx = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ea_server {
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    int max_running = 0;
+    uint64_t chunk = 0;
+    ea_batch *batch = nullptr;
+    std::deque<ServerJob *> queue;
+    std::vector<ServerJob *> running;
+    std::map<int64_t, ServerJob *> jobs;
+    size_t in_use = 0;
+    int64_t next_id = 1;
+    uint64_t flips = 0;
+    uint64_t steps = 0;
+    std::string err;
+};
+
+namespace {
+
+int sfail(ea_server *srv, int code, const std::string &msg)
+{
+    if (srv)
+        srv->err = msg;
+    return code;
+}
+
+// Create, schedule and quench the job's context on the server's stream.
+int start_job(ea_server *srv, ServerJob *j)
+{
+    const ea_job_spec &sp = j->spec;
+    ea_ctx *c = nullptr;
+    int rc = ea_create_samples(&c, sp.L, sp.p_neg, sp.seed, sp.n_samples, sp.rng_group_G,
+                               (void *)srv->stream);
+    if (rc != EA_OK)
+        return rc;
+    rc = ea_set_schedule(c, j->tw.data(), (int)j->tw.size(), j->tt.data(), (int)j->tt.size());
+    if (rc == EA_OK)
+        rc = ea_quench(c, sp.T, sp.rule);
+    if (rc == EA_OK)
+        rc = ea_batch_add(srv->batch, c);
+    if (rc != EA_OK) {
+        ea_destroy(c);
+        return rc;
+    }
+    j->ctx = c;
+    return EA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ea_server_create(ea_server **out, size_t budget_bytes, int max_running, uint64_t chunk_sweeps,
+                     void *cuda_stream)
+{
+    if (!out || max_running < 1 || chunk_sweeps == 0 || chunk_sweeps > ea::kMaxTime)
+        return EA_ERR_INVALID_ARG;
+    *out = nullptr;
+    ea_server *srv = new (std::nothrow) ea_server();
+    if (!srv)
+        return EA_ERR_OOM;
+    srv->stream = (cudaStream_t)cuda_stream;
+    srv->budget = budget_bytes;
+    srv->max_running = max_running;
+    srv->chunk = chunk_sweeps;
+    const int rc = ea_batch_create(&srv->batch, cuda_stream);
+    if (rc != EA_OK) {
+        delete srv;
+        return rc;
+    }
+    *out = srv;
+    return EA_OK;
+}
+
+int ea_server_submit(ea_server *srv, const ea_job_spec *spec, int64_t *job_id)
+{
+    if (!srv || !spec || !job_id)
+        return EA_ERR_INVALID_ARG;
+    Geo g;
+    if (ea::make_geo(spec->L, &g) != 0 || !(spec->p_neg >= 0.0 && spec->p_neg <= 1.0) ||
+        spec->n_samples < 1 || spec->n_samples > ea::kMaxSamples || spec->rng_group_G < 1 ||
+        !(spec->T >= 0.0) || (spec->rule != EA_RULE_METROPOLIS && spec->rule != EA_RULE_HEATBATH) ||
+        spec->sweeps >= ea::kMaxTime || spec->n_tw < 0 || spec->n_t < 0 ||
+        spec->n_tw > ea::kMaxSchedule || spec->n_t > ea::kMaxSchedule ||
+        (spec->n_tw > 0 && !spec->t_w) || (spec->n_t > 0 && !spec->t))
+        return sfail(srv, EA_ERR_INVALID_ARG, "invalid job spec");
+    ServerJob *j = new (std::nothrow) ServerJob();
+    if (!j)
+        return EA_ERR_OOM;
+    j->spec = *spec;
+    j->tw.assign(spec->t_w, spec->t_w + spec->n_tw);
+    j->tt.assign(spec->t, spec->t + spec->n_t);
+    j->spec.t_w = nullptr;
+    j->spec.t = nullptr;
+    if (ea_footprint(spec->L, spec->n_samples, spec->n_tw, spec->n_t, &j->bytes) != EA_OK ||
+        j->bytes > srv->budget) {
+        delete j;
+        return sfail(srv, EA_ERR_INVALID_ARG, "job footprint exceeds the server budget");
+    }
+    j->id = srv->next_id++;
+    srv->jobs[j->id] = j;
+    srv->queue.push_back(j);
+    *job_id = j->id;
+    return EA_OK;
+}
+
+int ea_server_step(ea_server *srv, int *n_finished)
+{
+    if (!srv)
+        return EA_ERR_INVALID_ARG;
+    if (n_finished)
+        *n_finished = 0;
+    // 1. admission, first fit in submission order
+    for (auto it = srv->queue.begin(); it != srv->queue.end();) {
+        ServerJob *j = *it;
+        if ((int)srv->running.size() >= srv->max_running)
+            break;
+        if (srv->in_use + j->bytes > srv->budget) {
+            ++it;
+            continue;
+        }
+        const int rc = start_job(srv, j);
+        if (rc == EA_ERR_OOM) {
+            ++it;  // the device is fuller than the budget says: try again later
+            continue;
+        }
+        if (rc != EA_OK)
+            return sfail(srv, rc, "job admission failed");
+        srv->in_use += j->bytes;
+        j->state = EA_JOB_RUNNING;
+        srv->running.push_back(j);
+        it = srv->queue.erase(it);
+    }
+    if (srv->running.empty())
+        return EA_OK;
+    // 2. one chunk for every running job, each stopping at its own sweep count
+    std::vector<uint64_t> limits;
+    for (ea_ctx *m : srv->batch->members) {
+        ServerJob *owner = nullptr;
+        for (ServerJob *j : srv->running)
+            if (j->ctx == m)
+                owner = j;
+        limits.push_back(owner ? owner->spec.sweeps - m->t : 0);
+    }
+    std::vector<uint64_t> before;
+    for (ServerJob *j : srv->running)
+        before.push_back(j->ctx->t);
+    int rc = batch_sweep_impl(srv->batch, srv->chunk, &limits);
+    if (rc != EA_OK)
+        return sfail(srv, rc, "batch sweep failed: " + srv->batch->err);
+    ++srv->steps;
+    // 3. retire
+    std::vector<ServerJob *> still;
+    for (size_t i = 0; i < srv->running.size(); ++i) {
+        ServerJob *j = srv->running[i];
+        const uint64_t N = (uint64_t)j->spec.L * j->spec.L * j->spec.L;
+        srv->flips += (j->ctx->t - before[i]) * 2ull * (uint64_t)j->spec.n_samples * N;
+        if (j->ctx->t >= j->spec.sweeps) {
+            ea_batch_remove(srv->batch, j->ctx);
+            j->state = EA_JOB_DONE;
+            if (n_finished)
+                ++*n_finished;
+        } else {
+            still.push_back(j);
+        }
+    }
+    srv->running.swap(still);
+    return EA_OK;
+}
+
+int ea_server_job_state(const ea_server *srv, int64_t job_id, int *state, uint64_t *time)
+{
+    if (!srv || !state)
+        return EA_ERR_INVALID_ARG;
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end())
+        return EA_ERR_INVALID_ARG;
+    *state = it->second->state;
+    if (time)
+        *time = it->second->ctx ? it->second->ctx->t : 0;
+    return EA_OK;
+}
+
+int ea_server_job(ea_server *srv, int64_t job_id, ea_ctx **job)
+{
+    if (!srv || !job)
+        return EA_ERR_INVALID_ARG;
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end())
+        return EA_ERR_INVALID_ARG;
+    if (!it->second->ctx)
+        return sfail(srv, EA_ERR_STATE, "job still queued");
+    *job = it->second->ctx;
+    return EA_OK;
+}
+
+int ea_server_release(ea_server *srv, int64_t job_id)
+{
+    if (!srv)
+        return EA_ERR_INVALID_ARG;
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end())
+        return EA_ERR_INVALID_ARG;
+    ServerJob *j = it->second;
+    if (j->state != EA_JOB_DONE)
+        return sfail(srv, EA_ERR_STATE, "job not done");
+    ea_destroy(j->ctx);
+    srv->in_use -= j->bytes;
+    srv->jobs.erase(it);
+    delete j;
+    return EA_OK;
+}
+
+int ea_server_get_stats(const ea_server *srv, ea_server_stats *out)
+{
+    if (!srv || !out)
+        return EA_ERR_INVALID_ARG;
+    out->queued = (int)srv->queue.size();
+    out->running = (int)srv->running.size();
+    out->done = (int)(srv->jobs.size() - srv->queue.size() - srv->running.size());
+    out->bytes_in_use = srv->in_use;
+    out->flips = srv->flips;
+    out->steps = srv->steps;
+    return EA_OK;
+}
+
+int ea_server_destroy(ea_server *srv)
+{
+    if (!srv)
+        return EA_OK;
+    ea_batch_destroy(srv->batch);
+    for (auto &kv : srv->jobs) {
+        ea_destroy(kv.second->ctx);
+        delete kv.second;
+    }
+    delete srv;
+    return EA_OK;
+}
+
+const char *ea_server_last_error(const ea_server *srv) { return srv ? srv->err.c_str() : ""; }
 
 }  // extern "C"

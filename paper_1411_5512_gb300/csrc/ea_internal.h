@@ -47,9 +47,14 @@ struct Geo {
 
 int make_geo(int L, Geo *g);  // 0 or -1
 
+// C[g] = floor(2^64 (1 - (1 - p)^g)), g = 0..32, clamped to 2^64 - 1 (0 < p < 1).
+int geo_table(double p, uint64_t C[33]);
+
 // Threshold planes for the bit-sliced comparison r < thr (MSB first).
 struct Thr {
     uint64_t thr_u[7];      // indexed by u = number of unsatisfied bonds = 6 - k
+    uint64_t geoC[3][33];   // Metropolis geometric-gap tables, u = 0, 1, 2
+    uint32_t geo_live;      // bit u: 0 < p_u < 1
     uint32_t always_u;      // bit u set: accepted without a random number
     uint32_t zero_calls;    // bit c set: planes 4c..4c+3 of every needed threshold are 0
     int rule;               // 0 Metropolis, 1 heat bath
@@ -57,22 +62,64 @@ struct Thr {
     int none_random;        // no lane ever needs a random number
 };
 
-struct SweepLaunch {
-    uint32_t *spins;       // [S][2][words]
-    const uint32_t *J;     // [S][3][words]
+// One job as the sweep kernel sees it (device memory).  A launch covers a
+// table of jobs; block b works for the job j with block_begin[j] <= b <
+// block_begin[j+1].  The plain path launches a one-entry table per job, the
+// batched path one table for all jobs of a batch.
+struct alignas(16) JobDev {
+    uint32_t *spins;          // [S][2][words]
+    const uint32_t *J;        // [S][3][words]
+    uint64_t t;               // sweep index of the next sweep
+    uint64_t t_end;           // the job sweeps while t < t_end (its own stop)
     Geo geo;
-    Thr thr;
-    uint32_t key0, key1;   // Philox key = seed
+    uint32_t rk[20];          // Philox round keys: rk[2r], rk[2r+1] for round r
+    alignas(16) uint32_t tm[16][7][4];  // heat bath: threshold plane masks
+                                        // [call][u][plane in call], read as uint4
+    uint32_t gC_hi[3][33];    // Metropolis: geometric-gap tables C_u[g], high words
+    uint32_t gC_lo[3][33];    //   and low words, u = 0, 1, 2 (dE = 12, 8, 4)
+    uint32_t geo_live;        // bit u: class u can accept (0 < p_u < 1)
+    uint32_t zero_calls;      // bit c: planes 4c..4c+3 of every needed threshold are 0
+    uint32_t always_u;        // bit u: accepted without a random number
+    int rule;
+    int all_always;
+    int none_random;
     int n_samples;
-    int rng_group;         // G
+    uint32_t rng_group;       // G
+    int cols;                 // word columns per sample, n[0] * n[1]
+    uint32_t div_n0_magic;    // fast division by n[0] (col -> x', y')
+    int div_n0_shift;
+    int blocks_per_sample;
+    int cols_per_thread;
 };
+
+static_assert(offsetof(JobDev, tm) % 16 == 0, "JobDev::tm is read with 16-byte loads");
+static_assert(sizeof(JobDev) % 16 == 0, "JobDev tables are arrays of 16-byte aligned rows");
+
+// Host-side preparation of a JobDev (ea_sweep.cu).
+void fill_job_keys(JobDev *jd, uint64_t seed);
+void fill_job_thresholds(JobDev *jd, const Thr &thr);
+void fill_job_layout(JobDev *jd, int cols_per_thread);
+
+constexpr int kSweepThreads = 128;
+
+// Enqueue n sweeps of every job of a table: 2n launches (one per half-step)
+// per rule present.  jobs_dev/block_begin_dev describe the table on the device,
+// n_blocks[rule] is the grid of the launch for that rule (0: none).
+cudaError_t launch_sweep_table(const JobDev *jobs_dev_rule0, const int *bb_dev_rule0,
+                               int n_jobs_rule0, int blocks_rule0,
+                               const JobDev *jobs_dev_rule1, const int *bb_dev_rule1,
+                               int n_jobs_rule1, int blocks_rule1, uint64_t n,
+                               cudaStream_t stream, unsigned long long *counters = nullptr);
+
+// Add n to the time field of every job of a table, stopping at its t_end
+// (device side, for graphs).
+cudaError_t launch_advance_time(JobDev *jobs_dev, int n_jobs, uint64_t n, cudaStream_t stream);
 
 // kernels (ea_kernels.cu); all enqueue on `stream` and return cudaGetLastError()
 cudaError_t launch_init_couplings(uint32_t *J, const Geo &g, int n_samples, double p_neg,
                                   uint64_t seed, cudaStream_t stream);
 cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int n_samples, uint64_t seed,
                               cudaStream_t stream);
-cudaError_t launch_sweeps(const SweepLaunch &p, uint64_t t0, uint64_t n, cudaStream_t stream);
 
 // observable sums (popcounts) accumulated with integer atomics
 cudaError_t launch_obs_state(const uint32_t *spins, const uint32_t *J, const Geo &g, int n_samples,

@@ -1,60 +1,20 @@
-// ea_kernels.cu -- sm_103a kernels of the EA ageing library.
+// ea_kernels.cu -- initial-state and observable kernels of the EA ageing library
+// (the sweep kernel is in ea_sweep.cu).
 //
 // All state is bit-packed: one 32-bit word holds up to 32 sites of ONE sample
-// (Geo in ea_internal.h), so every lane of a word shares one temperature and
-// one Philox key, and a per-sample reduction is a plain popcount of words.
-//
-// The update of a word is pure bitwise logic (Sec. III: "bit operations are
-// used to perform the update for all bit-coded spins at the same time"):
-//   unsatisfied-bond bits  u_j = s ^ n_j ^ J_j                      (6 LOP3)
-//   bit-sliced count of the six u_j -> (b2 b1 b0) = u in 0..6       (8 LOP3)
-//   dE = 12 - 4u (Eq. 9); Metropolis accepts u >= 3 outright and compares a
-//   64-bit uniform r against the integer threshold of dE otherwise.
-// The comparison r < thr is done bit-sliced from the most significant bit:
-// plane k of the Philox stream gives bit 63-k of r for all 32 lanes at once;
-// a lane is decided at the first plane where its r bit differs from its
-// threshold bit, so most words finish after one or two Philox calls.
+// (Geo in ea_internal.h), so a per-sample reduction is a plain popcount of
+// words: sum_i S_i S'_i = N - 2 * (number of differing bits).
 #include <cstdint>
 
+#include "ea_device.cuh"
 #include "ea_internal.h"
 
 namespace ea {
 namespace {
 
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
-// multiplies (0xD2511F53, 0xCD9E8D57) with the key bumped by the Weyl
-// constants (0x9E3779B9, 0xBB67AE85) between rounds.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-constexpr uint32_t kStreamCouplings = 0u << 30;
-constexpr uint32_t kStreamSpins = 1u << 30;
-constexpr uint32_t kStreamSweep = 2u << 30;
-
-// c ? x : y, bitwise
-__device__ __forceinline__ uint32_t sel(uint32_t c, uint32_t x, uint32_t y)
-{
-    return (c & x) | (~c & y);
-}
-
-__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c)
-{
-    return (a & b) | (a & c) | (b & c);
-}
+using dev::kStreamCouplings;
+using dev::kStreamSpins;
+using dev::philox10;
 
 // Neighbour word read across the periodic wrap of axis d (dir 0: +1, 1: -1).
 __device__ __forceinline__ uint32_t realign(uint32_t w, const Geo &g, int d, int dir)
@@ -121,165 +81,6 @@ __global__ void init_spins_kernel(uint32_t *__restrict__ spins, Geo g, uint32_t 
     uint32_t *Ss = spins + (size_t)s * 2 * W;
     Ss[w] = rep[0 ^ c];      // area 0 holds replica (0 XOR colour)
     Ss[W + w] = rep[1 ^ c];  // area 1 holds replica (1 XOR colour)
-}
-
-// ---------------------------------------------------------------------------
-// half-step update
-// ---------------------------------------------------------------------------
-template <int RULE>
-struct RuleInfo;
-template <>
-struct RuleInfo<0> {
-    static constexpr int NT = 3;  // thresholds of u = 0, 1, 2 (dE = 12, 8, 4)
-};
-template <>
-struct RuleInfo<1> {
-    static constexpr int NT = 7;  // thresholds of u = 0..6
-};
-
-// bitwise 8-way select on (b2 b1 b0) of the values f[0..6] (f[7] = 0)
-__device__ __forceinline__ uint32_t mux7(uint32_t b2, uint32_t b1, uint32_t b0, uint32_t f0,
-                                         uint32_t f1, uint32_t f2, uint32_t f3, uint32_t f4,
-                                         uint32_t f5, uint32_t f6)
-{
-    const uint32_t m0 = sel(b0, f1, f0), m1 = sel(b0, f3, f2), m2 = sel(b0, f5, f4),
-                   m3 = ~b0 & f6;
-    return sel(b2, sel(b1, m3, m2), sel(b1, m1, m0));
-}
-
-template <int RULE>
-__global__ void __launch_bounds__(256) halfstep_kernel(SweepLaunch p, int h, uint64_t t)
-{
-    constexpr int NT = RuleInfo<RULE>::NT;
-    // s_tm[call][u] = the four plane masks (all-ones where the threshold bit is 1)
-    __shared__ uint4 s_tm[16][NT];
-    for (int idx = threadIdx.x; idx < 16 * NT * 4; idx += blockDim.x) {
-        const int call = idx / (NT * 4), u = (idx / 4) % NT, j = idx % 4;
-        const int k = 4 * call + j;
-        const uint32_t bit = (uint32_t)(p.thr.thr_u[u] >> (63 - k)) & 1u;
-        reinterpret_cast<uint32_t *>(s_tm)[idx] = 0u - bit;
-    }
-    __syncthreads();
-
-    const Geo &g = p.geo;
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (w >= g.words)
-        return;
-    int xw, yw, zw;
-    word_coords(g, w, xw, yw, zw);
-    const int c = (xw + yw + zw) & 1;
-    const int a = h ^ c;  // replica updated at this word-site in half-step h
-
-    const size_t W = (size_t)g.words;
-    uint32_t *upd = p.spins + ((size_t)s * 2 + h) * W;
-    const uint32_t *__restrict__ nb = p.spins + ((size_t)s * 2 + (h ^ 1)) * W;
-    const uint32_t *__restrict__ Jx = p.J + (size_t)s * 3 * W;
-    const uint32_t *__restrict__ Jy = Jx + W;
-    const uint32_t *__restrict__ Jz = Jy + W;
-
-    const uint32_t sp = upd[w];
-    const int sy = g.n[0], sz = g.n[0] * g.n[1];
-    uint32_t nxp, nxm, jxm, nyp, nym, jym, nzp, nzm, jzm;
-    if (xw + 1 < g.n[0])
-        nxp = nb[w + 1];
-    else
-        nxp = realign(nb[w - (g.n[0] - 1)], g, 0, 0);
-    if (xw > 0) {
-        nxm = nb[w - 1];
-        jxm = Jx[w - 1];
-    } else {
-        nxm = realign(nb[w + (g.n[0] - 1)], g, 0, 1);
-        jxm = realign(Jx[w + (g.n[0] - 1)], g, 0, 1);
-    }
-    if (yw + 1 < g.n[1])
-        nyp = nb[w + sy];
-    else
-        nyp = realign(nb[w - (g.n[1] - 1) * sy], g, 1, 0);
-    if (yw > 0) {
-        nym = nb[w - sy];
-        jym = Jy[w - sy];
-    } else {
-        nym = realign(nb[w + (g.n[1] - 1) * sy], g, 1, 1);
-        jym = realign(Jy[w + (g.n[1] - 1) * sy], g, 1, 1);
-    }
-    if (zw + 1 < g.n[2])
-        nzp = nb[w + sz];
-    else
-        nzp = realign(nb[w - (g.n[2] - 1) * sz], g, 2, 0);
-    if (zw > 0) {
-        nzm = nb[w - sz];
-        jzm = Jz[w - sz];
-    } else {
-        nzm = realign(nb[w + (g.n[2] - 1) * sz], g, 2, 1);
-        jzm = realign(Jz[w + (g.n[2] - 1) * sz], g, 2, 1);
-    }
-
-    // unsatisfied bonds and their bit-sliced count u = 4 b2 + 2 b1 + b0
-    const uint32_t u0 = sp ^ nxp ^ Jx[w], u1 = sp ^ nxm ^ jxm;
-    const uint32_t u2 = sp ^ nyp ^ Jy[w], u3 = sp ^ nym ^ jym;
-    const uint32_t u4 = sp ^ nzp ^ Jz[w], u5 = sp ^ nzm ^ jzm;
-    const uint32_t s1 = u0 ^ u1 ^ u2, c1 = maj3(u0, u1, u2);
-    const uint32_t s2 = u3 ^ u4 ^ u5, c2 = maj3(u3, u4, u5);
-    const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
-    const uint32_t b1 = c1 ^ c2 ^ c3, b2 = maj3(c1, c2, c3);
-
-    uint32_t alw;
-    if (RULE == 0) {
-        alw = b2 | (b1 & b0);  // u >= 3 <=> dE <= 0
-    } else {
-        const uint32_t f = p.thr.always_u;
-        alw = mux7(b2, b1, b0, 0u - (f & 1u), 0u - ((f >> 1) & 1u), 0u - ((f >> 2) & 1u),
-                   0u - ((f >> 3) & 1u), 0u - ((f >> 4) & 1u), 0u - ((f >> 5) & 1u),
-                   0u - ((f >> 6) & 1u));
-    }
-    uint32_t flip;
-    if (p.thr.all_always) {
-        flip = ~0u;
-    } else if (p.thr.none_random) {
-        flip = alw;
-    } else {
-        uint32_t U = ~alw & g.valid;  // lanes still comparing r with their threshold
-        uint32_t A = 0u;              // lanes accepted by the comparison
-        const uint32_t c2base =
-            kStreamSweep | (((uint32_t)(t >> 32) & 0xFFFFu) << 8) | ((uint32_t)a << 4);
-        const uint32_t c3 = (uint32_t)(s / p.rng_group);
-        for (int call = 0; call < 16 && U != 0u; ++call) {
-            const uint4 R =
-                philox10(make_uint4((uint32_t)w, (uint32_t)t, c2base | (uint32_t)call, c3), p.key0,
-                         p.key1);
-            if ((p.thr.zero_calls >> call) & 1u) {
-                // every needed threshold bit is 0 on these planes: a 1 bit rejects
-                U &= ~(R.x | R.y | R.z | R.w);
-                continue;
-            }
-            uint32_t tk[4];
-            if (RULE == 0) {
-                const uint4 T0 = s_tm[call][0], T1 = s_tm[call][1], T2 = s_tm[call][2];
-                tk[0] = sel(b1, T2.x, sel(b0, T1.x, T0.x));
-                tk[1] = sel(b1, T2.y, sel(b0, T1.y, T0.y));
-                tk[2] = sel(b1, T2.z, sel(b0, T1.z, T0.z));
-                tk[3] = sel(b1, T2.w, sel(b0, T1.w, T0.w));
-            } else {
-                uint4 T[7];
-#pragma unroll
-                for (int u = 0; u < 7; ++u)
-                    T[u] = s_tm[call][u];
-                tk[0] = mux7(b2, b1, b0, T[0].x, T[1].x, T[2].x, T[3].x, T[4].x, T[5].x, T[6].x);
-                tk[1] = mux7(b2, b1, b0, T[0].y, T[1].y, T[2].y, T[3].y, T[4].y, T[5].y, T[6].y);
-                tk[2] = mux7(b2, b1, b0, T[0].z, T[1].z, T[2].z, T[3].z, T[4].z, T[5].z, T[6].z);
-                tk[3] = mux7(b2, b1, b0, T[0].w, T[1].w, T[2].w, T[3].w, T[4].w, T[5].w, T[6].w);
-            }
-            const uint32_t r[4] = {R.x, R.y, R.z, R.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                A |= U & ~r[j] & tk[j];   // r bit 0 < threshold bit 1: accept
-                U &= ~(r[j] ^ tk[j]);     // bits differ: decided
-            }
-        }
-        flip = alw | A;
-    }
-    upd[w] = sp ^ (flip & g.valid);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,20 +247,6 @@ cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int n_samples, uint
 {
     init_spins_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(spins, g, (uint32_t)seed,
                                                                      (uint32_t)(seed >> 32));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sweeps(const SweepLaunch &p, uint64_t t0, uint64_t n, cudaStream_t stream)
-{
-    const dim3 grid = grid_for(p.geo, p.n_samples);
-    for (uint64_t k = 0; k < n; ++k) {
-        for (int h = 0; h < 2; ++h) {
-            if (p.thr.rule == 0)
-                halfstep_kernel<0><<<grid, kBlock, 0, stream>>>(p, h, t0 + k);
-            else
-                halfstep_kernel<1><<<grid, kBlock, 0, stream>>>(p, h, t0 + k);
-        }
-    }
     return cudaGetLastError();
 }
 

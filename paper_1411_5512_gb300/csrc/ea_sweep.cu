@@ -1,0 +1,641 @@
+// ea_sweep.cu -- the checkerboard half-step kernels (Sec. III) over a table of jobs.
+//
+// One thread updates a column of word-sites (x', y', z' = 0..n2-1) of one
+// sample in half-step h.  Every word-site of area h is updated (it holds the
+// replica whose colour is due in half-step h, Fig. 1), so a column is a run of
+// contiguous work with its z-neighbours in a register window.
+//
+// Per word (32 sites of one sample):
+//   u_j = s ^ n_j ^ J_j for the six bonds (1 = unsatisfied)         6 LOP3
+//   bit-sliced count (b2 b1 b0) = u                                 8 LOP3
+//   dE = 12 - 4u (Eq. 9): u >= 3 (dE <= 0) flips outright.
+//   Metropolis (metro_kernel): the lanes of class u = 0, 1, 2 (dE = 12, 8,
+//     4) flip independently with p_u = exp(-dE/T); taken in lane order they
+//     form a Bernoulli sequence whose first acceptance rank is geometric, so
+//     one 64-bit draw V per class decides: no flip when V >= C_u[n] (n lanes
+//     in the class), else the lane of rank min{g : V < C_u[g+1]}, after which
+//     the remaining lanes take the next draw.  One Philox call per word holds
+//     the first draw of every class and the second of class 2; its high words
+//     settle ~97% of class tests at T = 0.7 without a branch.  Two words are
+//     processed together so that their Philox chains overlap.
+//   Heat bath (heat_kernel): every lane compares its own 64-bit uniform r
+//     with its threshold, MSB first, four planes per Philox call; a lane is
+//     decided at the first plane where its bit of r differs from its
+//     threshold bit.
+#include <cstdint>
+#include <cstring>
+
+#include "ea_device.cuh"
+#include "ea_internal.h"
+
+namespace ea {
+namespace {
+
+using dev::maj3;
+using dev::realign;
+using dev::sel;
+
+// bitwise 8-way select on (b2 b1 b0) of f[0..6], f[7] = 0
+__device__ __forceinline__ uint32_t mux7(uint32_t b2, uint32_t b1, uint32_t b0, const uint32_t f[7])
+{
+    const uint32_t m0 = sel(b0, f[1], f[0]), m1 = sel(b0, f[3], f[2]), m2 = sel(b0, f[5], f[4]),
+                   m3 = ~b0 & f[6];
+    return sel(b2, sel(b1, m3, m2), sel(b1, m1, m0));
+}
+
+struct Axis {
+    int sA[2], sB[2];
+    uint32_t mA[2], mB[2];
+};
+
+__device__ __forceinline__ uint32_t fixup(uint32_t w, const Axis &a, int dir)
+{
+    return realign(w, a.sA[dir], a.mA[dir], a.sB[dir], a.mB[dir]);
+}
+
+__device__ __forceinline__ void load_axis(Axis &a, const Geo &g, int d)
+{
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+        a.sA[dir] = g.sA[d][dir];
+        a.sB[dir] = g.sB[d][dir];
+        a.mA[dir] = g.mA[d][dir];
+        a.mB[dir] = g.mB[d][dir];
+    }
+}
+
+__device__ __forceinline__ uint32_t comp(const uint4 &v, int i)
+{
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Block -> job of the table (the last j with block_begin[j] <= blockIdx.x).
+__device__ __forceinline__ int find_job(const int *__restrict__ block_begin, int n_jobs)
+{
+    int lo = 0, hi = n_jobs - 1;
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (block_begin[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// The bit-sliced count u = 4 b2 + 2 b1 + b0 of six unsatisfied-bond bits.
+struct Count {
+    uint32_t b0, b1, b2;
+};
+
+__device__ __forceinline__ Count count6(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3,
+                                        uint32_t u4, uint32_t u5)
+{
+    const uint32_t s1 = u0 ^ u1 ^ u2, k1 = maj3(u0, u1, u2);
+    const uint32_t s2 = u3 ^ u4 ^ u5, k2 = maj3(u3, u4, u5);
+    Count c;
+    c.b0 = s1 ^ s2;
+    const uint32_t k3 = s1 & s2;
+    c.b1 = k1 ^ k2 ^ k3;
+    c.b2 = maj3(k1, k2, k3);
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Metropolis: the accepted lanes of one word when a class test hit
+// ---------------------------------------------------------------------------
+// Draw d of class u: call 0 output (class 2: d = 0 -> 0, d = 1 -> 1; class 1:
+// d = 0 -> 2; class 0: d = 0 -> 3); later draws e = d - f_u (f = 1, 1, 2) are
+// output e mod 4 of call 1 + u + 3 (e div 4).  Low words: call + 64.
+__device__ __forceinline__ uint32_t metro_rare(const JobDev *__restrict__ jb, uint32_t M0,
+                                            uint32_t M1, uint32_t M2, uint4 R, uint32_t w,
+                                            uint32_t c1, uint32_t c2, uint32_t c3,
+                                            unsigned int *extra_calls)
+{
+    uint32_t acc = 0u;
+    const uint32_t Ms[3] = {M0, M1, M2};
+    for (int u = 0; u < 3; ++u) {
+        uint32_t Mr = Ms[u];
+        int rem = __popc(Mr);
+        int d = 0;
+        while (rem > 0) {
+            int call, out;
+            const int f = u == 2 ? 2 : 1;
+            if (d < f) {
+                call = 0;
+                out = u == 2 ? d : 3 - u;
+            } else {
+                const int e = d - f;
+                call = 1 + u + 3 * (e >> 2);
+                out = e & 3;
+            }
+            uint32_t rk[20];
+            bool have_rk = false;
+            uint32_t vhi;
+            if (call == 0) {
+                vhi = comp(R, out);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 20; ++i)
+                    rk[i] = jb->rk[i];
+                have_rk = true;
+                vhi = comp(dev::philox10_rk(make_uint4(w, c1, c2 | (uint32_t)call, c3), rk), out);
+                ++*extra_calls;
+            }
+            bool have_lo = false;
+            uint32_t vlo = 0u;
+            // V < C_u[g], fetching V's low word only when the high words tie
+            auto below = [&](int g) -> bool {
+                const uint32_t ch = jb->gC_hi[u][g];
+                if (vhi != ch)
+                    return vhi < ch;
+                if (!have_lo) {
+                    if (!have_rk) {
+#pragma unroll
+                        for (int i = 0; i < 20; ++i)
+                            rk[i] = jb->rk[i];
+                        have_rk = true;
+                    }
+                    vlo = comp(dev::philox10_rk(
+                                   make_uint4(w, c1, c2 | (uint32_t)(call + 64), c3), rk),
+                               out);
+                    ++*extra_calls;
+                    have_lo = true;
+                }
+                return vlo < jb->gC_lo[u][g];
+            };
+            if (!below(rem))
+                break;
+            int G = 0;
+            while (!below(G + 1))
+                ++G;
+            for (int i = 0; i < G; ++i)
+                Mr &= Mr - 1u;
+            acc |= Mr & (0u - Mr);  // the lane of rank G among the remaining ones
+            Mr &= Mr - 1u;
+            rem -= G + 1;
+            ++d;
+        }
+    }
+    return acc;
+}
+
+// Class masks of a word (u = 0, 1, 2 <=> b2 = 0 and not b1 & b0)
+struct Classes {
+    uint32_t M0, M1, M2;
+};
+
+__device__ __forceinline__ Classes classes(const Count &c, uint32_t alw, uint32_t valid,
+                                           uint32_t live0, uint32_t live1, uint32_t live2)
+{
+    const uint32_t need = ~alw & valid;
+    Classes k;
+    k.M0 = need & ~(c.b1 | c.b0) & live0;
+    k.M1 = need & c.b0 & live1;
+    k.M2 = need & c.b1 & live2;
+    return k;
+}
+
+// Might some lane of the word flip?  An exact "no" for ~97% of words at T = 0.7.
+__device__ __forceinline__ bool class_hit(const Classes &k, const uint4 &R,
+                                          const uint32_t (*gh)[33])
+{
+    const int n0 = __popc(k.M0), n1 = __popc(k.M1), n2 = __popc(k.M2);
+    const bool h2 = (n2 != 0) & (R.x <= gh[2][n2]);
+    const bool h1 = (n1 != 0) & (R.z <= gh[1][n1]);
+    const bool h0 = (n0 != 0) & (R.w <= gh[0][n0]);
+    return h0 | h1 | h2;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kSweepThreads, 6)
+    metro_kernel(const JobDev *__restrict__ jobs, const int *__restrict__ block_begin, int n_jobs,
+                 int h, uint32_t sweep_offset, unsigned long long *counters)
+{
+    __shared__ uint32_t s_gh[3][33];
+    __shared__ int s_job;
+    if (threadIdx.x == 0)
+        s_job = find_job(block_begin, n_jobs);
+    __syncthreads();
+    const JobDev *__restrict__ jb = &jobs[s_job];
+    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x)
+        (&s_gh[0][0])[i] = (&jb->gC_hi[0][0])[i];
+    __syncthreads();
+    const uint64_t t = jb->t + sweep_offset;
+    if (t >= jb->t_end)
+        return;  // this job has stopped (uniform over the block)
+
+    const int local = (int)blockIdx.x - block_begin[s_job];
+    const int bps = jb->blocks_per_sample;
+    const int s = local / bps;
+    const int cb = local - s * bps;
+    const int cols = jb->cols;
+    const int cpt = jb->cols_per_thread;
+    const int n0 = jb->geo.n[0], n1 = jb->geo.n[1], n2 = jb->geo.n[2];
+    const uint32_t valid = jb->geo.valid;
+    const uint32_t magic = jb->div_n0_magic;
+    const int dshift = jb->div_n0_shift;
+    const bool all_always = jb->all_always != 0;
+    const bool none_random = jb->none_random != 0;
+    const uint32_t live0 = 0u - (jb->geo_live & 1u), live1 = 0u - ((jb->geo_live >> 1) & 1u),
+                   live2 = 0u - ((jb->geo_live >> 2) & 1u);
+    uint32_t rk[20];
+#pragma unroll
+    for (int i = 0; i < 20; ++i)
+        rk[i] = jb->rk[i];
+    Axis az;
+    load_axis(az, jb->geo, 2);
+    const size_t W = (size_t)jb->geo.words;
+    uint32_t *__restrict__ upd = jb->spins + ((size_t)s * 2 + h) * W;
+    const uint32_t *__restrict__ nb = jb->spins + ((size_t)s * 2 + (h ^ 1)) * W;
+    const uint32_t *__restrict__ Jx = jb->J + (size_t)s * 3 * W;
+    const uint32_t *__restrict__ Jy = Jx + W;
+    const uint32_t *__restrict__ Jz = Jy + W;
+    const uint32_t c3 = (uint32_t)s / jb->rng_group;
+    const uint32_t c1 = (uint32_t)t;
+    const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
+    const int sz = n0 * n1;
+    unsigned int n_words = 0, n_calls = 0, n_extra = 0;
+
+    for (int k = 0; k < cpt; ++k) {
+        const int col = (cb * cpt + k) * kSweepThreads + (int)threadIdx.x;
+        if (col >= cols)
+            break;
+        const int y = (int)((__umulhi((uint32_t)col, magic) + (uint32_t)col) >> dshift);
+        const int x = col - y * n0;
+        int cxp = col + 1, cxm = col - 1, cyp = col + n0, cym = col - n0;
+        const bool wxp = (x + 1 == n0), wxm = (x == 0), wyp = (y + 1 == n1), wym = (y == 0);
+        if (wxp)
+            cxp = col - (n0 - 1);
+        if (wxm)
+            cxm = col + (n0 - 1);
+        if (wyp)
+            cyp = col - (n1 - 1) * n0;
+        if (wym)
+            cym = col + (n1 - 1) * n0;
+        Axis ax, ay;
+        if (wxp || wxm)
+            load_axis(ax, jb->geo, 0);
+        if (wyp || wym)
+            load_axis(ay, jb->geo, 1);
+        // replica updated at word-site (x, y, z) in half-step h: h ^ ((x + y + z) & 1)
+        const uint32_t c2e = c2m | ((uint32_t)(h ^ ((x + y) & 1)) << 11);      // even z
+        const uint32_t c2o = c2m | ((uint32_t)(h ^ ((x + y + 1) & 1)) << 11);  // odd z
+        // z window: neighbour area at z' - 1 and the backward z bond below z'
+        uint32_t nz_prev = fixup(nb[col + (n2 - 1) * sz], az, 1);
+        uint32_t jz_prev = fixup(Jz[col + (n2 - 1) * sz], az, 1);
+        uint32_t nz_cur = nb[col];
+        for (int z = 0; z < n2; z += 2) {  // n2 is even: words at z (a) and z + 1 (b)
+            const int wa = col + z * sz, wb = wa + sz;
+            const uint32_t nz_b = nb[wb];                                             // z + 1
+            const uint32_t nz_n = (z + 2 < n2) ? nb[wb + sz] : fixup(nb[col], az, 0);  // z + 2
+            const uint32_t spa = upd[wa], spb = upd[wb];
+            uint32_t nxpa = nb[cxp + z * sz], nxma = nb[cxm + z * sz];
+            uint32_t nypa = nb[cyp + z * sz], nyma = nb[cym + z * sz];
+            uint32_t jxma = Jx[cxm + z * sz], jyma = Jy[cym + z * sz];
+            uint32_t nxpb = nb[cxp + z * sz + sz], nxmb = nb[cxm + z * sz + sz];
+            uint32_t nypb = nb[cyp + z * sz + sz], nymb = nb[cym + z * sz + sz];
+            uint32_t jxmb = Jx[cxm + z * sz + sz], jymb = Jy[cym + z * sz + sz];
+            const uint32_t jxa = Jx[wa], jya = Jy[wa], jza = Jz[wa];
+            const uint32_t jxb = Jx[wb], jyb = Jy[wb], jzb = Jz[wb];
+            if (wxp) {
+                nxpa = fixup(nxpa, ax, 0);
+                nxpb = fixup(nxpb, ax, 0);
+            }
+            if (wxm) {
+                nxma = fixup(nxma, ax, 1);
+                nxmb = fixup(nxmb, ax, 1);
+                jxma = fixup(jxma, ax, 1);
+                jxmb = fixup(jxmb, ax, 1);
+            }
+            if (wyp) {
+                nypa = fixup(nypa, ay, 0);
+                nypb = fixup(nypb, ay, 0);
+            }
+            if (wym) {
+                nyma = fixup(nyma, ay, 1);
+                nymb = fixup(nymb, ay, 1);
+                jyma = fixup(jyma, ay, 1);
+                jymb = fixup(jymb, ay, 1);
+            }
+            // word b's -z neighbour is the neighbour area at z; its backward z bond is jza
+            const Count ca = count6(spa ^ nxpa ^ jxa, spa ^ nxma ^ jxma, spa ^ nypa ^ jya,
+                                    spa ^ nyma ^ jyma, spa ^ nz_b ^ jza, spa ^ nz_prev ^ jz_prev);
+            const Count cw = count6(spb ^ nxpb ^ jxb, spb ^ nxmb ^ jxmb, spb ^ nypb ^ jyb,
+                                    spb ^ nymb ^ jymb, spb ^ nz_n ^ jzb, spb ^ nz_cur ^ jza);
+            nz_prev = nz_b;
+            nz_cur = nz_n;
+            jz_prev = jzb;
+
+            const uint32_t alwa = ca.b2 | (ca.b1 & ca.b0);  // u >= 3 <=> dE <= 0
+            const uint32_t alwb = cw.b2 | (cw.b1 & cw.b0);
+            uint32_t fa, fb;
+            if (all_always) {
+                fa = fb = 0xffffffffu;
+            } else if (none_random) {
+                fa = alwa;
+                fb = alwb;
+            } else {
+                const Classes ka = classes(ca, alwa, valid, live0, live1, live2);
+                const Classes kb = classes(cw, alwb, valid, live0, live1, live2);
+                // first draws of both words: two independent Philox chains
+                const uint4 Ra = dev::philox10_rk(make_uint4((uint32_t)wa, c1, c2e, c3), rk);
+                const uint4 Rb = dev::philox10_rk(make_uint4((uint32_t)wb, c1, c2o, c3), rk);
+                if (COUNT)
+                    n_calls += ((ka.M0 | ka.M1 | ka.M2) != 0u) + ((kb.M0 | kb.M1 | kb.M2) != 0u);
+                uint32_t Aa = 0u, Ab = 0u;
+                const bool ha = class_hit(ka, Ra, s_gh), hb = class_hit(kb, Rb, s_gh);
+                unsigned int extra = 0;
+                if (ha)
+                    Aa = metro_rare(jb, ka.M0, ka.M1, ka.M2, Ra, (uint32_t)wa, c1, c2e, c3,
+                                    &extra);
+                if (hb)
+                    Ab = metro_rare(jb, kb.M0, kb.M1, kb.M2, Rb, (uint32_t)wb, c1, c2o, c3,
+                                    &extra);
+                if (COUNT)
+                    n_extra += extra;
+                fa = alwa | Aa;
+                fb = alwb | Ab;
+            }
+            upd[wa] = spa ^ (fa & valid);
+            upd[wb] = spb ^ (fb & valid);
+            if (COUNT)
+                n_words += 2;
+        }
+    }
+    if (COUNT) {
+        atomicAdd(&counters[0], (unsigned long long)n_words);
+        atomicAdd(&counters[1], (unsigned long long)(n_calls + n_extra));
+        atomicAdd(&counters[2], (unsigned long long)n_extra);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// heat bath: per-lane 64-bit comparison by bit planes
+// ---------------------------------------------------------------------------
+template <bool COUNT>
+__global__ void __launch_bounds__(kSweepThreads)
+    heat_kernel(const JobDev *__restrict__ jobs, const int *__restrict__ block_begin, int n_jobs,
+                int h, uint32_t sweep_offset, unsigned long long *counters)
+{
+    __shared__ uint4 s_tm[16][7];
+    __shared__ int s_job;
+    if (threadIdx.x == 0)
+        s_job = find_job(block_begin, n_jobs);
+    __syncthreads();
+    const JobDev &jb = jobs[s_job];
+    for (int i = threadIdx.x; i < 16 * 7; i += blockDim.x) {
+        const int call = i / 7, u = i % 7;
+        s_tm[call][u] = *reinterpret_cast<const uint4 *>(&jb.tm[call][u][0]);
+    }
+    __syncthreads();
+    const uint64_t t = jb.t + sweep_offset;
+    if (t >= jb.t_end)
+        return;
+
+    const int local = (int)blockIdx.x - block_begin[s_job];
+    const int bps = jb.blocks_per_sample;
+    const int s = local / bps;
+    const int cb = local - s * bps;
+    const int cols = jb.cols;
+    const int cpt = jb.cols_per_thread;
+    const int n0 = jb.geo.n[0], n1 = jb.geo.n[1], n2 = jb.geo.n[2];
+    const uint32_t valid = jb.geo.valid;
+    const uint32_t magic = jb.div_n0_magic;
+    const int dshift = jb.div_n0_shift;
+    const uint32_t zero_calls = jb.zero_calls;
+    const bool all_always = jb.all_always != 0;
+    const bool none_random = jb.none_random != 0;
+    const uint32_t always_u = jb.always_u;
+    uint32_t rk[20];
+#pragma unroll
+    for (int i = 0; i < 20; ++i)
+        rk[i] = jb.rk[i];
+    const size_t W = (size_t)jb.geo.words;
+    uint32_t *__restrict__ upd = jb.spins + ((size_t)s * 2 + h) * W;
+    const uint32_t *__restrict__ nb = jb.spins + ((size_t)s * 2 + (h ^ 1)) * W;
+    const uint32_t *__restrict__ Jx = jb.J + (size_t)s * 3 * W;
+    const uint32_t *__restrict__ Jy = Jx + W;
+    const uint32_t *__restrict__ Jz = Jy + W;
+    const uint32_t c3 = (uint32_t)s / jb.rng_group;
+    const uint32_t c1 = (uint32_t)t;
+    const uint32_t c2t = dev::kStreamSweep | (((uint32_t)(t >> 32) & 0xFFFFu) << 8);
+    const int sz = n0 * n1;
+    Axis az;
+    load_axis(az, jb.geo, 2);
+    unsigned long long n_words = 0, n_calls = 0, n_general = 0;
+
+    for (int k = 0; k < cpt; ++k) {
+        const int col = (cb * cpt + k) * kSweepThreads + (int)threadIdx.x;
+        if (col >= cols)
+            break;
+        const int y = (int)((__umulhi((uint32_t)col, magic) + (uint32_t)col) >> dshift);
+        const int x = col - y * n0;
+        int cxp = col + 1, cxm = col - 1, cyp = col + n0, cym = col - n0;
+        const bool wxp = (x + 1 == n0), wxm = (x == 0), wyp = (y + 1 == n1), wym = (y == 0);
+        if (wxp)
+            cxp = col - (n0 - 1);
+        if (wxm)
+            cxm = col + (n0 - 1);
+        if (wyp)
+            cyp = col - (n1 - 1) * n0;
+        if (wym)
+            cym = col + (n1 - 1) * n0;
+        Axis ax, ay;
+        if (wxp || wxm)
+            load_axis(ax, jb.geo, 0);
+        if (wyp || wym)
+            load_axis(ay, jb.geo, 1);
+        uint32_t nz_prev = fixup(nb[col + (n2 - 1) * sz], az, 1);  // z' = -1
+        uint32_t nz_cur = nb[col];                                  // z' = 0
+        uint32_t jz_prev = fixup(Jz[col + (n2 - 1) * sz], az, 1);  // backward z bond at z' = 0
+        const int par0 = (x + y) & 1;
+        for (int z = 0; z < n2; ++z) {
+            const int w = col + z * sz;
+            const uint32_t nz_next = (z + 1 < n2) ? nb[w + sz] : fixup(nb[col], az, 0);
+            const uint32_t sp = upd[w];
+            uint32_t nxp = nb[cxp + z * sz], nxm = nb[cxm + z * sz];
+            uint32_t jxm = Jx[cxm + z * sz];
+            uint32_t nyp = nb[cyp + z * sz], nym = nb[cym + z * sz];
+            uint32_t jym = Jy[cym + z * sz];
+            if (wxp)
+                nxp = fixup(nxp, ax, 0);
+            if (wxm) {
+                nxm = fixup(nxm, ax, 1);
+                jxm = fixup(jxm, ax, 1);
+            }
+            if (wyp)
+                nyp = fixup(nyp, ay, 0);
+            if (wym) {
+                nym = fixup(nym, ay, 1);
+                jym = fixup(jym, ay, 1);
+            }
+            const uint32_t jz = Jz[w];
+            const Count c = count6(sp ^ nxp ^ Jx[w], sp ^ nxm ^ jxm, sp ^ nyp ^ Jy[w],
+                                   sp ^ nym ^ jym, sp ^ nz_next ^ jz, sp ^ nz_prev ^ jz_prev);
+            nz_prev = nz_cur;
+            nz_cur = nz_next;
+            jz_prev = jz;
+
+            uint32_t f[7];
+#pragma unroll
+            for (int u = 0; u < 7; ++u)
+                f[u] = 0u - ((always_u >> u) & 1u);
+            const uint32_t alw = mux7(c.b2, c.b1, c.b0, f);
+            uint32_t flip;
+            if (all_always) {
+                flip = 0xffffffffu;
+            } else if (none_random) {
+                flip = alw;
+            } else {
+                const int a = h ^ par0 ^ (z & 1);  // replica at this word-site
+                const uint32_t c2 = c2t | ((uint32_t)a << 4);
+                uint32_t U = ~alw & valid;  // lanes still comparing
+                uint32_t A = 0u;            // lanes accepted by the comparison
+#pragma unroll 1
+                for (int call = 0; call < 16; ++call) {
+                    if (U == 0u)
+                        break;
+                    const uint4 R = dev::philox10_rk(
+                        make_uint4((uint32_t)w, c1, c2 | (uint32_t)call, c3), rk);
+                    if (COUNT)
+                        ++n_calls;
+                    if ((zero_calls >> call) & 1u) {
+                        U &= ~(R.x | R.y | R.z | R.w);
+                        continue;
+                    }
+                    if (COUNT)
+                        ++n_general;
+                    uint4 T[7];
+#pragma unroll
+                    for (int u = 0; u < 7; ++u)
+                        T[u] = s_tm[call][u];
+                    const uint32_t fx[7] = {T[0].x, T[1].x, T[2].x, T[3].x, T[4].x, T[5].x, T[6].x};
+                    const uint32_t fy[7] = {T[0].y, T[1].y, T[2].y, T[3].y, T[4].y, T[5].y, T[6].y};
+                    const uint32_t fz[7] = {T[0].z, T[1].z, T[2].z, T[3].z, T[4].z, T[5].z, T[6].z};
+                    const uint32_t fw[7] = {T[0].w, T[1].w, T[2].w, T[3].w, T[4].w, T[5].w, T[6].w};
+                    const uint32_t tk[4] = {mux7(c.b2, c.b1, c.b0, fx), mux7(c.b2, c.b1, c.b0, fy),
+                                            mux7(c.b2, c.b1, c.b0, fz), mux7(c.b2, c.b1, c.b0, fw)};
+                    const uint32_t r[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        A |= U & ~r[j] & tk[j];  // r bit 0 below threshold bit 1: accept
+                        U &= ~(r[j] ^ tk[j]);    // bits differ: decided
+                    }
+                }
+                flip = alw | A;
+            }
+            upd[w] = sp ^ (flip & valid);
+            if (COUNT)
+                ++n_words;
+        }
+    }
+    if (COUNT) {
+        atomicAdd(&counters[0], n_words);
+        atomicAdd(&counters[1], n_calls);
+        atomicAdd(&counters[2], n_general);
+    }
+}
+
+__global__ void advance_time_kernel(JobDev *jobs, int n_jobs, uint64_t n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n_jobs) {
+        const uint64_t t = jobs[j].t + n;
+        jobs[j].t = t < jobs[j].t_end ? t : jobs[j].t_end;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+void fill_job_keys(JobDev *jd, uint64_t seed)
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        jd->rk[2 * r] = k0;
+        jd->rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+void fill_job_thresholds(JobDev *jd, const Thr &thr)
+{
+    std::memset(jd->tm, 0, sizeof(jd->tm));
+    for (int call = 0; call < 16; ++call)
+        for (int u = 0; u < 7; ++u)
+            for (int j = 0; j < 4; ++j) {
+                const int k = 4 * call + j;  // plane k = bit 63 - k of the threshold
+                const uint32_t bit = (uint32_t)(thr.thr_u[u] >> (63 - k)) & 1u;
+                jd->tm[call][u][j] = 0u - bit;
+            }
+    for (int u = 0; u < 3; ++u)
+        for (int g = 0; g < 33; ++g) {
+            jd->gC_hi[u][g] = (uint32_t)(thr.geoC[u][g] >> 32);
+            jd->gC_lo[u][g] = (uint32_t)thr.geoC[u][g];
+        }
+    jd->geo_live = thr.geo_live;
+    jd->zero_calls = thr.zero_calls;
+    jd->always_u = thr.always_u;
+    jd->rule = thr.rule;
+    jd->all_always = thr.all_always;
+    jd->none_random = thr.none_random;
+}
+
+void fill_job_layout(JobDev *jd, int cols_per_thread)
+{
+    const Geo &g = jd->geo;
+    jd->cols = g.n[0] * g.n[1];
+    // q = (umulhi(c, m) + c) >> l with l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1;
+    // exact for c + umulhi(c, m) < 2^32 (here c < 2^21)
+    const uint32_t d = (uint32_t)g.n[0];
+    int l = 0;
+    while ((1u << l) < d)
+        ++l;
+    const uint64_t m = (((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1;
+    jd->div_n0_magic = (uint32_t)m;
+    jd->div_n0_shift = l;
+    jd->cols_per_thread = cols_per_thread < 1 ? 1 : cols_per_thread;
+    const int per_block = kSweepThreads * jd->cols_per_thread;
+    jd->blocks_per_sample = (jd->cols + per_block - 1) / per_block;
+}
+
+cudaError_t launch_sweep_table(const JobDev *jobs0, const int *bb0, int n_jobs0, int blocks0,
+                               const JobDev *jobs1, const int *bb1, int n_jobs1, int blocks1,
+                               uint64_t n, cudaStream_t stream, unsigned long long *counters)
+{
+    for (uint64_t k = 0; k < n; ++k) {
+        for (int h = 0; h < 2; ++h) {
+            if (counters) {
+                if (blocks0 > 0)
+                    metro_kernel<true><<<blocks0, kSweepThreads, 0, stream>>>(
+                        jobs0, bb0, n_jobs0, h, (uint32_t)k, counters);
+                if (blocks1 > 0)
+                    heat_kernel<true><<<blocks1, kSweepThreads, 0, stream>>>(
+                        jobs1, bb1, n_jobs1, h, (uint32_t)k, counters);
+            } else {
+                if (blocks0 > 0)
+                    metro_kernel<false><<<blocks0, kSweepThreads, 0, stream>>>(
+                        jobs0, bb0, n_jobs0, h, (uint32_t)k, nullptr);
+                if (blocks1 > 0)
+                    heat_kernel<false><<<blocks1, kSweepThreads, 0, stream>>>(
+                        jobs1, bb1, n_jobs1, h, (uint32_t)k, nullptr);
+            }
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_time(JobDev *jobs_dev, int n_jobs, uint64_t n, cudaStream_t stream)
+{
+    if (n_jobs <= 0)
+        return cudaSuccess;
+    advance_time_kernel<<<(n_jobs + 127) / 128, 128, 0, stream>>>(jobs_dev, n_jobs, n);
+    return cudaGetLastError();
+}
+
+}  // namespace ea

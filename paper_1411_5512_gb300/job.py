@@ -186,3 +186,130 @@ class EAJob:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class EABatch:
+    """Many jobs swept together: one launch per half-step for all of them."""
+
+    def __init__(self, stream=None):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.ea_batch_create(ctypes.byref(h), _stream_handle(stream)))
+        self.h = h
+        self.jobs = []
+
+    def add(self, job):
+        _lib.check(self.lib.ea_batch_add(self.h, job.h), batch=self.h)
+        self.jobs.append(job)
+
+    def remove(self, job):
+        _lib.check(self.lib.ea_batch_remove(self.h, job.h), batch=self.h)
+        self.jobs.remove(job)
+
+    def __len__(self):
+        n = ctypes.c_int()
+        _lib.check(self.lib.ea_batch_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def configure(self, cols_per_thread=0, graph_sweeps=0):
+        _lib.check(self.lib.ea_batch_configure(self.h, int(cols_per_thread), int(graph_sweeps)),
+                   batch=self.h)
+
+    def config(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _lib.check(self.lib.ea_batch_get_config(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, trial_sweeps=8):
+        _lib.check(self.lib.ea_batch_autotune(self.h, int(trial_sweeps)), batch=self.h)
+        return self.config()
+
+    def sweep(self, n):
+        _lib.check(self.lib.ea_batch_sweep(self.h, int(n)), batch=self.h)
+
+    def profile(self, sweeps=4):
+        """{words, philox_calls, general_calls, flips} over `sweeps` counted sweeps
+        (the members' state is put back afterwards)."""
+        out = np.zeros(4, dtype=np.uint64)
+        _lib.check(self.lib.ea_batch_profile(self.h, int(sweeps), out.ctypes.data_as(_lib.u64p)),
+                   batch=self.h)
+        return {"words": int(out[0]), "philox_calls": int(out[1]),
+                "general_calls": int(out[2]), "flips": int(out[3])}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h:
+            self.lib.ea_batch_destroy(self.h)
+            self.h = None
+            self.jobs = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class EAServer:
+    """Continuous batching of ageing jobs (admission by device footprint)."""
+
+    def __init__(self, budget_bytes, max_running=64, chunk_sweeps=256, stream=None):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.ea_server_create(ctypes.byref(h), int(budget_bytes), int(max_running),
+                                             int(chunk_sweeps), _stream_handle(stream)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, L, p_neg, seed, n_samples, T, sweeps, t_w=(), t=(), rule=0, rng_group=1):
+        tw = np.ascontiguousarray(np.array(list(t_w), dtype=np.uint64))
+        tt = np.ascontiguousarray(np.array(list(t), dtype=np.uint64))
+        spec = _lib.EaJobSpec(int(L), float(p_neg), int(seed), int(n_samples), int(rng_group),
+                              float(T), int(rule), int(sweeps), tw.ctypes.data_as(_lib.u64p),
+                              len(tw), tt.ctypes.data_as(_lib.u64p), len(tt))
+        jid = ctypes.c_int64()
+        _lib.check(self.lib.ea_server_submit(self.h, ctypes.byref(spec), ctypes.byref(jid)),
+                   server=self.h)
+        self._keep[jid.value] = (int(L), int(n_samples))
+        return jid.value
+
+    def step(self):
+        n = ctypes.c_int()
+        _lib.check(self.lib.ea_server_step(self.h, ctypes.byref(n)), server=self.h)
+        return n.value
+
+    def state(self, job_id):
+        st = ctypes.c_int()
+        t = ctypes.c_uint64()
+        _lib.check(self.lib.ea_server_job_state(self.h, int(job_id), ctypes.byref(st),
+                                                ctypes.byref(t)), server=self.h)
+        return st.value, t.value
+
+    def job(self, job_id):
+        """The job's context as an EAJob view (owned by the server)."""
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.ea_server_job(self.h, int(job_id), ctypes.byref(h)), server=self.h)
+        L, S = self._keep[int(job_id)]
+        view = EAJob(L, 0.0, 0, S, _handle=h)
+        view.close = lambda: None  # the server owns it
+        return view
+
+    def release(self, job_id):
+        _lib.check(self.lib.ea_server_release(self.h, int(job_id)), server=self.h)
+        self._keep.pop(int(job_id), None)
+
+    def stats(self):
+        st = _lib.EaServerStats()
+        _lib.check(self.lib.ea_server_get_stats(self.h, ctypes.byref(st)))
+        return {"queued": st.queued, "running": st.running, "done": st.done,
+                "bytes_in_use": st.bytes_in_use, "flips": st.flips, "steps": st.steps}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h:
+            self.lib.ea_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

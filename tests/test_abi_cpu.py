@@ -88,3 +88,17 @@ def test_footprint(lib):
     b = job.footprint(128, 16, 0, 0)
     assert b == 16 * 65536 * 4 * 5
     assert job.footprint(128, 16, 4, 4) > b
+
+
+def test_geo_table_matches_oracle(lib):
+    import numpy as np
+    from paper_1411_5512_gb300 import _lib
+    for T in (0.5, 0.6, 0.7, 0.8, 1.0, 3.0):
+        for dE in (4, 8, 12):
+            p = math.exp(-dE / T)
+            C = np.zeros(33, dtype=np.uint64)
+            assert lib.ea_geo_table(p, C.ctypes.data_as(_lib.u64p)) == 0
+            assert np.array_equal(C, ora.geo_table(p)), (T, dE)
+    C = np.zeros(33, dtype=np.uint64)
+    for bad in (0.0, 1.0, -1.0):
+        assert lib.ea_geo_table(bad, C.ctypes.data_as(_lib.u64p)) == -1

@@ -1,0 +1,164 @@
+"""Batched sweeps: a job's results are bit-identical alone, in any batch, under
+any launch shape, across joins and leaves, and equal to the oracle."""
+import numpy as np
+import pytest
+
+import oracle as ora
+
+pytestmark = pytest.mark.gpu
+
+# L, p_neg, seed, S, T, rule, t_w, t
+MIX = [
+    (16, 0.5, 11, 2, 0.7, 0, [0, 2, 8], [0, 1, 4]),
+    (24, 0.3, 12, 1, 0.9, 0, [0, 4], [0, 2, 8]),
+    (8, 0.1, 13, 3, 0.6, 0, [0, 1, 3], [0, 5]),
+    (12, 0.5, 14, 1, 1.2, 1, [0, 8], [0, 1]),   # heat bath in the same batch
+    (32, 0.4, 15, 1, 0.5, 0, [0], [0, 16]),
+    (6, 0.5, 16, 2, 0.8, 0, [], []),
+]
+
+
+@pytest.fixture(scope="module")
+def J():
+    from paper_1411_5512_gb300 import build, job
+    build.build()
+    return job
+
+
+def make(J, spec, stream=None):
+    L, p, seed, S, T, rule, tw, tt = spec
+    j = J.EAJob(L, p, seed, S, stream=stream)
+    j.set_schedule(tw, tt)
+    j.quench(T, rule)
+    return j
+
+
+def snapshot(j, spec, n):
+    L, p, seed, S, T, rule, tw, tt = spec
+    out = {"spins": [j.all_spins(s) for s in range(S)], "m": {}}
+    for a in tw:
+        for b in tt:
+            if a + b <= n:
+                m = j.measure(a, b)
+                out["m"][(a, b)] = {k: m[k] for k in ("A", "Q", "E", "G")}
+    return out
+
+
+def same(x, y):
+    if len(x["spins"]) != len(y["spins"]):
+        return False
+    for a, b in zip(x["spins"], y["spins"]):
+        if not np.array_equal(a, b):
+            return False
+    if set(x["m"]) != set(y["m"]):
+        return False
+    for k in x["m"]:
+        for f in ("A", "Q", "E", "G"):
+            if not np.array_equal(x["m"][k][f], y["m"][k][f]):
+                return False
+    return True
+
+
+def alone(J, n):
+    res = []
+    for spec in MIX:
+        j = make(J, spec)
+        j.sweep(n)
+        res.append(snapshot(j, spec, n))
+        j.close()
+    return res
+
+
+@pytest.mark.parametrize("cpt,graph", [(0, 0), (1, 0), (2, 4), (4, 16), (1, 7)])
+def test_batch_equals_alone(J, cpt, graph):
+    import torch
+    n = 21
+    ref = alone(J, n)
+    stream = torch.cuda.Stream()
+    b = J.EABatch(stream=stream)
+    b.configure(cpt, graph)
+    jobs = [make(J, spec, stream=stream) for spec in MIX]
+    for j in jobs:
+        b.add(j)
+    assert len(b) == len(MIX)
+    b.sweep(5)
+    b.sweep(16)
+    for j, spec, r in zip(jobs, MIX, ref):
+        assert same(snapshot(j, spec, n), r), spec
+    b.close()
+    for j in jobs:
+        j.close()
+
+
+def test_batch_matches_oracle(J):
+    import torch
+    stream = torch.cuda.Stream()
+    b = J.EABatch(stream=stream)
+    b.configure(2, 8)
+    jobs = [make(J, spec, stream=stream) for spec in MIX[:4]]
+    for j in jobs:
+        b.add(j)
+    n = 12
+    b.sweep(n)
+    for j, spec in zip(jobs, MIX[:4]):
+        L, p, seed, S, T, rule, tw, tt = spec
+        out = ora.run_job(L, p, seed, S, T, rule, tw, tt, n, keep_spins=True)
+        for s in range(S):
+            assert np.array_equal(j.all_spins(s), out["spins"][s])
+        for a in tw:
+            for c in tt:
+                if a + c <= n:
+                    m = j.measure(a, c)
+                    assert np.array_equal(m["A"], out["A"][(a, c)])
+                    assert np.array_equal(m["G"], out["G"][a])
+    b.close()
+
+
+def test_join_and_leave_mid_run(J):
+    import torch
+    n = 30
+    ref = alone(J, n)
+    stream = torch.cuda.Stream()
+    b = J.EABatch(stream=stream)
+    b.configure(1, 4)
+    jobs = [make(J, spec) for spec in MIX]  # own (default) streams
+    # first two jobs run alone for a while, then join; the others join at once
+    jobs[0].sweep(7)
+    jobs[1].sweep(3)
+    for j in jobs[2:]:
+        b.add(j)
+    b.sweep(3)
+    b.add(jobs[1])
+    b.sweep(4)
+    b.add(jobs[0])
+    # now jobs[0] is at 7, jobs[1] at 7, others at 7: run to n together
+    b.sweep(n - 7 - 10)
+    b.remove(jobs[2])
+    jobs[2].sweep(10)  # finishes alone
+    b.sweep(10)
+    for j, spec, r in zip(jobs, MIX, ref):
+        assert j.time == n
+        assert same(snapshot(j, spec, n), r), spec
+    b.close()
+    for j in jobs:
+        j.close()
+
+
+def test_autotune_changes_nothing(J):
+    import torch
+    n = 16
+    ref = alone(J, n)
+    stream = torch.cuda.Stream()
+    b = J.EABatch(stream=stream)
+    jobs = [make(J, spec, stream=stream) for spec in MIX]
+    for j in jobs:
+        b.add(j)
+    b.sweep(4)
+    cfg = b.autotune(trial_sweeps=6)
+    assert cfg[0] in (1, 2, 4) and cfg[1] >= 0
+    b.sweep(n - 4)
+    for j, spec, r in zip(jobs, MIX, ref):
+        assert same(snapshot(j, spec, n), r), spec
+    b.close()
+    for j in jobs:
+        j.close()

@@ -215,11 +215,17 @@ def _chain_histogram(J, T, rule, seed, n_sweeps, burn=200):
 
 
 def _chi2(hist, E, T):
+    """chi2 of the histogram against exp(-E/T)/Z, each state folded with its global
+    flip (H(S) = H(-S) for every J).  Folding removes the slow tunnelling between
+    the two halves of state space of an ordered lattice, which would otherwise
+    dominate the statistic, and keeps every energy level."""
     w = np.exp(-(E - E.min()) / T)
     p = w / w.sum()
-    n = hist.sum()
-    exp_ = n * p
-    return float(np.sum((hist - exp_) ** 2 / exp_))
+    flip = 255 - np.arange(256)
+    hf = (hist + hist[flip])[:128]
+    pf = (p + p[flip])[:128]
+    exp_ = hist.sum() * pf
+    return float(np.sum((hf - exp_) ** 2 / exp_))
 
 
 @pytest.mark.parametrize("p_neg,T,rule,seed", [(0.0, 3.0, 0, 1), (0.5, 2.0, 0, 2),
@@ -229,7 +235,7 @@ def test_L2_chain_samples_boltzmann(p_neg, T, rule, seed):
     E = _energy_table_L2(J)
     hist = _chain_histogram(J, T, rule, seed, 60000)
     chi2 = _chi2(hist, E, T)
-    dof = 255
+    dof = 127
     # samples are correlated in time (chi2/dof falls towards 1 as the run grows,
     # where a biased chain would make it grow); a 2x allowance is still far below
     # the value for a wrong temperature or a wrong sign of dE
@@ -419,3 +425,107 @@ def test_c4_curve_average_and_sem():
     c4, sem = ora.c4_curve(G, N)
     assert c4[0] == 1.0 and c4[1] == 0.25
     assert sem[1] == pytest.approx(0.25, rel=1e-15)  # std([0.5, 0]) / sqrt(2)
+
+
+# ----------------------------------------------------------------------------------
+# Metropolis by geometric gaps (Eq. 9 decided per class of a word-site)
+# ----------------------------------------------------------------------------------
+def test_geo_table_closed_form():
+    # p = 1/2: C[g] = 2^64 (1 - 2^-g)
+    C = ora.geo_table(0.5)
+    assert int(C[0]) == 0
+    for g in range(1, 33):
+        assert abs(int(C[g]) - (2 ** 64 - 2 ** (64 - g))) <= 2 ** 12
+    # tiny p: 1 - (1-p)^g = g p - g(g-1)/2 p^2 + O(p^3); floor loses < 1 unit
+    p = math.exp(-24.0)
+    C = ora.geo_table(p)
+    for g in (1, 2, 7, 32):
+        expect = math.ldexp(g * p - g * (g - 1) / 2.0 * p * p, 64)
+        assert abs(int(C[g]) - expect) <= 4.0, g
+    C = ora.geo_table(0.3)
+    assert all(int(C[g]) < int(C[g + 1]) for g in range(32))
+    for bad in (0.0, 1.0, -0.1, float("nan")):
+        with pytest.raises(ValueError):
+            ora.geo_table(bad)
+
+
+def _half_step_stats(L, T, n_rep, seed=5):
+    """Flip outcomes of the sites updated in half-step 0, grouped per word-site and
+    class, over n_rep independent half-steps from the same state."""
+    kx, ky, kz, Lx, Ly, Lz = ora.geometry(L)
+    J = ora.init_couplings(L, 0.5, seed, 0)
+    S0 = ora.init_spins(L, seed, 0)
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    widx = (x % Lx) + Lx * ((y % Ly) + Ly * (z % Lz))
+    lane = (x // Lx) + kx * ((y // Ly) + ky * (z // Lz))
+    colour = (x + y + z) & 1
+    dEs = []
+    for a in range(2):
+        s = S0[a].astype(np.int64)
+        hloc = np.zeros_like(s)
+        for d, ax in ((0, 2), (1, 1), (2, 0)):
+            hloc += J[d] * np.roll(s, -1, axis=ax) + np.roll(J[d] * s, 1, axis=ax)
+        dEs.append(2 * s * hloc)
+    groups = {}  # (rep, a, widx, dE) -> list of (lane, flipped)
+    for rep in range(n_rep):
+        S = S0.copy()
+        ora.half_step(L, seed, 0, S, J, T, 0, 1000 + rep, 0)
+        for a in range(2):
+            upd = colour == (0 ^ a)
+            fl = (S[a] != S0[a]) & upd
+            for dE in (4, 8, 12):
+                m = upd & (dEs[a] == dE)
+                for w, b, f in zip(widx[m], lane[m], fl[m]):
+                    groups.setdefault((rep, a, int(w), dE), []).append((int(b), bool(f)))
+            # sites with dE <= 0 always flip
+            assert np.all(fl[upd & (dEs[a] <= 0)])
+    return groups
+
+
+def test_metropolis_class_statistics():
+    T = 3.0
+    groups = _half_step_stats(32, T, 6)
+    for dE in (4, 8, 12):
+        p = math.exp(-dE / T)
+        tot = acc = 0
+        rank_n = np.zeros(32)
+        rank_acc = np.zeros(32)
+        pair_n = pair_both = 0
+        for (rep, a, w, e), lst in groups.items():
+            if e != dE:
+                continue
+            lst.sort()
+            f = [x[1] for x in lst]
+            tot += len(f)
+            acc += sum(f)
+            for j, v in enumerate(f):
+                rank_n[j] += 1
+                rank_acc[j] += v
+            if len(f) >= 2:
+                pair_n += 1
+                pair_both += f[0] and f[-1]
+        sig = math.sqrt(tot * p * (1 - p))
+        assert abs(acc - tot * p) < 5 * sig, (dE, acc, tot * p)
+        for j in range(4):  # the first ranks each accept with probability p
+            if rank_n[j] > 200:
+                sj = math.sqrt(rank_n[j] * p * (1 - p))
+                assert abs(rank_acc[j] - rank_n[j] * p) < 5 * sj, (dE, j)
+        if pair_n > 200:  # first and last site of a class decide independently
+            q = p * p
+            assert abs(pair_both - pair_n * q) < 5 * math.sqrt(pair_n * q * (1 - q)) + 1, dE
+
+
+def test_metropolis_zero_and_infinite_temperature_classes():
+    # T = 0: no uphill flip; T = inf: every site flips
+    L = 8
+    J = ora.init_couplings(L, 0.5, 2, 0)
+    S0 = ora.init_spins(L, 2, 0)
+    S = S0.copy()
+    E0 = ora.energy(S, J)
+    ora.half_step(L, 2, 0, S, J, 0.0, 0, 0, 0)
+    assert np.all(ora.energy(S, J) <= E0)
+    S = S0.copy()
+    ora.half_step(L, 2, 0, S, J, float("inf"), 0, 0, 0)
+    colour = np.indices((L, L, L)).sum(axis=0) & 1
+    assert np.array_equal(S[0][colour == 0], -S0[0][colour == 0])
+    assert np.array_equal(S[0][colour == 1], S0[0][colour == 1])
