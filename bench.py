@@ -190,7 +190,7 @@ def pct(v, q):
 def run_ours(args, world, rank, local):
     import torch
 
-    from paper_1411_5512_gb300 import job, workloads
+    from paper_1411_5512_gb300 import job, shard, workloads
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -245,11 +245,7 @@ def run_ours(args, world, rank, local):
     if world > 1:
         torch.distributed.barrier()
     sampler.stop()
-    t_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = shard.max_over_ranks(sum(step_ms), device="cuda")
     value = world * flips_per_step * args.steps / (t_ms * 1e6)
     launches_per_step = 2 * sps  # one launch per half-step covers all 80 samples
     launches = args.steps * launches_per_step
@@ -294,6 +290,12 @@ def run_ours(args, world, rank, local):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, job, workloads, stream, rank, world)
+    serving = None
+    if not args.no_serve:
+        serving = run_serving(args, job, workloads, stream)
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed(args, job, workloads, stream, flush)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -322,6 +324,10 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "wall_s": wall}
     if e2e is not None:
         line["e2e"] = e2e
+    if serving is not None:
+        line["serving"] = serving
+    if mixed is not None:
+        line["mixed_l"] = mixed
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -329,6 +335,102 @@ def run_ours(args, world, rank, local):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_mixed(args, job, workloads, stream, flush):
+    """Mixed-L batch (364 single-sample jobs over L in {24, 48, 64, 96, 128}): the
+    same sweeps as one batched launch per half-step vs per-job launch sequences."""
+    import torch
+
+    specs = workloads.mixed_l_jobs()
+    jobs = []
+    for w in specs:
+        j = job.EAJob(w["L"], w["p_neg"], w["seed"], w["n_samples"], stream=stream)
+        j.quench(w["T"])
+        jobs.append(j)
+    flips_per_sweep = sum(2 * w["n_samples"] * w["L"] ** 3 for w in specs)
+    b = job.EABatch(stream=stream)
+    for j in jobs:
+        b.add(j)
+    cfg = b.autotune(trial_sweeps=8)
+    n_b = args.mixed_sweeps
+    b.sweep(4)
+    ms_b = timed_steps(stream, 3, lambda: b.sweep(n_b), flush)
+    b.close()
+    n_p = max(1, n_b // 8)
+
+    def plain():
+        for j in jobs:
+            j.sweep(n_p)
+
+    plain()
+    ms_p = timed_steps(stream, 3, plain, flush)
+    for j in jobs:
+        j.close()
+    vb = flips_per_sweep * n_b / (min(ms_b) * 1e6)
+    vp = flips_per_sweep * n_p / (min(ms_p) * 1e6)
+    return {"workload": workloads.MIXED_L["name"], "jobs": len(specs),
+            "flips_per_sweep": flips_per_sweep,
+            "batched": {"value": vb, "unit": UNIT, "sweeps": n_b, "ms": min(ms_b),
+                        "cols_per_thread": cfg[0], "graph_sweeps": cfg[1]},
+            "plain": {"value": vp, "unit": UNIT, "sweeps": n_p, "ms": min(ms_p)},
+            "batched_over_plain": vb / vp}
+
+
+def run_serving(args, job, workloads, stream):
+    """Continuous batching of a seeded Poisson stream of ageing jobs (rate 50/s,
+    L in {16, 32, 64, 128}, p_neg in [0.1, 0.5], T in [0.5, 1.0], sweeps
+    log-uniform in [1e3, 1e6]), admitted by footprint.  Latency = completion
+    (results read back on the host) minus the job's scheduled arrival."""
+    import numpy as np
+    import torch
+
+    specs = workloads.serving_stream(args.serve_jobs)
+    srv = job.EAServer(budget_bytes=args.serve_budget_gb << 30, max_running=256,
+                       chunk_sweeps=args.serve_chunk, stream=stream)
+    t_sched = [0, 1, 2, 4, 8, 16, 32, 64, 128, 256, 512]
+    arrival = {}
+    lat = []
+    flips = 0
+    nxt = 0
+    open_ids = []
+    t0 = time.perf_counter()
+    while len(lat) < len(specs):
+        now = time.perf_counter() - t0
+        while nxt < len(specs) and specs[nxt]["arrival"] <= now:
+            sp = specs[nxt]
+            jid = srv.submit(sp["L"], sp["p_neg"], sp["seed"], sp["n_samples"], sp["T"],
+                             sp["sweeps"], t_w=t_sched, t=t_sched)
+            arrival[jid] = sp["arrival"]
+            flips += sp["sweeps"] * 2 * sp["n_samples"] * sp["L"] ** 3
+            open_ids.append(jid)
+            nxt += 1
+        st = srv.stats()
+        if st["running"] == 0 and st["queued"] == 0:
+            if nxt < len(specs):
+                time.sleep(max(0.0, specs[nxt]["arrival"] - now))
+            continue
+        srv.step()
+        still = []
+        for jid in open_ids:
+            state, _ = srv.state(jid)
+            if state == 2:
+                srv.job(jid).measure(0, 512)  # reads the results back (synchronises)
+                lat.append(time.perf_counter() - t0 - arrival[jid])
+                srv.release(jid)
+            else:
+                still.append(jid)
+        open_ids = still
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    return {"workload": workloads.SERVING["name"], "jobs": len(specs),
+            "rate_per_s": workloads.SERVING["rate"], "chunk_sweeps": args.serve_chunk,
+            "latency_s": {"p50": float(np.percentile(lat, 50)),
+                          "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "flips": int(flips), "wall_s": wall, "value": flips / (wall * 1e9), "unit": UNIT}
 
 
 def run_e2e(args, job, workloads, stream, rank, world):
@@ -391,6 +493,12 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--ref-sweeps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-sweeps", type=int, default=64)
+    ap.add_argument("--serve-jobs", type=int, default=40)
+    ap.add_argument("--serve-chunk", type=int, default=1024)
+    ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

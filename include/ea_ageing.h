@@ -316,6 +316,11 @@ int ea_server_submit(ea_server *srv, const ea_job_spec *spec, int64_t *job_id);
  * ea_measure on its context (ea_server_job), which synchronises. */
 int ea_server_step(ea_server *srv, int *n_finished);
 
+/* Launch shape of the running set, as ea_batch_configure (default: 4 word
+ * columns per thread, 16-sweep graphs off the legacy stream).  No result
+ * depends on it. */
+int ea_server_configure(ea_server *srv, int cols_per_thread, int graph_sweeps);
+
 /* State (EA_JOB_*) and time of a job. */
 int ea_server_job_state(const ea_server *srv, int64_t job_id, int *state, uint64_t *time);
 

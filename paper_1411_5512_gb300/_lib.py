@@ -102,6 +102,7 @@ SIGNATURES = {
     "ea_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(EaJobSpec),
                                         ctypes.POINTER(ctypes.c_int64)]),
     "ea_server_step": (ctypes.c_int, [vp, intp]),
+    "ea_server_configure": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
     "ea_server_job_state": (ctypes.c_int, [vp, ctypes.c_int64, intp, u64p]),
     "ea_server_job": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.POINTER(vp)]),
     "ea_server_release": (ctypes.c_int, [vp, ctypes.c_int64]),

@@ -1583,6 +1583,10 @@ int ea_server_create(ea_server **out, size_t budget_bytes, int max_running, uint
         delete srv;
         return rc;
     }
+    // launch shape of the running set: 4 word columns per thread and, off the
+    // legacy stream, 16-sweep graphs (the shape the autotuner picks for large
+    // lattices); ea_server_configure changes it
+    ea_batch_configure(srv->batch, 4, cuda_stream ? 16 : 0);
     *out = srv;
     return EA_OK;
 }
@@ -1681,6 +1685,13 @@ int ea_server_step(ea_server *srv, int *n_finished)
     }
     srv->running.swap(still);
     return EA_OK;
+}
+
+int ea_server_configure(ea_server *srv, int cols_per_thread, int graph_sweeps)
+{
+    if (!srv)
+        return EA_ERR_INVALID_ARG;
+    return ea_batch_configure(srv->batch, cols_per_thread, graph_sweeps);
 }
 
 int ea_server_job_state(const ea_server *srv, int64_t job_id, int *state, uint64_t *time)

@@ -181,43 +181,101 @@ __device__ __forceinline__ uint32_t low_bits(int n)
 }
 
 // g_pop[s][d][r] += sites i where q_i != q_{i + r e_d}, q = replica 0 XOR 1
-__global__ void obs_c4_kernel(const uint32_t *__restrict__ spins, Geo g,
-                              unsigned long long *g_pop)
+// (the overlap field of Eq. 2; its correlation along the axes is Eq. 3).
+//
+// A block stages whole word-lines along axis d (n_d words each, every word a
+// bundle of 32 / k_d lattice lines) as q in shared memory; thread r then sums,
+// over the staged lines, popc(q[i] ^ q[i + r]) with the lanes realigned where
+// the shift crosses the periodic wrap of the word lattice: for r = A n_d + B,
+// positions i + B < n_d read word i + B rotated by A blocks, the others word
+// i + B - n_d rotated by A + 1 blocks (mod k_d).
+constexpr int kC4Words = 2048;  // staged words per block
+
+
+// out[b] = in[b with block index b_d + q (mod k)] for the lanes of axis d
+struct Rot {
+    int sA, sB;
+    uint32_t mA, mB;
+};
+
+__device__ __forceinline__ Rot make_rot(const Geo &g, int d, int q)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    const int R = g.L / 2 + 1;
-    const int d = blockIdx.z / R, r = blockIdx.z % R;
-    const size_t W = (size_t)g.words;
-    unsigned long long cnt = 0;
-    if (w < g.words) {
-        const uint32_t *A0 = spins + (size_t)s * 2 * W, *A1 = A0 + W;
-        int xw, yw, zw;
-        word_coords(g, w, xw, yw, zw);
-        const int coord[3] = {xw, yw, zw};
-        const int step[3] = {1, g.n[0], g.n[0] * g.n[1]};
-        const int nd = g.n[d], kd = g.k[d], st = g.stride[d];
-        const int m = coord[d] + r;
-        const int w2 = w + (m % nd - coord[d]) * step[d];
-        const int qrot = (m / nd) % kd;  // block-index shift of every lane
-        const uint32_t q = A0[w] ^ A1[w];
-        uint32_t q2 = A0[w2] ^ A1[w2];
-        if (qrot != 0) {
-            // lane with block index b_d reads lane b_d + qrot (mod kd)
-            const int period = st * kd;
-            const uint32_t base = low_bits((kd - qrot) * st);
-            uint32_t mA = 0;
-            for (int j = 0; j < g.lanes; j += period)
-                mA |= base << j;
-            mA &= g.valid;
-            const uint32_t mB = g.valid & ~mA;
-            q2 = ((q2 >> (qrot * st)) & mA) | ((q2 << ((kd - qrot) * st)) & mB);
-        }
-        cnt = __popc(q ^ q2);
+    Rot r;
+    const int k = g.k[d], st = g.stride[d];
+    q %= k;
+    if (q == 0) {
+        r.sA = 0;
+        r.sB = 0;
+        r.mA = g.valid;
+        r.mB = 0u;
+        return r;
     }
-    const unsigned long long tot = block_sum(cnt);
-    if (threadIdx.x == 0 && tot)
-        atomicAdd(&g_pop[((size_t)s * 3 + d) * R + r], tot);
+    const int period = st * k;
+    const uint32_t base = low_bits((k - q) * st);
+    uint32_t mA = 0u;
+    for (int j = 0; j < g.lanes; j += period)
+        mA |= base << j;
+    r.mA = mA & g.valid;
+    r.mB = g.valid & ~r.mA;
+    r.sA = q * st;
+    r.sB = (k - q) * st;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t rot(uint32_t w, const Rot &r)
+{
+    return ((w >> r.sA) & r.mA) | ((w << r.sB) & r.mB);
+}
+
+__global__ void __launch_bounds__(256) obs_c4_kernel(const uint32_t *__restrict__ spins, Geo g,
+                                                     unsigned long long *g_pop)
+{
+    __shared__ uint32_t s_q[kC4Words];
+    const int d = blockIdx.y;
+    const int s = blockIdx.z;
+    const int nd = g.n[d];
+    const int n_lines = g.words / nd;
+    const int lines_per_block = kC4Words / nd > 0 ? kC4Words / nd : 1;
+    const int l0 = blockIdx.x * lines_per_block;
+    const int nl = min(lines_per_block, n_lines - l0);  // <= 0: nothing for this block
+    const size_t W = (size_t)g.words;
+    const uint32_t *A0 = spins + (size_t)s * 2 * W, *A1 = A0 + W;
+    // word index of position i of line l along axis d
+    const int n0 = g.n[0], n1 = g.n[1];
+    auto word_of = [&](int l, int i) -> int {
+        if (d == 0)
+            return i + n0 * l;                      // l = y' + n1 z'
+        if (d == 1)
+            return (l % n0) + n0 * (i + n1 * (l / n0));  // l = x' + n0 z'
+        return l + n0 * n1 * i;                     // l = x' + n0 y'
+    };
+    for (int e = threadIdx.x; e < nl * nd; e += blockDim.x) {
+        const int l = e / nd, i = e - l * nd;
+        const int w = word_of(l0 + l, i);
+        s_q[e] = A0[w] ^ A1[w];
+    }
+    __syncthreads();
+    const int R = g.L / 2 + 1;
+    // thread (group gi, shift r): the lane rotations of r are set up once, and
+    // the groups split the staged lines between them
+    const int groups = blockDim.x / R > 0 ? blockDim.x / R : 1;
+    for (int task = threadIdx.x; task < groups * R; task += blockDim.x) {
+        const int gi = task / R, r = task - gi * R;
+        const int A = r / nd, B = r - A * nd;
+        const Rot r0 = make_rot(g, d, A), r1 = make_rot(g, d, A + 1);
+        unsigned long long cnt = 0;
+        for (int l = gi; l < nl; l += groups) {
+            const uint32_t *q = s_q + l * nd;
+            unsigned int c = 0;
+            for (int i = 0; i < nd - B; ++i)
+                c += __popc(q[i] ^ rot(q[i + B], r0));
+            for (int i = nd - B; i < nd; ++i)
+                c += __popc(q[i] ^ rot(q[i + B - nd], r1));
+            cnt += c;
+        }
+        if (cnt)
+            atomicAdd(&g_pop[((size_t)s * 3 + d) * R + r], cnt);
+    }
 }
 
 constexpr int kBlock = 256;
@@ -268,8 +326,16 @@ cudaError_t launch_obs_autocorr(const uint32_t *snap, const uint32_t *spins, con
 cudaError_t launch_obs_c4(const uint32_t *spins, const Geo &g, int n_samples,
                           unsigned long long *g_pop, cudaStream_t stream)
 {
-    const int R = g.L / 2 + 1;
-    obs_c4_kernel<<<grid_for(g, n_samples, 3 * R), kBlock, 0, stream>>>(spins, g, g_pop);
+    // a block stages up to kC4Words words of whole lines of one axis
+    unsigned bx = 1;
+    for (int d = 0; d < 3; ++d) {
+        const int lpb = kC4Words / g.n[d] > 0 ? kC4Words / g.n[d] : 1;
+        const int lines = g.words / g.n[d];
+        const unsigned b = (unsigned)((lines + lpb - 1) / lpb);
+        bx = b > bx ? b : bx;
+    }
+    const dim3 grid(bx, 3u, (unsigned)n_samples);
+    obs_c4_kernel<<<grid, 256, 0, stream>>>(spins, g, g_pop);
     return cudaGetLastError();
 }
 

@@ -103,80 +103,71 @@ __device__ __forceinline__ Count count6(uint32_t u0, uint32_t u1, uint32_t u2, u
 }
 
 // ---------------------------------------------------------------------------
-// Metropolis: the accepted lanes of one word when a class test hit
+// Metropolis: the accepted lanes of one class of a word whose class test hit
 // ---------------------------------------------------------------------------
 // Draw d of class u: call 0 output (class 2: d = 0 -> 0, d = 1 -> 1; class 1:
 // d = 0 -> 2; class 0: d = 0 -> 3); later draws e = d - f_u (f = 1, 1, 2) are
 // output e mod 4 of call 1 + u + 3 (e div 4).  Low words: call + 64.
-__device__ __forceinline__ uint32_t metro_rare(const JobDev *__restrict__ jb, uint32_t M0,
-                                            uint32_t M1, uint32_t M2, uint4 R, uint32_t w,
-                                            uint32_t c1, uint32_t c2, uint32_t c3,
-                                            unsigned int *extra_calls)
+__device__ __forceinline__ uint32_t metro_class(const JobDev *__restrict__ jb, int u, uint32_t Mr,
+                                                const uint4 &R, uint32_t w, uint32_t c1,
+                                                uint32_t c2, uint32_t c3, unsigned int &calls)
 {
     uint32_t acc = 0u;
-    const uint32_t Ms[3] = {M0, M1, M2};
-    for (int u = 0; u < 3; ++u) {
-        uint32_t Mr = Ms[u];
-        int rem = __popc(Mr);
-        int d = 0;
-        while (rem > 0) {
-            int call, out;
-            const int f = u == 2 ? 2 : 1;
-            if (d < f) {
-                call = 0;
-                out = u == 2 ? d : 3 - u;
-            } else {
-                const int e = d - f;
-                call = 1 + u + 3 * (e >> 2);
-                out = e & 3;
-            }
+    int rem = __popc(Mr);
+    int d = 0;
+    const int f = u == 2 ? 2 : 1;
+    while (rem > 0) {
+        int call, out;
+        if (d < f) {
+            call = 0;
+            out = u == 2 ? d : 3 - u;
+        } else {
+            const int e = d - f;
+            call = 1 + u + 3 * (e >> 2);
+            out = e & 3;
+        }
+        uint32_t vhi;
+        if (call == 0) {
+            vhi = comp(R, out);
+        } else {
             uint32_t rk[20];
-            bool have_rk = false;
-            uint32_t vhi;
-            if (call == 0) {
-                vhi = comp(R, out);
-            } else {
+#pragma unroll
+            for (int i = 0; i < 20; ++i)
+                rk[i] = jb->rk[i];
+            vhi = comp(dev::philox10_rk(make_uint4(w, c1, c2 | (uint32_t)call, c3), rk), out);
+            ++calls;
+        }
+        bool have_lo = false;
+        uint32_t vlo = 0u;
+        // V < C_u[g], fetching V's low word only when the high words tie
+        auto below = [&](int g) -> bool {
+            const uint32_t ch = jb->gC_hi[u][g];
+            if (vhi != ch)
+                return vhi < ch;
+            if (!have_lo) {
+                uint32_t rk[20];
 #pragma unroll
                 for (int i = 0; i < 20; ++i)
                     rk[i] = jb->rk[i];
-                have_rk = true;
-                vhi = comp(dev::philox10_rk(make_uint4(w, c1, c2 | (uint32_t)call, c3), rk), out);
-                ++*extra_calls;
+                vlo = comp(dev::philox10_rk(make_uint4(w, c1, c2 | (uint32_t)(call + 64), c3),
+                                            rk),
+                           out);
+                ++calls;
+                have_lo = true;
             }
-            bool have_lo = false;
-            uint32_t vlo = 0u;
-            // V < C_u[g], fetching V's low word only when the high words tie
-            auto below = [&](int g) -> bool {
-                const uint32_t ch = jb->gC_hi[u][g];
-                if (vhi != ch)
-                    return vhi < ch;
-                if (!have_lo) {
-                    if (!have_rk) {
-#pragma unroll
-                        for (int i = 0; i < 20; ++i)
-                            rk[i] = jb->rk[i];
-                        have_rk = true;
-                    }
-                    vlo = comp(dev::philox10_rk(
-                                   make_uint4(w, c1, c2 | (uint32_t)(call + 64), c3), rk),
-                               out);
-                    ++*extra_calls;
-                    have_lo = true;
-                }
-                return vlo < jb->gC_lo[u][g];
-            };
-            if (!below(rem))
-                break;
-            int G = 0;
-            while (!below(G + 1))
-                ++G;
-            for (int i = 0; i < G; ++i)
-                Mr &= Mr - 1u;
-            acc |= Mr & (0u - Mr);  // the lane of rank G among the remaining ones
+            return vlo < jb->gC_lo[u][g];
+        };
+        if (!below(rem))
+            break;
+        int G = 0;
+        while (!below(G + 1))
+            ++G;
+        for (int i = 0; i < G; ++i)
             Mr &= Mr - 1u;
-            rem -= G + 1;
-            ++d;
-        }
+        acc |= Mr & (0u - Mr);  // the lane of rank G among the remaining ones
+        Mr &= Mr - 1u;
+        rem -= G + 1;
+        ++d;
     }
     return acc;
 }
@@ -208,12 +199,36 @@ __device__ __forceinline__ bool class_hit(const Classes &k, const uint4 &R,
     return h0 | h1 | h2;
 }
 
+// Words whose class test hit wait in a per-warp queue and are finished by the
+// whole warp at once, one word per lane, so the rare path runs converged.
+constexpr int kQueue = 96;  // entries per warp (up to 64 are added per step)
+
+struct Pending {
+    uint32_t w, base, M0, M1, M2, c2;
+    uint4 R;
+};
+
+__device__ __forceinline__ void finish_word(const JobDev *__restrict__ jb, const Pending &e,
+                                            uint32_t *__restrict__ upd, uint32_t valid,
+                                            uint32_t c1, uint32_t c3, unsigned int &calls)
+{
+    uint32_t A = 0u;
+    if (e.M0)
+        A |= metro_class(jb, 0, e.M0, e.R, e.w, c1, e.c2, c3, calls);
+    if (e.M1)
+        A |= metro_class(jb, 1, e.M1, e.R, e.w, c1, e.c2, c3, calls);
+    if (e.M2)
+        A |= metro_class(jb, 2, e.M2, e.R, e.w, c1, e.c2, c3, calls);
+    upd[e.w] = e.base ^ (A & valid);
+}
+
 template <bool COUNT>
 __global__ void __launch_bounds__(kSweepThreads, 6)
     metro_kernel(const JobDev *__restrict__ jobs, const int *__restrict__ block_begin, int n_jobs,
                  int h, uint32_t sweep_offset, unsigned long long *counters)
 {
     __shared__ uint32_t s_gh[3][33];
+    __shared__ Pending s_q[kSweepThreads / 32][kQueue];
     __shared__ int s_job;
     if (threadIdx.x == 0)
         s_job = find_job(block_begin, n_jobs);
@@ -226,6 +241,9 @@ __global__ void __launch_bounds__(kSweepThreads, 6)
     if (t >= jb->t_end)
         return;  // this job has stopped (uniform over the block)
 
+    const int lane = threadIdx.x & 31;
+    Pending *q = s_q[threadIdx.x >> 5];
+    int q_n = 0;  // warp-uniform queue length
     const int local = (int)blockIdx.x - block_begin[s_job];
     const int bps = jb->blocks_per_sample;
     const int s = local / bps;
@@ -233,6 +251,7 @@ __global__ void __launch_bounds__(kSweepThreads, 6)
     const int cols = jb->cols;
     const int cpt = jb->cols_per_thread;
     const int n0 = jb->geo.n[0], n1 = jb->geo.n[1], n2 = jb->geo.n[2];
+    const bool fix_x = jb->geo.k[0] > 1, fix_y = jb->geo.k[1] > 1;
     const uint32_t valid = jb->geo.valid;
     const uint32_t magic = jb->div_n0_magic;
     const int dshift = jb->div_n0_shift;
@@ -244,8 +263,12 @@ __global__ void __launch_bounds__(kSweepThreads, 6)
 #pragma unroll
     for (int i = 0; i < 20; ++i)
         rk[i] = jb->rk[i];
-    Axis az;
+    Axis az, ax, ay;
     load_axis(az, jb->geo, 2);
+    if (fix_x)
+        load_axis(ax, jb->geo, 0);
+    if (fix_y)
+        load_axis(ay, jb->geo, 1);
     const size_t W = (size_t)jb->geo.words;
     uint32_t *__restrict__ upd = jb->spins + ((size_t)s * 2 + h) * W;
     const uint32_t *__restrict__ nb = jb->spins + ((size_t)s * 2 + (h ^ 1)) * W;
@@ -259,9 +282,11 @@ __global__ void __launch_bounds__(kSweepThreads, 6)
     unsigned int n_words = 0, n_calls = 0, n_extra = 0;
 
     for (int k = 0; k < cpt; ++k) {
-        const int col = (cb * cpt + k) * kSweepThreads + (int)threadIdx.x;
-        if (col >= cols)
+        const int col0 = (cb * cpt + k) * kSweepThreads + (int)threadIdx.x;
+        const bool act = col0 < cols;  // lanes past the last column idle in step
+        if (__all_sync(0xffffffffu, !act))
             break;
+        const int col = act ? col0 : 0;
         const int y = (int)((__umulhi((uint32_t)col, magic) + (uint32_t)col) >> dshift);
         const int x = col - y * n0;
         int cxp = col + 1, cxm = col - 1, cyp = col + n0, cym = col - n0;
@@ -274,11 +299,6 @@ __global__ void __launch_bounds__(kSweepThreads, 6)
             cyp = col - (n1 - 1) * n0;
         if (wym)
             cym = col + (n1 - 1) * n0;
-        Axis ax, ay;
-        if (wxp || wxm)
-            load_axis(ax, jb->geo, 0);
-        if (wyp || wym)
-            load_axis(ay, jb->geo, 1);
         // replica updated at word-site (x, y, z) in half-step h: h ^ ((x + y + z) & 1)
         const uint32_t c2e = c2m | ((uint32_t)(h ^ ((x + y) & 1)) << 11);      // even z
         const uint32_t c2o = c2m | ((uint32_t)(h ^ ((x + y + 1) & 1)) << 11);  // odd z
@@ -299,25 +319,29 @@ __global__ void __launch_bounds__(kSweepThreads, 6)
             uint32_t jxmb = Jx[cxm + z * sz + sz], jymb = Jy[cym + z * sz + sz];
             const uint32_t jxa = Jx[wa], jya = Jy[wa], jza = Jz[wa];
             const uint32_t jxb = Jx[wb], jyb = Jy[wb], jzb = Jz[wb];
-            if (wxp) {
-                nxpa = fixup(nxpa, ax, 0);
-                nxpb = fixup(nxpb, ax, 0);
+            if (fix_x) {
+                if (wxp) {
+                    nxpa = fixup(nxpa, ax, 0);
+                    nxpb = fixup(nxpb, ax, 0);
+                }
+                if (wxm) {
+                    nxma = fixup(nxma, ax, 1);
+                    nxmb = fixup(nxmb, ax, 1);
+                    jxma = fixup(jxma, ax, 1);
+                    jxmb = fixup(jxmb, ax, 1);
+                }
             }
-            if (wxm) {
-                nxma = fixup(nxma, ax, 1);
-                nxmb = fixup(nxmb, ax, 1);
-                jxma = fixup(jxma, ax, 1);
-                jxmb = fixup(jxmb, ax, 1);
-            }
-            if (wyp) {
-                nypa = fixup(nypa, ay, 0);
-                nypb = fixup(nypb, ay, 0);
-            }
-            if (wym) {
-                nyma = fixup(nyma, ay, 1);
-                nymb = fixup(nymb, ay, 1);
-                jyma = fixup(jyma, ay, 1);
-                jymb = fixup(jymb, ay, 1);
+            if (fix_y) {
+                if (wyp) {
+                    nypa = fixup(nypa, ay, 0);
+                    nypb = fixup(nypb, ay, 0);
+                }
+                if (wym) {
+                    nyma = fixup(nyma, ay, 1);
+                    nymb = fixup(nymb, ay, 1);
+                    jyma = fixup(jyma, ay, 1);
+                    jymb = fixup(jymb, ay, 1);
+                }
             }
             // word b's -z neighbour is the neighbour area at z; its backward z bond is jza
             const Count ca = count6(spa ^ nxpa ^ jxa, spa ^ nxma ^ jxma, spa ^ nypa ^ jya,
@@ -330,39 +354,76 @@ __global__ void __launch_bounds__(kSweepThreads, 6)
 
             const uint32_t alwa = ca.b2 | (ca.b1 & ca.b0);  // u >= 3 <=> dE <= 0
             const uint32_t alwb = cw.b2 | (cw.b1 & cw.b0);
-            uint32_t fa, fb;
-            if (all_always) {
-                fa = fb = 0xffffffffu;
-            } else if (none_random) {
-                fa = alwa;
-                fb = alwb;
-            } else {
-                const Classes ka = classes(ca, alwa, valid, live0, live1, live2);
-                const Classes kb = classes(cw, alwb, valid, live0, live1, live2);
-                // first draws of both words: two independent Philox chains
-                const uint4 Ra = dev::philox10_rk(make_uint4((uint32_t)wa, c1, c2e, c3), rk);
-                const uint4 Rb = dev::philox10_rk(make_uint4((uint32_t)wb, c1, c2o, c3), rk);
-                if (COUNT)
-                    n_calls += ((ka.M0 | ka.M1 | ka.M2) != 0u) + ((kb.M0 | kb.M1 | kb.M2) != 0u);
-                uint32_t Aa = 0u, Ab = 0u;
-                const bool ha = class_hit(ka, Ra, s_gh), hb = class_hit(kb, Rb, s_gh);
+            if (all_always || none_random) {
+                if (act) {
+                    upd[wa] = spa ^ ((all_always ? 0xffffffffu : alwa) & valid);
+                    upd[wb] = spb ^ ((all_always ? 0xffffffffu : alwb) & valid);
+                }
+                if (COUNT && act)
+                    n_words += 2;
+                continue;
+            }
+            const Classes ka = classes(ca, alwa, valid, live0, live1, live2);
+            const Classes kb = classes(cw, alwb, valid, live0, live1, live2);
+            // first draws of both words: two independent Philox chains
+            const uint4 Ra = dev::philox10_rk(make_uint4((uint32_t)wa, c1, c2e, c3), rk);
+            const uint4 Rb = dev::philox10_rk(make_uint4((uint32_t)wb, c1, c2o, c3), rk);
+            if (COUNT && act)
+                n_calls += ((ka.M0 | ka.M1 | ka.M2) != 0u) + ((kb.M0 | kb.M1 | kb.M2) != 0u);
+            const bool ha = act && class_hit(ka, Ra, s_gh);
+            const bool hb = act && class_hit(kb, Rb, s_gh);
+            const uint32_t basea = spa ^ (alwa & valid), baseb = spb ^ (alwb & valid);
+            if (act && !ha)
+                upd[wa] = basea;
+            if (act && !hb)
+                upd[wb] = baseb;
+            if (COUNT && act)
+                n_words += 2;
+            // queue the words that may flip more lanes
+            const uint32_t ba = __ballot_sync(0xffffffffu, ha);
+            const uint32_t bbm = __ballot_sync(0xffffffffu, hb);
+            const uint32_t below_me = (1u << lane) - 1u;
+            if (ha) {
+                Pending &e = q[q_n + __popc(ba & below_me)];
+                e.w = (uint32_t)wa;
+                e.base = basea;
+                e.M0 = ka.M0;
+                e.M1 = ka.M1;
+                e.M2 = ka.M2;
+                e.c2 = c2e;
+                e.R = Ra;
+            }
+            q_n += __popc(ba);
+            if (hb) {
+                Pending &e = q[q_n + __popc(bbm & below_me)];
+                e.w = (uint32_t)wb;
+                e.base = baseb;
+                e.M0 = kb.M0;
+                e.M1 = kb.M1;
+                e.M2 = kb.M2;
+                e.c2 = c2o;
+                e.R = Rb;
+            }
+            q_n += __popc(bbm);
+            __syncwarp();
+            while (q_n >= 32) {  // a full round: one queued word per lane
+                q_n -= 32;
+                const Pending e = q[q_n + lane];
                 unsigned int extra = 0;
-                if (ha)
-                    Aa = metro_rare(jb, ka.M0, ka.M1, ka.M2, Ra, (uint32_t)wa, c1, c2e, c3,
-                                    &extra);
-                if (hb)
-                    Ab = metro_rare(jb, kb.M0, kb.M1, kb.M2, Rb, (uint32_t)wb, c1, c2o, c3,
-                                    &extra);
+                finish_word(jb, e, upd, valid, c1, c3, extra);
                 if (COUNT)
                     n_extra += extra;
-                fa = alwa | Aa;
-                fb = alwb | Ab;
+                __syncwarp();
             }
-            upd[wa] = spa ^ (fa & valid);
-            upd[wb] = spb ^ (fb & valid);
-            if (COUNT)
-                n_words += 2;
         }
+    }
+    // the last, partial round
+    if (lane < q_n) {
+        const Pending e = q[lane];
+        unsigned int extra = 0;
+        finish_word(jb, e, upd, valid, c1, c3, extra);
+        if (COUNT)
+            n_extra += extra;
     }
     if (COUNT) {
         atomicAdd(&counters[0], (unsigned long long)n_words);

@@ -272,6 +272,10 @@ class EAServer:
         self._keep[jid.value] = (int(L), int(n_samples))
         return jid.value
 
+    def configure(self, cols_per_thread=4, graph_sweeps=16):
+        _lib.check(self.lib.ea_server_configure(self.h, int(cols_per_thread), int(graph_sweeps)),
+                   server=self.h)
+
     def step(self):
         n = ctypes.c_int()
         _lib.check(self.lib.ea_server_step(self.h, ctypes.byref(n)), server=self.h)
