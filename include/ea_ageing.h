@@ -332,6 +332,11 @@ int ea_server_job(ea_server *srv, int64_t job_id, ea_ctx **job);
  * EA_ERR_STATE unless the job is done. */
 int ea_server_release(ea_server *srv, int64_t job_id);
 
+/* Cancel a queued or running job: it leaves the queue or the batch at once
+ * (work already enqueued completes first) and its memory is freed.  A done
+ * job is released.  EA_ERR_INVALID_ARG for an unknown id. */
+int ea_server_cancel(ea_server *srv, int64_t job_id);
+
 int ea_server_get_stats(const ea_server *srv, ea_server_stats *out);
 
 /* Destroy the server and every job it still holds.  NULL is accepted. */

@@ -106,6 +106,7 @@ SIGNATURES = {
     "ea_server_job_state": (ctypes.c_int, [vp, ctypes.c_int64, intp, u64p]),
     "ea_server_job": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.POINTER(vp)]),
     "ea_server_release": (ctypes.c_int, [vp, ctypes.c_int64]),
+    "ea_server_cancel": (ctypes.c_int, [vp, ctypes.c_int64]),
     "ea_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(EaServerStats)]),
     "ea_server_destroy": (ctypes.c_int, [vp]),
     "ea_server_last_error": (ctypes.c_char_p, [vp]),

@@ -365,10 +365,10 @@ int upload_time(ea_ctx *c, uint64_t t_end)
 int launch_plain(ea_ctx *c, uint64_t n)
 {
     const bool heat = c->rule == EA_RULE_HEATBATH;
-    EA_CUDA(c, ea::launch_sweep_table(heat ? nullptr : c->jd_dev, heat ? nullptr : c->bb_dev,
-                                      heat ? 0 : 1, heat ? 0 : c->blocks,
-                                      heat ? c->jd_dev : nullptr, heat ? c->bb_dev : nullptr,
-                                      heat ? 1 : 0, heat ? c->blocks : 0, n, c->stream));
+    EA_CUDA(c, ea::launch_sweep_table(heat ? nullptr : &c->jd, heat ? nullptr : c->jd_dev,
+                                      heat ? 0 : 1, heat ? c->jd_dev : nullptr,
+                                      heat ? c->bb_dev : nullptr, heat ? 1 : 0,
+                                      heat ? c->blocks : 0, n, c->stream));
     return EA_OK;
 }
 
@@ -1107,6 +1107,10 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
         b->tab_host[r].push_back(jd);
         b->bb_host[r].push_back(b->bb_host[r].back() + m->S * jd.blocks_per_sample);
     }
+    // equal sides next to each other: runs of one L share a specialised launch
+    // (the order of rows changes no result)
+    std::stable_sort(b->tab_host[0].begin(), b->tab_host[0].end(),
+                     [](const ea::JobDev &a, const ea::JobDev &c) { return a.geo.L < c.geo.L; });
     for (int r = 0; r < 2; ++r) {
         const size_t n = b->tab_host[r].size();
         b->n_jobs[r] = (int)n;
@@ -1133,7 +1137,7 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
 
 int enqueue_direct(ea_batch *b, uint64_t n, unsigned long long *counters = nullptr)
 {
-    EA_BCUDA(b, ea::launch_sweep_table(b->tab_dev[0], b->bb_dev[0], b->n_jobs[0], b->blocks[0],
+    EA_BCUDA(b, ea::launch_sweep_table(b->tab_host[0].data(), b->tab_dev[0], b->n_jobs[0],
                                        b->tab_dev[1], b->bb_dev[1], b->n_jobs[1], b->blocks[1], n,
                                        b->stream, counters));
     for (int r = 0; r < 2; ++r)
@@ -1732,6 +1736,29 @@ int ea_server_release(ea_server *srv, int64_t job_id)
         return sfail(srv, EA_ERR_STATE, "job not done");
     ea_destroy(j->ctx);
     srv->in_use -= j->bytes;
+    srv->jobs.erase(it);
+    delete j;
+    return EA_OK;
+}
+
+int ea_server_cancel(ea_server *srv, int64_t job_id)
+{
+    if (!srv)
+        return EA_ERR_INVALID_ARG;
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end())
+        return sfail(srv, EA_ERR_INVALID_ARG, "unknown job");
+    ServerJob *j = it->second;
+    if (j->state == EA_JOB_QUEUED) {
+        srv->queue.erase(std::find(srv->queue.begin(), srv->queue.end(), j));
+    } else if (j->state == EA_JOB_RUNNING) {
+        ea_batch_remove(srv->batch, j->ctx);
+        srv->running.erase(std::find(srv->running.begin(), srv->running.end(), j));
+    }
+    if (j->ctx) {
+        ea_destroy(j->ctx);
+        srv->in_use -= j->bytes;
+    }
     srv->jobs.erase(it);
     delete j;
     return EA_OK;

@@ -102,14 +102,57 @@ void fill_job_layout(JobDev *jd, int cols_per_thread);
 
 constexpr int kSweepThreads = 128;
 
-// Enqueue n sweeps of every job of a table: 2n launches (one per half-step)
-// per rule present.  jobs_dev/block_begin_dev describe the table on the device,
-// n_blocks[rule] is the grid of the launch for that rule (0: none).
-cudaError_t launch_sweep_table(const JobDev *jobs_dev_rule0, const int *bb_dev_rule0,
-                               int n_jobs_rule0, int blocks_rule0,
-                               const JobDev *jobs_dev_rule1, const int *bb_dev_rule1,
-                               int n_jobs_rule1, int blocks_rule1, uint64_t n,
-                               cudaStream_t stream, unsigned long long *counters = nullptr);
+// What the Metropolis sweep kernel reads on every word, passed in the launch's
+// parameter block: indexed by a block-uniform job number, it goes through the
+// uniform datapath and costs no per-thread registers.  Jobs of one side share
+// a geometry record; a job record is 32 bytes, so one launch holds hundreds
+// of jobs.
+struct MetroGeo {
+    int n0, n1, n2, cols;
+    int bps, cpt;          // blocks per sample, word columns per thread
+    uint32_t words;        // words per area
+    uint32_t valid, magic;
+    int dshift;
+    uint32_t fix;          // bit 0: lanes realign across the x wrap, bit 1: y wrap
+    int zsA[2], zsB[2];    // lane realignment across the periodic wrap along z
+    uint32_t zmA[2], zmB[2];
+};
+
+struct MetroJob {
+    uint32_t *spins;
+    const uint32_t *J;
+    uint32_t key0, key1;   // Philox key (the seed); round keys are derived per block
+    uint32_t rng_group;
+    uint32_t meta;         // bits 0-2 live classes, 3 all_always, 4 none_random, 8-15 geometry
+};
+
+constexpr int kMetroMaxGeo = 8;
+constexpr int kMetroMaxJobs = 768;  // jobs per launch (parameter block <= 32 KB)
+
+// A launch's job table, sized for at most MAXJ jobs; a launch takes the
+// smallest size that holds its jobs, so small tables do not pay for copying a
+// large parameter block.
+template <int MAXJ>
+struct MetroParams {
+    const JobDev *jobs_dev;  // the same jobs' device rows: t, t_end, tables
+    int n_jobs;
+    int h;
+    uint32_t sweep_offset;
+    MetroGeo geo[kMetroMaxGeo];
+    int block_begin[MAXJ + 1];
+    MetroJob job[MAXJ];
+};
+
+static_assert(sizeof(MetroParams<kMetroMaxJobs>) <= 32000, "kernel parameter block limit");
+
+// Enqueue n sweeps of every job of a table: one launch per half-step per rule
+// (Metropolis tables of more than kMetroMaxJobs jobs take several).  host0 and
+// dev0 are the host and device copies of the Metropolis rows; the heat-bath
+// rows are read from dev1 with block offsets bb_dev1 (blocks1 blocks).
+cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
+                               const JobDev *dev1, const int *bb_dev1, int n_jobs1, int blocks1,
+                               uint64_t n, cudaStream_t stream,
+                               unsigned long long *counters = nullptr);
 
 // Add n to the time field of every job of a table, stopping at its t_end
 // (device side, for graphs).

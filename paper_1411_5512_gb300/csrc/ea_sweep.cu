@@ -24,6 +24,7 @@
 //     threshold bit.
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "ea_device.cuh"
 #include "ea_internal.h"
@@ -222,72 +223,95 @@ __device__ __forceinline__ void finish_word(const JobDev *__restrict__ jb, const
     upd[e.w] = e.base ^ (A & valid);
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(kSweepThreads, 6)
-    metro_kernel(const JobDev *__restrict__ jobs, const int *__restrict__ block_begin, int n_jobs,
-                 int h, uint32_t sweep_offset, unsigned long long *counters)
+// GL = 0: geometry read from the job table; GL = 64 or 128: every job of the
+// launch has side GL, whose word lattice is GL x GL x GL/32 with no lane
+// realignment along x or y, fixed at compile time.
+template <bool COUNT, int MAXJ, int GL>
+__global__ void __launch_bounds__(kSweepThreads, 10)
+    metro_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
 {
+    constexpr bool STATIC = GL != 0;
+    constexpr int SLOG = GL == 128 ? 7 : 6;
+    // the job of this block, found from blockIdx alone: the loads below stay
+    // in the uniform datapath
+    int j = 0;
+    {
+        int lo = 0, hi = P.n_jobs - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.block_begin[mid] <= b)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    const MetroJob &J = P.job[j];
+    const MetroGeo &G = P.geo[(J.meta >> 8) & 0xFFu];
+    const JobDev *__restrict__ jb = P.jobs_dev + j;
+    uint32_t rk[20];  // round keys of the job's Philox key (block-uniform)
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = J.key0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = J.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     __shared__ uint32_t s_gh[3][33];
     __shared__ Pending s_q[kSweepThreads / 32][kQueue];
-    __shared__ int s_job;
-    if (threadIdx.x == 0)
-        s_job = find_job(block_begin, n_jobs);
-    __syncthreads();
-    const JobDev *__restrict__ jb = &jobs[s_job];
     for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x)
         (&s_gh[0][0])[i] = (&jb->gC_hi[0][0])[i];
     __syncthreads();
-    const uint64_t t = jb->t + sweep_offset;
+    const uint64_t t = jb->t + P.sweep_offset;
     if (t >= jb->t_end)
         return;  // this job has stopped (uniform over the block)
 
+    const int h = P.h;
     const int lane = threadIdx.x & 31;
     Pending *q = s_q[threadIdx.x >> 5];
     int q_n = 0;  // warp-uniform queue length
-    const int local = (int)blockIdx.x - block_begin[s_job];
-    const int bps = jb->blocks_per_sample;
-    const int s = local / bps;
-    const int cb = local - s * bps;
-    const int cols = jb->cols;
-    const int cpt = jb->cols_per_thread;
-    const int n0 = jb->geo.n[0], n1 = jb->geo.n[1], n2 = jb->geo.n[2];
-    const bool fix_x = jb->geo.k[0] > 1, fix_y = jb->geo.k[1] > 1;
-    const uint32_t valid = jb->geo.valid;
-    const uint32_t magic = jb->div_n0_magic;
-    const int dshift = jb->div_n0_shift;
-    const bool all_always = jb->all_always != 0;
-    const bool none_random = jb->none_random != 0;
-    const uint32_t live0 = 0u - (jb->geo_live & 1u), live1 = 0u - ((jb->geo_live >> 1) & 1u),
-                   live2 = 0u - ((jb->geo_live >> 2) & 1u);
-    uint32_t rk[20];
-#pragma unroll
-    for (int i = 0; i < 20; ++i)
-        rk[i] = jb->rk[i];
+    const int local = (int)blockIdx.x - P.block_begin[j];
+    const int s = local / G.bps;
+    const int cb = local - s * G.bps;
+    const int n0 = STATIC ? GL : G.n0, n1 = STATIC ? GL : G.n1, n2 = STATIC ? GL / 32 : G.n2;
+    const bool all_always = (J.meta >> 3) & 1u, none_random = (J.meta >> 4) & 1u;
+    const bool fix_x = STATIC ? false : (G.fix & 1u) != 0;
+    const bool fix_y = STATIC ? false : (G.fix & 2u) != 0;
+    const uint32_t valid = STATIC ? 0xffffffffu : G.valid;
+    const uint32_t live0 = 0u - (J.meta & 1u), live1 = 0u - ((J.meta >> 1) & 1u),
+                   live2 = 0u - ((J.meta >> 2) & 1u);
     Axis az, ax, ay;
-    load_axis(az, jb->geo, 2);
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+        az.sA[dir] = G.zsA[dir];
+        az.sB[dir] = G.zsB[dir];
+        az.mA[dir] = G.zmA[dir];
+        az.mB[dir] = G.zmB[dir];
+    }
     if (fix_x)
         load_axis(ax, jb->geo, 0);
     if (fix_y)
         load_axis(ay, jb->geo, 1);
-    const size_t W = (size_t)jb->geo.words;
-    uint32_t *__restrict__ upd = jb->spins + ((size_t)s * 2 + h) * W;
-    const uint32_t *__restrict__ nb = jb->spins + ((size_t)s * 2 + (h ^ 1)) * W;
-    const uint32_t *__restrict__ Jx = jb->J + (size_t)s * 3 * W;
+    const uint32_t W = STATIC ? (uint32_t)GL * GL * (GL / 32) : G.words;
+    uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
+    const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
+    const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
     const uint32_t *__restrict__ Jy = Jx + W;
     const uint32_t *__restrict__ Jz = Jy + W;
-    const uint32_t c3 = (uint32_t)s / jb->rng_group;
+    const uint32_t c3 = (uint32_t)s / J.rng_group;
     const uint32_t c1 = (uint32_t)t;
     const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
     const int sz = n0 * n1;
     unsigned int n_words = 0, n_calls = 0, n_extra = 0;
 
-    for (int k = 0; k < cpt; ++k) {
-        const int col0 = (cb * cpt + k) * kSweepThreads + (int)threadIdx.x;
+    const int cols = STATIC ? GL * GL : G.cols;
+    for (int k = 0; k < G.cpt; ++k) {
+        const int col0 = (cb * G.cpt + k) * kSweepThreads + (int)threadIdx.x;
         const bool act = col0 < cols;  // lanes past the last column idle in step
         if (__all_sync(0xffffffffu, !act))
             break;
         const int col = act ? col0 : 0;
-        const int y = (int)((__umulhi((uint32_t)col, magic) + (uint32_t)col) >> dshift);
+        const int y = STATIC ? (col >> SLOG)
+                             : (int)((__umulhi((uint32_t)col, G.magic) + (uint32_t)col) >> G.dshift);
         const int x = col - y * n0;
         int cxp = col + 1, cxm = col - 1, cyp = col + n0, cym = col - n0;
         const bool wxp = (x + 1 == n0), wxm = (x == 0), wyp = (y + 1 == n1), wym = (y == 0);
@@ -306,6 +330,7 @@ __global__ void __launch_bounds__(kSweepThreads, 6)
         uint32_t nz_prev = fixup(nb[col + (n2 - 1) * sz], az, 1);
         uint32_t jz_prev = fixup(Jz[col + (n2 - 1) * sz], az, 1);
         uint32_t nz_cur = nb[col];
+#pragma unroll(STATIC ? GL / 64 : 1)
         for (int z = 0; z < n2; z += 2) {  // n2 is even: words at z (a) and z + 1 (b)
             const int wa = col + z * sz, wb = wa + sz;
             const uint32_t nz_b = nb[wb];                                             // z + 1
@@ -665,28 +690,144 @@ void fill_job_layout(JobDev *jd, int cols_per_thread)
     jd->blocks_per_sample = (jd->cols + per_block - 1) / per_block;
 }
 
-cudaError_t launch_sweep_table(const JobDev *jobs0, const int *bb0, int n_jobs0, int blocks0,
-                               const JobDev *jobs1, const int *bb1, int n_jobs1, int blocks1,
+static void metro_geo(MetroGeo &g, const JobDev &jd)
+{
+    std::memset(&g, 0, sizeof(g));
+    g.n0 = jd.geo.n[0];
+    g.n1 = jd.geo.n[1];
+    g.n2 = jd.geo.n[2];
+    g.cols = jd.cols;
+    g.bps = jd.blocks_per_sample;
+    g.cpt = jd.cols_per_thread;
+    g.words = (uint32_t)jd.geo.words;
+    g.valid = jd.geo.valid;
+    g.magic = jd.div_n0_magic;
+    g.dshift = jd.div_n0_shift;
+    g.fix = (jd.geo.k[0] > 1 ? 1u : 0u) | (jd.geo.k[1] > 1 ? 2u : 0u);
+    for (int dir = 0; dir < 2; ++dir) {
+        g.zsA[dir] = jd.geo.sA[2][dir];
+        g.zsB[dir] = jd.geo.sB[2][dir];
+        g.zmA[dir] = jd.geo.mA[2][dir];
+        g.zmB[dir] = jd.geo.mB[2][dir];
+    }
+}
+
+static void metro_job(MetroJob &m, const JobDev &jd, int geo_index)
+{
+    m.spins = jd.spins;
+    m.J = jd.J;
+    m.key0 = jd.rk[0];
+    m.key1 = jd.rk[1];
+    m.rng_group = jd.rng_group;
+    m.meta = (jd.geo_live & 7u) | (jd.all_always ? 8u : 0u) | (jd.none_random ? 16u : 0u) |
+             ((uint32_t)geo_index << 8);
+}
+
+// Jobs host[0..cnt) in one launch sequence; all of them share at most
+// kMetroMaxGeo (side, layout) geometries.
+template <int MAXJ, int GL>
+static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, uint64_t n,
+                               cudaStream_t stream, unsigned long long *counters)
+{
+    MetroParams<MAXJ> p;
+    std::memset(p.geo, 0, sizeof(p.geo));
+    p.jobs_dev = dev;
+    p.n_jobs = cnt;
+    p.block_begin[0] = 0;
+    int n_geo = 0;
+    int geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
+    for (int i = 0; i < cnt; ++i) {
+        const JobDev &jd = host[i];
+        int gi = 0;
+        while (gi < n_geo && !(geo_L[gi] == jd.geo.L && geo_cpt[gi] == jd.cols_per_thread))
+            ++gi;
+        if (gi == n_geo) {
+            geo_L[gi] = jd.geo.L;
+            geo_cpt[gi] = jd.cols_per_thread;
+            metro_geo(p.geo[gi], jd);
+            ++n_geo;
+        }
+        metro_job(p.job[i], jd, gi);
+        p.block_begin[i + 1] = p.block_begin[i] + jd.n_samples * jd.blocks_per_sample;
+    }
+    const int grid = p.block_begin[cnt];
+    if (grid == 0)
+        return;
+    for (uint64_t k = 0; k < n; ++k)
+        for (int h = 0; h < 2; ++h) {
+            p.h = h;
+            p.sweep_offset = (uint32_t)k;
+            if (counters)
+                metro_kernel<true, MAXJ, GL><<<grid, kSweepThreads, 0, stream>>>(p, counters);
+            else
+                metro_kernel<false, MAXJ, GL><<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+        }
+}
+
+cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
+                               const JobDev *dev1, const int *bb1, int n_jobs1, int blocks1,
                                uint64_t n, cudaStream_t stream, unsigned long long *counters)
 {
-    for (uint64_t k = 0; k < n; ++k) {
-        for (int h = 0; h < 2; ++h) {
-            if (counters) {
-                if (blocks0 > 0)
-                    metro_kernel<true><<<blocks0, kSweepThreads, 0, stream>>>(
-                        jobs0, bb0, n_jobs0, h, (uint32_t)k, counters);
-                if (blocks1 > 0)
-                    heat_kernel<true><<<blocks1, kSweepThreads, 0, stream>>>(
-                        jobs1, bb1, n_jobs1, h, (uint32_t)k, counters);
-            } else {
-                if (blocks0 > 0)
-                    metro_kernel<false><<<blocks0, kSweepThreads, 0, stream>>>(
-                        jobs0, bb0, n_jobs0, h, (uint32_t)k, nullptr);
-                if (blocks1 > 0)
-                    heat_kernel<false><<<blocks1, kSweepThreads, 0, stream>>>(
-                        jobs1, bb1, n_jobs1, h, (uint32_t)k, nullptr);
+    // Tables hold different jobs, so they need no order between them: each
+    // issues its own n sweeps (two launches per sweep) in turn.  Metropolis
+    // jobs go in chunks of kMetroMaxJobs through the parameter block.
+    // a table of one side 64 or 128 takes the compile-time geometry kernel;
+    // a mixed table stays in one launch (per kMetroMaxJobs chunk) so that small
+    // lattices share the GPU with the others
+    bool same_L = n_jobs0 > 0;
+    for (int i = 1; i < n_jobs0 && same_L; ++i)
+        same_L = host0[i].geo.L == host0[0].geo.L;
+    const int L0 = n_jobs0 > 0 ? host0[0].geo.L : 0;
+    for (int first = 0, cnt = 0; first < n_jobs0; first += cnt) {
+        // as many jobs as fit: kMetroMaxJobs of at most kMetroMaxGeo geometries
+        int n_geo = 0, geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
+        for (cnt = 0; first + cnt < n_jobs0 && cnt < kMetroMaxJobs; ++cnt) {
+            const JobDev &jd = host0[first + cnt];
+            int gi = 0;
+            while (gi < n_geo && !(geo_L[gi] == jd.geo.L && geo_cpt[gi] == jd.cols_per_thread))
+                ++gi;
+            if (gi == n_geo) {
+                if (n_geo == kMetroMaxGeo)
+                    break;
+                geo_L[gi] = jd.geo.L;
+                geo_cpt[gi] = jd.cols_per_thread;
+                ++n_geo;
             }
         }
+        const JobDev *h = host0 + first;
+        const JobDev *d = dev0 + first;
+        if (same_L && L0 == 128) {
+            if (cnt <= 8)
+                launch_metro_chunk<8, 128>(h, d, cnt, n, stream, counters);
+            else
+                launch_metro_chunk<kMetroMaxJobs, 128>(h, d, cnt, n, stream, counters);
+        } else if (same_L && L0 == 64) {
+            if (cnt <= 8)
+                launch_metro_chunk<8, 64>(h, d, cnt, n, stream, counters);
+            else
+                launch_metro_chunk<kMetroMaxJobs, 64>(h, d, cnt, n, stream, counters);
+        } else if (cnt <= 1) {
+            launch_metro_chunk<1, 0>(h, d, cnt, n, stream, counters);
+        } else if (cnt <= 8) {
+            launch_metro_chunk<8, 0>(h, d, cnt, n, stream, counters);
+        } else if (cnt <= 32) {
+            launch_metro_chunk<32, 0>(h, d, cnt, n, stream, counters);
+        } else if (cnt <= 128) {
+            launch_metro_chunk<128, 0>(h, d, cnt, n, stream, counters);
+        } else {
+            launch_metro_chunk<kMetroMaxJobs, 0>(h, d, cnt, n, stream, counters);
+        }
+    }
+    if (blocks1 > 0) {
+        for (uint64_t k = 0; k < n; ++k)
+            for (int h = 0; h < 2; ++h) {
+                if (counters)
+                    heat_kernel<true><<<blocks1, kSweepThreads, 0, stream>>>(
+                        dev1, bb1, n_jobs1, h, (uint32_t)k, counters);
+                else
+                    heat_kernel<false><<<blocks1, kSweepThreads, 0, stream>>>(
+                        dev1, bb1, n_jobs1, h, (uint32_t)k, nullptr);
+            }
     }
     return cudaGetLastError();
 }

@@ -301,6 +301,10 @@ class EAServer:
         _lib.check(self.lib.ea_server_release(self.h, int(job_id)), server=self.h)
         self._keep.pop(int(job_id), None)
 
+    def cancel(self, job_id):
+        _lib.check(self.lib.ea_server_cancel(self.h, int(job_id)), server=self.h)
+        self._keep.pop(int(job_id), None)
+
     def stats(self):
         st = _lib.EaServerStats()
         _lib.check(self.lib.ea_server_get_stats(self.h, ctypes.byref(st)))
