@@ -163,6 +163,11 @@ OPS_FIXED_PER_WORD = 35
 OPS_PER_PHILOX = 60        # 10 rounds x (2 mul.lo + 2 mul.hi + 2 three-input XOR)
 INT_LANES_PER_SM = 128     # int32-capable lanes per SM (4 SMSP x 32)
 N_SM = 152
+# DRAM bytes (read + write) of one batched half-step launch of this workload,
+# from an ncu capture of this command (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass, caches flushed before each captured launch;
+# profiles/launches_bench_L128_S16x5.md).  Refresh it when the kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = 104.94e6 + 2.49e6
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
@@ -275,17 +280,28 @@ def run_ours(args, world, rank, local):
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     peak_tops = N_SM * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     flips_per_launch = samples * N  # one half-step updates every site of one replica
-    achieved_tops = flips_per_launch * ops_per_flip / (kernel_ms * 1e-3) / 1e12
+    launch_s = kernel_ms * 1e-3
+    achieved_tops = flips_per_launch * ops_per_flip / launch_s / 1e12
     bytes_per_flip = 6.0 / 8.0
-    achieved_gbs = flips_per_launch * bytes_per_flip / (kernel_ms * 1e6)
-    roof = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
-            "frac": achieved_tops / peak_tops, "traffic": None,
-            "peak_basis": "152 SMs x 128 int32 lanes x %.0f MHz (max SM clock)" % sm_mhz,
-            "kernel": "sweep_kernel<0,false>", "kernel_us_per_launch": kernel_ms * 1e3,
-            "ops_per_flip": ops_per_flip, "philox_calls_per_word": prof["philox_calls"] / words,
-            "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": pk["hbm_gbs"],
-                    "frac": achieved_gbs / pk["hbm_gbs"], "bytes_per_flip": bytes_per_flip,
-                    "peak_kind": pk_kind}}
+    achieved_gbs = flips_per_launch * bytes_per_flip / launch_s / 1e9
+    # the two roofs in flips/ns; the slower one bounds the kernel
+    hbm_roof = pk["hbm_gbs"] / bytes_per_flip
+    alu_roof = peak_tops * 1e3 / ops_per_flip
+    alu = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+           "frac": achieved_tops / peak_tops, "roof_flips_per_ns": alu_roof,
+           "peak_basis": "152 SMs x 128 int32 lanes x %.0f MHz (max SM clock)" % sm_mhz,
+           "ops_per_flip": ops_per_flip,
+           "philox_calls_per_word": prof["philox_calls"] / words}
+    hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved_gbs / pk["hbm_gbs"], "roof_flips_per_ns": hbm_roof,
+           "bytes_per_flip": bytes_per_flip, "peak_kind": pk_kind + " (copy bandwidth)"}
+    primary, other = (hbm, alu) if hbm_roof <= alu_roof else (alu, hbm)
+    roof = dict(primary)
+    traffic = args.traffic_bytes if args.traffic_bytes is not None else TRAFFIC_BYTES_PER_LAUNCH
+    roof.update({"traffic": traffic, "kernel": "metro_kernel",
+                 "traffic_over_algorithmic": traffic / (flips_per_launch * bytes_per_flip),
+                 "kernel_us_per_launch": kernel_ms * 1e3,
+                 "flips_per_launch": flips_per_launch, "other": other})
 
     e2e = None
     if not args.no_e2e:
@@ -493,6 +509,8 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--ref-sweeps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--traffic-bytes", type=float, default=None,
+                    help="DRAM bytes per half-step launch from an ncu capture of this command")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--mixed-sweeps", type=int, default=64)

@@ -306,8 +306,10 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
     const int cols = STATIC ? GL * GL : G.cols;
     for (int k = 0; k < G.cpt; ++k) {
         const int col0 = (cb * G.cpt + k) * kSweepThreads + (int)threadIdx.x;
-        const bool act = col0 < cols;  // lanes past the last column idle in step
-        if (__all_sync(0xffffffffu, !act))
+        // lanes past the last column idle in step; with a compile-time geometry
+        // the columns (GL^2) fill whole blocks
+        const bool act = STATIC ? true : col0 < cols;
+        if (!STATIC && __all_sync(0xffffffffu, !act))
             break;
         const int col = act ? col0 : 0;
         const int y = STATIC ? (col >> SLOG)
