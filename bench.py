@@ -166,8 +166,9 @@ N_SM = 152
 # DRAM bytes (read + write) of one batched half-step launch of this workload,
 # from an ncu capture of this command (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass, caches flushed before each captured launch;
-# profiles/launches_bench_L128_S16x5.md).  Refresh it when the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 104.94e6 + 2.49e6
+# profiles/launches_bench_L128_S16x5.md).  None until it is taken again after
+# a change of the kernel.
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
@@ -299,7 +300,8 @@ def run_ours(args, world, rank, local):
     roof = dict(primary)
     traffic = args.traffic_bytes if args.traffic_bytes is not None else TRAFFIC_BYTES_PER_LAUNCH
     roof.update({"traffic": traffic, "kernel": "metro_kernel",
-                 "traffic_over_algorithmic": traffic / (flips_per_launch * bytes_per_flip),
+                 "traffic_over_algorithmic": (None if traffic is None else
+                                              traffic / (flips_per_launch * bytes_per_flip)),
                  "kernel_us_per_launch": kernel_ms * 1e3,
                  "flips_per_launch": flips_per_launch, "other": other})
 

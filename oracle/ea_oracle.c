@@ -284,17 +284,22 @@ int ora_init_spins(int L, uint64_t seed, uint32_t s, int8_t *S)
 /*   floor(ldexp(-expm1(g * log1p(-p_u)), 64)), clamped to 2^64 - 1.         */
 /* The sites after an acceptance start a fresh gap with the next draw.      */
 /*                                                                          */
-/* Draw d of class u (64 bits) of the word-site update.  Call 0 holds the   */
-/* draws a word-site usually needs: output 0 = draw 0 and output 1 = draw 1 */
-/* of class 2 (dE = 4), output 2 = draw 0 of class 1, output 3 = draw 0 of   */
-/* class 0.  Draw d >= f_u (f = 1, 1, 2 for u = 0, 1, 2) is output e mod 4   */
-/* of call 1 + u + 3 (e div 4), e = d - f_u.  The high word of a draw is that */
-/* output; its low word is the same output of call (that call + 64).  Calls  */
-/* use counter                                                               */
-/*   c0 = widx, c1 = lo32(t),                                               */
-/*   c2 = (3 << 30) | (bits 32..47 of t) << 12 | a << 11 | call,            */
-/*   c3 = s (sample index, or sample index / G).                            */
-/* ------------------------------------------------------------------------ */
+/* Draws.  Word-sites pair up along z (z' even with z' + 1): one Philox call */
+/* per pair holds the leading bits of both words' first draws:               */
+/*   main call of the pair: counter (widx of the even word, lo32(t),         */
+/*     (3 << 30) | (bits 32..47 of t) << 12 | a_even << 11 | 0, s), where    */
+/*     a_even is the replica updated at the even word in this half-step;     */
+/*     outputs 0, 1 belong to the even word, 2, 3 to the odd word:           */
+/*     first output = bits 63..32 of draw 0 of class 2 (dE = 4),             */
+/*     second output = bits 63..48 of draw 0 of class 1 (high half) and of   */
+/*     class 0 (low half).                                                   */
+/*   extension call of a word: counter (its widx, lo32(t), ... | a << 11 |   */
+/*     64, s): output 0 = bits 31..0 of class 2's draw 0; outputs 1, 2 =     */
+/*     bits 47..16 of class 1's and class 0's draw 0; output 3 = bits 15..0  */
+/*     of class 1's (high half) and class 0's (low half) draw 0.             */
+/*   draw d >= 1 of class u of a word: the 64-bit number (out[2e] << 32) |   */
+/*     out[2e + 1] of call 1 + u + 3 (d-1 div 2), e = (d-1) mod 2, with the   */
+/*     word's own widx and replica.                                          */
 #define STREAM_METROPOLIS 3u
 
 int ora_geo_table(double p, uint64_t C[33])
@@ -310,38 +315,53 @@ int ora_geo_table(double p, uint64_t C[33])
     return ORA_OK;
 }
 
-static uint64_t metro_draw(uint32_t widx, uint64_t seed, uint32_t s, int a, uint64_t t, int u, int d)
+static void metro_call(uint32_t widx, uint64_t seed, uint32_t s, int a, uint64_t t, int call,
+                       uint32_t out[4])
 {
-    static const int first_out[3][2] = {{3, -1}, {2, -1}, {0, 1}}; /* [u][d] in call 0 */
-    static const int n_first[3] = {1, 1, 2};
-    int call, out;
-    if (d < n_first[u]) {
-        call = 0;
-        out = first_out[u][d];
-    } else {
-        int e = d - n_first[u];
-        call = 1 + u + 3 * (e / 4);
-        out = e % 4;
-    }
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t c2 = (STREAM_METROPOLIS << 30) | ((uint32_t)((t >> 32) & 0xFFFFu) << 12) |
-                  ((uint32_t)a << 11);
-    uint32_t hi_ctr[4] = {widx, (uint32_t)t, c2 | (uint32_t)call, s};
-    uint32_t lo_ctr[4] = {widx, (uint32_t)t, c2 | (uint32_t)(call + 64), s};
-    uint32_t hi[4], lo[4];
-    ora_philox4x32_10(hi_ctr, key, hi);
-    ora_philox4x32_10(lo_ctr, key, lo);
-    return ((uint64_t)hi[out] << 32) | (uint64_t)lo[out];
+    uint32_t ctr[4] = {widx, (uint32_t)t,
+                       (STREAM_METROPOLIS << 30) | ((uint32_t)((t >> 32) & 0xFFFFu) << 12) |
+                           ((uint32_t)a << 11) | (uint32_t)call,
+                       s};
+    ora_philox4x32_10(ctr, key, out);
+}
+
+/* Draw d of class u for the word-site (xw, yw, zw) of a lattice whose word
+   lattice is Lx x Ly x Lz, updated in replica a. */
+static uint64_t metro_draw(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s,
+                           int a, uint64_t t, int u, int d)
+{
+    uint32_t widx = (uint32_t)(xw + Lx * (yw + Ly * zw));
+    if (d >= 1) {
+        uint32_t out[4];
+        int e = (d - 1) % 2;
+        metro_call(widx, seed, s, a, t, 1 + u + 3 * ((d - 1) / 2), out);
+        return ((uint64_t)out[2 * e] << 32) | (uint64_t)out[2 * e + 1];
+    }
+    /* leading bits from the pair's main call */
+    int odd = zw & 1;
+    uint32_t widx_even = (uint32_t)(xw + Lx * (yw + Ly * (zw - odd)));
+    int a_even = odd ? (a ^ 1) : a; /* the two words of a pair hold different replicas */
+    uint32_t m[4], x[4];
+    metro_call(widx_even, seed, s, a_even, t, 0, m);
+    metro_call(widx, seed, s, a, t, 64, x);
+    uint32_t first = m[2 * odd], second = m[2 * odd + 1];
+    if (u == 2)
+        return ((uint64_t)first << 32) | (uint64_t)x[0];
+    if (u == 1)
+        return ((uint64_t)(second >> 16) << 48) | ((uint64_t)x[1] << 16) | (uint64_t)(x[3] >> 16);
+    return ((uint64_t)(second & 0xFFFFu) << 48) | ((uint64_t)x[2] << 16) | (uint64_t)(x[3] & 0xFFFFu);
 }
 
 /* Flip decisions of the lanes lane_list[0..n) (increasing lane order) of one
    class: sets flip[lane] = 1 for the accepted ones. */
-static void metro_class(const uint64_t C[33], const int *lane_list, int n, uint32_t widx,
-                        uint64_t seed, uint32_t s, int a, uint64_t t, int u, uint8_t *flip)
+static void metro_class(const uint64_t C[33], const int *lane_list, int n, int Lx, int Ly,
+                        int xw, int yw, int zw, uint64_t seed, uint32_t s, int a, uint64_t t,
+                        int u, uint8_t *flip)
 {
     int start = 0, d = 0;
     while (n - start > 0) {
-        uint64_t V = metro_draw(widx, seed, s, a, t, u, d);
+        uint64_t V = metro_draw(Lx, Ly, xw, yw, zw, seed, s, a, t, u, d);
         d++;
         int rem = n - start;
         if (V >= C[rem])
@@ -420,7 +440,6 @@ int ora_half_step(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, 
                 for (int xw = 0; xw < Lx; xw++) {
                     if (((xw + yw + zw) & 1) != (h ^ a))
                         continue;
-                    uint32_t widx = (uint32_t)(xw + Lx * (yw + Ly * zw));
                     int dE[32], sx[32], sy[32], sz[32];
                     uint8_t flip[32];
                     for (int b = 0; b < lanes; b++) {
@@ -439,7 +458,8 @@ int ora_half_step(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, 
                                 if (dE[b] == 12 - 4 * u)
                                     list[n++] = b;
                             if (n > 0)
-                                metro_class(C[u], list, n, widx, seed, s, a, t, u, flip);
+                                metro_class(C[u], list, n, Lx, Ly, xw, yw, zw, seed, s, a, t,
+                                            u, flip);
                         }
                     } else {
                         for (int b = 0; b < lanes; b++)

@@ -14,10 +14,10 @@
 //     form a Bernoulli sequence whose first acceptance rank is geometric, so
 //     one 64-bit draw V per class decides: no flip when V >= C_u[n] (n lanes
 //     in the class), else the lane of rank min{g : V < C_u[g+1]}, after which
-//     the remaining lanes take the next draw.  One Philox call per word holds
-//     the first draw of every class and the second of class 2; its high words
-//     settle ~97% of class tests at T = 0.7 without a branch.  Two words are
-//     processed together so that their Philox chains overlap.
+//     the remaining lanes take the next draw.  One Philox call per pair of
+//     words holds the leading 32 (class 2) and 16 (classes 1, 0) bits of
+//     their first draws, enough to settle ~97% of words at T = 0.7 without a
+//     branch; the rest of a draw is fetched only when the test hits.
 //   Heat bath (heat_kernel): every lane compares its own 64-bit uniform r
 //     with its threshold, MSB first, four planes per Philox call; a lane is
 //     decided at the first plane where its bit of r differs from its
@@ -104,71 +104,52 @@ __device__ __forceinline__ Count count6(uint32_t u0, uint32_t u1, uint32_t u2, u
 }
 
 // ---------------------------------------------------------------------------
-// Metropolis: the accepted lanes of one class of a word whose class test hit
+// Metropolis draws.  Word-sites pair up along z (z' even with z' + 1); one
+// Philox call per pair ("main", call 0, keyed by the even word and its
+// replica) holds the leading bits of both words' first draws: outputs 0, 1
+// for the even word, 2, 3 for the odd one; the first of the two is bits
+// 63..32 of class 2's draw 0, the second bits 63..48 of class 1's (high half)
+// and class 0's (low half) draw 0.  A word's "extension" call (call 64, its
+// own widx and replica) holds the remaining bits: output 0 = bits 31..0 of
+// class 2's draw; outputs 1, 2 = bits 47..16 of class 1's and class 0's
+// draw; output 3 = their bits 15..0 (high, low half).  Draw d >= 1 of class
+// u is (out[2e] << 32) | out[2e + 1] of call 1 + u + 3 ((d - 1) div 2),
+// e = (d - 1) mod 2.
 // ---------------------------------------------------------------------------
-// Draw d of class u: call 0 output (class 2: d = 0 -> 0, d = 1 -> 1; class 1:
-// d = 0 -> 2; class 0: d = 0 -> 3); later draws e = d - f_u (f = 1, 1, 2) are
-// output e mod 4 of call 1 + u + 3 (e div 4).  Low words: call + 64.
+__device__ __forceinline__ uint64_t c64(const JobDev *__restrict__ jb, int u, int g)
+{
+    return ((uint64_t)jb->gC_hi[u][g] << 32) | jb->gC_lo[u][g];
+}
+
+// The accepted lanes of one class of a word, from its full first draw V0.
 __device__ __forceinline__ uint32_t metro_class(const JobDev *__restrict__ jb, int u, uint32_t Mr,
-                                                const uint4 &R, uint32_t w, uint32_t c1,
-                                                uint32_t c2, uint32_t c3, unsigned int &calls)
+                                                uint64_t V0, uint32_t w, uint32_t c1,
+                                                uint32_t c2, uint32_t c3, const uint32_t (&rk)[20],
+                                                unsigned int &calls)
 {
     uint32_t acc = 0u;
     int rem = __popc(Mr);
     int d = 0;
-    const int f = u == 2 ? 2 : 1;
+    uint64_t V = V0;
     while (rem > 0) {
-        int call, out;
-        if (d < f) {
-            call = 0;
-            out = u == 2 ? d : 3 - u;
-        } else {
-            const int e = d - f;
-            call = 1 + u + 3 * (e >> 2);
-            out = e & 3;
-        }
-        uint32_t vhi;
-        if (call == 0) {
-            vhi = comp(R, out);
-        } else {
-            uint32_t rk[20];
-#pragma unroll
-            for (int i = 0; i < 20; ++i)
-                rk[i] = jb->rk[i];
-            vhi = comp(dev::philox10_rk(make_uint4(w, c1, c2 | (uint32_t)call, c3), rk), out);
-            ++calls;
-        }
-        bool have_lo = false;
-        uint32_t vlo = 0u;
-        // V < C_u[g], fetching V's low word only when the high words tie
-        auto below = [&](int g) -> bool {
-            const uint32_t ch = jb->gC_hi[u][g];
-            if (vhi != ch)
-                return vhi < ch;
-            if (!have_lo) {
-                uint32_t rk[20];
-#pragma unroll
-                for (int i = 0; i < 20; ++i)
-                    rk[i] = jb->rk[i];
-                vlo = comp(dev::philox10_rk(make_uint4(w, c1, c2 | (uint32_t)(call + 64), c3),
-                                            rk),
-                           out);
-                ++calls;
-                have_lo = true;
-            }
-            return vlo < jb->gC_lo[u][g];
-        };
-        if (!below(rem))
-            break;
+        if (!(V < c64(jb, u, rem)))
+            break;  // no acceptance among the remaining lanes
         int G = 0;
-        while (!below(G + 1))
+        while (!(V < c64(jb, u, G + 1)))
             ++G;
         for (int i = 0; i < G; ++i)
             Mr &= Mr - 1u;
         acc |= Mr & (0u - Mr);  // the lane of rank G among the remaining ones
         Mr &= Mr - 1u;
         rem -= G + 1;
+        if (rem == 0)
+            break;
         ++d;
+        const int e = (d - 1) & 1;
+        const uint4 Q = dev::philox10_rk(
+            make_uint4(w, c1, c2 | (uint32_t)(1 + u + 3 * ((d - 1) >> 1)), c3), rk);
+        ++calls;
+        V = e == 0 ? (((uint64_t)Q.x << 32) | Q.y) : (((uint64_t)Q.z << 32) | Q.w);
     }
     return acc;
 }
@@ -189,14 +170,15 @@ __device__ __forceinline__ Classes classes(const Count &c, uint32_t alw, uint32_
     return k;
 }
 
-// Might some lane of the word flip?  An exact "no" for ~97% of words at T = 0.7.
-__device__ __forceinline__ bool class_hit(const Classes &k, const uint4 &R,
+// Might some lane of the word flip?  The leading bits of the first draws
+// against the tables: an exact "no" for ~97% of words at T = 0.7.
+__device__ __forceinline__ bool class_hit(const Classes &k, uint32_t first, uint32_t second,
                                           const uint32_t (*gh)[33])
 {
     const int n0 = __popc(k.M0), n1 = __popc(k.M1), n2 = __popc(k.M2);
-    const bool h2 = (n2 != 0) & (R.x <= gh[2][n2]);
-    const bool h1 = (n1 != 0) & (R.z <= gh[1][n1]);
-    const bool h0 = (n0 != 0) & (R.w <= gh[0][n0]);
+    const bool h2 = (n2 != 0) & (first <= gh[2][n2]);
+    const bool h1 = (n1 != 0) & ((second >> 16) <= (gh[1][n1] >> 16));
+    const bool h0 = (n0 != 0) & ((second & 0xFFFFu) <= (gh[0][n0] >> 16));
     return h0 | h1 | h2;
 }
 
@@ -205,21 +187,29 @@ __device__ __forceinline__ bool class_hit(const Classes &k, const uint4 &R,
 constexpr int kQueue = 96;  // entries per warp (up to 64 are added per step)
 
 struct Pending {
-    uint32_t w, base, M0, M1, M2, c2;
-    uint4 R;
+    uint32_t w, base, M0, M1, M2, c2, first, second;
 };
 
 __device__ __forceinline__ void finish_word(const JobDev *__restrict__ jb, const Pending &e,
                                             uint32_t *__restrict__ upd, uint32_t valid,
-                                            uint32_t c1, uint32_t c3, unsigned int &calls)
+                                            uint32_t c1, uint32_t c3, const uint32_t (&rk)[20],
+                                            unsigned int &calls)
 {
+    // the extension call completes the three first draws to 64 bits
+    const uint4 X = dev::philox10_rk(make_uint4(e.w, c1, e.c2 | 64u, c3), rk);
+    ++calls;
     uint32_t A = 0u;
-    if (e.M0)
-        A |= metro_class(jb, 0, e.M0, e.R, e.w, c1, e.c2, c3, calls);
-    if (e.M1)
-        A |= metro_class(jb, 1, e.M1, e.R, e.w, c1, e.c2, c3, calls);
     if (e.M2)
-        A |= metro_class(jb, 2, e.M2, e.R, e.w, c1, e.c2, c3, calls);
+        A |= metro_class(jb, 2, e.M2, ((uint64_t)e.first << 32) | X.x, e.w, c1, e.c2, c3, rk, calls);
+    if (e.M1)
+        A |= metro_class(jb, 1, e.M1,
+                         ((uint64_t)(e.second >> 16) << 48) | ((uint64_t)X.y << 16) | (X.w >> 16),
+                         e.w, c1, e.c2, c3, rk, calls);
+    if (e.M0)
+        A |= metro_class(jb, 0, e.M0,
+                         ((uint64_t)(e.second & 0xFFFFu) << 48) | ((uint64_t)X.z << 16) |
+                             (X.w & 0xFFFFu),
+                         e.w, c1, e.c2, c3, rk, calls);
     upd[e.w] = e.base ^ (A & valid);
 }
 
@@ -392,13 +382,12 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
             }
             const Classes ka = classes(ca, alwa, valid, live0, live1, live2);
             const Classes kb = classes(cw, alwb, valid, live0, live1, live2);
-            // first draws of both words: two independent Philox chains
-            const uint4 Ra = dev::philox10_rk(make_uint4((uint32_t)wa, c1, c2e, c3), rk);
-            const uint4 Rb = dev::philox10_rk(make_uint4((uint32_t)wb, c1, c2o, c3), rk);
+            // leading bits of the first draws of both words: one call per pair
+            const uint4 Rm = dev::philox10_rk(make_uint4((uint32_t)wa, c1, c2e, c3), rk);
             if (COUNT && act)
-                n_calls += ((ka.M0 | ka.M1 | ka.M2) != 0u) + ((kb.M0 | kb.M1 | kb.M2) != 0u);
-            const bool ha = act && class_hit(ka, Ra, s_gh);
-            const bool hb = act && class_hit(kb, Rb, s_gh);
+                n_calls += ((ka.M0 | ka.M1 | ka.M2 | kb.M0 | kb.M1 | kb.M2) != 0u);
+            const bool ha = act && class_hit(ka, Rm.x, Rm.y, s_gh);
+            const bool hb = act && class_hit(kb, Rm.z, Rm.w, s_gh);
             const uint32_t basea = spa ^ (alwa & valid), baseb = spb ^ (alwb & valid);
             if (act && !ha)
                 upd[wa] = basea;
@@ -418,7 +407,8 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
                 e.M1 = ka.M1;
                 e.M2 = ka.M2;
                 e.c2 = c2e;
-                e.R = Ra;
+                e.first = Rm.x;
+                e.second = Rm.y;
             }
             q_n += __popc(ba);
             if (hb) {
@@ -429,7 +419,8 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
                 e.M1 = kb.M1;
                 e.M2 = kb.M2;
                 e.c2 = c2o;
-                e.R = Rb;
+                e.first = Rm.z;
+                e.second = Rm.w;
             }
             q_n += __popc(bbm);
             __syncwarp();
@@ -437,7 +428,7 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
                 q_n -= 32;
                 const Pending e = q[q_n + lane];
                 unsigned int extra = 0;
-                finish_word(jb, e, upd, valid, c1, c3, extra);
+                finish_word(jb, e, upd, valid, c1, c3, rk, extra);
                 if (COUNT)
                     n_extra += extra;
                 __syncwarp();
@@ -448,7 +439,7 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
     if (lane < q_n) {
         const Pending e = q[lane];
         unsigned int extra = 0;
-        finish_word(jb, e, upd, valid, c1, c3, extra);
+        finish_word(jb, e, upd, valid, c1, c3, rk, extra);
         if (COUNT)
             n_extra += extra;
     }
