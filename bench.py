@@ -166,9 +166,9 @@ N_SM = 152
 # DRAM bytes (read + write) of one batched half-step launch of this workload,
 # from an ncu capture of this command (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass, caches flushed before each captured launch;
-# profiles/launches_bench_L128_S16x5.md).  None until it is taken again after
-# a change of the kernel.
-TRAFFIC_BYTES_PER_LAUNCH = None
+# profiles/launches_bench_L128_S16x5.md, mean of three launches).  Take it
+# again (or set None) when the kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = 110.35e6 + 5.20e6
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
@@ -299,7 +299,7 @@ def run_ours(args, world, rank, local):
     primary, other = (hbm, alu) if hbm_roof <= alu_roof else (alu, hbm)
     roof = dict(primary)
     traffic = args.traffic_bytes if args.traffic_bytes is not None else TRAFFIC_BYTES_PER_LAUNCH
-    roof.update({"traffic": traffic, "kernel": "metro_kernel",
+    roof.update({"traffic": traffic, "kernel": "metro_tile_kernel",
                  "traffic_over_algorithmic": (None if traffic is None else
                                               traffic / (flips_per_launch * bytes_per_flip)),
                  "kernel_us_per_launch": kernel_ms * 1e3,

@@ -230,9 +230,11 @@ int ea_batch_remove(ea_batch *b, ea_ctx *job);
 /* Number of member jobs. */
 int ea_batch_size(const ea_batch *b, int *n_jobs);
 
-/* Launch shape used by ea_batch_sweep: word columns per thread of the sweep
- * kernel (1, 2 or 4; 0 = per-job default) and sweeps per captured graph
- * (0 = direct launches).  Neither changes any result. */
+/* Launch shape used by ea_batch_sweep: work per thread of the sweep kernel
+ * (1, 2 or 4; 0 = per-job default) and sweeps per captured graph (0 = direct
+ * launches).  The work per thread is that many word columns, or for a table
+ * whose jobs all have side 64 or 128, segments of 4, 8 or 16 rows of 2 x 2
+ * word-sites.  Neither changes any result. */
 int ea_batch_configure(ea_batch *b, int cols_per_thread, int graph_sweeps);
 int ea_batch_get_config(const ea_batch *b, int *cols_per_thread, int *graph_sweeps);
 

@@ -166,7 +166,13 @@ static ea::Thr make_thr(int rule, double T, const uint64_t thr_k[7], const uint8
         // classes u = 0, 1, 2 (dE = 12, 8, 4) decided by geometric gaps
         for (int u = 0; u < 3; ++u) {
             const int k = 6 - u;
-            if (!always_k[k] && thr_k[k] > 0) {
+            if (always_k[k]) {
+                // accepted outright: every non-empty class hits its table and
+                // the rare path flips all of its lanes
+                t.geo_live |= 1u << u;
+                for (int g = 1; g <= 32; ++g)
+                    t.geoC[u][g] = ~(uint64_t)0;
+            } else if (thr_k[k] > 0) {
                 t.geo_live |= 1u << u;
                 ea::geo_table(std::exp(-(double)(12 - 4 * u) / T), t.geoC[u]);
             }
@@ -404,10 +410,14 @@ int check_ctx(const ea_ctx *c) { return c ? EA_OK : EA_ERR_INVALID_ARG; }
 
 }  // namespace
 
-// Columns per thread of the sweep kernel: enough blocks to fill the GPU a
-// few times over for one job, fewer per-thread set-ups for large lattices.
+// Launch shape of the Metropolis kernel: enough blocks to fill the GPU a few
+// times over for one job, fewer per-thread set-ups for large lattices.  Sides
+// 64 and 128 take the tile kernel, whose threads already hold 4 rows of 2 x 2
+// word-sites at the smallest shape.
 static int default_cols_per_thread(const Geo &g)
 {
+    if (g.L == 64 || g.L == 128)
+        return 1;
     const int cols = g.n[0] * g.n[1];
     return cols >= 8192 ? 2 : 1;
 }

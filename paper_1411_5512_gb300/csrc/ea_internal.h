@@ -110,6 +110,7 @@ constexpr int kSweepThreads = 128;
 struct MetroGeo {
     int n0, n1, n2, cols;
     int bps, cpt;          // blocks per sample, word columns per thread
+    int seg;               // rows per thread of the side-64/128 tile kernel
     uint32_t words;        // words per area
     uint32_t valid, magic;
     int dshift;

@@ -65,11 +65,6 @@ __device__ __forceinline__ void load_axis(Axis &a, const Geo &g, int d)
     }
 }
 
-__device__ __forceinline__ uint32_t comp(const uint4 &v, int i)
-{
-    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
-}
-
 // Block -> job of the table (the last j with block_begin[j] <= blockIdx.x).
 __device__ __forceinline__ int find_job(const int *__restrict__ block_begin, int n_jobs)
 {
@@ -198,30 +193,34 @@ __device__ __forceinline__ void finish_word(const JobDev *__restrict__ jb, const
     // the extension call completes the three first draws to 64 bits
     const uint4 X = dev::philox10_rk(make_uint4(e.w, c1, e.c2 | 64u, c3), rk);
     ++calls;
-    uint32_t A = 0u;
-    if (e.M2)
-        A |= metro_class(jb, 2, e.M2, ((uint64_t)e.first << 32) | X.x, e.w, c1, e.c2, c3, rk, calls);
-    if (e.M1)
-        A |= metro_class(jb, 1, e.M1,
+    uint32_t A = 0u, M0 = e.M0, M1 = e.M1, M2 = e.M2;
+    const uint32_t always3 = jb->always_u & 7u;
+    if (always3) {  // classes accepted outright (exp(-dE/T) rounds to 1)
+        A = ((always3 & 4u) ? M2 : 0u) | ((always3 & 2u) ? M1 : 0u) | ((always3 & 1u) ? M0 : 0u);
+        M2 = (always3 & 4u) ? 0u : M2;
+        M1 = (always3 & 2u) ? 0u : M1;
+        M0 = (always3 & 1u) ? 0u : M0;
+    }
+    if (M2)
+        A |= metro_class(jb, 2, M2, ((uint64_t)e.first << 32) | X.x, e.w, c1, e.c2, c3, rk, calls);
+    if (M1)
+        A |= metro_class(jb, 1, M1,
                          ((uint64_t)(e.second >> 16) << 48) | ((uint64_t)X.y << 16) | (X.w >> 16),
                          e.w, c1, e.c2, c3, rk, calls);
-    if (e.M0)
-        A |= metro_class(jb, 0, e.M0,
+    if (M0)
+        A |= metro_class(jb, 0, M0,
                          ((uint64_t)(e.second & 0xFFFFu) << 48) | ((uint64_t)X.z << 16) |
                              (X.w & 0xFFFFu),
                          e.w, c1, e.c2, c3, rk, calls);
     upd[e.w] = e.base ^ (A & valid);
 }
 
-// GL = 0: geometry read from the job table; GL = 64 or 128: every job of the
-// launch has side GL, whose word lattice is GL x GL x GL/32 with no lane
-// realignment along x or y, fixed at compile time.
-template <bool COUNT, int MAXJ, int GL>
+// Any side: the geometry is read from the job table.  A thread updates a
+// column of word-sites along z.
+template <bool COUNT, int MAXJ>
 __global__ void __launch_bounds__(kSweepThreads, 10)
     metro_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
 {
-    constexpr bool STATIC = GL != 0;
-    constexpr int SLOG = GL == 128 ? 7 : 6;
     // the job of this block, found from blockIdx alone: the loads below stay
     // in the uniform datapath
     int j = 0;
@@ -262,11 +261,11 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
     const int local = (int)blockIdx.x - P.block_begin[j];
     const int s = local / G.bps;
     const int cb = local - s * G.bps;
-    const int n0 = STATIC ? GL : G.n0, n1 = STATIC ? GL : G.n1, n2 = STATIC ? GL / 32 : G.n2;
+    const int n0 = G.n0, n1 = G.n1, n2 = G.n2;
     const bool all_always = (J.meta >> 3) & 1u, none_random = (J.meta >> 4) & 1u;
-    const bool fix_x = STATIC ? false : (G.fix & 1u) != 0;
-    const bool fix_y = STATIC ? false : (G.fix & 2u) != 0;
-    const uint32_t valid = STATIC ? 0xffffffffu : G.valid;
+    const bool fix_x = (G.fix & 1u) != 0;
+    const bool fix_y = (G.fix & 2u) != 0;
+    const uint32_t valid = G.valid;
     const uint32_t live0 = 0u - (J.meta & 1u), live1 = 0u - ((J.meta >> 1) & 1u),
                    live2 = 0u - ((J.meta >> 2) & 1u);
     Axis az, ax, ay;
@@ -281,7 +280,7 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
         load_axis(ax, jb->geo, 0);
     if (fix_y)
         load_axis(ay, jb->geo, 1);
-    const uint32_t W = STATIC ? (uint32_t)GL * GL * (GL / 32) : G.words;
+    const uint32_t W = G.words;
     uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
     const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
@@ -293,17 +292,15 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
     const int sz = n0 * n1;
     unsigned int n_words = 0, n_calls = 0, n_extra = 0;
 
-    const int cols = STATIC ? GL * GL : G.cols;
+    const int cols = G.cols;
     for (int k = 0; k < G.cpt; ++k) {
         const int col0 = (cb * G.cpt + k) * kSweepThreads + (int)threadIdx.x;
-        // lanes past the last column idle in step; with a compile-time geometry
-        // the columns (GL^2) fill whole blocks
-        const bool act = STATIC ? true : col0 < cols;
-        if (!STATIC && __all_sync(0xffffffffu, !act))
+        // lanes past the last column idle in step
+        const bool act = col0 < cols;
+        if (__all_sync(0xffffffffu, !act))
             break;
         const int col = act ? col0 : 0;
-        const int y = STATIC ? (col >> SLOG)
-                             : (int)((__umulhi((uint32_t)col, G.magic) + (uint32_t)col) >> G.dshift);
+        const int y = (int)((__umulhi((uint32_t)col, G.magic) + (uint32_t)col) >> G.dshift);
         const int x = col - y * n0;
         int cxp = col + 1, cxm = col - 1, cyp = col + n0, cym = col - n0;
         const bool wxp = (x + 1 == n0), wxm = (x == 0), wyp = (y + 1 == n1), wym = (y == 0);
@@ -322,7 +319,6 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
         uint32_t nz_prev = fixup(nb[col + (n2 - 1) * sz], az, 1);
         uint32_t jz_prev = fixup(Jz[col + (n2 - 1) * sz], az, 1);
         uint32_t nz_cur = nb[col];
-#pragma unroll(STATIC ? GL / 64 : 1)
         for (int z = 0; z < n2; z += 2) {  // n2 is even: words at z (a) and z + 1 (b)
             const int wa = col + z * sz, wb = wa + sz;
             const uint32_t nz_b = nb[wb];                                             // z + 1
@@ -385,7 +381,7 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
             // leading bits of the first draws of both words: one call per pair
             const uint4 Rm = dev::philox10_rk(make_uint4((uint32_t)wa, c1, c2e, c3), rk);
             if (COUNT && act)
-                n_calls += ((ka.M0 | ka.M1 | ka.M2 | kb.M0 | kb.M1 | kb.M2) != 0u);
+                n_calls += 1;  // the main call of the pair
             const bool ha = act && class_hit(ka, Rm.x, Rm.y, s_gh);
             const bool hb = act && class_hit(kb, Rm.z, Rm.w, s_gh);
             const uint32_t basea = spa ^ (alwa & valid), baseb = spb ^ (alwb & valid);
@@ -440,6 +436,391 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
         const Pending e = q[lane];
         unsigned int extra = 0;
         finish_word(jb, e, upd, valid, c1, c3, rk, extra);
+        if (COUNT)
+            n_extra += extra;
+    }
+    if (COUNT) {
+        atomicAdd(&counters[0], (unsigned long long)n_words);
+        atomicAdd(&counters[1], (unsigned long long)(n_calls + n_extra));
+        atomicAdd(&counters[2], (unsigned long long)n_extra);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Metropolis half-step for a table whose jobs all have side GL = 64 or 128.
+// Their word lattice is GL x GL x GL/32 with all 32 lanes along z: x and y
+// wrap without realignment, and a z wrap rotates the word by one lane.  A
+// thread owns the word-sites (x0, x0 + 1) x (z0, z0 + 1), x0 and z0 even, of a
+// segment of Y rows along y.  Rows y - 1 and y of the neighbour area and the y
+// bonds of row y - 1 stay in registers from one row to the next, and the two
+// words of an x pair are read and written as one 8-byte access.  The z pair
+// is the pair that shares the main Philox call.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t rot_zp(uint32_t w)  // +z neighbour across the wrap
+{
+    return __funnelshift_r(w, w, 1);
+}
+
+__device__ __forceinline__ uint32_t rot_zm(uint32_t w)  // -z neighbour across the wrap
+{
+    return __funnelshift_l(w, w, 1);
+}
+
+__device__ __forceinline__ uint2 ld2(const uint32_t *__restrict__ p, int i)
+{
+    return *reinterpret_cast<const uint2 *>(p + i);
+}
+
+constexpr int kTileQueue = 224;  // entries per warp: up to 95 left over + 128 added per row
+
+// Threshold tables of a block's job in shared memory.
+struct TileTables {
+    uint32_t hi[3][33];  // C_u[n] >> 32
+    uint32_t t1[33];     // C_1[n] >> 48 followed by 16 one bits
+    uint32_t t0[33];     // C_0[n] >> 48
+};
+
+// The rare path of one queued word: e = (word-site, spins before the update,
+// leading bits of the first draws).  The classes are counted again from the
+// neighbour area, which this half-step does not write.  Class 2 is decided on
+// the 32 leading bits of its draws; the extension call, which completes the
+// first draws of all three classes, is fetched only when those bits tie with
+// the table or when the 16 leading bits of class 1 or 0 do not rule them out.
+template <int GL>
+__device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const TileTables &tb,
+                                            const uint4 &e, uint32_t *__restrict__ upd,
+                                            const uint32_t *__restrict__ nb,
+                                            const uint32_t *__restrict__ Jx,
+                                            const uint32_t *__restrict__ Jy,
+                                            const uint32_t *__restrict__ Jz, int h, uint32_t live0,
+                                            uint32_t live1, uint32_t live2, uint32_t always3,
+                                            uint32_t c1, uint32_t c2m, uint32_t c3,
+                                            const uint32_t (&rk)[20], unsigned int &calls)
+{
+    constexpr int SLOG = GL == 128 ? 7 : 6;
+    constexpr int N2 = GL / 32, SZ = GL * GL;
+    const int w = (int)e.x;
+    const uint32_t s = e.y, first = e.z, second = e.w;
+    const int x = w & (GL - 1), y = (w >> SLOG) & (GL - 1), z = w >> (2 * SLOG);
+    const int wxp = x == GL - 1 ? w - (GL - 1) : w + 1;
+    const int wxm = x == 0 ? w + (GL - 1) : w - 1;
+    const int wyp = y == GL - 1 ? w - (GL - 1) * GL : w + GL;
+    const int wym = y == 0 ? w + (GL - 1) * GL : w - GL;
+    const int wzp = z == N2 - 1 ? w - (N2 - 1) * SZ : w + SZ;
+    const int wzm = z == 0 ? w + (N2 - 1) * SZ : w - SZ;
+    uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
+    if (z == N2 - 1)
+        nzp = rot_zp(nzp);
+    if (z == 0) {
+        nzm = rot_zm(nzm);
+        jzm = rot_zm(jzm);
+    }
+    const Count c = count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nb[wyp] ^ Jy[w],
+                           s ^ nb[wym] ^ Jy[wym], s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
+    const uint32_t alw = c.b2 | (c.b1 & c.b0);
+    Classes k = classes(c, alw, 0xffffffffu, live0, live1, live2);
+    const uint32_t c2 = c2m | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
+    uint32_t A = 0u;
+    if (always3) {  // classes accepted outright (exp(-dE/T) rounds to 1)
+        if (always3 & 4u) {
+            A |= k.M2;
+            k.M2 = 0u;
+        }
+        if (always3 & 2u) {
+            A |= k.M1;
+            k.M1 = 0u;
+        }
+        if (always3 & 1u) {
+            A |= k.M0;
+            k.M0 = 0u;
+        }
+    }
+    uint4 X = make_uint4(0u, 0u, 0u, 0u);
+    bool have_x = false;
+    if (k.M2) {
+        uint32_t Mr = k.M2;
+        int rem = __popc(Mr);
+        uint32_t vh = first, vl = 0u;
+        bool exact = false;  // vl holds the draw's low word
+        int d = 0;
+        // V < C_2[g], from the high words unless they tie
+        auto below = [&](int g) -> bool {
+            const uint32_t ch = tb.hi[2][g];
+            if (vh != ch)
+                return vh < ch;
+            if (!exact) {
+                if (!have_x) {
+                    X = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 64u, c3), rk);
+                    ++calls;
+                    have_x = true;
+                }
+                vl = X.x;
+                exact = true;
+            }
+            return vl < jb->gC_lo[2][g];
+        };
+        while (below(rem)) {
+            int G = 0;
+            while (!below(G + 1))
+                ++G;
+            for (int i = 0; i < G; ++i)
+                Mr &= Mr - 1u;
+            A |= Mr & (0u - Mr);  // the lane of rank G among the remaining ones
+            Mr &= Mr - 1u;
+            rem -= G + 1;
+            if (rem == 0)
+                break;
+            ++d;
+            const uint4 Q = dev::philox10_rk(
+                make_uint4((uint32_t)w, c1, c2 | (uint32_t)(3 + 3 * ((d - 1) >> 1)), c3), rk);
+            ++calls;
+            const bool odd = ((d - 1) & 1) != 0;
+            vh = odd ? Q.z : Q.x;
+            vl = odd ? Q.w : Q.y;
+            exact = true;
+        }
+    }
+    const bool t1 = k.M1 && (second >> 16) <= (tb.hi[1][__popc(k.M1)] >> 16);
+    const bool t0 = k.M0 && (second & 0xFFFFu) <= (tb.hi[0][__popc(k.M0)] >> 16);
+    if (t1 || t0) {
+        if (!have_x) {
+            X = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 64u, c3), rk);
+            ++calls;
+        }
+        if (t1)
+            A |= metro_class(jb, 1, k.M1,
+                             ((uint64_t)(second >> 16) << 48) | ((uint64_t)X.y << 16) | (X.w >> 16),
+                             (uint32_t)w, c1, c2, c3, rk, calls);
+        if (t0)
+            A |= metro_class(jb, 0, k.M0,
+                             ((uint64_t)(second & 0xFFFFu) << 48) | ((uint64_t)X.z << 16) |
+                                 (X.w & 0xFFFFu),
+                             (uint32_t)w, c1, c2, c3, rk, calls);
+    }
+    upd[w] = s ^ alw ^ A;
+}
+
+// Full adders of three bits: sum and carry.
+__device__ __forceinline__ void add3(uint32_t a, uint32_t b, uint32_t c, uint32_t &sum,
+                                     uint32_t &carry)
+{
+    sum = a ^ b ^ c;
+    carry = maj3(a, b, c);
+}
+
+// One word of a tile: its outright flips (u >= 3) and whether the leading bits
+// of its first draws might accept a lane (first: class 2; second: class 1 high
+// half, class 0 low half).  With LOWT the classes 1 and 0 are tested against
+// the job's 32-lane bounds T1x, T0, a superset of the exact per-count test.
+template <bool LOWT>
+__device__ __forceinline__ bool tile_word(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3,
+                                          uint32_t u4, uint32_t u5, uint32_t first,
+                                          uint32_t second, const TileTables &tb, uint32_t T1x,
+                                          uint32_t T0, uint32_t live0, uint32_t live1,
+                                          uint32_t live2, uint32_t &alw)
+{
+    if (LOWT) {
+        // u = 2 (k1 + k2) + s1 + s2 from two full adders
+        uint32_t s1, k1, s2, k2;
+        add3(u0, u1, u2, s1, k1);
+        add3(u3, u4, u5, s2, k2);
+        alw = maj3(k1, k2, s1 | s2);                   // u >= 3
+        const uint32_t m2 = (k1 | k2 | (s1 & s2)) & ~alw;  // u == 2
+        return (first <= tb.hi[2][__popc(m2)]) | (second <= T1x) | ((second & 0xFFFFu) <= T0);
+    } else {
+        const Count c = count6(u0, u1, u2, u3, u4, u5);
+        alw = c.b2 | (c.b1 & c.b0);
+        const Classes k = classes(c, alw, 0xffffffffu, live0, live1, live2);
+        return (first <= tb.hi[2][__popc(k.M2)]) | (second <= tb.t1[__popc(k.M1)]) |
+               ((second & 0xFFFFu) <= tb.t0[__popc(k.M0)]);
+    }
+}
+
+template <bool COUNT, int MAXJ, int GL, bool LOWT>
+__global__ void __launch_bounds__(kSweepThreads, 9)
+    metro_tile_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
+{
+    constexpr int N2 = GL / 32, SZ = GL * GL;
+    constexpr int XP = GL / 2, ZP = N2 / 2;
+    constexpr int XPLOG = GL == 128 ? 6 : 5;
+    constexpr uint32_t W = (uint32_t)SZ * N2;
+    int j = 0;
+    {
+        int lo = 0, hi = P.n_jobs - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.block_begin[mid] <= b)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    const MetroJob &J = P.job[j];
+    const MetroGeo &G = P.geo[(J.meta >> 8) & 0xFFu];
+    const JobDev *__restrict__ jb = P.jobs_dev + j;
+    uint32_t rk[20];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = J.key0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = J.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    __shared__ TileTables tb;
+    __shared__ uint4 s_q[kSweepThreads / 32][kTileQueue];
+    __shared__ int s_qn[kSweepThreads / 32];
+    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x) {
+        const int u = i / 33, n = i - 33 * u;
+        const uint32_t hi = jb->gC_hi[u][n];
+        tb.hi[u][n] = hi;
+        if (u == 1)
+            tb.t1[n] = (hi & 0xFFFF0000u) | 0xFFFFu;
+        if (u == 0)
+            tb.t0[n] = hi >> 16;
+    }
+    if (threadIdx.x < kSweepThreads / 32)
+        s_qn[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t t = jb->t + P.sweep_offset;
+    if (t >= jb->t_end)
+        return;
+
+    const int h = P.h;
+    const int lane = threadIdx.x & 31;
+    uint4 *q = s_q[threadIdx.x >> 5];
+    int *qn = &s_qn[threadIdx.x >> 5];
+    const int Y = G.seg;
+    const int local = (int)blockIdx.x - P.block_begin[j];
+    const int s = local / G.bps;
+    const int tl = (local - s * G.bps) * kSweepThreads + (int)threadIdx.x;
+    const int x0 = 2 * (tl & (XP - 1));
+    const int z0 = 2 * ((tl >> XPLOG) & (ZP - 1));  // uniform over a warp (XP >= 32)
+    const int y0 = (tl >> XPLOG) / ZP * Y;
+    const bool all_always = (J.meta >> 3) & 1u, none_random = (J.meta >> 4) & 1u;
+    const uint32_t live0 = 0u - (J.meta & 1u), live1 = 0u - ((J.meta >> 1) & 1u),
+                   live2 = 0u - ((J.meta >> 2) & 1u);
+    const uint32_t always3 = jb->always_u & 7u;
+    const uint32_t T1x = (jb->gC_hi[1][32] & 0xFFFF0000u) | 0xFFFFu, T0 = jb->gC_hi[0][32] >> 16;
+    uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
+    const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
+    const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
+    const uint32_t *__restrict__ Jy = Jx + W;
+    const uint32_t *__restrict__ Jz = Jy + W;
+    const uint32_t c3 = (uint32_t)s / J.rng_group;
+    const uint32_t c1 = (uint32_t)t;
+    const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
+    const int oz0 = z0 * SZ, oz1 = oz0 + SZ;
+    const int ozm = (z0 == 0 ? N2 - 1 : z0 - 1) * SZ;
+    const int ozp = (z0 + 2 == N2 ? 0 : z0 + 2) * SZ;
+    const bool wrap_m = z0 == 0, wrap_p = z0 + 2 == N2;
+    const int xm = (x0 - 1) & (GL - 1), xq = (x0 + 2) & (GL - 1);
+    unsigned int n_words = 0, n_calls = 0, n_extra = 0;
+
+    // the window: neighbour rows y - 1 (m) and y (c), y bonds of row y - 1
+    const int rym = ((y0 - 1) & (GL - 1)) * GL;
+    uint2 Nm0 = ld2(nb, x0 + rym + oz0), Nm1 = ld2(nb, x0 + rym + oz1);
+    uint2 Jym0 = ld2(Jy, x0 + rym + oz0), Jym1 = ld2(Jy, x0 + rym + oz1);
+    uint2 Nc0 = ld2(nb, x0 + y0 * GL + oz0), Nc1 = ld2(nb, x0 + y0 * GL + oz1);
+    for (int i = 0; i < Y; ++i) {
+        const int y = y0 + i;
+        const int ry = y * GL, ryp = ((y + 1) & (GL - 1)) * GL;
+        const int w0 = x0 + ry + oz0, w1 = x0 + ry + oz1;  // the even-x words at z0, z0 + 1
+        const uint2 S0 = ld2(upd, w0), S1 = ld2(upd, w1);
+        const uint2 Nn0 = ld2(nb, x0 + ryp + oz0), Nn1 = ld2(nb, x0 + ryp + oz1);
+        uint2 Nzm = ld2(nb, x0 + ry + ozm), Nzp = ld2(nb, x0 + ry + ozp);
+        uint2 Jzm = ld2(Jz, x0 + ry + ozm);
+        const uint32_t Xm0 = nb[xm + ry + oz0], Xm1 = nb[xm + ry + oz1];
+        const uint32_t Xp0 = nb[xq + ry + oz0], Xp1 = nb[xq + ry + oz1];
+        const uint32_t Jxm0 = Jx[xm + ry + oz0], Jxm1 = Jx[xm + ry + oz1];
+        const uint2 Jx0 = ld2(Jx, w0), Jx1 = ld2(Jx, w1);
+        const uint2 Jy0 = ld2(Jy, w0), Jy1 = ld2(Jy, w1);
+        const uint2 Jz0 = ld2(Jz, w0), Jz1 = ld2(Jz, w1);
+        if (wrap_m) {
+            Nzm = make_uint2(rot_zm(Nzm.x), rot_zm(Nzm.y));
+            Jzm = make_uint2(rot_zm(Jzm.x), rot_zm(Jzm.y));
+        }
+        if (wrap_p)
+            Nzp = make_uint2(rot_zp(Nzp.x), rot_zp(Nzp.y));
+        // main calls: pair (x0, z0 | z0 + 1) and pair (x0 + 1, z0 | z0 + 1)
+        const uint32_t c2A = c2m | ((uint32_t)(h ^ (y & 1)) << 11);
+        const uint32_t c2B = c2A ^ (1u << 11);
+        uint4 RA = make_uint4(0u, 0u, 0u, 0u), RB = RA;
+        if (!(all_always || none_random)) {  // the pairs' main calls
+            RA = dev::philox10_rk(make_uint4((uint32_t)w0, c1, c2A, c3), rk);
+            RB = dev::philox10_rk(make_uint4((uint32_t)w0 + 1u, c1, c2B, c3), rk);
+        }
+        // words a0 = (x0, z0), a1 = (x0 + 1, z0), b0 = (x0, z0 + 1), b1 = (x0 + 1, z0 + 1)
+        uint32_t alwa0, alwa1, alwb0, alwb1;
+        uint32_t sp = S0.x;
+        const bool draw = !(all_always || none_random);
+        bool ha0 = tile_word<LOWT>(sp ^ Nc0.y ^ Jx0.x, sp ^ Xm0 ^ Jxm0, sp ^ Nn0.x ^ Jy0.x,
+                                   sp ^ Nm0.x ^ Jym0.x, sp ^ Nc1.x ^ Jz0.x, sp ^ Nzm.x ^ Jzm.x,
+                                   RA.x, RA.y, tb, T1x, T0, live0, live1, live2, alwa0);
+        sp = S0.y;
+        bool ha1 = tile_word<LOWT>(sp ^ Xp0 ^ Jx0.y, sp ^ Nc0.x ^ Jx0.x, sp ^ Nn0.y ^ Jy0.y,
+                                   sp ^ Nm0.y ^ Jym0.y, sp ^ Nc1.y ^ Jz0.y, sp ^ Nzm.y ^ Jzm.y,
+                                   RB.x, RB.y, tb, T1x, T0, live0, live1, live2, alwa1);
+        sp = S1.x;
+        bool hb0 = tile_word<LOWT>(sp ^ Nc1.y ^ Jx1.x, sp ^ Xm1 ^ Jxm1, sp ^ Nn1.x ^ Jy1.x,
+                                   sp ^ Nm1.x ^ Jym1.x, sp ^ Nzp.x ^ Jz1.x, sp ^ Nc0.x ^ Jz0.x,
+                                   RA.z, RA.w, tb, T1x, T0, live0, live1, live2, alwb0);
+        sp = S1.y;
+        bool hb1 = tile_word<LOWT>(sp ^ Xp1 ^ Jx1.y, sp ^ Nc1.x ^ Jx1.x, sp ^ Nn1.y ^ Jy1.y,
+                                   sp ^ Nm1.y ^ Jym1.y, sp ^ Nzp.y ^ Jz1.y, sp ^ Nc0.y ^ Jz0.y,
+                                   RB.z, RB.w, tb, T1x, T0, live0, live1, live2, alwb1);
+        ha0 = ha0 && draw;
+        ha1 = ha1 && draw;
+        hb0 = hb0 && draw;
+        hb1 = hb1 && draw;
+        Nm0 = Nc0;
+        Nm1 = Nc1;
+        Nc0 = Nn0;
+        Nc1 = Nn1;
+        Jym0 = Jy0;
+        Jym1 = Jy1;
+        // every word is written with its outright flips; a queued word is
+        // written again by the rare path
+        const uint32_t fx = all_always ? 0xffffffffu : 0u;
+        *reinterpret_cast<uint2 *>(upd + w0) = make_uint2(S0.x ^ (alwa0 | fx), S0.y ^ (alwa1 | fx));
+        *reinterpret_cast<uint2 *>(upd + w1) = make_uint2(S1.x ^ (alwb0 | fx), S1.y ^ (alwb1 | fx));
+        if (COUNT)
+            n_words += 4;
+        if (all_always || none_random)
+            continue;
+        if (COUNT)
+            n_calls += 2;
+        if (ha0)
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0, S0.x, RA.x, RA.y);
+        if (ha1)
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0 + 1u, S0.y, RB.x, RB.y);
+        if (hb0)
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1, S1.x, RA.z, RA.w);
+        if (hb1)
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1 + 1u, S1.y, RB.z, RB.w);
+        __syncwarp();
+        int q_n = *qn;
+        if (q_n >= 96) {  // full rounds, one queued word per lane, while 32 are queued
+            do {
+                q_n -= 32;
+                const uint4 e = q[q_n + lane];
+                unsigned int extra = 0;
+                tile_finish<GL>(jb, tb, e, upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3,
+                                c1, c2m, c3, rk, extra);
+                if (COUNT)
+                    n_extra += extra;
+                __syncwarp();
+            } while (q_n >= 32);
+            if (lane == 0)
+                *qn = q_n;
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    const int q_n = *qn;
+    for (int k = lane; k < q_n; k += 32) {  // the words still queued
+        unsigned int extra = 0;
+        tile_finish<GL>(jb, tb, q[k], upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3, c1,
+                        c2m, c3, rk, extra);
         if (COUNT)
             n_extra += extra;
     }
@@ -738,22 +1119,51 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
             geo_L[gi] = jd.geo.L;
             geo_cpt[gi] = jd.cols_per_thread;
             metro_geo(p.geo[gi], jd);
+            if (GL != 0) {
+                // tiles of 2 x 2 word-sites times a segment of Y = 4, 8 or 16 rows
+                const int Y = jd.cols_per_thread >= 4 ? 16 : jd.cols_per_thread >= 2 ? 8 : 4;
+                p.geo[gi].seg = Y;
+                p.geo[gi].bps = (GL / 2) * (GL / 64) * (GL / Y) / kSweepThreads;
+            }
             ++n_geo;
         }
         metro_job(p.job[i], jd, gi);
-        p.block_begin[i + 1] = p.block_begin[i] + jd.n_samples * jd.blocks_per_sample;
+        p.block_begin[i + 1] = p.block_begin[i] + jd.n_samples * p.geo[gi].bps;
     }
     const int grid = p.block_begin[cnt];
     if (grid == 0)
         return;
+    // the classes dE = 8 and 12 take the 32-lane bound test when their tables
+    // are small for every job (C_u[32] < 2^56) and no class is accepted outright
+    bool lowt = true;
+    for (int i = 0; i < cnt; ++i)
+        lowt = lowt && (host[i].gC_hi[1][32] >> 24) == 0u && (host[i].gC_hi[0][32] >> 24) == 0u &&
+               (host[i].always_u & 7u) == 0u;
     for (uint64_t k = 0; k < n; ++k)
         for (int h = 0; h < 2; ++h) {
             p.h = h;
             p.sweep_offset = (uint32_t)k;
-            if (counters)
-                metro_kernel<true, MAXJ, GL><<<grid, kSweepThreads, 0, stream>>>(p, counters);
-            else
-                metro_kernel<false, MAXJ, GL><<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+            if constexpr (GL != 0) {
+                if (counters) {
+                    if (lowt)
+                        metro_tile_kernel<true, MAXJ, GL, true>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                    else
+                        metro_tile_kernel<true, MAXJ, GL, false>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                } else if (lowt) {
+                    metro_tile_kernel<false, MAXJ, GL, true>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                } else {
+                    metro_tile_kernel<false, MAXJ, GL, false>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                }
+            } else {
+                if (counters)
+                        metro_kernel<true, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                else
+                    metro_kernel<false, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+            }
         }
 }
 

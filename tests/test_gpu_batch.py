@@ -163,3 +163,27 @@ def test_autotune_changes_nothing(J):
     b.close()
     for j in jobs:
         j.close()
+
+
+@pytest.mark.parametrize("L", [24, 64, 128])
+def test_profile_counts_words_and_restores_state(J, L):
+    """The counting launch visits every word once per half-step, counts at least
+    one Philox call per two words that need one, and leaves the state as it was."""
+    spec = (L, 0.5, 77, 2, 0.8, 0, [], [])
+    S, n = spec[3], 3
+    j, ref = make(J, spec), make(J, spec)
+    b = J.EABatch()
+    b.add(j)
+    prof = b.profile(sweeps=n)
+    words = L ** 3 // 32  # all three sides have 32 lanes per word
+    assert prof["words"] == n * 2 * S * words
+    assert prof["flips"] == n * 2 * S * L ** 3
+    assert prof["general_calls"] <= prof["philox_calls"] <= prof["words"]
+    assert prof["philox_calls"] >= prof["words"] // 4
+    b.sweep(5)
+    ref.sweep(5)
+    for s in range(S):
+        assert np.array_equal(j.all_spins(s), ref.all_spins(s))
+    b.close()
+    j.close()
+    ref.close()

@@ -95,6 +95,7 @@ SWEEP_CASES = [
     (16, 0.5, float("inf"), 0, 1, 2, 3),
     (16, 0.5, 0.0, 1, 1, 2, 8),   # heat bath at T = 0: dE = 0 flips with 1/2
     (16, 1.0, 0.5, 0, 1, 2, 10),
+    (16, 0.5, 1e17, 0, 1, 2, 3),  # exp(-4/T) rounds to 1: dE = 4 accepted outright
     (24, 0.3, 0.9, 0, 1, 2, 15),
     (32, 0.5, 0.6, 0, 1, 2, 12),
     (48, 0.2, 0.7, 0, 1, 1, 4),
@@ -110,6 +111,53 @@ def test_sweeps_bit_exact(J, L, p_neg, T, rule, G, S, n):
     ref = ora.run_job(L, p_neg, seed, S, T, rule, [], [], n, keep_spins=True, rng_group=G)
     for s in range(S):
         assert np.array_equal(j.all_spins(s), ref["spins"][s]), s
+    j.close()
+
+
+# the side-64/128 kernel (2 x 2 word tiles, rows along y) under each segment length,
+# including temperatures where many words take the rare path and its later draws
+TILE_CASES = [
+    # L, p_neg, T, cols_per_thread (segment 4, 8, 16 rows), S, sweeps
+    (64, 0.5, 0.7, 1, 2, 4),
+    (64, 0.3, 2.0, 2, 2, 3),
+    (64, 0.5, 5.0, 4, 2, 3),
+    (64, 0.5, 0.0, 2, 1, 3),   # T = 0: no random numbers
+    (64, 0.5, 1e17, 1, 1, 2),  # dE = 4 accepted outright, dE = 8, 12 by draws
+    (128, 0.5, 1.5, 1, 3, 2),
+    (128, 0.2, 0.7, 4, 3, 2),
+]
+
+
+@pytest.mark.parametrize("L,p_neg,T,cpt,S,n", TILE_CASES)
+def test_tile_kernel_bit_exact(J, L, p_neg, T, cpt, S, n):
+    seed = 500 + L + cpt
+    j = J.EAJob(L, p_neg, seed, S)
+    j.quench(T)
+    b = J.EABatch()
+    b.configure(cpt, 0)
+    b.add(j)
+    b.sweep(n)
+    pick = [0, S - 1] if S > 1 else [0]
+    ref = ora.run_job(L, p_neg, seed, S, T, 0, [], [], n, samples=pick, keep_spins=True)
+    for i, s in enumerate(pick):
+        assert np.array_equal(j.all_spins(s), ref["spins"][i]), s
+    b.close()
+    j.close()
+
+
+@pytest.mark.parametrize("t0", [(1 << 32) - 1, (1 << 44) + 77])
+def test_tile_kernel_late_time(J, t0):
+    """The high bits of the sweep counter in the tile kernel's draws."""
+    L, seed, p_neg, T = 64, 41, 0.5, 0.9
+    Jc = ora.init_couplings(L, p_neg, seed, 0)
+    S0 = ora.init_spins(L, seed, 0)
+    ref = S0.copy()
+    ora.sweeps(L, seed, 0, ref, Jc, T, 0, t0, 3)
+    j = J.EAJob(L, p_neg, seed, 1)
+    j.quench(T)
+    j.set_time(t0)
+    j.sweep(3)
+    assert np.array_equal(j.all_spins(0), ref)
     j.close()
 
 
