@@ -163,12 +163,13 @@ OPS_FIXED_PER_WORD = 35
 OPS_PER_PHILOX = 60        # 10 rounds x (2 mul.lo + 2 mul.hi + 2 three-input XOR)
 INT_LANES_PER_SM = 128     # int32-capable lanes per SM (4 SMSP x 32)
 N_SM = 152
-# DRAM bytes (read + write) of one batched half-step launch of this workload,
-# from an ncu capture of this command (dram__bytes_read.sum +
+# DRAM bytes (read + write) of one batched half-step launch of this workload
+# per launch shape (rows per thread 4, 8, 16 <-> --cpt 1, 2, 4), from an ncu
+# capture of this command with that fixed shape (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass, caches flushed before each captured launch;
-# profiles/launches_bench_L128_S16x5.md, mean of three launches).  Take it
+# profiles/launches_bench_L128_S16x5.md, mean of three launches).  Take them
 # again (or set None) when the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 110.35e6 + 5.20e6
+TRAFFIC_BYTES_PER_LAUNCH = {1: 104.95e6 + 3.03e6, 2: 114.11e6 + 6.97e6, 4: 120.80e6 + 10.02e6}
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
@@ -230,7 +231,11 @@ def run_ours(args, world, rank, local):
     batch = job.EABatch(stream=stream)
     for j in jobs:
         batch.add(j)
-    batch_cfg = batch.autotune(trial_sweeps=8)
+    if args.cpt:
+        batch.configure(args.cpt, args.graph_sweeps)
+        batch_cfg = (args.cpt, args.graph_sweeps)
+    else:
+        batch_cfg = batch.autotune(trial_sweeps=8)
 
     def batched_step():
         batch.sweep(sps)
@@ -298,7 +303,8 @@ def run_ours(args, world, rank, local):
            "bytes_per_flip": bytes_per_flip, "peak_kind": pk_kind + " (copy bandwidth)"}
     primary, other = (hbm, alu) if hbm_roof <= alu_roof else (alu, hbm)
     roof = dict(primary)
-    traffic = args.traffic_bytes if args.traffic_bytes is not None else TRAFFIC_BYTES_PER_LAUNCH
+    traffic = (args.traffic_bytes if args.traffic_bytes is not None
+               else TRAFFIC_BYTES_PER_LAUNCH.get(batch_cfg[0]))
     roof.update({"traffic": traffic, "kernel": "metro_tile_kernel",
                  "traffic_over_algorithmic": (None if traffic is None else
                                               traffic / (flips_per_launch * bytes_per_flip)),
@@ -511,6 +517,9 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--ref-sweeps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpt", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="fixed launch shape of the batched path instead of the autotuned one")
+    ap.add_argument("--graph-sweeps", type=int, default=8)
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per half-step launch from an ncu capture of this command")
     ap.add_argument("--no-serve", action="store_true")

@@ -284,19 +284,20 @@ int ora_init_spins(int L, uint64_t seed, uint32_t s, int8_t *S)
 /*   floor(ldexp(-expm1(g * log1p(-p_u)), 64)), clamped to 2^64 - 1.         */
 /* The sites after an acceptance start a fresh gap with the next draw.      */
 /*                                                                          */
-/* Draws.  Word-sites pair up along z (z' even with z' + 1): one Philox call */
-/* per pair holds the leading bits of both words' first draws:               */
-/*   main call of the pair: counter (widx of the even word, lo32(t),         */
-/*     (3 << 30) | (bits 32..47 of t) << 12 | a_even << 11 | 0, s), where    */
-/*     a_even is the replica updated at the even word in this half-step;     */
-/*     outputs 0, 1 belong to the even word, 2, 3 to the odd word:           */
-/*     first output = bits 63..32 of draw 0 of class 2 (dE = 4),             */
-/*     second output = bits 63..48 of draw 0 of class 1 (high half) and of   */
-/*     class 0 (low half).                                                   */
-/*   extension call of a word: counter (its widx, lo32(t), ... | a << 11 |   */
-/*     64, s): output 0 = bits 31..0 of class 2's draw 0; outputs 1, 2 =     */
-/*     bits 47..16 of class 1's and class 0's draw 0; output 3 = bits 15..0  */
-/*     of class 1's (high half) and class 0's (low half) draw 0.             */
+/* Draws.  Word-sites group in quads (x' even, x' + 1) x (z' even, z' + 1) */
+/* of the word lattice: one Philox call per quad holds the leading bits of  */
+/* the first draws of all four words:                                       */
+/*   main call of the quad: counter (widx of its word (x' even, z' even),   */
+/*     lo32(t), (3 << 30) | (bits 32..47 of t) << 12 | a_q << 11 | 0, s),     */
+/*     where a_q is the replica updated at that word in this half-step;     */
+/*     output k = (x' mod 2) + 2 (z' mod 2) belongs to word (x', y', z'):    */
+/*     its bits 31..20 are bits 63..52 of draw 0 of class 2 (dE = 4), bits  */
+/*     19..10 bits 63..54 of class 1's (dE = 8), bits 9..0 bits 63..54 of   */
+/*     class 0's (dE = 12).                                                 */
+/*   extension calls of a word: counter (its widx, lo32(t), ... | a << 11 | */
+/*     call, s).  Call 64: (out0 << 32 | out1) >> 12 = bits 51..0 of class */
+/*     2's draw 0, (out2 << 32 | out3) >> 10 = bits 53..0 of class 1's.    */
+/*     Call 65: (out0 << 32 | out1) >> 10 = bits 53..0 of class 0's.        */
 /*   draw d >= 1 of class u of a word: the 64-bit number (out[2e] << 32) |   */
 /*     out[2e + 1] of call 1 + u + 3 (d-1 div 2), e = (d-1) mod 2, with the   */
 /*     word's own widx and replica.                                          */
@@ -338,19 +339,23 @@ static uint64_t metro_draw(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed
         metro_call(widx, seed, s, a, t, 1 + u + 3 * ((d - 1) / 2), out);
         return ((uint64_t)out[2 * e] << 32) | (uint64_t)out[2 * e + 1];
     }
-    /* leading bits from the pair's main call */
-    int odd = zw & 1;
-    uint32_t widx_even = (uint32_t)(xw + Lx * (yw + Ly * (zw - odd)));
-    int a_even = odd ? (a ^ 1) : a; /* the two words of a pair hold different replicas */
+    /* leading bits from the quad's main call */
+    int ox = xw & 1, oz = zw & 1;
+    uint32_t widx_q = (uint32_t)((xw - ox) + Lx * (yw + Ly * (zw - oz)));
+    int a_q = a ^ ox ^ oz; /* the replica updated at the quad's first word */
     uint32_t m[4], x[4];
-    metro_call(widx_even, seed, s, a_even, t, 0, m);
-    metro_call(widx, seed, s, a, t, 64, x);
-    uint32_t first = m[2 * odd], second = m[2 * odd + 1];
-    if (u == 2)
-        return ((uint64_t)first << 32) | (uint64_t)x[0];
-    if (u == 1)
-        return ((uint64_t)(second >> 16) << 48) | ((uint64_t)x[1] << 16) | (uint64_t)(x[3] >> 16);
-    return ((uint64_t)(second & 0xFFFFu) << 48) | ((uint64_t)x[2] << 16) | (uint64_t)(x[3] & 0xFFFFu);
+    metro_call(widx_q, seed, s, a_q, t, 0, m);
+    uint32_t lead = m[ox + 2 * oz];
+    if (u == 2) {
+        metro_call(widx, seed, s, a, t, 64, x);
+        return ((uint64_t)(lead >> 20) << 52) | ((((uint64_t)x[0] << 32) | x[1]) >> 12);
+    }
+    if (u == 1) {
+        metro_call(widx, seed, s, a, t, 64, x);
+        return ((uint64_t)((lead >> 10) & 0x3FFu) << 54) | ((((uint64_t)x[2] << 32) | x[3]) >> 10);
+    }
+    metro_call(widx, seed, s, a, t, 65, x);
+    return ((uint64_t)(lead & 0x3FFu) << 54) | ((((uint64_t)x[0] << 32) | x[1]) >> 10);
 }
 
 /* Flip decisions of the lanes lane_list[0..n) (increasing lane order) of one

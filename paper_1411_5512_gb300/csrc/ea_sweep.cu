@@ -99,21 +99,49 @@ __device__ __forceinline__ Count count6(uint32_t u0, uint32_t u1, uint32_t u2, u
 }
 
 // ---------------------------------------------------------------------------
-// Metropolis draws.  Word-sites pair up along z (z' even with z' + 1); one
-// Philox call per pair ("main", call 0, keyed by the even word and its
-// replica) holds the leading bits of both words' first draws: outputs 0, 1
-// for the even word, 2, 3 for the odd one; the first of the two is bits
-// 63..32 of class 2's draw 0, the second bits 63..48 of class 1's (high half)
-// and class 0's (low half) draw 0.  A word's "extension" call (call 64, its
-// own widx and replica) holds the remaining bits: output 0 = bits 31..0 of
-// class 2's draw; outputs 1, 2 = bits 47..16 of class 1's and class 0's
-// draw; output 3 = their bits 15..0 (high, low half).  Draw d >= 1 of class
-// u is (out[2e] << 32) | out[2e + 1] of call 1 + u + 3 ((d - 1) div 2),
-// e = (d - 1) mod 2.
+// Metropolis draws.  Word-sites group in quads (x' even, x' + 1) x (z' even,
+// z' + 1); one Philox call per quad ("main", call 0, keyed by the quad's word
+// (x' even, z' even) and its replica) holds the leading bits of the first
+// draws of all four words.  Output k = (x' & 1) + 2 (z' & 1) belongs to word
+// (x', y', z'): bits 31..20 lead class 2's draw 0 (bits 63..52), bits 19..10
+// class 1's (63..54), bits 9..0 class 0's.  A word's extension calls (its
+// own widx and replica) hold the rest: call 64 gives (out0:out1) >> 12 =
+// bits 51..0 of class 2's draw and (out2:out3) >> 10 = bits 53..0 of class
+// 1's; call 65 gives (out0:out1) >> 10 = bits 53..0 of class 0's.  Draw
+// d >= 1 of class u is (out[2e] << 32) | out[2e + 1] of call
+// 1 + u + 3 ((d - 1) div 2), e = (d - 1) mod 2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t c64(const JobDev *__restrict__ jb, int u, int g)
 {
     return ((uint64_t)jb->gC_hi[u][g] << 32) | jb->gC_lo[u][g];
+}
+
+// The lane (as a one-bit mask) of rank k among the set bits of m, k < popc(m).
+__device__ __forceinline__ uint32_t nth_bit(uint32_t m, int k)
+{
+    int p = 0, c = __popc(m & 0xFFFFu);
+    if (k >= c) {
+        k -= c;
+        p = 16;
+    }
+    c = __popc((m >> p) & 0xFFu);
+    if (k >= c) {
+        k -= c;
+        p += 8;
+    }
+    c = __popc((m >> p) & 0xFu);
+    if (k >= c) {
+        k -= c;
+        p += 4;
+    }
+    c = __popc((m >> p) & 0x3u);
+    if (k >= c) {
+        k -= c;
+        p += 2;
+    }
+    if (k >= (int)((m >> p) & 1u))
+        p += 1;
+    return 1u << p;
 }
 
 // The accepted lanes of one class of a word, from its full first draw V0.
@@ -129,13 +157,19 @@ __device__ __forceinline__ uint32_t metro_class(const JobDev *__restrict__ jb, i
     while (rem > 0) {
         if (!(V < c64(jb, u, rem)))
             break;  // no acceptance among the remaining lanes
-        int G = 0;
-        while (!(V < c64(jb, u, G + 1)))
-            ++G;
-        for (int i = 0; i < G; ++i)
-            Mr &= Mr - 1u;
-        acc |= Mr & (0u - Mr);  // the lane of rank G among the remaining ones
-        Mr &= Mr - 1u;
+        // G = min{g : V < C[g + 1]} by bisection over the nondecreasing table
+        int lo = 1, hi = rem;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (V < c64(jb, u, mid))
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const int G = lo - 1;
+        const uint32_t bit = nth_bit(Mr, G);  // the lane of rank G among the remaining ones
+        acc |= bit;
+        Mr &= ~(bit | (bit - 1u));
         rem -= G + 1;
         if (rem == 0)
             break;
@@ -165,16 +199,51 @@ __device__ __forceinline__ Classes classes(const Count &c, uint32_t alw, uint32_
     return k;
 }
 
+// Leading-bit tables: a word's 32 main bits M might accept a lane of class 2
+// iff M <= lead2(C_2[n]), of class 1 iff (M & 0xFFC00) <= lead1(C_1[n]), of
+// class 0 iff (M & 0x3FF) <= lead0(C_0[n]); hi = C_u[n] >> 32.
+__device__ __forceinline__ uint32_t lead2(uint32_t hi)
+{
+    return (hi & 0xFFF00000u) | 0xFFFFFu;
+}
+
+__device__ __forceinline__ uint32_t lead1(uint32_t hi)
+{
+    return ((hi >> 22) << 10) | 0x3FFu;
+}
+
+__device__ __forceinline__ uint32_t lead0(uint32_t hi)
+{
+    return hi >> 22;
+}
+
 // Might some lane of the word flip?  The leading bits of the first draws
-// against the tables: an exact "no" for ~97% of words at T = 0.7.
-__device__ __forceinline__ bool class_hit(const Classes &k, uint32_t first, uint32_t second,
-                                          const uint32_t (*gh)[33])
+// against the tables (lead2, lead1, lead0 of C_u[n]): an exact "no" for ~97%
+// of words at T = 0.7.
+__device__ __forceinline__ bool class_hit(const Classes &k, uint32_t M, const uint32_t (*gh)[33])
 {
     const int n0 = __popc(k.M0), n1 = __popc(k.M1), n2 = __popc(k.M2);
-    const bool h2 = (n2 != 0) & (first <= gh[2][n2]);
-    const bool h1 = (n1 != 0) & ((second >> 16) <= (gh[1][n1] >> 16));
-    const bool h0 = (n0 != 0) & ((second & 0xFFFFu) <= (gh[0][n0] >> 16));
+    const bool h2 = (n2 != 0) & (M <= gh[2][n2]);
+    const bool h1 = (n1 != 0) & ((M & 0xFFC00u) <= gh[1][n1]);
+    const bool h0 = (n0 != 0) & ((M & 0x3FFu) <= gh[0][n0]);
     return h0 | h1 | h2;
+}
+
+// The first draw of class u of a word from its main bits M and its extension
+// calls X (call 64) and Y (call 65).
+__device__ __forceinline__ uint64_t first_draw2(uint32_t M, const uint4 &X)
+{
+    return ((uint64_t)(M >> 20) << 52) | ((((uint64_t)X.x << 32) | X.y) >> 12);
+}
+
+__device__ __forceinline__ uint64_t first_draw1(uint32_t M, const uint4 &X)
+{
+    return ((uint64_t)((M >> 10) & 0x3FFu) << 54) | ((((uint64_t)X.z << 32) | X.w) >> 10);
+}
+
+__device__ __forceinline__ uint64_t first_draw0(uint32_t M, const uint4 &Y)
+{
+    return ((uint64_t)(M & 0x3FFu) << 54) | ((((uint64_t)Y.x << 32) | Y.y) >> 10);
 }
 
 // Words whose class test hit wait in a per-warp queue and are finished by the
@@ -182,7 +251,7 @@ __device__ __forceinline__ bool class_hit(const Classes &k, uint32_t first, uint
 constexpr int kQueue = 96;  // entries per warp (up to 64 are added per step)
 
 struct Pending {
-    uint32_t w, base, M0, M1, M2, c2, first, second;
+    uint32_t w, base, M0, M1, M2, c2, lead;  // lead: the word's 32 main bits
 };
 
 __device__ __forceinline__ void finish_word(const JobDev *__restrict__ jb, const Pending &e,
@@ -190,7 +259,7 @@ __device__ __forceinline__ void finish_word(const JobDev *__restrict__ jb, const
                                             uint32_t c1, uint32_t c3, const uint32_t (&rk)[20],
                                             unsigned int &calls)
 {
-    // the extension call completes the three first draws to 64 bits
+    // the extension call completes the first draws of classes 2 and 1
     const uint4 X = dev::philox10_rk(make_uint4(e.w, c1, e.c2 | 64u, c3), rk);
     ++calls;
     uint32_t A = 0u, M0 = e.M0, M1 = e.M1, M2 = e.M2;
@@ -202,16 +271,15 @@ __device__ __forceinline__ void finish_word(const JobDev *__restrict__ jb, const
         M0 = (always3 & 1u) ? 0u : M0;
     }
     if (M2)
-        A |= metro_class(jb, 2, M2, ((uint64_t)e.first << 32) | X.x, e.w, c1, e.c2, c3, rk, calls);
+        A |= metro_class(jb, 2, M2, first_draw2(e.lead, X), e.w, c1, e.c2, c3, rk, calls);
     if (M1)
-        A |= metro_class(jb, 1, M1,
-                         ((uint64_t)(e.second >> 16) << 48) | ((uint64_t)X.y << 16) | (X.w >> 16),
-                         e.w, c1, e.c2, c3, rk, calls);
-    if (M0)
-        A |= metro_class(jb, 0, M0,
-                         ((uint64_t)(e.second & 0xFFFFu) << 48) | ((uint64_t)X.z << 16) |
-                             (X.w & 0xFFFFu),
-                         e.w, c1, e.c2, c3, rk, calls);
+        A |= metro_class(jb, 1, M1, first_draw1(e.lead, X), e.w, c1, e.c2, c3, rk, calls);
+    // class 0 needs its own extension call, unless its leading bits rule it out
+    if (M0 && (e.lead & 0x3FFu) <= lead0(jb->gC_hi[0][__popc(M0)])) {
+        const uint4 Y = dev::philox10_rk(make_uint4(e.w, c1, e.c2 | 65u, c3), rk);
+        ++calls;
+        A |= metro_class(jb, 0, M0, first_draw0(e.lead, Y), e.w, c1, e.c2, c3, rk, calls);
+    }
     upd[e.w] = e.base ^ (A & valid);
 }
 
@@ -247,8 +315,11 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
     }
     __shared__ uint32_t s_gh[3][33];
     __shared__ Pending s_q[kSweepThreads / 32][kQueue];
-    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x)
-        (&s_gh[0][0])[i] = (&jb->gC_hi[0][0])[i];
+    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x) {
+        const int u = i / 33;
+        const uint32_t hi = (&jb->gC_hi[0][0])[i];
+        (&s_gh[0][0])[i] = u == 2 ? lead2(hi) : u == 1 ? lead1(hi) : lead0(hi);
+    }
     __syncthreads();
     const uint64_t t = jb->t + P.sweep_offset;
     if (t >= jb->t_end)
@@ -315,6 +386,8 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
         // replica updated at word-site (x, y, z) in half-step h: h ^ ((x + y + z) & 1)
         const uint32_t c2e = c2m | ((uint32_t)(h ^ ((x + y) & 1)) << 11);      // even z
         const uint32_t c2o = c2m | ((uint32_t)(h ^ ((x + y + 1) & 1)) << 11);  // odd z
+        const int xo = x & 1;                                                   // odd x
+        const uint32_t c2q = c2e ^ ((uint32_t)xo << 11);  // the quad's first word
         // z window: neighbour area at z' - 1 and the backward z bond below z'
         uint32_t nz_prev = fixup(nb[col + (n2 - 1) * sz], az, 1);
         uint32_t jz_prev = fixup(Jz[col + (n2 - 1) * sz], az, 1);
@@ -378,12 +451,14 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
             }
             const Classes ka = classes(ca, alwa, valid, live0, live1, live2);
             const Classes kb = classes(cw, alwb, valid, live0, live1, live2);
-            // leading bits of the first draws of both words: one call per pair
-            const uint4 Rm = dev::philox10_rk(make_uint4((uint32_t)wa, c1, c2e, c3), rk);
+            // leading bits of the first draws: the main call of the quad
+            // (x & ~1, y, z | z + 1), computed by both of its columns
+            const uint4 Rm = dev::philox10_rk(make_uint4((uint32_t)(wa - xo), c1, c2q, c3), rk);
             if (COUNT && act)
-                n_calls += 1;  // the main call of the pair
-            const bool ha = act && class_hit(ka, Rm.x, Rm.y, s_gh);
-            const bool hb = act && class_hit(kb, Rm.z, Rm.w, s_gh);
+                n_calls += 1;
+            const uint32_t La = xo ? Rm.y : Rm.x, Lb = xo ? Rm.w : Rm.z;
+            const bool ha = act && class_hit(ka, La, s_gh);
+            const bool hb = act && class_hit(kb, Lb, s_gh);
             const uint32_t basea = spa ^ (alwa & valid), baseb = spb ^ (alwb & valid);
             if (act && !ha)
                 upd[wa] = basea;
@@ -403,8 +478,7 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
                 e.M1 = ka.M1;
                 e.M2 = ka.M2;
                 e.c2 = c2e;
-                e.first = Rm.x;
-                e.second = Rm.y;
+                e.lead = La;
             }
             q_n += __popc(ba);
             if (hb) {
@@ -415,8 +489,7 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
                 e.M1 = kb.M1;
                 e.M2 = kb.M2;
                 e.c2 = c2o;
-                e.first = Rm.z;
-                e.second = Rm.w;
+                e.lead = Lb;
             }
             q_n += __popc(bbm);
             __syncwarp();
@@ -475,17 +548,17 @@ constexpr int kTileQueue = 224;  // entries per warp: up to 95 left over + 128 a
 
 // Threshold tables of a block's job in shared memory.
 struct TileTables {
-    uint32_t hi[3][33];  // C_u[n] >> 32
-    uint32_t t1[33];     // C_1[n] >> 48 followed by 16 one bits
-    uint32_t t0[33];     // C_0[n] >> 48
+    uint32_t hi[3][33];    // C_u[n] >> 32
+    uint32_t lead[3][33];  // lead0, lead1, lead2 of C_u[n]
 };
 
 // The rare path of one queued word: e = (word-site, spins before the update,
-// leading bits of the first draws).  The classes are counted again from the
-// neighbour area, which this half-step does not write.  Class 2 is decided on
-// the 32 leading bits of its draws; the extension call, which completes the
-// first draws of all three classes, is fetched only when those bits tie with
-// the table or when the 16 leading bits of class 1 or 0 do not rule them out.
+// its 32 main bits M).  The classes are counted again from the neighbour
+// area, which this half-step does not write.  Class 2 is decided on the 12
+// leading bits of its first draw and the full 64 bits of later draws; the
+// extension call 64, which completes the first draws of classes 2 and 1, is
+// drawn only when those leading bits tie with the table or when class 1's 10
+// leading bits do not rule it out; call 65 (class 0) likewise.
 template <int GL>
 __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const TileTables &tb,
                                             const uint4 &e, uint32_t *__restrict__ upd,
@@ -500,7 +573,7 @@ __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const
     constexpr int SLOG = GL == 128 ? 7 : 6;
     constexpr int N2 = GL / 32, SZ = GL * GL;
     const int w = (int)e.x;
-    const uint32_t s = e.y, first = e.z, second = e.w;
+    const uint32_t s = e.y, M = e.z;
     const int x = w & (GL - 1), y = (w >> SLOG) & (GL - 1), z = w >> (2 * SLOG);
     const int wxp = x == GL - 1 ? w - (GL - 1) : w + 1;
     const int wxm = x == 0 ? w + (GL - 1) : w - 1;
@@ -540,33 +613,44 @@ __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const
     if (k.M2) {
         uint32_t Mr = k.M2;
         int rem = __popc(Mr);
-        uint32_t vh = first, vl = 0u;
-        bool exact = false;  // vl holds the draw's low word
+        uint32_t vh = M >> 20, vl = 0u;  // draw 0: its 12 leading bits until extended
+        bool exact = false;
         int d = 0;
-        // V < C_2[g], from the high words unless they tie
+        // V < C_2[g]: by the leading bits unless they tie, then by all 64
         auto below = [&](int g) -> bool {
             const uint32_t ch = tb.hi[2][g];
-            if (vh != ch)
-                return vh < ch;
             if (!exact) {
+                const uint32_t c12 = ch >> 20;
+                if (vh != c12)
+                    return vh < c12;
                 if (!have_x) {
                     X = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 64u, c3), rk);
                     ++calls;
                     have_x = true;
                 }
-                vl = X.x;
+                const uint64_t V = first_draw2(M, X);
+                vh = (uint32_t)(V >> 32);
+                vl = (uint32_t)V;
                 exact = true;
             }
+            if (vh != ch)
+                return vh < ch;
             return vl < jb->gC_lo[2][g];
         };
         while (below(rem)) {
-            int G = 0;
-            while (!below(G + 1))
-                ++G;
-            for (int i = 0; i < G; ++i)
-                Mr &= Mr - 1u;
-            A |= Mr & (0u - Mr);  // the lane of rank G among the remaining ones
-            Mr &= Mr - 1u;
+            // G = min{g : V < C_2[g + 1]} by bisection over the nondecreasing table
+            int lo = 1, hi = rem;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (below(mid))
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            const int G = lo - 1;
+            const uint32_t bit = nth_bit(Mr, G);  // the lane of rank G among the remaining ones
+            A |= bit;
+            Mr &= ~(bit | (bit - 1u));
             rem -= G + 1;
             if (rem == 0)
                 break;
@@ -580,22 +664,17 @@ __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const
             exact = true;
         }
     }
-    const bool t1 = k.M1 && (second >> 16) <= (tb.hi[1][__popc(k.M1)] >> 16);
-    const bool t0 = k.M0 && (second & 0xFFFFu) <= (tb.hi[0][__popc(k.M0)] >> 16);
-    if (t1 || t0) {
+    if (k.M1 && (M & 0xFFC00u) <= tb.lead[1][__popc(k.M1)]) {
         if (!have_x) {
             X = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 64u, c3), rk);
             ++calls;
         }
-        if (t1)
-            A |= metro_class(jb, 1, k.M1,
-                             ((uint64_t)(second >> 16) << 48) | ((uint64_t)X.y << 16) | (X.w >> 16),
-                             (uint32_t)w, c1, c2, c3, rk, calls);
-        if (t0)
-            A |= metro_class(jb, 0, k.M0,
-                             ((uint64_t)(second & 0xFFFFu) << 48) | ((uint64_t)X.z << 16) |
-                                 (X.w & 0xFFFFu),
-                             (uint32_t)w, c1, c2, c3, rk, calls);
+        A |= metro_class(jb, 1, k.M1, first_draw1(M, X), (uint32_t)w, c1, c2, c3, rk, calls);
+    }
+    if (k.M0 && (M & 0x3FFu) <= tb.lead[0][__popc(k.M0)]) {
+        const uint4 Y = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 65u, c3), rk);
+        ++calls;
+        A |= metro_class(jb, 0, k.M0, first_draw0(M, Y), (uint32_t)w, c1, c2, c3, rk, calls);
     }
     upd[w] = s ^ alw ^ A;
 }
@@ -608,16 +687,16 @@ __device__ __forceinline__ void add3(uint32_t a, uint32_t b, uint32_t c, uint32_
     carry = maj3(a, b, c);
 }
 
-// One word of a tile: its outright flips (u >= 3) and whether the leading bits
-// of its first draws might accept a lane (first: class 2; second: class 1 high
-// half, class 0 low half).  With LOWT the classes 1 and 0 are tested against
-// the job's 32-lane bounds T1x, T0, a superset of the exact per-count test.
+// One word of a tile: its outright flips (u >= 3) and whether the leading
+// bits M of its first draws might accept a lane.  With LOWT the classes 1 and
+// 0 are tested against the job's 32-lane bounds T1x, T0, a superset of the
+// exact per-count test.
 template <bool LOWT>
 __device__ __forceinline__ bool tile_word(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3,
-                                          uint32_t u4, uint32_t u5, uint32_t first,
-                                          uint32_t second, const TileTables &tb, uint32_t T1x,
-                                          uint32_t T0, uint32_t live0, uint32_t live1,
-                                          uint32_t live2, uint32_t &alw)
+                                          uint32_t u4, uint32_t u5, uint32_t M,
+                                          const TileTables &tb, uint32_t T1x, uint32_t T0,
+                                          uint32_t live0, uint32_t live1, uint32_t live2,
+                                          uint32_t &alw)
 {
     if (LOWT) {
         // u = 2 (k1 + k2) + s1 + s2 from two full adders
@@ -626,13 +705,13 @@ __device__ __forceinline__ bool tile_word(uint32_t u0, uint32_t u1, uint32_t u2,
         add3(u3, u4, u5, s2, k2);
         alw = maj3(k1, k2, s1 | s2);                   // u >= 3
         const uint32_t m2 = (k1 | k2 | (s1 & s2)) & ~alw;  // u == 2
-        return (first <= tb.hi[2][__popc(m2)]) | (second <= T1x) | ((second & 0xFFFFu) <= T0);
+        return (M <= tb.lead[2][__popc(m2)]) | ((M & 0xFFC00u) <= T1x) | ((M & 0x3FFu) <= T0);
     } else {
         const Count c = count6(u0, u1, u2, u3, u4, u5);
         alw = c.b2 | (c.b1 & c.b0);
         const Classes k = classes(c, alw, 0xffffffffu, live0, live1, live2);
-        return (first <= tb.hi[2][__popc(k.M2)]) | (second <= tb.t1[__popc(k.M1)]) |
-               ((second & 0xFFFFu) <= tb.t0[__popc(k.M0)]);
+        return (M <= tb.lead[2][__popc(k.M2)]) | ((M & 0xFFC00u) <= tb.lead[1][__popc(k.M1)]) |
+               ((M & 0x3FFu) <= tb.lead[0][__popc(k.M0)]);
     }
 }
 
@@ -673,10 +752,7 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
         const int u = i / 33, n = i - 33 * u;
         const uint32_t hi = jb->gC_hi[u][n];
         tb.hi[u][n] = hi;
-        if (u == 1)
-            tb.t1[n] = (hi & 0xFFFF0000u) | 0xFFFFu;
-        if (u == 0)
-            tb.t0[n] = hi >> 16;
+        tb.lead[u][n] = u == 2 ? lead2(hi) : u == 1 ? lead1(hi) : lead0(hi);
     }
     if (threadIdx.x < kSweepThreads / 32)
         s_qn[threadIdx.x] = 0;
@@ -700,7 +776,7 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
     const uint32_t live0 = 0u - (J.meta & 1u), live1 = 0u - ((J.meta >> 1) & 1u),
                    live2 = 0u - ((J.meta >> 2) & 1u);
     const uint32_t always3 = jb->always_u & 7u;
-    const uint32_t T1x = (jb->gC_hi[1][32] & 0xFFFF0000u) | 0xFFFFu, T0 = jb->gC_hi[0][32] >> 16;
+    const uint32_t T1x = lead1(jb->gC_hi[1][32]), T0 = lead0(jb->gC_hi[0][32]);
     uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
     const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
@@ -743,31 +819,28 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
             Nzp = make_uint2(rot_zp(Nzp.x), rot_zp(Nzp.y));
         // main calls: pair (x0, z0 | z0 + 1) and pair (x0 + 1, z0 | z0 + 1)
         const uint32_t c2A = c2m | ((uint32_t)(h ^ (y & 1)) << 11);
-        const uint32_t c2B = c2A ^ (1u << 11);
-        uint4 RA = make_uint4(0u, 0u, 0u, 0u), RB = RA;
-        if (!(all_always || none_random)) {  // the pairs' main calls
-            RA = dev::philox10_rk(make_uint4((uint32_t)w0, c1, c2A, c3), rk);
-            RB = dev::philox10_rk(make_uint4((uint32_t)w0 + 1u, c1, c2B, c3), rk);
-        }
+        uint4 R = make_uint4(0u, 0u, 0u, 0u);
+        if (!(all_always || none_random))  // the quad's main call
+            R = dev::philox10_rk(make_uint4((uint32_t)w0, c1, c2A, c3), rk);
         // words a0 = (x0, z0), a1 = (x0 + 1, z0), b0 = (x0, z0 + 1), b1 = (x0 + 1, z0 + 1)
         uint32_t alwa0, alwa1, alwb0, alwb1;
         uint32_t sp = S0.x;
         const bool draw = !(all_always || none_random);
         bool ha0 = tile_word<LOWT>(sp ^ Nc0.y ^ Jx0.x, sp ^ Xm0 ^ Jxm0, sp ^ Nn0.x ^ Jy0.x,
                                    sp ^ Nm0.x ^ Jym0.x, sp ^ Nc1.x ^ Jz0.x, sp ^ Nzm.x ^ Jzm.x,
-                                   RA.x, RA.y, tb, T1x, T0, live0, live1, live2, alwa0);
+                                   R.x, tb, T1x, T0, live0, live1, live2, alwa0);
         sp = S0.y;
         bool ha1 = tile_word<LOWT>(sp ^ Xp0 ^ Jx0.y, sp ^ Nc0.x ^ Jx0.x, sp ^ Nn0.y ^ Jy0.y,
                                    sp ^ Nm0.y ^ Jym0.y, sp ^ Nc1.y ^ Jz0.y, sp ^ Nzm.y ^ Jzm.y,
-                                   RB.x, RB.y, tb, T1x, T0, live0, live1, live2, alwa1);
+                                   R.y, tb, T1x, T0, live0, live1, live2, alwa1);
         sp = S1.x;
         bool hb0 = tile_word<LOWT>(sp ^ Nc1.y ^ Jx1.x, sp ^ Xm1 ^ Jxm1, sp ^ Nn1.x ^ Jy1.x,
                                    sp ^ Nm1.x ^ Jym1.x, sp ^ Nzp.x ^ Jz1.x, sp ^ Nc0.x ^ Jz0.x,
-                                   RA.z, RA.w, tb, T1x, T0, live0, live1, live2, alwb0);
+                                   R.z, tb, T1x, T0, live0, live1, live2, alwb0);
         sp = S1.y;
         bool hb1 = tile_word<LOWT>(sp ^ Xp1 ^ Jx1.y, sp ^ Nc1.x ^ Jx1.x, sp ^ Nn1.y ^ Jy1.y,
                                    sp ^ Nm1.y ^ Jym1.y, sp ^ Nzp.y ^ Jz1.y, sp ^ Nc0.y ^ Jz0.y,
-                                   RB.z, RB.w, tb, T1x, T0, live0, live1, live2, alwb1);
+                                   R.w, tb, T1x, T0, live0, live1, live2, alwb1);
         ha0 = ha0 && draw;
         ha1 = ha1 && draw;
         hb0 = hb0 && draw;
@@ -788,15 +861,15 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
         if (all_always || none_random)
             continue;
         if (COUNT)
-            n_calls += 2;
+            n_calls += 1;
         if (ha0)
-            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0, S0.x, RA.x, RA.y);
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0, S0.x, R.x, 0u);
         if (ha1)
-            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0 + 1u, S0.y, RB.x, RB.y);
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0 + 1u, S0.y, R.y, 0u);
         if (hb0)
-            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1, S1.x, RA.z, RA.w);
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1, S1.x, R.z, 0u);
         if (hb1)
-            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1 + 1u, S1.y, RB.z, RB.w);
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1 + 1u, S1.y, R.w, 0u);
         __syncwarp();
         int q_n = *qn;
         if (q_n >= 96) {  // full rounds, one queued word per lane, while 32 are queued
@@ -815,12 +888,16 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
             __syncwarp();
         }
     }
-    __syncwarp();
-    const int q_n = *qn;
-    for (int k = lane; k < q_n; k += 32) {  // the words still queued
+    // the words still queued in the block's four warps, pooled and shared out
+    // in rounds of 32 over the warps
+    __syncthreads();
+    const int n0q = s_qn[0], n1q = n0q + s_qn[1], n2q = n1q + s_qn[2], n3q = n2q + s_qn[3];
+    for (int g = (int)threadIdx.x; g < n3q; g += kSweepThreads) {
+        const int wq = g < n0q ? 0 : g < n1q ? 1 : g < n2q ? 2 : 3;
+        const int off = g - (wq == 0 ? 0 : wq == 1 ? n0q : wq == 2 ? n1q : n2q);
         unsigned int extra = 0;
-        tile_finish<GL>(jb, tb, q[k], upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3, c1,
-                        c2m, c3, rk, extra);
+        tile_finish<GL>(jb, tb, s_q[wq][off], upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3,
+                        c1, c2m, c3, rk, extra);
         if (COUNT)
             n_extra += extra;
     }
