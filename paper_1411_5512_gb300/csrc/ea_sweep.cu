@@ -553,12 +553,14 @@ struct TileTables {
 };
 
 // The rare path of one queued word: e = (word-site, spins before the update,
-// its 32 main bits M).  The classes are counted again from the neighbour
-// area, which this half-step does not write.  Class 2 is decided on the 12
+// its 32 main bits M, its class-2 lanes).  The row loop stored the word with
+// its outright flips, which it reads back.  Class 2 is decided on the 12
 // leading bits of its first draw and the full 64 bits of later draws; the
-// extension call 64, which completes the first draws of classes 2 and 1, is
-// drawn only when those leading bits tie with the table or when class 1's 10
-// leading bits do not rule it out; call 65 (class 0) likewise.
+// extension call 64 is drawn only when those leading bits tie with the
+// table.  Only when the 10 leading bits of class 1 or 0 fall at or below the
+// class's 32-lane bound (T1x, T0) are the word's classes counted again from
+// the neighbour area, which this half-step does not write, and decided
+// exactly, with calls 64 and 65 as needed.
 template <int GL>
 __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const TileTables &tb,
                                             const uint4 &e, uint32_t *__restrict__ upd,
@@ -567,51 +569,27 @@ __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const
                                             const uint32_t *__restrict__ Jy,
                                             const uint32_t *__restrict__ Jz, int h, uint32_t live0,
                                             uint32_t live1, uint32_t live2, uint32_t always3,
-                                            uint32_t c1, uint32_t c2m, uint32_t c3,
-                                            const uint32_t (&rk)[20], unsigned int &calls)
+                                            uint32_t T1x, uint32_t T0, uint32_t c1, uint32_t c2m,
+                                            uint32_t c3, const uint32_t (&rk)[20],
+                                            unsigned int &calls)
 {
     constexpr int SLOG = GL == 128 ? 7 : 6;
     constexpr int N2 = GL / 32, SZ = GL * GL;
     const int w = (int)e.x;
     const uint32_t s = e.y, M = e.z;
+    uint32_t M2 = e.w;
+    const uint32_t base = upd[w];  // s with its outright flips
     const int x = w & (GL - 1), y = (w >> SLOG) & (GL - 1), z = w >> (2 * SLOG);
-    const int wxp = x == GL - 1 ? w - (GL - 1) : w + 1;
-    const int wxm = x == 0 ? w + (GL - 1) : w - 1;
-    const int wyp = y == GL - 1 ? w - (GL - 1) * GL : w + GL;
-    const int wym = y == 0 ? w + (GL - 1) * GL : w - GL;
-    const int wzp = z == N2 - 1 ? w - (N2 - 1) * SZ : w + SZ;
-    const int wzm = z == 0 ? w + (N2 - 1) * SZ : w - SZ;
-    uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
-    if (z == N2 - 1)
-        nzp = rot_zp(nzp);
-    if (z == 0) {
-        nzm = rot_zm(nzm);
-        jzm = rot_zm(jzm);
-    }
-    const Count c = count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nb[wyp] ^ Jy[w],
-                           s ^ nb[wym] ^ Jy[wym], s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
-    const uint32_t alw = c.b2 | (c.b1 & c.b0);
-    Classes k = classes(c, alw, 0xffffffffu, live0, live1, live2);
     const uint32_t c2 = c2m | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
     uint32_t A = 0u;
-    if (always3) {  // classes accepted outright (exp(-dE/T) rounds to 1)
-        if (always3 & 4u) {
-            A |= k.M2;
-            k.M2 = 0u;
-        }
-        if (always3 & 2u) {
-            A |= k.M1;
-            k.M1 = 0u;
-        }
-        if (always3 & 1u) {
-            A |= k.M0;
-            k.M0 = 0u;
-        }
+    if (always3 & 4u) {  // accepted outright (exp(-dE/T) rounds to 1)
+        A = M2;
+        M2 = 0u;
     }
     uint4 X = make_uint4(0u, 0u, 0u, 0u);
     bool have_x = false;
-    if (k.M2) {
-        uint32_t Mr = k.M2;
+    if (M2) {
+        uint32_t Mr = M2;
         int rem = __popc(Mr);
         uint32_t vh = M >> 20, vl = 0u;  // draw 0: its 12 leading bits until extended
         bool exact = false;
@@ -664,19 +642,47 @@ __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const
             exact = true;
         }
     }
-    if (k.M1 && (M & 0xFFC00u) <= tb.lead[1][__popc(k.M1)]) {
-        if (!have_x) {
-            X = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 64u, c3), rk);
-            ++calls;
+    if ((M & 0xFFC00u) <= T1x || (M & 0x3FFu) <= T0) {
+        const int wxp = x == GL - 1 ? w - (GL - 1) : w + 1;
+        const int wxm = x == 0 ? w + (GL - 1) : w - 1;
+        const int wyp = y == GL - 1 ? w - (GL - 1) * GL : w + GL;
+        const int wym = y == 0 ? w + (GL - 1) * GL : w - GL;
+        const int wzp = z == N2 - 1 ? w - (N2 - 1) * SZ : w + SZ;
+        const int wzm = z == 0 ? w + (N2 - 1) * SZ : w - SZ;
+        uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
+        if (z == N2 - 1)
+            nzp = rot_zp(nzp);
+        if (z == 0) {
+            nzm = rot_zm(nzm);
+            jzm = rot_zm(jzm);
         }
-        A |= metro_class(jb, 1, k.M1, first_draw1(M, X), (uint32_t)w, c1, c2, c3, rk, calls);
+        const Count c = count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nb[wyp] ^ Jy[w],
+                               s ^ nb[wym] ^ Jy[wym], s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
+        const uint32_t alw = c.b2 | (c.b1 & c.b0);
+        const Classes k = classes(c, alw, 0xffffffffu, live0, live1, live2);
+        uint32_t M1 = k.M1, M0 = k.M0;
+        if (always3 & 2u) {
+            A |= M1;
+            M1 = 0u;
+        }
+        if (always3 & 1u) {
+            A |= M0;
+            M0 = 0u;
+        }
+        if (M1 && (M & 0xFFC00u) <= tb.lead[1][__popc(M1)]) {
+            if (!have_x) {
+                X = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 64u, c3), rk);
+                ++calls;
+            }
+            A |= metro_class(jb, 1, M1, first_draw1(M, X), (uint32_t)w, c1, c2, c3, rk, calls);
+        }
+        if (M0 && (M & 0x3FFu) <= tb.lead[0][__popc(M0)]) {
+            const uint4 Y = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 65u, c3), rk);
+            ++calls;
+            A |= metro_class(jb, 0, M0, first_draw0(M, Y), (uint32_t)w, c1, c2, c3, rk, calls);
+        }
     }
-    if (k.M0 && (M & 0x3FFu) <= tb.lead[0][__popc(k.M0)]) {
-        const uint4 Y = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 65u, c3), rk);
-        ++calls;
-        A |= metro_class(jb, 0, k.M0, first_draw0(M, Y), (uint32_t)w, c1, c2, c3, rk, calls);
-    }
-    upd[w] = s ^ alw ^ A;
+    upd[w] = base ^ A;
 }
 
 // Full adders of three bits: sum and carry.
@@ -696,20 +702,21 @@ __device__ __forceinline__ bool tile_word(uint32_t u0, uint32_t u1, uint32_t u2,
                                           uint32_t u4, uint32_t u5, uint32_t M,
                                           const TileTables &tb, uint32_t T1x, uint32_t T0,
                                           uint32_t live0, uint32_t live1, uint32_t live2,
-                                          uint32_t &alw)
+                                          uint32_t &alw, uint32_t &m2)
 {
     if (LOWT) {
         // u = 2 (k1 + k2) + s1 + s2 from two full adders
         uint32_t s1, k1, s2, k2;
         add3(u0, u1, u2, s1, k1);
         add3(u3, u4, u5, s2, k2);
-        alw = maj3(k1, k2, s1 | s2);                   // u >= 3
-        const uint32_t m2 = (k1 | k2 | (s1 & s2)) & ~alw;  // u == 2
+        alw = maj3(k1, k2, s1 | s2);           // u >= 3
+        m2 = (k1 | k2 | (s1 & s2)) & ~alw;     // u == 2
         return (M <= tb.lead[2][__popc(m2)]) | ((M & 0xFFC00u) <= T1x) | ((M & 0x3FFu) <= T0);
     } else {
         const Count c = count6(u0, u1, u2, u3, u4, u5);
         alw = c.b2 | (c.b1 & c.b0);
         const Classes k = classes(c, alw, 0xffffffffu, live0, live1, live2);
+        m2 = k.M2;
         return (M <= tb.lead[2][__popc(k.M2)]) | ((M & 0xFFC00u) <= tb.lead[1][__popc(k.M1)]) |
                ((M & 0x3FFu) <= tb.lead[0][__popc(k.M0)]);
     }
@@ -823,24 +830,24 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
         if (!(all_always || none_random))  // the quad's main call
             R = dev::philox10_rk(make_uint4((uint32_t)w0, c1, c2A, c3), rk);
         // words a0 = (x0, z0), a1 = (x0 + 1, z0), b0 = (x0, z0 + 1), b1 = (x0 + 1, z0 + 1)
-        uint32_t alwa0, alwa1, alwb0, alwb1;
+        uint32_t alwa0, alwa1, alwb0, alwb1, m2a0, m2a1, m2b0, m2b1;
         uint32_t sp = S0.x;
         const bool draw = !(all_always || none_random);
         bool ha0 = tile_word<LOWT>(sp ^ Nc0.y ^ Jx0.x, sp ^ Xm0 ^ Jxm0, sp ^ Nn0.x ^ Jy0.x,
                                    sp ^ Nm0.x ^ Jym0.x, sp ^ Nc1.x ^ Jz0.x, sp ^ Nzm.x ^ Jzm.x,
-                                   R.x, tb, T1x, T0, live0, live1, live2, alwa0);
+                                   R.x, tb, T1x, T0, live0, live1, live2, alwa0, m2a0);
         sp = S0.y;
         bool ha1 = tile_word<LOWT>(sp ^ Xp0 ^ Jx0.y, sp ^ Nc0.x ^ Jx0.x, sp ^ Nn0.y ^ Jy0.y,
                                    sp ^ Nm0.y ^ Jym0.y, sp ^ Nc1.y ^ Jz0.y, sp ^ Nzm.y ^ Jzm.y,
-                                   R.y, tb, T1x, T0, live0, live1, live2, alwa1);
+                                   R.y, tb, T1x, T0, live0, live1, live2, alwa1, m2a1);
         sp = S1.x;
         bool hb0 = tile_word<LOWT>(sp ^ Nc1.y ^ Jx1.x, sp ^ Xm1 ^ Jxm1, sp ^ Nn1.x ^ Jy1.x,
                                    sp ^ Nm1.x ^ Jym1.x, sp ^ Nzp.x ^ Jz1.x, sp ^ Nc0.x ^ Jz0.x,
-                                   R.z, tb, T1x, T0, live0, live1, live2, alwb0);
+                                   R.z, tb, T1x, T0, live0, live1, live2, alwb0, m2b0);
         sp = S1.y;
         bool hb1 = tile_word<LOWT>(sp ^ Xp1 ^ Jx1.y, sp ^ Nc1.x ^ Jx1.x, sp ^ Nn1.y ^ Jy1.y,
                                    sp ^ Nm1.y ^ Jym1.y, sp ^ Nzp.y ^ Jz1.y, sp ^ Nc0.y ^ Jz0.y,
-                                   R.w, tb, T1x, T0, live0, live1, live2, alwb1);
+                                   R.w, tb, T1x, T0, live0, live1, live2, alwb1, m2b1);
         ha0 = ha0 && draw;
         ha1 = ha1 && draw;
         hb0 = hb0 && draw;
@@ -863,13 +870,13 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
         if (COUNT)
             n_calls += 1;
         if (ha0)
-            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0, S0.x, R.x, 0u);
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0, S0.x, R.x, m2a0);
         if (ha1)
-            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0 + 1u, S0.y, R.y, 0u);
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0 + 1u, S0.y, R.y, m2a1);
         if (hb0)
-            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1, S1.x, R.z, 0u);
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1, S1.x, R.z, m2b0);
         if (hb1)
-            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1 + 1u, S1.y, R.w, 0u);
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1 + 1u, S1.y, R.w, m2b1);
         __syncwarp();
         int q_n = *qn;
         if (q_n >= 96) {  // full rounds, one queued word per lane, while 32 are queued
@@ -878,7 +885,7 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
                 const uint4 e = q[q_n + lane];
                 unsigned int extra = 0;
                 tile_finish<GL>(jb, tb, e, upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3,
-                                c1, c2m, c3, rk, extra);
+                                T1x, T0, c1, c2m, c3, rk, extra);
                 if (COUNT)
                     n_extra += extra;
                 __syncwarp();
@@ -897,7 +904,7 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
         const int off = g - (wq == 0 ? 0 : wq == 1 ? n0q : wq == 2 ? n1q : n2q);
         unsigned int extra = 0;
         tile_finish<GL>(jb, tb, s_q[wq][off], upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3,
-                        c1, c2m, c3, rk, extra);
+                        T1x, T0, c1, c2m, c3, rk, extra);
         if (COUNT)
             n_extra += extra;
     }
