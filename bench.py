@@ -169,7 +169,7 @@ N_SM = 152
 # dram__bytes_write.sum, one pass, caches flushed before each captured launch;
 # profiles/launches_bench_L128_S16x5.md, mean of three launches).  Take them
 # again (or set None) when the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = {1: None, 2: None, 4: None}
+TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 2.17e6, 2: 108.41e6 + 3.49e6, 4: 110.52e6 + 5.54e6}
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
