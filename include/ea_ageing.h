@@ -122,6 +122,15 @@ typedef void *(*ea_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*ea_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 int ea_set_allocator(ea_alloc_fn alloc, ea_free_fn release, void *user);
 
+/* ---- launch accounting --------------------------------------------------- */
+
+/* Number of kernel launches the library has issued in this process: every
+ * direct launch, plus the kernels of a captured CUDA graph each time the graph
+ * is replayed (capturing itself counts nothing).  Thread-safe; never fails.
+ * The difference across a region of host code counts the library's kernels
+ * enqueued in it. */
+uint64_t ea_launch_count(void);
+
 /* ---- job lifecycle ------------------------------------------------------- */
 
 /* Create a job of n_samples samples of side L and generate their couplings on

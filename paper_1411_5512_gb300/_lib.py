@@ -109,6 +109,7 @@ SIGNATURES = {
     "ea_server_cancel": (ctypes.c_int, [vp, ctypes.c_int64]),
     "ea_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(EaServerStats)]),
     "ea_server_destroy": (ctypes.c_int, [vp]),
+    "ea_launch_count": (ctypes.c_uint64, []),
     "ea_server_last_error": (ctypes.c_char_p, [vp]),
 }
 

@@ -8,6 +8,7 @@
 // half-step gives the global synchronisation), measurements are enqueued
 // in between, and nothing synchronises until results are read back.
 #include <algorithm>
+#include <atomic>
 #include <deque>
 #include <map>
 #include <cmath>
@@ -57,6 +58,35 @@ void dev_free(void *p, size_t bytes, cudaStream_t stream)
 }  // namespace
 
 namespace ea {
+
+static std::atomic<uint64_t> g_launches{0};
+static thread_local bool tl_capturing = false;
+static thread_local uint64_t tl_captured = 0;
+
+void count_launches(uint64_t n)
+{
+    if (tl_capturing)
+        tl_captured += n;
+    else
+        g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+void capture_begin()
+{
+    tl_capturing = true;
+    tl_captured = 0;
+}
+
+uint64_t capture_end()
+{
+    tl_capturing = false;
+    return tl_captured;
+}
+
+uint64_t launches_total()
+{
+    return g_launches.load(std::memory_order_relaxed);
+}
 
 int make_geo(int L, Geo *g)
 {
@@ -1063,6 +1093,7 @@ struct ea_batch {
     // captured graph of graph_sweeps sweeps over the current tables
     cudaGraphExec_t graph = nullptr;
     int graph_K = 0;
+    uint64_t graph_kernels = 0;  // kernels per replay
     const void *graph_key[2] = {nullptr, nullptr};
     int graph_blocks[2] = {0, 0};
     std::string err;
@@ -1165,7 +1196,9 @@ int ensure_graph(ea_batch *b)
     drop_graph(b);
     cudaGraph_t g = nullptr;
     EA_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    ea::capture_begin();
     const int rc = enqueue_direct(b, (uint64_t)K);
+    const uint64_t kernels = ea::capture_end();
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (rc != EA_OK || e != cudaSuccess) {
         cudaGetLastError();
@@ -1181,6 +1214,7 @@ int ensure_graph(ea_batch *b)
         return bfail(b, EA_ERR_CUDA, "graph instantiation failed");
     }
     b->graph_K = K;
+    b->graph_kernels = kernels;
     b->graph_key[0] = b->tab_dev[0];
     b->graph_key[1] = b->tab_dev[1];
     b->graph_blocks[0] = b->blocks[0];
@@ -1199,8 +1233,10 @@ int run_sweeps(ea_batch *b, uint64_t n)
         if (rc != EA_OK)
             return rc;
         const uint64_t full = n / (uint64_t)b->graph_sweeps;
-        for (uint64_t i = 0; i < full; ++i)
+        for (uint64_t i = 0; i < full; ++i) {
             EA_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+            ea::count_launches(b->graph_kernels);
+        }
         rem = n - full * (uint64_t)b->graph_sweeps;
     }
     if (rem)
@@ -1211,6 +1247,11 @@ int run_sweeps(ea_batch *b, uint64_t n)
 }  // namespace
 
 extern "C" {
+
+uint64_t ea_launch_count(void)
+{
+    return ea::launches_total();
+}
 
 int ea_batch_create(ea_batch **out, void *cuda_stream)
 {

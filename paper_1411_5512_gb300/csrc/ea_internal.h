@@ -150,6 +150,15 @@ static_assert(sizeof(MetroParams<kMetroMaxJobs>) <= 32000, "kernel parameter blo
 // (Metropolis tables of more than kMetroMaxJobs jobs take several).  host0 and
 // dev0 are the host and device copies of the Metropolis rows; the heat-bath
 // rows are read from dev1 with block offsets bb_dev1 (blocks1 blocks).
+// Kernel launches issued by the library (process-wide).  A launch made while
+// the calling thread captures a graph is counted into that capture instead;
+// capture_begin/capture_end bracket it and give the number of kernels the
+// graph holds, which a replay adds with count_launches.
+void count_launches(uint64_t n);
+void capture_begin();
+uint64_t capture_end();
+uint64_t launches_total();
+
 cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
                                const JobDev *dev1, const int *bb_dev1, int n_jobs1, int blocks1,
                                uint64_t n, cudaStream_t stream,

@@ -297,6 +297,7 @@ cudaError_t launch_init_couplings(uint32_t *J, const Geo &g, int n_samples, doub
         p_neg >= 1.0 ? ((uint64_t)1 << 32) : (uint64_t)floor(ldexp(p_neg, 32));
     init_couplings_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(
         J, g, thr_p, (uint32_t)seed, (uint32_t)(seed >> 32));
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -305,6 +306,7 @@ cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int n_samples, uint
 {
     init_spins_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(spins, g, (uint32_t)seed,
                                                                      (uint32_t)(seed >> 32));
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -313,6 +315,7 @@ cudaError_t launch_obs_state(const uint32_t *spins, const uint32_t *J, const Geo
                              cudaStream_t stream)
 {
     obs_state_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(spins, J, g, q_pop, u_pop);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -320,6 +323,7 @@ cudaError_t launch_obs_autocorr(const uint32_t *snap, const uint32_t *spins, con
                                 int n_samples, unsigned long long *a_pop, cudaStream_t stream)
 {
     obs_autocorr_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(snap, spins, g, a_pop);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -336,6 +340,7 @@ cudaError_t launch_obs_c4(const uint32_t *spins, const Geo &g, int n_samples,
     }
     const dim3 grid(bx, 3u, (unsigned)n_samples);
     obs_c4_kernel<<<grid, 256, 0, stream>>>(spins, g, g_pop);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -1244,10 +1244,11 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
                 }
             } else {
                 if (counters)
-                        metro_kernel<true, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                    metro_kernel<true, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, counters);
                 else
                     metro_kernel<false, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
             }
+            count_launches(1);
         }
 }
 
@@ -1314,6 +1315,7 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
                 else
                     heat_kernel<false><<<blocks1, kSweepThreads, 0, stream>>>(
                         dev1, bb1, n_jobs1, h, (uint32_t)k, nullptr);
+                count_launches(1);
             }
     }
     return cudaGetLastError();
@@ -1324,6 +1326,7 @@ cudaError_t launch_advance_time(JobDev *jobs_dev, int n_jobs, uint64_t n, cudaSt
     if (n_jobs <= 0)
         return cudaSuccess;
     advance_time_kernel<<<(n_jobs + 127) / 128, 128, 0, stream>>>(jobs_dev, n_jobs, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 

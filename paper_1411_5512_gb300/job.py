@@ -52,6 +52,12 @@ def use_cuda_allocator():
     _torch_alloc_refs = None
 
 
+def launch_count():
+    """Kernel launches the library has issued in this process (a replayed graph
+    counts the kernels it holds)."""
+    return int(_lib.load().ea_launch_count())
+
+
 def geometry(L):
     out = (ctypes.c_int * 6)()
     _lib.check(_lib.load().ea_geometry(L, out))

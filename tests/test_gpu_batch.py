@@ -187,3 +187,31 @@ def test_profile_counts_words_and_restores_state(J, L):
     b.close()
     j.close()
     ref.close()
+
+
+def test_launch_count(J):
+    """The library's launch counter: two half-step launches per plain sweep; a batch
+    adds one time-advance kernel per enqueue, and a graph of K sweeps, replayed,
+    counts its 2K half-steps and its time advance."""
+    import torch
+    j = make(J, (16, 0.5, 3, 1, 0.7, 0, [], []))
+    n0 = J.launch_count()
+    j.sweep(5)
+    assert J.launch_count() - n0 == 10
+    b = J.EABatch()  # default stream: direct launches, no graph
+    b.configure(1, 4)
+    b.add(j)
+    n0 = J.launch_count()
+    b.sweep(8)
+    assert J.launch_count() - n0 == 2 * 8 + 1
+    b.close()
+    stream = torch.cuda.Stream()
+    b = J.EABatch(stream=stream)
+    b.configure(1, 4)
+    b.add(j)
+    b.sweep(4)  # captures the graph (capturing counts nothing) and replays it once
+    n0 = J.launch_count()
+    b.sweep(8)
+    assert J.launch_count() - n0 == 2 * (2 * 4 + 1)
+    b.close()
+    j.close()
