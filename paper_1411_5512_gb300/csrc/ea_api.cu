@@ -1096,6 +1096,10 @@ struct ea_batch {
     uint64_t graph_kernels = 0;  // kernels per replay
     const void *graph_key[2] = {nullptr, nullptr};
     int graph_blocks[2] = {0, 0};
+    // side streams: the runs of a mixed table (column kernel, side 64, side
+    // 128) are enqueued concurrently
+    ea::SideStreams side{};
+    bool have_side = false;
     std::string err;
 };
 
@@ -1148,10 +1152,13 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
         b->tab_host[r].push_back(jd);
         b->bb_host[r].push_back(b->bb_host[r].back() + m->S * jd.blocks_per_sample);
     }
-    // equal sides next to each other: runs of one L share a specialised launch
-    // (the order of rows changes no result)
+    // equal sides next to each other, sides 64 and 128 last: they form the
+    // runs that the tile kernel takes (the order of rows changes no result)
+    auto run_key = [](int L) { return (L == 64 || L == 128) ? (1 << 20) + L : L; };
     std::stable_sort(b->tab_host[0].begin(), b->tab_host[0].end(),
-                     [](const ea::JobDev &a, const ea::JobDev &c) { return a.geo.L < c.geo.L; });
+                     [&](const ea::JobDev &a, const ea::JobDev &c) {
+                         return run_key(a.geo.L) < run_key(c.geo.L);
+                     });
     for (int r = 0; r < 2; ++r) {
         const size_t n = b->tab_host[r].size();
         b->n_jobs[r] = (int)n;
@@ -1180,7 +1187,7 @@ int enqueue_direct(ea_batch *b, uint64_t n, unsigned long long *counters = nullp
 {
     EA_BCUDA(b, ea::launch_sweep_table(b->tab_host[0].data(), b->tab_dev[0], b->n_jobs[0],
                                        b->tab_dev[1], b->bb_dev[1], b->n_jobs[1], b->blocks[1], n,
-                                       b->stream, counters));
+                                       b->stream, counters, b->have_side ? &b->side : nullptr));
     for (int r = 0; r < 2; ++r)
         EA_BCUDA(b, ea::launch_advance_time(b->tab_dev[r], b->n_jobs[r], n, b->stream));
     return EA_OK;
@@ -1261,6 +1268,16 @@ int ea_batch_create(ea_batch **out, void *cuda_stream)
     if (!b)
         return EA_ERR_OOM;
     b->stream = (cudaStream_t)cuda_stream;
+    // without side streams a mixed table runs its parts one after another
+    bool ok = true;
+    for (int i = 0; i < 2; ++i)
+        ok = ok && cudaStreamCreateWithFlags(&b->side.stream[i], cudaStreamNonBlocking) ==
+                       cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 2; ++i)
+        ok = ok && cudaEventCreateWithFlags(&b->side.join[i], cudaEventDisableTiming) == cudaSuccess;
+    cudaGetLastError();
+    b->have_side = ok;
     *out = b;
     return EA_OK;
 }
@@ -1545,6 +1562,14 @@ int ea_batch_destroy(ea_batch *b)
         dev_free(b->tab_dev[r], b->cap[r] * sizeof(ea::JobDev), b->stream);
         dev_free(b->bb_dev[r], (b->cap[r] + 1) * sizeof(int), b->stream);
     }
+    for (int i = 0; i < 2; ++i) {
+        if (b->side.stream[i])
+            cudaStreamDestroy(b->side.stream[i]);
+        if (b->side.join[i])
+            cudaEventDestroy(b->side.join[i]);
+    }
+    if (b->side.fork)
+        cudaEventDestroy(b->side.fork);
     delete b;
     return EA_OK;
 }

@@ -159,10 +159,19 @@ void capture_begin();
 uint64_t capture_end();
 uint64_t launches_total();
 
+// Two side streams and the events that fork them from a launching stream and
+// join them back: independent runs of a table then share the GPU.
+struct SideStreams {
+    cudaStream_t stream[2];
+    cudaEvent_t fork;
+    cudaEvent_t join[2];
+};
+
 cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
                                const JobDev *dev1, const int *bb_dev1, int n_jobs1, int blocks1,
                                uint64_t n, cudaStream_t stream,
-                               unsigned long long *counters = nullptr);
+                               unsigned long long *counters = nullptr,
+                               const SideStreams *side = nullptr);
 
 // Add n to the time field of every job of a table, stopping at its t_end
 // (device side, for graphs).

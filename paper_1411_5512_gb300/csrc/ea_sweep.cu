@@ -22,6 +22,7 @@
 //     with its threshold, MSB first, four planes per Philox call; a lane is
 //     decided at the first plane where its bit of r differs from its
 //     threshold bit.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -545,6 +546,7 @@ __device__ __forceinline__ uint2 ld2(const uint32_t *__restrict__ p, int i)
 }
 
 constexpr int kTileQueue = 224;  // entries per warp: up to 95 left over + 128 added per row
+constexpr int kTileMinSMs = 152;  // SMs of a GB300: launches below 2 blocks per SM take shorter rows
 
 // Threshold tables of a block's job in shared memory.
 struct TileTables {
@@ -1194,6 +1196,17 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
     p.block_begin[0] = 0;
     int n_geo = 0;
     int geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
+    // tile kernel: rows per thread from the launch shape, halved (down to 2)
+    // while the launch would hold fewer than two blocks per SM
+    int y_max = 16;
+    if (GL != 0) {
+        long samples = 0;
+        for (int i = 0; i < cnt; ++i)
+            samples += host[i].n_samples;
+        const long per_row = (long)(GL / 2) * (GL / 64) * GL / kSweepThreads;  // blocks x rows
+        while (y_max > 2 && samples * per_row / y_max < 2L * kTileMinSMs)
+            y_max >>= 1;
+    }
     for (int i = 0; i < cnt; ++i) {
         const JobDev &jd = host[i];
         int gi = 0;
@@ -1205,7 +1218,8 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
             metro_geo(p.geo[gi], jd);
             if (GL != 0) {
                 // tiles of 2 x 2 word-sites times a segment of Y = 4, 8 or 16 rows
-                const int Y = jd.cols_per_thread >= 4 ? 16 : jd.cols_per_thread >= 2 ? 8 : 4;
+                const int Y = std::min(
+                    y_max, jd.cols_per_thread >= 4 ? 16 : jd.cols_per_thread >= 2 ? 8 : 4);
                 p.geo[gi].seg = Y;
                 p.geo[gi].bps = (GL / 2) * (GL / 64) * (GL / Y) / kSweepThreads;
             }
@@ -1252,25 +1266,16 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
         }
 }
 
-cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
-                               const JobDev *dev1, const int *bb1, int n_jobs1, int blocks1,
-                               uint64_t n, cudaStream_t stream, unsigned long long *counters)
+// Jobs host[0..cnt) of one run of the Metropolis table: side GLR (64 or 128,
+// the tile kernel) or any sides (GLR = 0, the column kernel), in chunks of at
+// most kMetroMaxJobs jobs and kMetroMaxGeo geometries per launch.
+static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int GLR, uint64_t n,
+                             cudaStream_t stream, unsigned long long *counters)
 {
-    // Tables hold different jobs, so they need no order between them: each
-    // issues its own n sweeps (two launches per sweep) in turn.  Metropolis
-    // jobs go in chunks of kMetroMaxJobs through the parameter block.
-    // a table of one side 64 or 128 takes the compile-time geometry kernel;
-    // a mixed table stays in one launch (per kMetroMaxJobs chunk) so that small
-    // lattices share the GPU with the others
-    bool same_L = n_jobs0 > 0;
-    for (int i = 1; i < n_jobs0 && same_L; ++i)
-        same_L = host0[i].geo.L == host0[0].geo.L;
-    const int L0 = n_jobs0 > 0 ? host0[0].geo.L : 0;
-    for (int first = 0, cnt = 0; first < n_jobs0; first += cnt) {
-        // as many jobs as fit: kMetroMaxJobs of at most kMetroMaxGeo geometries
+    for (int first = 0, c = 0; first < cnt; first += c) {
         int n_geo = 0, geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
-        for (cnt = 0; first + cnt < n_jobs0 && cnt < kMetroMaxJobs; ++cnt) {
-            const JobDev &jd = host0[first + cnt];
+        for (c = 0; first + c < cnt && c < kMetroMaxJobs; ++c) {
+            const JobDev &jd = host[first + c];
             int gi = 0;
             while (gi < n_geo && !(geo_L[gi] == jd.geo.L && geo_cpt[gi] == jd.cols_per_thread))
                 ++gi;
@@ -1282,29 +1287,87 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
                 ++n_geo;
             }
         }
-        const JobDev *h = host0 + first;
-        const JobDev *d = dev0 + first;
-        if (same_L && L0 == 128) {
-            if (cnt <= 8)
-                launch_metro_chunk<8, 128>(h, d, cnt, n, stream, counters);
+        const JobDev *h = host + first;
+        const JobDev *d = dev + first;
+        if (GLR == 128) {
+            if (c <= 8)
+                launch_metro_chunk<8, 128>(h, d, c, n, stream, counters);
             else
-                launch_metro_chunk<kMetroMaxJobs, 128>(h, d, cnt, n, stream, counters);
-        } else if (same_L && L0 == 64) {
-            if (cnt <= 8)
-                launch_metro_chunk<8, 64>(h, d, cnt, n, stream, counters);
+                launch_metro_chunk<kMetroMaxJobs, 128>(h, d, c, n, stream, counters);
+        } else if (GLR == 64) {
+            if (c <= 8)
+                launch_metro_chunk<8, 64>(h, d, c, n, stream, counters);
             else
-                launch_metro_chunk<kMetroMaxJobs, 64>(h, d, cnt, n, stream, counters);
-        } else if (cnt <= 1) {
-            launch_metro_chunk<1, 0>(h, d, cnt, n, stream, counters);
-        } else if (cnt <= 8) {
-            launch_metro_chunk<8, 0>(h, d, cnt, n, stream, counters);
-        } else if (cnt <= 32) {
-            launch_metro_chunk<32, 0>(h, d, cnt, n, stream, counters);
-        } else if (cnt <= 128) {
-            launch_metro_chunk<128, 0>(h, d, cnt, n, stream, counters);
+                launch_metro_chunk<kMetroMaxJobs, 64>(h, d, c, n, stream, counters);
+        } else if (c <= 1) {
+            launch_metro_chunk<1, 0>(h, d, c, n, stream, counters);
+        } else if (c <= 8) {
+            launch_metro_chunk<8, 0>(h, d, c, n, stream, counters);
+        } else if (c <= 32) {
+            launch_metro_chunk<32, 0>(h, d, c, n, stream, counters);
+        } else if (c <= 128) {
+            launch_metro_chunk<128, 0>(h, d, c, n, stream, counters);
         } else {
-            launch_metro_chunk<kMetroMaxJobs, 0>(h, d, cnt, n, stream, counters);
+            launch_metro_chunk<kMetroMaxJobs, 0>(h, d, c, n, stream, counters);
         }
+    }
+}
+
+cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
+                               const JobDev *dev1, const int *bb1, int n_jobs1, int blocks1,
+                               uint64_t n, cudaStream_t stream, unsigned long long *counters,
+                               const SideStreams *side)
+{
+    // The Metropolis table is read as up to three runs: jobs of sides other
+    // than 64 and 128 (the column kernel), then side 64, then side 128 (the
+    // tile kernel).  A table in any other order runs whole on the column
+    // kernel.  Runs hold different jobs, so they need no order between them:
+    // given side streams, the second and third run are forked from `stream`
+    // and joined back after their n sweeps, so the runs share the GPU.
+    int a = 0;
+    while (a < n_jobs0 && host0[a].geo.L != 64 && host0[a].geo.L != 128)
+        ++a;
+    int b = a;
+    while (b < n_jobs0 && host0[b].geo.L == 64)
+        ++b;
+    int e = b;
+    while (e < n_jobs0 && host0[e].geo.L == 128)
+        ++e;
+    struct Run {
+        int first, cnt, GLR;
+    } runs[3];
+    int n_runs = 0;
+    if (e != n_jobs0) {  // not in run order
+        if (n_jobs0 > 0)
+            runs[n_runs++] = {0, n_jobs0, 0};
+    } else {
+        if (a > 0)
+            runs[n_runs++] = {0, a, 0};
+        if (b > a)
+            runs[n_runs++] = {a, b - a, 64};
+        if (e > b)
+            runs[n_runs++] = {b, e - b, 128};
+    }
+    const bool fork = side != nullptr && n_runs > 1;
+    if (fork) {
+        cudaError_t err = cudaEventRecord(side->fork, stream);
+        for (int r = 1; r < n_runs && err == cudaSuccess; ++r)
+            err = cudaStreamWaitEvent(side->stream[r - 1], side->fork, 0);
+        if (err != cudaSuccess)
+            return err;
+    }
+    for (int r = 0; r < n_runs; ++r)
+        launch_metro_run(host0 + runs[r].first, dev0 + runs[r].first, runs[r].cnt, runs[r].GLR, n,
+                         fork && r > 0 ? side->stream[r - 1] : stream, counters);
+    if (fork) {
+        cudaError_t err = cudaSuccess;
+        for (int r = 1; r < n_runs && err == cudaSuccess; ++r) {
+            err = cudaEventRecord(side->join[r - 1], side->stream[r - 1]);
+            if (err == cudaSuccess)
+                err = cudaStreamWaitEvent(stream, side->join[r - 1], 0);
+        }
+        if (err != cudaSuccess)
+            return err;
     }
     if (blocks1 > 0) {
         for (uint64_t k = 0; k < n; ++k)

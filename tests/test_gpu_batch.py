@@ -15,7 +15,8 @@ MIX = [
     (12, 0.5, 14, 1, 1.2, 1, [0, 8], [0, 1]),   # heat bath in the same batch
     (32, 0.4, 15, 1, 0.5, 0, [0], [0, 16]),
     (6, 0.5, 16, 2, 0.8, 0, [], []),
-    (64, 0.3, 17, 1, 0.7, 0, [0, 4], [0, 8]),  # compile-time geometry kernel in a mixed batch
+    (64, 0.3, 17, 1, 0.7, 0, [0, 4], [0, 8]),  # tile kernel run, forked from the column kernel's
+    (128, 0.5, 18, 1, 0.7, 0, [0, 2], [0, 4]),  # a second tile kernel run on the other side stream
 ]
 
 
