@@ -40,7 +40,8 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms.  Started ahead of
+    the timed region; mark() and stop() bound the window whose samples count."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -48,15 +49,16 @@ class ClockSampler:
 
     def __init__(self, index):
         self.index = index
-        self.rows = []
+        self.rows = []       # (host time, fields)
         self.proc = None
         self.thread = None
+        self.t0 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -68,9 +70,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) == 9:
-                self.rows.append(parts)
+                self.rows.append((time.perf_counter(), parts))
+
+    def mark(self):
+        """The timed region starts now."""
+        self.t0 = time.perf_counter()
 
     def stop(self):
+        self.t1 = time.perf_counter()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -81,19 +88,22 @@ class ClockSampler:
             self.thread.join(timeout=5)
 
     def summary(self):
-        if not self.rows:
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = getattr(self, "t1", float("inf"))
+        rows = [r for t, r in self.rows if t0 <= t <= t1]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in rows:
             for name, v in zip(names, r[5:9]):
                 if v.strip().lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(rows)}
 
 
 def dist_setup():
@@ -240,15 +250,16 @@ def run_ours(args, world, rank, local):
     def batched_step():
         batch.sweep(sps)
 
+    sampler = ClockSampler(local)
+    sampler.start()  # running before the timed region starts
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             batched_step()
     stream.synchronize()
-    sampler = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    sampler.mark()
     n_launch0 = job.launch_count()
     wall0 = time.perf_counter()
     step_ms = timed_steps(stream, args.steps, batched_step, flush)
@@ -511,7 +522,7 @@ def run_e2e(args, job, workloads, stream, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweeps-per-step", type=int, default=64)
