@@ -546,7 +546,7 @@ __device__ __forceinline__ uint2 ld2(const uint32_t *__restrict__ p, int i)
 }
 
 constexpr int kTileQueue = 224;  // entries per warp: up to 95 left over + 128 added per row
-constexpr int kTileMinSMs = 152;  // SMs of a GB300: launches below 2 blocks per SM take shorter rows
+constexpr int kTileMinSMs = 152;  // SMs of a GB300: launches below 4 blocks per SM take shorter rows
 
 // Threshold tables of a block's job in shared memory.
 struct TileTables {
@@ -1197,14 +1197,14 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
     int n_geo = 0;
     int geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
     // tile kernel: rows per thread from the launch shape, halved (down to 2)
-    // while the launch would hold fewer than two blocks per SM
+    // while the launch would hold fewer than four blocks per SM
     int y_max = 16;
     if (GL != 0) {
         long samples = 0;
         for (int i = 0; i < cnt; ++i)
             samples += host[i].n_samples;
         const long per_row = (long)(GL / 2) * (GL / 64) * GL / kSweepThreads;  // blocks x rows
-        while (y_max > 2 && samples * per_row / y_max < 2L * kTileMinSMs)
+        while (y_max > 2 && samples * per_row / y_max < 4L * kTileMinSMs)
             y_max >>= 1;
     }
     for (int i = 0; i < cnt; ++i) {

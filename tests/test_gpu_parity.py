@@ -118,10 +118,10 @@ def test_sweeps_bit_exact(J, L, p_neg, T, rule, G, S, n):
 # including temperatures where many words take the rare path and its later draws
 TILE_CASES = [
     # L, p_neg, T, cols_per_thread (segments of 4, 8, 16 rows; launches of fewer than
-    # two blocks per SM take shorter segments, down to 2 rows), S, sweeps
-    (128, 0.5, 0.7, 4, 40, 2),  # 16 rows
-    (128, 0.4, 1.2, 2, 20, 2),  # 8 rows
-    (64, 0.5, 0.9, 1, 80, 2),   # 4 rows
+    # four blocks per SM take shorter segments, down to 2 rows), S, sweeps
+    (128, 0.5, 0.7, 4, 80, 2),  # 16 rows
+    (128, 0.4, 1.2, 2, 40, 2),  # 8 rows
+    (64, 0.5, 0.9, 1, 160, 2),  # 4 rows
     (64, 0.5, 0.7, 1, 2, 4),    # the small cases: 2 rows
     (64, 0.3, 2.0, 2, 2, 3),
     (64, 0.5, 5.0, 4, 2, 3),
