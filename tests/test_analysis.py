@@ -1,0 +1,115 @@
+"""The host analysis of Sec. IV (C4 multifit, xi_1 with the fitted tail, z, x,
+collapse) recovers the parameters of synthetic data built from the very forms it
+fits; on the GPU it runs on measured curves."""
+import numpy as np
+import pytest
+
+pytest.importorskip("scipy")
+
+import oracle as ora
+from paper_1411_5512_gb300 import analysis as an
+
+
+def model_curves(alpha, beta, xis, As, L=64, rel_err=1e-3):
+    r = np.arange(0, L // 2 + 1, dtype=np.float64)
+    curves = []
+    for xi, A in zip(xis, As):
+        c = np.ones_like(r)
+        c[1:] = an.c4_model(r[1:], A, alpha, xi, beta)
+        curves.append((r, c, rel_err * np.abs(c) + 1e-12))
+    return curves
+
+
+def test_multifit_recovers_exact_parameters():
+    alpha, beta = 0.45, 1.45
+    xis, As = [2.0, 3.1, 4.7, 7.5], [0.9, 0.85, 0.8, 0.78]
+    fit = an.multifit_c4(model_curves(alpha, beta, xis, As), r_min=3)
+    assert abs(fit["alpha"] - alpha) < 1e-6 and abs(fit["beta"] - beta) < 1e-6
+    assert np.allclose(fit["xi"], xis, rtol=1e-6) and np.allclose(fit["A"], As, rtol=1e-6)
+    assert fit["chi2_dof"] < 1e-10
+
+
+def test_multifit_with_noise_within_errors():
+    alpha, beta = 0.5, 1.5
+    xis, As = [2.5, 4.0, 6.0], [1.0, 1.0, 1.0]
+    rng = np.random.default_rng(3)
+    noisy = []
+    for r, c, e in model_curves(alpha, beta, xis, As, rel_err=0.01):
+        noisy.append((r, c + e * rng.standard_normal(len(c)), e))
+    fit = an.multifit_c4(noisy, r_min=3)
+    assert abs(fit["alpha"] - alpha) < 5 * fit["alpha_err"] + 1e-3
+    assert abs(fit["beta"] - beta) < 5 * fit["beta_err"] + 1e-3
+    assert np.all(np.abs(fit["xi"] - xis) < 5 * fit["xi_err"] + 1e-3)
+    assert 0.5 < fit["chi2_dof"] < 2.0
+
+
+def test_xi1_tail_continues_the_measured_sums():
+    L = 64
+    params = (0.9, 0.5, 4.0, 1.5)
+    r = np.arange(0, L // 2 + 1, dtype=np.float64)
+    c = np.ones_like(r)
+    c[1:] = an.c4_model(r[1:], *params)
+    full = an.xi1_with_tail(r, c, L // 2, L)
+    # a cutoff continued with the same form gives the uncut value
+    for r_c in (3, 7, 20):
+        assert abs(an.xi1_with_tail(r, c, r_c, L, fit=params) - full) < 1e-12 * full
+    # without a tail: the oracle's rectangle-sum estimator with the same cutoff
+    for r_c in (5, 11):
+        assert abs(an.xi1_with_tail(r, c, r_c, L) - ora.xi1(c, r_c)) < 1e-12
+
+
+def test_fit_z_recovers_power_law_with_constant():
+    t_w = np.logspace(1, 6, 16)
+    xi = 1.3 * t_w ** (1 / 10.0) - 0.4
+    res = an.fit_z(t_w, xi)
+    assert abs(res["z"] - 10.0) < 1e-6 and abs(res["c"] + 0.4) < 1e-6
+
+
+def test_fit_x_and_mean_over_windows():
+    t = 2.0 ** np.arange(0, 21)
+    assert abs(an.fit_x(t, 0.8 * t ** -0.019, 100, 1e4) - 0.019) < 1e-12
+    curves = [(t_w, t, 0.7 * t ** -0.019) for t_w in (1e6, 4e6, 2e7)]
+    assert abs(an.fit_x_mean(curves) - 0.019) < 1e-12
+    assert np.isnan(an.fit_x_mean([(1e4, t, t ** -0.1)]))  # window [100, 10] is empty
+
+
+def test_collapse_finds_the_exponent():
+    def xi_of_t(t):
+        return 1.2 * np.asarray(t, dtype=np.float64) ** 0.1
+
+    x_true = 0.016
+    t = np.unique(np.round(np.logspace(0, 6, 60)))
+    curves = []
+    for t_w in (1e3, 1e4, 1e5):
+        u = xi_of_t(t_w + t) / xi_of_t(t_w)
+        C = t ** -x_true * np.exp(-3.0 * (u - 1.0))
+        curves.append((t_w, t, C))
+    x, cost = an.collapse_x(curves, xi_of_t)
+    assert abs(x - x_true) < 1e-9 and cost < 1e-6  # what is left is interpolation error
+    # a wrong exponent spreads the curves apart
+    _, cost_off = an.collapse_x(curves, xi_of_t, x_grid=np.array([x_true + 0.01]))
+    assert cost_off > 100 * cost
+
+
+@pytest.mark.gpu
+def test_pipeline_on_measured_curves():
+    """A side-32 run: the measured C4 curves feed the multifit, and the library's
+    xi_1 equals the host estimator without tail on the same curve."""
+    from paper_1411_5512_gb300 import build, job
+    build.build()
+    L, S = 32, 64
+    tws = [16, 32, 64, 128]
+    j = job.EAJob(L, 0.5, 21, S)
+    j.set_schedule(tws, [0])
+    j.quench(0.7)
+    j.sweep(max(tws))
+    curves = []
+    r = np.arange(0, L // 2 + 1, dtype=np.float64)
+    for tw in tws:
+        m = j.measure(tw, 0)
+        curves.append((r, m["C4"], m["C4_sem"]))
+        assert abs(an.xi1_with_tail(r, m["C4"], m["r_cut"], L) - m["xi1"]) < 1e-9 * abs(m["xi1"])
+    fit = an.multifit_c4(curves, r_min=3)
+    assert np.isfinite(fit["alpha"]) and np.isfinite(fit["beta"])
+    assert np.all(np.isfinite(fit["xi"])) and np.all(fit["xi"] > 0)
+    j.close()
