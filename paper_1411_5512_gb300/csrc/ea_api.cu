@@ -266,6 +266,10 @@ struct ea_ctx {
     int blocks = 0;
     unsigned long long *res = nullptr;
     size_t spins_bytes = 0, J_bytes = 0, snaps_bytes = 0, res_bytes = 0;
+    // host copy of res, valid while res_gen == res_host_gen; res_gen moves on
+    // whenever work that writes res is enqueued
+    std::vector<unsigned long long> res_host;
+    uint64_t res_gen = 1, res_host_gen = 0;
 
     std::vector<uint64_t> tw, tt, meas;
     size_t off_q = 0, off_u = 0, off_g = 0, off_a = 0;  // in counters
@@ -361,6 +365,7 @@ int build_schedule(ea_ctx *c, std::vector<uint64_t> tw, std::vector<uint64_t> tt
     c->off_a = c->off_g + c->tw.size() * S * 3 * R;
     const size_t n_ctr = results_counters(c->S, c->R(), c->meas.size(), c->tw.size(), c->tt.size());
     c->res_bytes = n_ctr * sizeof(unsigned long long);
+    ++c->res_gen;
     c->snaps_bytes = c->tw.size() * c->area_words() * sizeof(uint32_t);
     if (c->res_bytes) {
         c->res = (unsigned long long *)dev_alloc(c->res_bytes, c->stream);
@@ -414,6 +419,7 @@ int fire_measurements(ea_ctx *c)
     const int mi = idx_of(c->meas, c->t);
     if (mi < 0)
         return EA_OK;
+    ++c->res_gen;
     const size_t S = (size_t)c->S, R = (size_t)c->R();
     const size_t area = c->area_words();
     EA_CUDA(c, ea::launch_obs_state(c->spins, c->J, c->geo, c->S, c->res + c->off_q + mi * S,
@@ -620,6 +626,7 @@ int ea_quench(ea_ctx *c, double T, int rule)
     EA_CUDA(c, ea::launch_init_spins(c->spins, c->geo, c->S, c->seed, c->stream));
     if (c->res)
         EA_CUDA(c, cudaMemsetAsync(c->res, 0, c->res_bytes, c->stream));
+    ++c->res_gen;
     c->t = 0;
     c->quenched = true;
     int rc = upload_job(c);
@@ -674,17 +681,22 @@ int ea_measure(ea_ctx *c, uint64_t t_w, uint64_t t, ea_obs *out)
     const int mi = idx_of(c->meas, t_w + t);
     const size_t S = (size_t)c->S, R = (size_t)c->R();
     const long long N = (long long)c->L * c->L * c->L;
-    std::vector<unsigned long long> a(S * 2), q(S), u(S * 2), gp(S * 3 * R);
+    // all of the job's sums in one copy, reused until new sums are made
+    if (c->res_host_gen != c->res_gen) {
+        c->res_host.resize(c->res_bytes / sizeof(unsigned long long));
+        EA_CUDA(c, cudaMemcpyAsync(c->res_host.data(), c->res, c->res_bytes,
+                                   cudaMemcpyDeviceToHost, c->stream));
+        EA_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->res_host_gen = c->res_gen;
+    }
+    const unsigned long long *res = c->res_host.data();
     const size_t slot_a = c->off_a + ((size_t)i * c->tt.size() + (size_t)j) * S * 2;
-    EA_CUDA(c, cudaMemcpyAsync(a.data(), c->res + slot_a, a.size() * 8, cudaMemcpyDeviceToHost,
-                               c->stream));
-    EA_CUDA(c, cudaMemcpyAsync(q.data(), c->res + c->off_q + mi * S, q.size() * 8,
-                               cudaMemcpyDeviceToHost, c->stream));
-    EA_CUDA(c, cudaMemcpyAsync(u.data(), c->res + c->off_u + mi * S * 2, u.size() * 8,
-                               cudaMemcpyDeviceToHost, c->stream));
-    EA_CUDA(c, cudaMemcpyAsync(gp.data(), c->res + c->off_g + (size_t)i * S * 3 * R,
-                               gp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
-    EA_CUDA(c, cudaStreamSynchronize(c->stream));
+    const std::vector<unsigned long long> a(res + slot_a, res + slot_a + S * 2);
+    const std::vector<unsigned long long> q(res + c->off_q + mi * S, res + c->off_q + mi * S + S);
+    const std::vector<unsigned long long> u(res + c->off_u + mi * S * 2,
+                                            res + c->off_u + mi * S * 2 + S * 2);
+    const std::vector<unsigned long long> gp(res + c->off_g + (size_t)i * S * 3 * R,
+                                             res + c->off_g + (size_t)(i + 1) * S * 3 * R);
 
     // integer observables: N - 2 * (number of differing sites), and
     // H = (unsatisfied bonds) - (satisfied bonds) = 2 U - 3N
@@ -1029,6 +1041,7 @@ int ea_restore(ea_ctx **out, const char *path, void *cuda_stream)
                   read_dev(f, c->J, c->J_bytes, c->stream) &&
                   read_dev(f, c->snaps, c->snaps_bytes, c->stream) &&
                   read_dev(f, c->res, c->res_bytes, c->stream);
+        ++c->res_gen;
         if (!ok)
             rc = EA_ERR_IO;
     }
