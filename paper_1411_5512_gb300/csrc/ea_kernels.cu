@@ -4,6 +4,7 @@
 // All state is bit-packed: one 32-bit word holds up to 32 sites of ONE sample
 // (Geo in ea_internal.h), so a per-sample reduction is a plain popcount of
 // words: sum_i S_i S'_i = N - 2 * (number of differing bits).
+#include <algorithm>
 #include <cstdint>
 
 #include "ea_device.cuh"
@@ -278,6 +279,136 @@ __global__ void __launch_bounds__(256) obs_c4_kernel(const uint32_t *__restrict_
     }
 }
 
+// The four-point sums of a side whose word lattice holds all 32 lanes along z
+// (kx = ky = 1, kz = 32; here L = 64 or 128).  x and y shifts move whole words,
+// a z shift by r = A n2 + B rotates the lanes by A (A + 1 across the wrap).
+// Grid (tiles, 3 axes, samples), 8 warps per block:
+//   x: a warp per line (y', z'), staged twice in shared memory so that a
+//      shift needs no wrap;
+//   y: a block per tile of 32 x-columns at one z', staged with a padded row
+//      (no bank conflicts along y) and doubled along y; a warp per 4 columns;
+//   z: a thread per column (x', y'), its N2 words in registers.
+// Each lane sums the popcounts of its words for one shift, the warp adds them
+// up with one reduction, and the block adds its totals into g_pop.
+constexpr int kC4FastMaxL = 128;
+
+template <int N2>
+__global__ void __launch_bounds__(256) obs_c4_fast_kernel(const uint32_t *__restrict__ spins,
+                                                          Geo g, unsigned long long *g_pop)
+{
+    const int d = blockIdx.y, s = blockIdx.z;
+    const int L = g.L, R = L / 2 + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t W = (size_t)g.words;
+    const uint32_t *__restrict__ A0 = spins + (size_t)s * 2 * W;
+    const uint32_t *__restrict__ A1 = A0 + W;
+    __shared__ uint32_t s_buf[2 * kC4FastMaxL * 33];   // lines (x) or a padded tile (y)
+    __shared__ unsigned int s_acc[8][kC4FastMaxL / 2 + 1];
+    for (int i = threadIdx.x; i < 8 * R; i += blockDim.x)
+        s_acc[i / R][i % R] = 0u;
+    __syncthreads();
+    const int n0 = L, n1 = L;  // words along x and y
+    if (d == 0) {
+        // lines (y', z') of n0 words, one per warp
+        const int n_lines = n1 * N2;
+        const int l = blockIdx.x * 8 + warp;
+        if (blockIdx.x * 8 < n_lines && l < n_lines) {
+            uint32_t *line = s_buf + warp * 2 * n0;
+            const int base = l * n0;  // word of x' = 0 on this line
+            uint32_t q[kC4FastMaxL / 32];
+#pragma unroll
+            for (int k = 0; k < kC4FastMaxL / 32; ++k) {
+                if (k * 32 < n0) {
+                    const int x = lane + 32 * k;
+                    q[k] = A0[base + x] ^ A1[base + x];
+                    line[x] = q[k];
+                    line[x + n0] = q[k];
+                }
+            }
+            __syncwarp();
+            for (int r = 0; r < R; ++r) {
+                unsigned int c = 0;
+#pragma unroll
+                for (int k = 0; k < kC4FastMaxL / 32; ++k)
+                    if (k * 32 < n0)
+                        c += __popc(q[k] ^ line[lane + 32 * k + r]);
+                const unsigned int tot = __reduce_add_sync(0xffffffffu, c);
+                if (lane == 0)
+                    s_acc[warp][r] += tot;
+            }
+        }
+    } else if (d == 1) {
+        // a tile of 32 x-columns at one z': rows y' = 0..n1-1, doubled
+        const int tiles = (n0 / 32) * N2;
+        if ((int)blockIdx.x < tiles) {
+            const int x0 = (blockIdx.x % (n0 / 32)) * 32, z = blockIdx.x / (n0 / 32);
+            for (int y = warp; y < n1; y += 8) {
+                const int w = x0 + lane + n0 * (y + n1 * z);
+                const uint32_t v = A0[w] ^ A1[w];
+                s_buf[y * 33 + lane] = v;
+                s_buf[(y + n1) * 33 + lane] = v;
+            }
+            __syncthreads();
+            for (int cx = warp * 4; cx < warp * 4 + 4; ++cx) {
+                uint32_t q[kC4FastMaxL / 32];
+#pragma unroll
+                for (int k = 0; k < kC4FastMaxL / 32; ++k)
+                    q[k] = k * 32 < n1 ? s_buf[(lane + 32 * k) * 33 + cx] : 0u;
+                for (int r = 0; r < R; ++r) {
+                    unsigned int c = 0;
+#pragma unroll
+                    for (int k = 0; k < kC4FastMaxL / 32; ++k)
+                        if (k * 32 < n1)
+                            c += __popc(q[k] ^ s_buf[(lane + 32 * k + r) * 33 + cx]);
+                    const unsigned int tot = __reduce_add_sync(0xffffffffu, c);
+                    if (lane == 0)
+                        s_acc[warp][r] += tot;
+                }
+            }
+        }
+    } else {
+        // a column (x', y') per thread, its N2 words in registers
+        const int cols = n0 * n1;
+        const int col = blockIdx.x * blockDim.x + threadIdx.x;
+        if ((int)(blockIdx.x * blockDim.x) < cols) {
+            const bool act = col < cols;
+            uint32_t q[N2];
+#pragma unroll
+            for (int z = 0; z < N2; ++z) {
+                const int w = (act ? col : 0) + n0 * n1 * z;
+                q[z] = act ? (A0[w] ^ A1[w]) : 0u;
+            }
+            for (int r0 = 0; r0 < R; r0 += N2) {
+                const int A = r0 / N2;
+#pragma unroll
+                for (int B = 0; B < N2; ++B) {
+                    if (r0 + B >= R)
+                        break;
+                    unsigned int c = 0;
+#pragma unroll
+                    for (int z = 0; z < N2; ++z) {
+                        const uint32_t p = z + B < N2 ? __funnelshift_r(q[z + B], q[z + B], A)
+                                                      : __funnelshift_r(q[z + B - N2],
+                                                                        q[z + B - N2], A + 1);
+                        c += __popc(q[z] ^ p);
+                    }
+                    const unsigned int tot = __reduce_add_sync(0xffffffffu, c);
+                    if (lane == 0)
+                        s_acc[warp][r0 + B] += tot;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        unsigned long long t = 0;
+        for (int w = 0; w < 8; ++w)
+            t += s_acc[w][r];
+        if (t)
+            atomicAdd(&g_pop[((size_t)s * 3 + d) * R + r], t);
+    }
+}
+
 constexpr int kBlock = 256;
 
 inline dim3 grid_for(const Geo &g, int n_samples, int z = 1)
@@ -330,6 +461,17 @@ cudaError_t launch_obs_autocorr(const uint32_t *snap, const uint32_t *spins, con
 cudaError_t launch_obs_c4(const uint32_t *spins, const Geo &g, int n_samples,
                           unsigned long long *g_pop, cudaStream_t stream)
 {
+    if (g.k[0] == 1 && g.k[1] == 1 && g.k[2] == 32 && (g.L == 64 || g.L == 128)) {
+        const int n2 = g.L / 32;
+        const unsigned bx = (unsigned)std::max({g.L * n2 / 8, (g.L / 32) * n2, g.L * g.L / 256});
+        const dim3 grid(bx, 3u, (unsigned)n_samples);
+        if (n2 == 2)
+            obs_c4_fast_kernel<2><<<grid, 256, 0, stream>>>(spins, g, g_pop);
+        else
+            obs_c4_fast_kernel<4><<<grid, 256, 0, stream>>>(spins, g, g_pop);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     // a block stages up to kC4Words words of whole lines of one axis
     unsigned bx = 1;
     for (int d = 0; d < 3; ++d) {

@@ -165,6 +165,22 @@ def test_tile_kernel_late_time(J, t0):
     j.close()
 
 
+@pytest.mark.parametrize("L,tws,n,pick", [(64, [0, 1, 3], 3, [0, 1]), (128, [0, 2], 2, [1])])
+def test_c4_sums_sides_64_128(J, L, tws, n, pick):
+    """The four-point sums of the sides whose lanes all lie along z (their own kernel):
+    every axis and shift of the picked samples against the oracle."""
+    seed, p_neg, T = 71, 0.5, 0.7
+    j = J.EAJob(L, p_neg, seed, 2)
+    j.set_schedule(tws, [0])
+    j.quench(T)
+    j.sweep(n)
+    ref = ora.run_job(L, p_neg, seed, 2, T, 0, tws, [0], n, samples=pick)
+    for tw in tws:
+        g = j.measure(tw, 0)["G"]
+        assert np.array_equal(g[pick], ref["G"][tw]), tw
+    j.close()
+
+
 # ----------------------------------------------------------------------------------
 # scheduled observables
 # ----------------------------------------------------------------------------------
