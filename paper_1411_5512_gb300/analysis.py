@@ -18,6 +18,8 @@ scipy and runs on the host only.
 - collapse_x: the x for which t^x C(t, t_w) plotted against
   xi(t_w + t) / xi(t_w) falls on one curve for all t_w (the multiplicative
   decomposition of Sec. II, tested in Sec. IV).
+- overlap_histogram: P(q), the distribution of the replica overlap q = Q / N
+  (Eq. 2) over samples and times.
 """
 import numpy as np
 
@@ -184,3 +186,11 @@ def collapse_x(curves, xi_of_t, x_grid=None):
     costs = np.array([cost(x) for x in x_grid])
     k = int(np.argmin(costs))
     return float(x_grid[k]), float(costs[k])
+
+
+def overlap_histogram(Q, N, bins=2 * 16):
+    """P(q) of the overlaps q = Q / N (Eq. 2): Q holds the exact integer overlaps of
+    any set of samples and times.  Returns (bin edges on [-1, 1], density, count)."""
+    q = np.asarray(Q, dtype=np.float64).ravel() / float(N)
+    hist, edges = np.histogram(q, bins=bins, range=(-1.0, 1.0), density=True)
+    return edges, hist, int(q.size)

@@ -91,6 +91,17 @@ def test_collapse_finds_the_exponent():
     assert cost_off > 100 * cost
 
 
+def test_overlap_histogram():
+    N = 16 ** 3
+    Q = np.array([N, -N, 0, 0, N // 2, -N // 2, 0, 0])  # q = 1, -1, 0, 0, 0.5, -0.5, 0, 0
+    edges, p, n = an.overlap_histogram(Q, N, bins=4)
+    assert n == 8 and np.allclose(edges, [-1, -0.5, 0, 0.5, 1])
+    width = 0.5
+    # bins [-1,-.5) [-.5,0) [0,.5) [.5,1]: counts 1, 1, 4, 2
+    assert np.allclose(p * width * n, [1, 1, 4, 2])
+    assert abs(np.sum(p) * width - 1.0) < 1e-12
+
+
 @pytest.mark.gpu
 def test_pipeline_on_measured_curves():
     """A side-32 run: the measured C4 curves feed the multifit, and the library's
