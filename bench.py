@@ -334,6 +334,9 @@ def run_ours(args, world, rank, local):
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed(args, job, workloads, stream, flush)
+    heat = None
+    if not args.no_heat:
+        heat = run_heat(args, job, workloads, stream, flush)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -366,6 +369,8 @@ def run_ours(args, world, rank, local):
         line["serving"] = serving
     if mixed is not None:
         line["mixed_l"] = mixed
+    if heat is not None:
+        line["heat_bath"] = heat
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -405,14 +410,40 @@ def run_mixed(args, job, workloads, stream, flush):
     ms_p = timed_steps(stream, 3, plain, flush)
     for j in jobs:
         j.close()
-    vb = flips_per_sweep * n_b / (min(ms_b) * 1e6)
-    vp = flips_per_sweep * n_p / (min(ms_p) * 1e6)
+    mb, mp = statistics.median(ms_b), statistics.median(ms_p)
+    vb = flips_per_sweep * n_b / (mb * 1e6)
+    vp = flips_per_sweep * n_p / (mp * 1e6)
     return {"workload": workloads.MIXED_L["name"], "jobs": len(specs),
             "flips_per_sweep": flips_per_sweep,
-            "batched": {"value": vb, "unit": UNIT, "sweeps": n_b, "ms": min(ms_b),
+            "batched": {"value": vb, "unit": UNIT, "sweeps": n_b, "ms": mb,
                         "cols_per_thread": cfg[0], "graph_sweeps": cfg[1]},
-            "plain": {"value": vp, "unit": UNIT, "sweeps": n_p, "ms": min(ms_p)},
+            "plain": {"value": vp, "unit": UNIT, "sweeps": n_p, "ms": mp},
             "batched_over_plain": vb / vp}
+
+
+def run_heat(args, job, workloads, stream, flush):
+    """The heat-bath variant on the paper-scale workload (side 128, five jobs of 16
+    samples, T = 0.7): batched, median of 3 steps of 64 sweeps, L2 flushed between."""
+    specs = workloads.PAPER_SCALE
+    jobs = []
+    for w in specs:
+        j = job.EAJob(w["L"], w["p_neg"], w["seed"], w["n_samples"], stream=stream)
+        j.quench(w["T"], 1)
+        jobs.append(j)
+    b = job.EABatch(stream=stream)
+    for j in jobs:
+        b.add(j)
+    cfg = b.autotune(trial_sweeps=8)
+    n = args.sweeps_per_step
+    b.sweep(n)
+    ms = timed_steps(stream, 3, lambda: b.sweep(n), flush)
+    b.close()
+    for j in jobs:
+        j.close()
+    flips = n * sum(2 * w["n_samples"] * w["L"] ** 3 for w in specs)
+    m = statistics.median(ms)
+    return {"workload": "L128_p0.5-0.1_S16x5_T0.7 heat bath", "value": flips / (m * 1e6),
+            "unit": UNIT, "ms_per_step": m, "cols_per_thread": cfg[0], "graph_sweeps": cfg[1]}
 
 
 def run_serving(args, job, workloads, stream):
@@ -544,6 +575,7 @@ def main():
                     help="DRAM bytes per half-step launch from an ncu capture of this command")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-heat", action="store_true")
     ap.add_argument("--mixed-sweeps", type=int, default=64)
     ap.add_argument("--serve-jobs", type=int, default=40)
     ap.add_argument("--serve-chunk", type=int, default=1024)
