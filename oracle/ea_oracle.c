@@ -27,10 +27,10 @@
  * Random numbers: the paper's xorshift1024 generator is replaced by the
  * counter-based Philox4x32-10 of Salmon, Moraes, Dror and Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3" (SC'11), written here from that
- * publication.  The mapping from (seed, sample, replica, site, sweep) to the
- * 64-bit uniform number compared against a threshold is a definition of this
+ * publication.  The mapping from (seed, sample, replica, word-site, sweep) to
+ * the 64-bit uniform numbers that decide the flips is a definition of this
  * library (the paper's generator cannot be reproduced); it is restated in
- * full in ora_random64 below.
+ * full beside metro_draw and heat_draw below.
  */
 #include <math.h>
 #include <stdint.h>
@@ -79,13 +79,13 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* Counter word 2 carries a stream tag in its top two bits. */
 #define STREAM_COUPLINGS 0u
 #define STREAM_SPINS 1u
-#define STREAM_SWEEP 2u
+#define STREAM_HEAT 2u
 
 /* ------------------------------------------------------------------------ */
 /* Lattice geometry of the random-number mapping.                           */
 /*                                                                          */
 /* A "word-site" groups up to 32 lattice sites of one sample that are drawn */
-/* from the same Philox outputs, one bit each (see ora_random64).  The      */
+/* from the same Philox calls (see metro_draw and heat_draw).  The        */
 /* lattice is cut into kx*ky*kz equal blocks, each of even side, and the    */
 /* word-site (x', y', z') of the sub-lattice of side (L/kx, L/ky, L/kz)     */
 /* gathers the sites at the same relative position in every block (the     */
@@ -130,63 +130,6 @@ int ora_site_to_word(int L, int x, int y, int z, uint32_t *widx, int *lane)
         return ORA_BAD_ARG;
     site_to_word(L, x, y, z, widx, lane);
     return ORA_OK;
-}
-
-/* ------------------------------------------------------------------------ */
-/* The 64-bit uniform number r(seed, s, a, site, t) used by the heat-bath    */
-/* update of replica a of sample s at the given site during sweep t.        */
-/*                                                                          */
-/* Bit (63 - k) of r, k = 0..63, is bit `lane` of plane k, where plane k is */
-/* output word (k mod 4) of Philox4x32-10 with key (lo32(seed), hi32(seed)) */
-/* and counter                                                              */
-/*   c0 = widx, c1 = lo32(t),                                               */
-/*   c2 = (2 << 30) | (bits 32..47 of t) << 8 | a << 4 | (k div 4),         */
-/*   c3 = s.                                                                */
-/* ------------------------------------------------------------------------ */
-/* Bits 63..32 (half = 0, calls 0..7) or bits 31..0 (half = 1, calls 8..15)
-   of r, as a 32-bit number. */
-static uint32_t random_half(int L, uint64_t seed, uint32_t s, int a, int x, int y, int z, uint64_t t,
-                            int half)
-{
-    uint32_t widx;
-    int lane;
-    site_to_word(L, x, y, z, &widx, &lane);
-    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t v = 0;
-    for (int call = 8 * half; call < 8 * half + 8; call++) {
-        uint32_t ctr[4] = {widx, (uint32_t)t,
-                           (STREAM_SWEEP << 30) | ((uint32_t)((t >> 32) & 0xFFFFu) << 8) |
-                               ((uint32_t)a << 4) | (uint32_t)call,
-                           s};
-        uint32_t out[4];
-        ora_philox4x32_10(ctr, key, out);
-        for (int j = 0; j < 4; j++) {
-            int k = 4 * call + j;          /* plane index, 0..63 */
-            uint32_t bit = (out[j] >> lane) & 1u;
-            v |= bit << (31 - (k - 32 * half));
-        }
-    }
-    return v;
-}
-
-uint64_t ora_random64(int L, uint64_t seed, uint32_t s, int a, int x, int y, int z, uint64_t t)
-{
-    uint64_t hi = random_half(L, seed, s, a, x, y, z, t, 0);
-    uint64_t lo = random_half(L, seed, s, a, x, y, z, t, 1);
-    return (hi << 32) | lo;
-}
-
-/* r < thr for r = ora_random64(...).  Two 64-bit numbers compare by their
-   top 32 bits unless those are equal, so the bottom half is drawn only then. */
-static int random_below(int L, uint64_t seed, uint32_t s, int a, int x, int y, int z, uint64_t t,
-                        uint64_t thr)
-{
-    uint32_t r_hi = random_half(L, seed, s, a, x, y, z, t, 0);
-    uint32_t t_hi = (uint32_t)(thr >> 32);
-    if (r_hi != t_hi)
-        return r_hi < t_hi;
-    uint32_t r_lo = random_half(L, seed, s, a, x, y, z, t, 1);
-    return r_lo < (uint32_t)thr;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -358,23 +301,94 @@ static uint64_t metro_draw(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed
     return ((uint64_t)(lead & 0x3FFu) << 54) | ((((uint64_t)x[0] << 32) | x[1]) >> 10);
 }
 
-/* Flip decisions of the lanes lane_list[0..n) (increasing lane order) of one
-   class: sets flip[lane] = 1 for the accepted ones. */
-static void metro_class(const uint64_t C[33], const int *lane_list, int n, int Lx, int Ly,
-                        int xw, int yw, int zw, uint64_t seed, uint32_t s, int a, uint64_t t,
-                        int u, uint8_t *flip)
+/* ------------------------------------------------------------------------ */
+/* Heat-bath acceptance by geometric gaps.                                  */
+/*                                                                          */
+/* The heat-bath rule flips a site with probability P(dE) = 1/(1+e^(dE/T)), */
+/* and P(dE) + P(-dE) = 1.  With p_j = P(12 - 4j) for j = 0, 1, 2 (dE = 12, */
+/* 8, 4), the sites of a word-site in class u (u unsatisfied bonds, dE =    */
+/* 12 - 4u) are decided as follows:                                          */
+/*   u = 0, 1, 2: the sites that flip are chosen by geometric gaps with     */
+/*     probability p_u, exactly as the Metropolis classes are;              */
+/*   u = 3 (dE = 0, P = 1/2): lane b flips when bit b of the coin word is 1; */
+/*   u = 4, 5, 6: a site keeps its spin with probability 1 - P(dE) =        */
+/*     p_(6-u); the sites that keep are chosen by geometric gaps with that   */
+/*     probability, and every other site of the class flips.                */
+/* The gap table of p_j serves classes j and 6 - j.  p_j = 0 (T = 0, or     */
+/* e^((12-4j)/T) beyond the double range) leaves class j unflipped and flips */
+/* all of class 6 - j.                                                       */
+/*                                                                          */
+/* Draws, per word-site, from Philox4x32-10 with counter                    */
+/*   (widx, lo32(t), (2 << 30) | (bits 32..47 of t) << 12 | a << 11 | call, s): */
+/*   call 0: out0 is the coin word; out1 holds bits 63..48 of draw 0 of     */
+/*     class 2 in its bits 31..16 and those of class 4 in bits 15..0; out2  */
+/*     the same for classes 1 and 5; out3 for classes 0 and 6.              */
+/*   call 128 + (2 - j) for the pair (j, 6 - j): (out0 << 32 | out1) >> 16 */
+/*     is bits 47..0 of draw 0 of class j, (out2 << 32 | out3) >> 16 that of */
+/*     class 6 - j.                                                         */
+/*   draw d >= 1 of class u: (out[2e] << 32) | out[2e + 1] of call          */
+/*     1 + u + 7 (d-1 div 2), e = (d-1) mod 2 (calls below 128 for d <= 32). */
+/* ------------------------------------------------------------------------ */
+static void heat_call(uint32_t widx, uint64_t seed, uint32_t s, int a, uint64_t t, int call,
+                      uint32_t out[4])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {widx, (uint32_t)t,
+                       (STREAM_HEAT << 30) | ((uint32_t)((t >> 32) & 0xFFFFu) << 12) |
+                           ((uint32_t)a << 11) | (uint32_t)call,
+                       s};
+    ora_philox4x32_10(ctr, key, out);
+}
+
+/* Draw d of class u (u != 3) for the word-site (xw, yw, zw), replica a. */
+static uint64_t heat_draw(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s,
+                          int a, uint64_t t, int u, int d)
+{
+    uint32_t widx = (uint32_t)(xw + Lx * (yw + Ly * zw));
+    uint32_t out[4];
+    if (d >= 1) {
+        int e = (d - 1) % 2;
+        heat_call(widx, seed, s, a, t, 1 + u + 7 * ((d - 1) / 2), out);
+        return ((uint64_t)out[2 * e] << 32) | (uint64_t)out[2 * e + 1];
+    }
+    int j = u < 3 ? u : 6 - u;      /* the pair (j, 6 - j) */
+    heat_call(widx, seed, s, a, t, 0, out);
+    uint32_t word = out[3 - j];     /* j = 2 -> out1, 1 -> out2, 0 -> out3 */
+    uint64_t lead = u < 3 ? (word >> 16) : (word & 0xFFFFu);
+    heat_call(widx, seed, s, a, t, 128 + (2 - j), out);
+    uint64_t low = u < 3 ? ((((uint64_t)out[0] << 32) | out[1]) >> 16)
+                         : ((((uint64_t)out[2] << 32) | out[3]) >> 16);
+    return (lead << 48) | low;
+}
+
+/* The coin word of the word-site: bit b decides lane b of class 3. */
+static uint32_t heat_coin(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s,
+                          int a, uint64_t t)
+{
+    uint32_t out[4];
+    heat_call((uint32_t)(xw + Lx * (yw + Ly * zw)), seed, s, a, t, 0, out);
+    return out[0];
+}
+
+/* Gap selection over the lanes lane_list[0..n) (increasing lane order) of
+   one class: sets mark[lane] = 1 for the selected ones.  rule 0 draws with
+   metro_draw, rule 1 with heat_draw. */
+static void gap_class(const uint64_t C[33], const int *lane_list, int n, int rule, int Lx,
+                      int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s, int a,
+                      uint64_t t, int u, uint8_t *mark)
 {
     int start = 0, d = 0;
     while (n - start > 0) {
-        uint64_t V = metro_draw(Lx, Ly, xw, yw, zw, seed, s, a, t, u, d);
+        uint64_t V = rule == 0 ? metro_draw(Lx, Ly, xw, yw, zw, seed, s, a, t, u, d)
+                               : heat_draw(Lx, Ly, xw, yw, zw, seed, s, a, t, u, d);
         d++;
         int rem = n - start;
         if (V >= C[rem])
-            break; /* no acceptance among the remaining sites */
+            break; /* no selection among the remaining sites */
         int G = 0;
         while (!(V < C[G + 1]))
             G++;
-        flip[lane_list[start + G]] = 1;
+        mark[lane_list[start + G]] = 1;
         start += G + 1;
     }
 }
@@ -405,11 +419,13 @@ static int delta_E(int L, const int8_t *Sa, const int8_t *J, int x, int y, int z
 /* one colour do not neighbour each other, so the sites of a colour are     */
 /* decided from the same configuration and may be taken in any order; here  */
 /* they are taken word-site by word-site.  Each site gets dE = 2 S_i sum_j  */
-/* J_ij S_j (Eq. 9), k = (dE + 12) / 4, and flips when always[k];           */
-/*   rule 0 (Metropolis): the other sites of a word-site are decided per    */
-/*     class by geometric gaps (above); a class with threshold 0 never flips */
-/*   rule 1 (heat bath): a site flips when its uniform r < thr[k]           */
-/*     (ora_random64).                                                      */
+/* J_ij S_j (Eq. 9) and class u = (12 - dE) / 4;                           */
+/*   rule 0 (Metropolis): dE <= 0 flips (always[k], k = (dE + 12) / 4), as  */
+/*     does a class whose e^(-dE/T) rounds to 1; the other classes are      */
+/*     decided by geometric gaps (metro_draw); a class with threshold 0     */
+/*     never flips.                                                         */
+/*   rule 1 (heat bath): every class is decided by heat_draw's coin word or */
+/*     gaps (above).                                                        */
 /* dE_acc[a] accumulates the energy change of accepted flips of replica a.  */
 /* s keys the random numbers (counter word 3): the sample index, or the     */
 /* sample index divided by G when G samples share their random numbers.     */
@@ -424,14 +440,22 @@ int ora_half_step(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, 
         return ORA_BAD_ARG;
     uint64_t C[3][33];
     int live[3] = {0, 0, 0};
-    if (rule == 0) {
-        for (int u = 0; u < 3; u++) {
+    for (int u = 0; u < 3; u++) {
+        double p;
+        if (rule == 0) {
             int k = 6 - u;
-            if (!always[k] && thr[k] > 0) {
-                live[u] = 1;
-                ora_geo_table(exp(-(double)(12 - 4 * u) / T), C[u]);
-            }
+            if (always[k] || thr[k] == 0)
+                continue;
+            p = exp(-(double)(12 - 4 * u) / T);
+        } else {
+            if (T == 0.0)
+                continue;
+            p = 1.0 / (1.0 + exp((double)(12 - 4 * u) / T));
+            if (!(p > 0.0))
+                continue;
         }
+        live[u] = 1;
+        ora_geo_table(p, C[u]);
     }
     int g[6];
     ora_geometry(L, g);
@@ -452,7 +476,7 @@ int ora_half_step(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, 
                         sy[b] = ((b / kx) % ky) * Ly + yw;
                         sz[b] = (b / (kx * ky)) * Lz + zw;
                         dE[b] = delta_E(L, Sa, J, sx[b], sy[b], sz[b]);
-                        flip[b] = always[(dE[b] + 12) / 4];
+                        flip[b] = rule == 0 ? always[(dE[b] + 12) / 4] : 0;
                     }
                     if (rule == 0) {
                         for (int u = 0; u < 3; u++) {
@@ -463,14 +487,31 @@ int ora_half_step(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, 
                                 if (dE[b] == 12 - 4 * u)
                                     list[n++] = b;
                             if (n > 0)
-                                metro_class(C[u], list, n, Lx, Ly, xw, yw, zw, seed, s, a, t,
-                                            u, flip);
+                                gap_class(C[u], list, n, 0, Lx, Ly, xw, yw, zw, seed, s, a, t,
+                                          u, flip);
                         }
                     } else {
-                        for (int b = 0; b < lanes; b++)
-                            if (!flip[b])
-                                flip[b] = (uint8_t)random_below(L, seed, s, a, sx[b], sy[b],
-                                                                sz[b], t, thr[(dE[b] + 12) / 4]);
+                        uint32_t coin = heat_coin(Lx, Ly, xw, yw, zw, seed, s, a, t);
+                        for (int u = 0; u <= 6; u++) {
+                            int list[32], n = 0;
+                            for (int b = 0; b < lanes; b++)
+                                if (dE[b] == 12 - 4 * u)
+                                    list[n++] = b;
+                            if (n == 0)
+                                continue;
+                            if (u == 3) {
+                                for (int i = 0; i < n; i++)
+                                    flip[list[i]] = (uint8_t)((coin >> list[i]) & 1u);
+                                continue;
+                            }
+                            int j = u < 3 ? u : 6 - u;
+                            uint8_t mark[32] = {0};
+                            if (live[j])
+                                gap_class(C[j], list, n, 1, Lx, Ly, xw, yw, zw, seed, s, a, t,
+                                          u, mark);
+                            for (int i = 0; i < n; i++)
+                                flip[list[i]] = u < 3 ? mark[list[i]] : (uint8_t)!mark[list[i]];
+                        }
                     }
                     for (int b = 0; b < lanes; b++)
                         if (flip[b]) {

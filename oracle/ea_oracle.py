@@ -55,9 +55,6 @@ def lib():
         L.ora_geometry.restype = ctypes.c_int
         L.ora_site_to_word.argtypes = [ctypes.c_int] * 4 + [u32p, ctypes.POINTER(ctypes.c_int)]
         L.ora_site_to_word.restype = ctypes.c_int
-        L.ora_random64.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
-                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
-        L.ora_random64.restype = ctypes.c_uint64
         L.ora_thresholds.argtypes = [ctypes.c_double, ctypes.c_int, u64p, u8p]
         L.ora_thresholds.restype = ctypes.c_int
         L.ora_init_couplings.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
@@ -112,10 +109,6 @@ def site_to_word(L, x, y, z):
     b = ctypes.c_int()
     _check(lib().ora_site_to_word(L, x, y, z, ctypes.byref(w), ctypes.byref(b)), "site_to_word")
     return w.value, b.value
-
-
-def random64(L, seed, s, a, x, y, z, t):
-    return int(lib().ora_random64(L, seed, s, a, x, y, z, t))
 
 
 def thresholds(T, rule=0):

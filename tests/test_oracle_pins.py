@@ -142,28 +142,6 @@ def test_thresholds_reject_bad_args():
 # ----------------------------------------------------------------------------------
 # random numbers and initial state
 # ----------------------------------------------------------------------------------
-def test_random64_uniform_top_bits():
-    L = 8
-    vals = []
-    for t in range(4):
-        for z, y, x in itertools.product(range(L), repeat=3):
-            vals.append(ora.random64(L, 12345, 3, t & 1, x, y, z, t) >> 60)
-    counts = np.bincount(np.array(vals), minlength=16)
-    n = len(vals)
-    chi2 = float(np.sum((counts - n / 16.0) ** 2 / (n / 16.0)))
-    assert chi2 < 45.0  # 15 dof, p ~ 1e-4
-
-
-def test_random64_depends_on_every_key_part():
-    base = ora.random64(16, 7, 2, 0, 3, 4, 5, 11)
-    assert base != ora.random64(16, 8, 2, 0, 3, 4, 5, 11)  # seed
-    assert base != ora.random64(16, 7, 3, 0, 3, 4, 5, 11)  # sample
-    assert base != ora.random64(16, 7, 2, 1, 3, 4, 5, 11)  # replica
-    assert base != ora.random64(16, 7, 2, 0, 4, 4, 5, 11)  # site
-    assert base != ora.random64(16, 7, 2, 0, 3, 4, 5, 12)  # sweep
-    assert base != ora.random64(16, 7, 2, 0, 3, 4, 5, 11 + (1 << 32))  # high sweep bits
-
-
 def test_couplings_bimodal_fraction():
     L = 16
     assert np.all(ora.init_couplings(L, 0.0, 5, 0) == 1)
@@ -449,9 +427,9 @@ def test_geo_table_closed_form():
             ora.geo_table(bad)
 
 
-def _half_step_stats(L, T, n_rep, seed=5):
+def _half_step_stats(L, T, n_rep, seed=5, rule=0):
     """Flip outcomes of the sites updated in half-step 0, grouped per word-site and
-    class, over n_rep independent half-steps from the same state."""
+    dE, over n_rep independent half-steps from the same state."""
     kx, ky, kz, Lx, Ly, Lz = ora.geometry(L)
     J = ora.init_couplings(L, 0.5, seed, 0)
     S0 = ora.init_spins(L, seed, 0)
@@ -469,50 +447,64 @@ def _half_step_stats(L, T, n_rep, seed=5):
     groups = {}  # (rep, a, widx, dE) -> list of (lane, flipped)
     for rep in range(n_rep):
         S = S0.copy()
-        ora.half_step(L, seed, 0, S, J, T, 0, 1000 + rep, 0)
+        ora.half_step(L, seed, 0, S, J, T, rule, 1000 + rep, 0)
         for a in range(2):
             upd = colour == (0 ^ a)
             fl = (S[a] != S0[a]) & upd
-            for dE in (4, 8, 12):
+            for dE in ((4, 8, 12) if rule == 0 else (-12, -8, -4, 0, 4, 8, 12)):
                 m = upd & (dEs[a] == dE)
                 for w, b, f in zip(widx[m], lane[m], fl[m]):
                     groups.setdefault((rep, a, int(w), dE), []).append((int(b), bool(f)))
-            # sites with dE <= 0 always flip
-            assert np.all(fl[upd & (dEs[a] <= 0)])
+            if rule == 0:  # sites with dE <= 0 always flip
+                assert np.all(fl[upd & (dEs[a] <= 0)])
     return groups
+
+
+def _class_checks(groups, dE, p):
+    """Each site of class dE flips with probability p, at every rank within its
+    word-site, and the first and last site of a class decide independently."""
+    tot = acc = 0
+    rank_n = np.zeros(32)
+    rank_acc = np.zeros(32)
+    pair_n = pair_both = 0
+    for (rep, a, w, e), lst in groups.items():
+        if e != dE:
+            continue
+        lst.sort()
+        f = [x[1] for x in lst]
+        tot += len(f)
+        acc += sum(f)
+        for j, v in enumerate(f):
+            rank_n[j] += 1
+            rank_acc[j] += v
+        if len(f) >= 2:
+            pair_n += 1
+            pair_both += f[0] and f[-1]
+    sig = math.sqrt(tot * p * (1 - p))
+    assert abs(acc - tot * p) < 5 * sig, (dE, acc, tot * p)
+    for j in range(4):  # the first ranks each accept with probability p
+        if rank_n[j] > 200:
+            sj = math.sqrt(rank_n[j] * p * (1 - p))
+            assert abs(rank_acc[j] - rank_n[j] * p) < 5 * sj, (dE, j)
+    if pair_n > 200:  # first and last site of a class decide independently
+        q = p * p
+        assert abs(pair_both - pair_n * q) < 5 * math.sqrt(pair_n * q * (1 - q)) + 1, dE
 
 
 def test_metropolis_class_statistics():
     T = 3.0
     groups = _half_step_stats(32, T, 6)
     for dE in (4, 8, 12):
-        p = math.exp(-dE / T)
-        tot = acc = 0
-        rank_n = np.zeros(32)
-        rank_acc = np.zeros(32)
-        pair_n = pair_both = 0
-        for (rep, a, w, e), lst in groups.items():
-            if e != dE:
-                continue
-            lst.sort()
-            f = [x[1] for x in lst]
-            tot += len(f)
-            acc += sum(f)
-            for j, v in enumerate(f):
-                rank_n[j] += 1
-                rank_acc[j] += v
-            if len(f) >= 2:
-                pair_n += 1
-                pair_both += f[0] and f[-1]
-        sig = math.sqrt(tot * p * (1 - p))
-        assert abs(acc - tot * p) < 5 * sig, (dE, acc, tot * p)
-        for j in range(4):  # the first ranks each accept with probability p
-            if rank_n[j] > 200:
-                sj = math.sqrt(rank_n[j] * p * (1 - p))
-                assert abs(rank_acc[j] - rank_n[j] * p) < 5 * sj, (dE, j)
-        if pair_n > 200:  # first and last site of a class decide independently
-            q = p * p
-            assert abs(pair_both - pair_n * q) < 5 * math.sqrt(pair_n * q * (1 - q)) + 1, dE
+        _class_checks(groups, dE, math.exp(-dE / T))
+
+
+@pytest.mark.parametrize("T", [1.5, 4.0])
+def test_heatbath_class_statistics(T):
+    """Every class, the gap-selected (dE > 0), the coin (dE = 0) and the
+    complement-selected (dE < 0), flips with 1 / (1 + e^(dE/T))."""
+    groups = _half_step_stats(32, T, 6, rule=1)
+    for dE in (-12, -8, -4, 0, 4, 8, 12):
+        _class_checks(groups, dE, 1.0 / (1.0 + math.exp(dE / T)))
 
 
 def test_metropolis_zero_and_infinite_temperature_classes():
@@ -529,3 +521,31 @@ def test_metropolis_zero_and_infinite_temperature_classes():
     colour = np.indices((L, L, L)).sum(axis=0) & 1
     assert np.array_equal(S[0][colour == 0], -S0[0][colour == 0])
     assert np.array_equal(S[0][colour == 1], S0[0][colour == 1])
+
+
+def test_heatbath_zero_temperature_classes():
+    """T = 0: every dE < 0 site flips, no dE > 0 site does, dE = 0 sites flip by a
+    fair coin; the coin of a word-site is shared by no two sites (one bit each)."""
+    L = 16
+    J = ora.init_couplings(L, 0.5, 6, 0)
+    S0 = ora.init_spins(L, 6, 0)
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    colour = (x + y + z) & 1
+    s = S0[0].astype(np.int64)
+    hloc = np.zeros_like(s)
+    for d, ax in ((0, 2), (1, 1), (2, 0)):
+        hloc += J[d] * np.roll(s, -1, axis=ax) + np.roll(J[d] * s, 1, axis=ax)
+    dE = 2 * s * hloc
+    upd = colour == 0
+    zero = 0
+    n_zero = 0
+    for t in range(8):
+        S = S0.copy()
+        ora.half_step(L, 6, 0, S, J, 0.0, 1, t, 0)
+        fl = S[0] != S0[0]
+        assert np.all(fl[upd & (dE < 0)]) and not np.any(fl[upd & (dE > 0)])
+        assert not np.any(fl[~upd])
+        zero += int(np.sum(fl[upd & (dE == 0)]))
+        n_zero += int(np.sum(upd & (dE == 0)))
+    assert n_zero > 1000
+    assert abs(zero - n_zero / 2) < 5 * math.sqrt(n_zero / 4)
