@@ -207,41 +207,27 @@ static ea::Thr make_thr(int rule, double T, const uint64_t thr_k[7], const uint8
                 ea::geo_table(std::exp(-(double)(12 - 4 * u) / T), t.geoC[u]);
             }
         }
-    }
-    int n_always = 0;
-    for (int u = 0; u < 7; ++u) {
-        // u unsatisfied bonds <=> dE = 12 - 4u <=> k = 6 - u
-        t.thr_u[u] = thr_k[6 - u];
-        if (always_k[6 - u]) {
-            t.always_u |= 1u << u;
-            ++n_always;
+        int n_always = 0;
+        for (int u = 0; u < 7; ++u)
+            if (always_k[6 - u]) {  // u unsatisfied bonds <=> k = 6 - u
+                t.always_u |= 1u << u;
+                ++n_always;
+            }
+        t.all_always = n_always == 7;
+        // no class can accept: the random numbers are skipped
+        t.none_random = t.geo_live == 0;
+    } else if (T > 0.0) {
+        // heat bath: p_u = 1 / (1 + e^((12 - 4u)/T)) for dE = 12 - 4u > 0; the
+        // table of p_u also selects the lanes of class 6 - u that keep their
+        // spin.  p_u = 0 (T = 0 or beyond the double range) leaves no table.
+        for (int u = 0; u < 3; ++u) {
+            const double p = 1.0 / (1.0 + std::exp((double)(12 - 4 * u) / T));
+            if (p > 0.0) {
+                t.geo_live |= 1u << u;
+                ea::geo_table(p, t.geoC[u]);
+            }
         }
     }
-    t.all_always = n_always == 7;
-    // lanes that compare a random number: every u not accepted outright
-    bool any_nonzero = false;
-    uint32_t zero_calls = 0;
-    const int nu = rule == EA_RULE_METROPOLIS ? 3 : 7;
-    for (int call = 0; call < 16; ++call) {
-        bool zero = true;
-        for (int u = 0; u < nu; ++u) {
-            if ((t.always_u >> u) & 1u)
-                continue;
-            const uint64_t nib = (t.thr_u[u] >> (60 - 4 * call)) & 0xFu;
-            if (nib)
-                zero = false;
-        }
-        if (zero)
-            zero_calls |= 1u << call;
-    }
-    for (int u = 0; u < nu; ++u)
-        if (!((t.always_u >> u) & 1u) && t.thr_u[u] != 0)
-            any_nonzero = true;
-    if (rule == EA_RULE_METROPOLIS)
-        any_nonzero = t.geo_live != 0;
-    t.zero_calls = zero_calls;
-    // with every needed threshold 0 no lane can accept: skip the random numbers
-    t.none_random = !any_nonzero;
     return t;
 }
 
@@ -407,9 +393,8 @@ int launch_plain(ea_ctx *c, uint64_t n)
 {
     const bool heat = c->rule == EA_RULE_HEATBATH;
     EA_CUDA(c, ea::launch_sweep_table(heat ? nullptr : &c->jd, heat ? nullptr : c->jd_dev,
-                                      heat ? 0 : 1, heat ? c->jd_dev : nullptr,
-                                      heat ? c->bb_dev : nullptr, heat ? 1 : 0,
-                                      heat ? c->blocks : 0, n, c->stream));
+                                      heat ? 0 : 1, heat ? &c->jd : nullptr,
+                                      heat ? c->jd_dev : nullptr, heat ? 1 : 0, n, c->stream));
     return EA_OK;
 }
 
@@ -1199,7 +1184,7 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
 int enqueue_direct(ea_batch *b, uint64_t n, unsigned long long *counters = nullptr)
 {
     EA_BCUDA(b, ea::launch_sweep_table(b->tab_host[0].data(), b->tab_dev[0], b->n_jobs[0],
-                                       b->tab_dev[1], b->bb_dev[1], b->n_jobs[1], b->blocks[1], n,
+                                       b->tab_host[1].data(), b->tab_dev[1], b->n_jobs[1], n,
                                        b->stream, counters, b->have_side ? &b->side : nullptr));
     for (int r = 0; r < 2; ++r)
         EA_BCUDA(b, ea::launch_advance_time(b->tab_dev[r], b->n_jobs[r], n, b->stream));

@@ -59,7 +59,7 @@ __device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t (&rk)[20])
 
 constexpr uint32_t kStreamCouplings = 0u << 30;
 constexpr uint32_t kStreamSpins = 1u << 30;
-constexpr uint32_t kStreamSweep = 2u << 30;        // heat-bath bit planes
+constexpr uint32_t kStreamHeat = 2u << 30;         // heat-bath coin words and gaps
 constexpr uint32_t kStreamMetropolis = 3u << 30;   // Metropolis geometric gaps
 
 }  // namespace dev

@@ -50,13 +50,14 @@ int make_geo(int L, Geo *g);  // 0 or -1
 // C[g] = floor(2^64 (1 - (1 - p)^g)), g = 0..32, clamped to 2^64 - 1 (0 < p < 1).
 int geo_table(double p, uint64_t C[33]);
 
-// Threshold planes for the bit-sliced comparison r < thr (MSB first).
+// Acceptance tables of a job.  Both rules decide the classes u = 0, 1, 2
+// (dE = 12, 8, 4) by geometric gaps with table C_u; the heat bath decides the
+// classes 6 - u (dE = -12, -8, -4) with the same table, selecting the lanes
+// that keep their spin, and dE = 0 by a coin word.
 struct Thr {
-    uint64_t thr_u[7];      // indexed by u = number of unsatisfied bonds = 6 - k
-    uint64_t geoC[3][33];   // Metropolis geometric-gap tables, u = 0, 1, 2
-    uint32_t geo_live;      // bit u: 0 < p_u < 1
-    uint32_t always_u;      // bit u set: accepted without a random number
-    uint32_t zero_calls;    // bit c set: planes 4c..4c+3 of every needed threshold are 0
+    uint64_t geoC[3][33];   // C_u[g] = floor(2^64 (1 - (1 - p_u)^g))
+    uint32_t geo_live;      // bit u: class u has a table (p_u > 0)
+    uint32_t always_u;      // Metropolis, bit u set: accepted without a random number
     int rule;               // 0 Metropolis, 1 heat bath
     int all_always;         // every u always accepted (Metropolis at T = inf)
     int none_random;        // no lane ever needs a random number
@@ -73,12 +74,9 @@ struct alignas(16) JobDev {
     uint64_t t_end;           // the job sweeps while t < t_end (its own stop)
     Geo geo;
     uint32_t rk[20];          // Philox round keys: rk[2r], rk[2r+1] for round r
-    alignas(16) uint32_t tm[16][7][4];  // heat bath: threshold plane masks
-                                        // [call][u][plane in call], read as uint4
-    uint32_t gC_hi[3][33];    // Metropolis: geometric-gap tables C_u[g], high words
+    uint32_t gC_hi[3][33];    // geometric-gap tables C_u[g], high words
     uint32_t gC_lo[3][33];    //   and low words, u = 0, 1, 2 (dE = 12, 8, 4)
-    uint32_t geo_live;        // bit u: class u can accept (0 < p_u < 1)
-    uint32_t zero_calls;      // bit c: planes 4c..4c+3 of every needed threshold are 0
+    uint32_t geo_live;        // bit u: class u has a table (0 < p_u < 1)
     uint32_t always_u;        // bit u: accepted without a random number
     int rule;
     int all_always;
@@ -92,7 +90,6 @@ struct alignas(16) JobDev {
     int cols_per_thread;
 };
 
-static_assert(offsetof(JobDev, tm) % 16 == 0, "JobDev::tm is read with 16-byte loads");
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev tables are arrays of 16-byte aligned rows");
 
 // Host-side preparation of a JobDev (ea_sweep.cu).
@@ -146,10 +143,6 @@ struct MetroParams {
 
 static_assert(sizeof(MetroParams<kMetroMaxJobs>) <= 32000, "kernel parameter block limit");
 
-// Enqueue n sweeps of every job of a table: one launch per half-step per rule
-// (Metropolis tables of more than kMetroMaxJobs jobs take several).  host0 and
-// dev0 are the host and device copies of the Metropolis rows; the heat-bath
-// rows are read from dev1 with block offsets bb_dev1 (blocks1 blocks).
 // Kernel launches issued by the library (process-wide).  A launch made while
 // the calling thread captures a graph is counted into that capture instead;
 // capture_begin/capture_end bracket it and give the number of kernels the
@@ -167,8 +160,12 @@ struct SideStreams {
     cudaEvent_t join[2];
 };
 
+// Enqueue n sweeps of every job of a table: one launch per half-step per rule
+// and run (tables of more than kMetroMaxJobs jobs take several).  host0/dev0
+// are the host and device copies of the Metropolis rows, host1/dev1 those of
+// the heat-bath rows.
 cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
-                               const JobDev *dev1, const int *bb_dev1, int n_jobs1, int blocks1,
+                               const JobDev *host1, const JobDev *dev1, int n_jobs1,
                                uint64_t n, cudaStream_t stream,
                                unsigned long long *counters = nullptr,
                                const SideStreams *side = nullptr);

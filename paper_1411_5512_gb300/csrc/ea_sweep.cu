@@ -18,10 +18,10 @@
 //     words holds the leading 32 (class 2) and 16 (classes 1, 0) bits of
 //     their first draws, enough to settle ~97% of words at T = 0.7 without a
 //     branch; the rest of a draw is fetched only when the test hits.
-//   Heat bath (heat_kernel): every lane compares its own 64-bit uniform r
-//     with its threshold, MSB first, four planes per Philox call; a lane is
-//     decided at the first plane where its bit of r differs from its
-//     threshold bit.
+//   Heat bath (heat_kernel): one Philox call per word holds a coin word for
+//     dE = 0 and the leading bits of the first gap draws of the other six
+//     classes; classes dE > 0 flip the lanes the gaps select, classes dE < 0
+//     keep them (P(dE) + P(-dE) = 1).
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -145,24 +145,27 @@ __device__ __forceinline__ uint32_t nth_bit(uint32_t m, int k)
     return 1u << p;
 }
 
-// The accepted lanes of one class of a word, from its full first draw V0.
-__device__ __forceinline__ uint32_t metro_class(const JobDev *__restrict__ jb, int u, uint32_t Mr,
-                                                uint64_t V0, uint32_t w, uint32_t c1,
-                                                uint32_t c2, uint32_t c3, const uint32_t (&rk)[20],
-                                                unsigned int &calls)
+// The lanes of Mr that the geometric gaps of table C_tab select, from the full
+// first draw V0; draw d >= 1 is taken from call 1 + cu + STRIDE ((d - 1) div 2)
+// (Metropolis: STRIDE 3 and cu = tab; heat bath: STRIDE 7, cu the class).
+template <int STRIDE>
+__device__ __forceinline__ uint32_t gap_class(const JobDev *__restrict__ jb, int tab, int cu,
+                                              uint32_t Mr, uint64_t V0, uint32_t w, uint32_t c1,
+                                              uint32_t c2, uint32_t c3, const uint32_t (&rk)[20],
+                                              unsigned int &calls)
 {
     uint32_t acc = 0u;
     int rem = __popc(Mr);
     int d = 0;
     uint64_t V = V0;
     while (rem > 0) {
-        if (!(V < c64(jb, u, rem)))
-            break;  // no acceptance among the remaining lanes
+        if (!(V < c64(jb, tab, rem)))
+            break;  // no selection among the remaining lanes
         // G = min{g : V < C[g + 1]} by bisection over the nondecreasing table
         int lo = 1, hi = rem;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (V < c64(jb, u, mid))
+            if (V < c64(jb, tab, mid))
                 hi = mid;
             else
                 lo = mid + 1;
@@ -177,11 +180,20 @@ __device__ __forceinline__ uint32_t metro_class(const JobDev *__restrict__ jb, i
         ++d;
         const int e = (d - 1) & 1;
         const uint4 Q = dev::philox10_rk(
-            make_uint4(w, c1, c2 | (uint32_t)(1 + u + 3 * ((d - 1) >> 1)), c3), rk);
+            make_uint4(w, c1, c2 | (uint32_t)(1 + cu + STRIDE * ((d - 1) >> 1)), c3), rk);
         ++calls;
         V = e == 0 ? (((uint64_t)Q.x << 32) | Q.y) : (((uint64_t)Q.z << 32) | Q.w);
     }
     return acc;
+}
+
+// The accepted lanes of Metropolis class u of a word, from its full first draw V0.
+__device__ __forceinline__ uint32_t metro_class(const JobDev *__restrict__ jb, int u, uint32_t Mr,
+                                                uint64_t V0, uint32_t w, uint32_t c1,
+                                                uint32_t c2, uint32_t c3, const uint32_t (&rk)[20],
+                                                unsigned int &calls)
+{
+    return gap_class<3>(jb, u, u, Mr, V0, w, c1, c2, c3, rk, calls);
 }
 
 // Class masks of a word (u = 0, 1, 2 <=> b2 = 0 and not b1 & b0)
@@ -918,65 +930,175 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
 }
 
 // ---------------------------------------------------------------------------
-// heat bath: per-lane 64-bit comparison by bit planes
+// Heat bath, any side.  Per word-site one Philox call (stream 2, call 0, the
+// word's own widx and replica): out0 is the coin word of class 3 (dE = 0, flip
+// probability 1/2), and out1, out2, out3 hold the 16 leading bits of the first
+// draws of the class pairs (2, 4), (1, 5), (0, 6), class u < 3 in the high
+// half.  Call 128 + (2 - j) completes both first draws of the pair (j, 6 - j):
+// (out0:out1) >> 16 and (out2:out3) >> 16.  Class u < 3 flips the lanes that
+// the gaps of table C_u select; class u > 3 keeps the lanes that the gaps of
+// C_(6-u) select and flips the rest (P(dE) + P(-dE) = 1).  Draw d >= 1 of
+// class u is (out[2e] << 32) | out[2e + 1] of call 1 + u + 7 ((d - 1) div 2).
+// Words whose leading bits might select a lane wait in a per-warp queue and
+// are finished 32 at a time, as in the Metropolis kernels.
 // ---------------------------------------------------------------------------
-template <bool COUNT>
-__global__ void __launch_bounds__(kSweepThreads)
-    heat_kernel(const JobDev *__restrict__ jobs, const int *__restrict__ block_begin, int n_jobs,
-                int h, uint32_t sweep_offset, unsigned long long *counters)
-{
-    __shared__ uint4 s_tm[16][7];
-    __shared__ int s_job;
-    if (threadIdx.x == 0)
-        s_job = find_job(block_begin, n_jobs);
-    __syncthreads();
-    const JobDev &jb = jobs[s_job];
-    for (int i = threadIdx.x; i < 16 * 7; i += blockDim.x) {
-        const int call = i / 7, u = i % 7;
-        s_tm[call][u] = *reinterpret_cast<const uint4 *>(&jb.tm[call][u][0]);
-    }
-    __syncthreads();
-    const uint64_t t = jb.t + sweep_offset;
-    if (t >= jb.t_end)
-        return;
+struct HeatPending {
+    uint32_t w, sp, b0, b1, b2, c2;
+};
+constexpr int kHeatQueue = 64;  // entries per warp (at most 32 are added per step)
 
-    const int local = (int)blockIdx.x - block_begin[s_job];
-    const int bps = jb.blocks_per_sample;
-    const int s = local / bps;
-    const int cb = local - s * bps;
-    const int cols = jb.cols;
-    const int cpt = jb.cols_per_thread;
-    const int n0 = jb.geo.n[0], n1 = jb.geo.n[1], n2 = jb.geo.n[2];
-    const uint32_t valid = jb.geo.valid;
-    const uint32_t magic = jb.div_n0_magic;
-    const int dshift = jb.div_n0_shift;
-    const uint32_t zero_calls = jb.zero_calls;
-    const bool all_always = jb.all_always != 0;
-    const bool none_random = jb.none_random != 0;
-    const uint32_t always_u = jb.always_u;
+// Class masks u = 0..6 of a word from its bit-sliced count (u <= 6, so
+// b2 & b1 & b0 never occurs).
+struct HeatMasks {
+    uint32_t M[7];
+};
+
+__device__ __forceinline__ HeatMasks heat_masks(uint32_t b2, uint32_t b1, uint32_t b0,
+                                                uint32_t valid)
+{
+    const uint32_t lo = ~b2 & valid, hi = b2 & valid;
+    HeatMasks m;
+    m.M[0] = lo & ~(b1 | b0);
+    m.M[1] = lo & ~b1 & b0;
+    m.M[2] = lo & b1 & ~b0;
+    m.M[3] = lo & b1 & b0;
+    m.M[4] = hi & ~(b1 | b0);
+    m.M[5] = hi & b0;
+    m.M[6] = hi & b1;
+    return m;
+}
+
+// Might the gaps select a lane of some class?  hl[j][n] = C_j[n] >> 48, or -1
+// where no draw can select (n = 0, or class j without a table): a first draw
+// whose 16 leading bits exceed it is >= C_j[n].
+__device__ __forceinline__ bool heat_hit(const uint4 &R, const HeatMasks &m, const int (*hl)[33])
+{
+    bool h = (int)(R.y >> 16) <= hl[2][__popc(m.M[2])];
+    h |= (int)(R.y & 0xFFFFu) <= hl[2][__popc(m.M[4])];
+    h |= (int)(R.z >> 16) <= hl[1][__popc(m.M[1])];
+    h |= (int)(R.z & 0xFFFFu) <= hl[1][__popc(m.M[5])];
+    h |= (int)(R.w >> 16) <= hl[0][__popc(m.M[0])];
+    h |= (int)(R.w & 0xFFFFu) <= hl[0][__popc(m.M[6])];
+    return h;
+}
+
+__device__ __forceinline__ void heat_finish(const JobDev *__restrict__ jb, const HeatPending &e,
+                                            uint32_t *__restrict__ upd, uint32_t valid,
+                                            uint32_t c1, uint32_t c3, const uint32_t (&rk)[20],
+                                            const int (*hl)[33], unsigned int &calls)
+{
+    const uint4 R = dev::philox10_rk(make_uint4(e.w, c1, e.c2, c3), rk);
+    ++calls;
+    const HeatMasks m = heat_masks(e.b2, e.b1, e.b0, valid);
+    uint32_t A = m.M[3] & R.x;
+    const uint32_t lead[3] = {R.w, R.z, R.y};  // pair j = 0, 1, 2
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const uint32_t Ml = m.M[j], Mh = m.M[6 - j];
+        const bool hit_l = (int)(lead[j] >> 16) <= hl[j][__popc(Ml)];
+        const bool hit_h = (int)(lead[j] & 0xFFFFu) <= hl[j][__popc(Mh)];
+        uint32_t keep = 0u;
+        if (hit_l || hit_h) {
+            const uint4 X =
+                dev::philox10_rk(make_uint4(e.w, c1, e.c2 | (uint32_t)(128 + 2 - j), c3), rk);
+            ++calls;
+            if (hit_l)
+                A |= gap_class<7>(jb, j, j, Ml,
+                                  ((uint64_t)(lead[j] >> 16) << 48) |
+                                      ((((uint64_t)X.x << 32) | X.y) >> 16),
+                                  e.w, c1, e.c2, c3, rk, calls);
+            if (hit_h)
+                keep = gap_class<7>(jb, j, 6 - j, Mh,
+                                    ((uint64_t)(lead[j] & 0xFFFFu) << 48) |
+                                        ((((uint64_t)X.z << 32) | X.w) >> 16),
+                                    e.w, c1, e.c2, c3, rk, calls);
+        }
+        A |= Mh & ~keep;
+    }
+    upd[e.w] = e.sp ^ (A & valid);
+}
+
+template <bool COUNT, int MAXJ>
+__global__ void __launch_bounds__(kSweepThreads, 8)
+    heat_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
+{
+    int j = 0;
+    {
+        int lo = 0, hi = P.n_jobs - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.block_begin[mid] <= b)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    const MetroJob &J = P.job[j];
+    const MetroGeo &G = P.geo[(J.meta >> 8) & 0xFFu];
+    const JobDev *__restrict__ jb = P.jobs_dev + j;
     uint32_t rk[20];
 #pragma unroll
-    for (int i = 0; i < 20; ++i)
-        rk[i] = jb.rk[i];
-    const size_t W = (size_t)jb.geo.words;
-    uint32_t *__restrict__ upd = jb.spins + ((size_t)s * 2 + h) * W;
-    const uint32_t *__restrict__ nb = jb.spins + ((size_t)s * 2 + (h ^ 1)) * W;
-    const uint32_t *__restrict__ Jx = jb.J + (size_t)s * 3 * W;
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = J.key0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = J.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    __shared__ int s_hl[3][33];
+    __shared__ HeatPending s_q[kSweepThreads / 32][kHeatQueue];
+    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x) {
+        const int u = i / 33, g = i % 33;
+        const bool live = ((J.meta >> u) & 1u) != 0 && g > 0;
+        (&s_hl[0][0])[i] = live ? (int)((&jb->gC_hi[0][0])[i] >> 16) : -1;
+    }
+    __syncthreads();
+    const uint64_t t = jb->t + P.sweep_offset;
+    if (t >= jb->t_end)
+        return;  // this job has stopped (uniform over the block)
+
+    const int h = P.h;
+    const int lane = threadIdx.x & 31;
+    HeatPending *q = s_q[threadIdx.x >> 5];
+    int q_n = 0;  // warp-uniform queue length
+    const int local = (int)blockIdx.x - P.block_begin[j];
+    const int s = local / G.bps;
+    const int cb = local - s * G.bps;
+    const int n0 = G.n0, n1 = G.n1, n2 = G.n2;
+    const bool fix_x = (G.fix & 1u) != 0;
+    const bool fix_y = (G.fix & 2u) != 0;
+    const uint32_t valid = G.valid;
+    Axis az, ax, ay;
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+        az.sA[dir] = G.zsA[dir];
+        az.sB[dir] = G.zsB[dir];
+        az.mA[dir] = G.zmA[dir];
+        az.mB[dir] = G.zmB[dir];
+    }
+    if (fix_x)
+        load_axis(ax, jb->geo, 0);
+    if (fix_y)
+        load_axis(ay, jb->geo, 1);
+    const uint32_t W = G.words;
+    uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
+    const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
+    const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
     const uint32_t *__restrict__ Jy = Jx + W;
     const uint32_t *__restrict__ Jz = Jy + W;
-    const uint32_t c3 = (uint32_t)s / jb.rng_group;
+    const uint32_t c3 = (uint32_t)s / J.rng_group;
     const uint32_t c1 = (uint32_t)t;
-    const uint32_t c2t = dev::kStreamSweep | (((uint32_t)(t >> 32) & 0xFFFFu) << 8);
+    const uint32_t c2h = dev::kStreamHeat | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
     const int sz = n0 * n1;
-    Axis az;
-    load_axis(az, jb.geo, 2);
-    unsigned long long n_words = 0, n_calls = 0, n_general = 0;
+    unsigned int n_words = 0, n_extra = 0;
 
-    for (int k = 0; k < cpt; ++k) {
-        const int col = (cb * cpt + k) * kSweepThreads + (int)threadIdx.x;
-        if (col >= cols)
+    const int cols = G.cols;
+    for (int k = 0; k < G.cpt; ++k) {
+        const int col0 = (cb * G.cpt + k) * kSweepThreads + (int)threadIdx.x;
+        const bool act = col0 < cols;  // lanes past the last column idle in step
+        if (__all_sync(0xffffffffu, !act))
             break;
-        const int y = (int)((__umulhi((uint32_t)col, magic) + (uint32_t)col) >> dshift);
+        const int col = act ? col0 : 0;
+        const int y = (int)((__umulhi((uint32_t)col, G.magic) + (uint32_t)col) >> G.dshift);
         const int x = col - y * n0;
         int cxp = col + 1, cxm = col - 1, cyp = col + n0, cym = col - n0;
         const bool wxp = (x + 1 == n0), wxm = (x == 0), wyp = (y + 1 == n1), wym = (y == 0);
@@ -988,34 +1110,33 @@ __global__ void __launch_bounds__(kSweepThreads)
             cyp = col - (n1 - 1) * n0;
         if (wym)
             cym = col + (n1 - 1) * n0;
-        Axis ax, ay;
-        if (wxp || wxm)
-            load_axis(ax, jb.geo, 0);
-        if (wyp || wym)
-            load_axis(ay, jb.geo, 1);
-        uint32_t nz_prev = fixup(nb[col + (n2 - 1) * sz], az, 1);  // z' = -1
-        uint32_t nz_cur = nb[col];                                  // z' = 0
-        uint32_t jz_prev = fixup(Jz[col + (n2 - 1) * sz], az, 1);  // backward z bond at z' = 0
-        const int par0 = (x + y) & 1;
+        // replica updated at word-site (x, y, z) in half-step h: h ^ ((x + y + z) & 1)
+        const uint32_t c2e = c2h | ((uint32_t)(h ^ ((x + y) & 1)) << 11);  // even z
+        uint32_t nz_prev = fixup(nb[col + (n2 - 1) * sz], az, 1);          // z' = -1
+        uint32_t jz_prev = fixup(Jz[col + (n2 - 1) * sz], az, 1);          // bond below z' = 0
+        uint32_t nz_cur = nb[col];
         for (int z = 0; z < n2; ++z) {
             const int w = col + z * sz;
             const uint32_t nz_next = (z + 1 < n2) ? nb[w + sz] : fixup(nb[col], az, 0);
             const uint32_t sp = upd[w];
             uint32_t nxp = nb[cxp + z * sz], nxm = nb[cxm + z * sz];
-            uint32_t jxm = Jx[cxm + z * sz];
             uint32_t nyp = nb[cyp + z * sz], nym = nb[cym + z * sz];
-            uint32_t jym = Jy[cym + z * sz];
-            if (wxp)
-                nxp = fixup(nxp, ax, 0);
-            if (wxm) {
-                nxm = fixup(nxm, ax, 1);
-                jxm = fixup(jxm, ax, 1);
+            uint32_t jxm = Jx[cxm + z * sz], jym = Jy[cym + z * sz];
+            if (fix_x) {
+                if (wxp)
+                    nxp = fixup(nxp, ax, 0);
+                if (wxm) {
+                    nxm = fixup(nxm, ax, 1);
+                    jxm = fixup(jxm, ax, 1);
+                }
             }
-            if (wyp)
-                nyp = fixup(nyp, ay, 0);
-            if (wym) {
-                nym = fixup(nym, ay, 1);
-                jym = fixup(jym, ay, 1);
+            if (fix_y) {
+                if (wyp)
+                    nyp = fixup(nyp, ay, 0);
+                if (wym) {
+                    nym = fixup(nym, ay, 1);
+                    jym = fixup(jym, ay, 1);
+                }
             }
             const uint32_t jz = Jz[w];
             const Count c = count6(sp ^ nxp ^ Jx[w], sp ^ nxm ^ jxm, sp ^ nyp ^ Jy[w],
@@ -1024,63 +1145,49 @@ __global__ void __launch_bounds__(kSweepThreads)
             nz_cur = nz_next;
             jz_prev = jz;
 
-            uint32_t f[7];
-#pragma unroll
-            for (int u = 0; u < 7; ++u)
-                f[u] = 0u - ((always_u >> u) & 1u);
-            const uint32_t alw = mux7(c.b2, c.b1, c.b0, f);
-            uint32_t flip;
-            if (all_always) {
-                flip = 0xffffffffu;
-            } else if (none_random) {
-                flip = alw;
-            } else {
-                const int a = h ^ par0 ^ (z & 1);  // replica at this word-site
-                const uint32_t c2 = c2t | ((uint32_t)a << 4);
-                uint32_t U = ~alw & valid;  // lanes still comparing
-                uint32_t A = 0u;            // lanes accepted by the comparison
-#pragma unroll 1
-                for (int call = 0; call < 16; ++call) {
-                    if (U == 0u)
-                        break;
-                    const uint4 R = dev::philox10_rk(
-                        make_uint4((uint32_t)w, c1, c2 | (uint32_t)call, c3), rk);
-                    if (COUNT)
-                        ++n_calls;
-                    if ((zero_calls >> call) & 1u) {
-                        U &= ~(R.x | R.y | R.z | R.w);
-                        continue;
-                    }
-                    if (COUNT)
-                        ++n_general;
-                    uint4 T[7];
-#pragma unroll
-                    for (int u = 0; u < 7; ++u)
-                        T[u] = s_tm[call][u];
-                    const uint32_t fx[7] = {T[0].x, T[1].x, T[2].x, T[3].x, T[4].x, T[5].x, T[6].x};
-                    const uint32_t fy[7] = {T[0].y, T[1].y, T[2].y, T[3].y, T[4].y, T[5].y, T[6].y};
-                    const uint32_t fz[7] = {T[0].z, T[1].z, T[2].z, T[3].z, T[4].z, T[5].z, T[6].z};
-                    const uint32_t fw[7] = {T[0].w, T[1].w, T[2].w, T[3].w, T[4].w, T[5].w, T[6].w};
-                    const uint32_t tk[4] = {mux7(c.b2, c.b1, c.b0, fx), mux7(c.b2, c.b1, c.b0, fy),
-                                            mux7(c.b2, c.b1, c.b0, fz), mux7(c.b2, c.b1, c.b0, fw)};
-                    const uint32_t r[4] = {R.x, R.y, R.z, R.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        A |= U & ~r[j] & tk[j];  // r bit 0 below threshold bit 1: accept
-                        U &= ~(r[j] ^ tk[j]);    // bits differ: decided
-                    }
-                }
-                flip = alw | A;
-            }
-            upd[w] = sp ^ (flip & valid);
-            if (COUNT)
+            const uint32_t c2 = c2e ^ ((uint32_t)(z & 1) << 11);
+            const uint4 R = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2, c3), rk);
+            const HeatMasks m = heat_masks(c.b2, c.b1, c.b0, valid);
+            const bool hit = act && heat_hit(R, m, s_hl);
+            // no selection: class 3 by its coin, classes 4-6 flip whole
+            if (act && !hit)
+                upd[w] = sp ^ ((m.M[3] & R.x) | (c.b2 & valid));
+            if (COUNT && act)
                 ++n_words;
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                HeatPending &e = q[q_n + __popc(bal & ((1u << lane) - 1u))];
+                e.w = (uint32_t)w;
+                e.sp = sp;
+                e.b0 = c.b0;
+                e.b1 = c.b1;
+                e.b2 = c.b2;
+                e.c2 = c2;
+            }
+            q_n += __popc(bal);
+            __syncwarp();
+            if (q_n >= 32) {  // a full round: one queued word per lane
+                q_n -= 32;
+                const HeatPending e = q[q_n + lane];
+                unsigned int extra = 0;
+                heat_finish(jb, e, upd, valid, c1, c3, rk, s_hl, extra);
+                if (COUNT)
+                    n_extra += extra;
+                __syncwarp();
+            }
         }
     }
+    if (lane < q_n) {  // the last, partial round
+        const HeatPending e = q[lane];
+        unsigned int extra = 0;
+        heat_finish(jb, e, upd, valid, c1, c3, rk, s_hl, extra);
+        if (COUNT)
+            n_extra += extra;
+    }
     if (COUNT) {
-        atomicAdd(&counters[0], n_words);
-        atomicAdd(&counters[1], n_calls);
-        atomicAdd(&counters[2], n_general);
+        atomicAdd(&counters[0], (unsigned long long)n_words);
+        atomicAdd(&counters[1], (unsigned long long)(n_words + n_extra));
+        atomicAdd(&counters[2], (unsigned long long)n_extra);
     }
 }
 
@@ -1111,21 +1218,12 @@ void fill_job_keys(JobDev *jd, uint64_t seed)
 
 void fill_job_thresholds(JobDev *jd, const Thr &thr)
 {
-    std::memset(jd->tm, 0, sizeof(jd->tm));
-    for (int call = 0; call < 16; ++call)
-        for (int u = 0; u < 7; ++u)
-            for (int j = 0; j < 4; ++j) {
-                const int k = 4 * call + j;  // plane k = bit 63 - k of the threshold
-                const uint32_t bit = (uint32_t)(thr.thr_u[u] >> (63 - k)) & 1u;
-                jd->tm[call][u][j] = 0u - bit;
-            }
     for (int u = 0; u < 3; ++u)
         for (int g = 0; g < 33; ++g) {
             jd->gC_hi[u][g] = (uint32_t)(thr.geoC[u][g] >> 32);
             jd->gC_lo[u][g] = (uint32_t)thr.geoC[u][g];
         }
     jd->geo_live = thr.geo_live;
-    jd->zero_calls = thr.zero_calls;
     jd->always_u = thr.always_u;
     jd->rule = thr.rule;
     jd->all_always = thr.all_always;
@@ -1185,7 +1283,7 @@ static void metro_job(MetroJob &m, const JobDev &jd, int geo_index)
 
 // Jobs host[0..cnt) in one launch sequence; all of them share at most
 // kMetroMaxGeo (side, layout) geometries.
-template <int MAXJ, int GL>
+template <int MAXJ, int GL, bool HEAT = false>
 static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, uint64_t n,
                                cudaStream_t stream, unsigned long long *counters)
 {
@@ -1241,7 +1339,12 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
         for (int h = 0; h < 2; ++h) {
             p.h = h;
             p.sweep_offset = (uint32_t)k;
-            if constexpr (GL != 0) {
+            if constexpr (HEAT) {
+                if (counters)
+                    heat_kernel<true, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                else
+                    heat_kernel<false, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+            } else if constexpr (GL != 0) {
                 if (counters) {
                     if (lowt)
                         metro_tile_kernel<true, MAXJ, GL, true>
@@ -1269,6 +1372,7 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
 // Jobs host[0..cnt) of one run of the Metropolis table: side GLR (64 or 128,
 // the tile kernel) or any sides (GLR = 0, the column kernel), in chunks of at
 // most kMetroMaxJobs jobs and kMetroMaxGeo geometries per launch.
+template <bool HEAT = false>
 static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int GLR, uint64_t n,
                              cudaStream_t stream, unsigned long long *counters)
 {
@@ -1289,7 +1393,16 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
         }
         const JobDev *h = host + first;
         const JobDev *d = dev + first;
-        if (GLR == 128) {
+        if (HEAT) {
+            if (c <= 1)
+                launch_metro_chunk<1, 0, true>(h, d, c, n, stream, counters);
+            else if (c <= 8)
+                launch_metro_chunk<8, 0, true>(h, d, c, n, stream, counters);
+            else if (c <= 128)
+                launch_metro_chunk<128, 0, true>(h, d, c, n, stream, counters);
+            else
+                launch_metro_chunk<kMetroMaxJobs, 0, true>(h, d, c, n, stream, counters);
+        } else if (GLR == 128) {
             if (c <= 8)
                 launch_metro_chunk<8, 128>(h, d, c, n, stream, counters);
             else
@@ -1314,7 +1427,7 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
 }
 
 cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
-                               const JobDev *dev1, const int *bb1, int n_jobs1, int blocks1,
+                               const JobDev *host1, const JobDev *dev1, int n_jobs1,
                                uint64_t n, cudaStream_t stream, unsigned long long *counters,
                                const SideStreams *side)
 {
@@ -1369,18 +1482,8 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
         if (err != cudaSuccess)
             return err;
     }
-    if (blocks1 > 0) {
-        for (uint64_t k = 0; k < n; ++k)
-            for (int h = 0; h < 2; ++h) {
-                if (counters)
-                    heat_kernel<true><<<blocks1, kSweepThreads, 0, stream>>>(
-                        dev1, bb1, n_jobs1, h, (uint32_t)k, counters);
-                else
-                    heat_kernel<false><<<blocks1, kSweepThreads, 0, stream>>>(
-                        dev1, bb1, n_jobs1, h, (uint32_t)k, nullptr);
-                count_launches(1);
-            }
-    }
+    if (n_jobs1 > 0)
+        launch_metro_run<true>(host1, dev1, n_jobs1, 0, n, stream, counters);
     return cudaGetLastError();
 }
 

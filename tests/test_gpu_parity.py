@@ -90,6 +90,14 @@ SWEEP_CASES = [
     (12, 0.5, 0.7, 0, 1, 2, 20),
     (16, 0.5, 0.7, 0, 1, 3, 30),
     (16, 0.5, 1.3, 1, 1, 2, 20),  # heat bath
+    (4, 0.5, 0.8, 1, 1, 2, 30),   # heat bath, 8 lanes per word
+    (6, 0.5, 1.0, 1, 1, 3, 25),   # heat bath, one site per word
+    (8, 0.3, 0.7, 1, 1, 2, 25),
+    (16, 0.5, float("inf"), 1, 1, 2, 4),  # heat bath at T = inf: every class by p = 1/2
+    (16, 0.5, 0.7, 1, 2, 4, 20),  # heat bath, pairs of samples share random numbers
+    (32, 0.5, 0.7, 1, 1, 2, 10),
+    (32, 0.5, 3.0, 1, 1, 2, 6),   # many words take the rare path, and later draws
+    (64, 0.5, 0.7, 1, 1, 1, 3),
     (16, 0.5, 0.7, 0, 2, 4, 20),  # pairs of samples share random numbers
     (16, 0.0, 0.0, 0, 1, 2, 10),  # T = 0 ferromagnet
     (16, 0.5, float("inf"), 0, 1, 2, 3),
@@ -159,6 +167,53 @@ def test_tile_kernel_late_time(J, t0):
     ora.sweeps(L, seed, 0, ref, Jc, T, 0, t0, 3)
     j = J.EAJob(L, p_neg, seed, 1)
     j.quench(T)
+    j.set_time(t0)
+    j.sweep(3)
+    assert np.array_equal(j.all_spins(0), ref)
+    j.close()
+
+
+HEAT_CASES = [
+    # L, p_neg, T, cols_per_thread, S, sweeps: the heat bath through a batch
+    (128, 0.5, 0.7, 1, 3, 2),
+    (128, 0.1, 0.7, 4, 2, 2),
+    (64, 0.3, 1.0, 2, 5, 3),
+    (64, 0.5, 6.0, 1, 2, 2),
+    (48, 0.5, 0.7, 2, 2, 3),
+]
+
+
+@pytest.mark.parametrize("L,p_neg,T,cpt,S,n", HEAT_CASES)
+def test_heat_bath_batch_bit_exact(J, L, p_neg, T, cpt, S, n):
+    seed = 700 + L + cpt
+    j = J.EAJob(L, p_neg, seed, S)
+    j.quench(T, 1)
+    b = J.EABatch()
+    b.configure(cpt, 0)
+    b.add(j)
+    b.sweep(n)
+    pick = [0, S - 1] if S > 1 else [0]
+    ref = ora.run_job(L, p_neg, seed, S, T, 1, [], [], n, samples=pick, keep_spins=True)
+    for i, s in enumerate(pick):
+        assert np.array_equal(j.all_spins(s), ref["spins"][i]), s
+    b.close()
+    j.close()
+
+
+@pytest.mark.parametrize("L,t0", [(16, (1 << 32) - 1), (64, (1 << 44) + 77)])
+def test_heat_bath_late_time(J, L, t0):
+    """The high bits of the sweep counter in the heat-bath draws, from an oracle-made state."""
+    seed, p_neg, T = 43, 0.5, 0.8
+    Jc = ora.init_couplings(L, p_neg, seed, 0)
+    S0 = ora.init_spins(L, seed, 0)
+    ora.sweeps(L, seed, 0, S0, Jc, T, 1, 0, 3)
+    ref = S0.copy()
+    ora.sweeps(L, seed, 0, ref, Jc, T, 1, t0, 3)
+    j = J.EAJob(L, p_neg, seed, 1)
+    j.quench(T, 1)
+    j.set_couplings(0, Jc)
+    j.set_spins(0, 0, S0[0])
+    j.set_spins(0, 1, S0[1])
     j.set_time(t0)
     j.sweep(3)
     assert np.array_equal(j.all_spins(0), ref)
