@@ -434,6 +434,7 @@ def run_heat(args, job, workloads, stream, flush):
     for j in jobs:
         b.add(j)
     cfg = b.autotune(trial_sweeps=8)
+    prof = b.profile(sweeps=4)
     n = args.sweeps_per_step
     b.sweep(n)
     ms = timed_steps(stream, 3, lambda: b.sweep(n), flush)
@@ -443,7 +444,8 @@ def run_heat(args, job, workloads, stream, flush):
     flips = n * sum(2 * w["n_samples"] * w["L"] ** 3 for w in specs)
     m = statistics.median(ms)
     return {"workload": "L128_p0.5-0.1_S16x5_T0.7 heat bath", "value": flips / (m * 1e6),
-            "unit": UNIT, "ms_per_step": m, "cols_per_thread": cfg[0], "graph_sweeps": cfg[1]}
+            "unit": UNIT, "ms_per_step": m, "cols_per_thread": cfg[0], "graph_sweeps": cfg[1],
+            "philox_calls_per_word": prof["philox_calls"] / max(prof["words"], 1)}
 
 
 def run_serving(args, job, workloads, stream):

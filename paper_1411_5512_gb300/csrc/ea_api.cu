@@ -1153,10 +1153,11 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
     // equal sides next to each other, sides 64 and 128 last: they form the
     // runs that the tile kernel takes (the order of rows changes no result)
     auto run_key = [](int L) { return (L == 64 || L == 128) ? (1 << 20) + L : L; };
-    std::stable_sort(b->tab_host[0].begin(), b->tab_host[0].end(),
-                     [&](const ea::JobDev &a, const ea::JobDev &c) {
-                         return run_key(a.geo.L) < run_key(c.geo.L);
-                     });
+    for (int r = 0; r < 2; ++r)
+        std::stable_sort(b->tab_host[r].begin(), b->tab_host[r].end(),
+                         [&](const ea::JobDev &a, const ea::JobDev &c) {
+                             return run_key(a.geo.L) < run_key(c.geo.L);
+                         });
     for (int r = 0; r < 2; ++r) {
         const size_t n = b->tab_host[r].size();
         b->n_jobs[r] = (int)n;

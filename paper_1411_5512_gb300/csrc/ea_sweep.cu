@@ -982,14 +982,17 @@ __device__ __forceinline__ bool heat_hit(const uint4 &R, const HeatMasks &m, con
     return h;
 }
 
-__device__ __forceinline__ void heat_finish(const JobDev *__restrict__ jb, const HeatPending &e,
-                                            uint32_t *__restrict__ upd, uint32_t valid,
-                                            uint32_t c1, uint32_t c3, const uint32_t (&rk)[20],
-                                            const int (*hl)[33], unsigned int &calls)
+// The flips of one word whose leading bits might select a lane: w its
+// word-site, sp its spins, (b2 b1 b0) its class count, c2 its counter word.
+__device__ __forceinline__ uint32_t heat_word_flips(const JobDev *__restrict__ jb, uint32_t w,
+                                                    uint32_t b2, uint32_t b1, uint32_t b0,
+                                                    uint32_t c2, uint32_t valid, uint32_t c1,
+                                                    uint32_t c3, const uint32_t (&rk)[20],
+                                                    const int (*hl)[33], unsigned int &calls)
 {
-    const uint4 R = dev::philox10_rk(make_uint4(e.w, c1, e.c2, c3), rk);
+    const uint4 R = dev::philox10_rk(make_uint4(w, c1, c2, c3), rk);
     ++calls;
-    const HeatMasks m = heat_masks(e.b2, e.b1, e.b0, valid);
+    const HeatMasks m = heat_masks(b2, b1, b0, valid);
     uint32_t A = m.M[3] & R.x;
     const uint32_t lead[3] = {R.w, R.z, R.y};  // pair j = 0, 1, 2
 #pragma unroll
@@ -1000,22 +1003,31 @@ __device__ __forceinline__ void heat_finish(const JobDev *__restrict__ jb, const
         uint32_t keep = 0u;
         if (hit_l || hit_h) {
             const uint4 X =
-                dev::philox10_rk(make_uint4(e.w, c1, e.c2 | (uint32_t)(128 + 2 - j), c3), rk);
+                dev::philox10_rk(make_uint4(w, c1, c2 | (uint32_t)(128 + 2 - j), c3), rk);
             ++calls;
             if (hit_l)
                 A |= gap_class<7>(jb, j, j, Ml,
                                   ((uint64_t)(lead[j] >> 16) << 48) |
                                       ((((uint64_t)X.x << 32) | X.y) >> 16),
-                                  e.w, c1, e.c2, c3, rk, calls);
+                                  w, c1, c2, c3, rk, calls);
             if (hit_h)
                 keep = gap_class<7>(jb, j, 6 - j, Mh,
                                     ((uint64_t)(lead[j] & 0xFFFFu) << 48) |
                                         ((((uint64_t)X.z << 32) | X.w) >> 16),
-                                    e.w, c1, e.c2, c3, rk, calls);
+                                    w, c1, c2, c3, rk, calls);
         }
         A |= Mh & ~keep;
     }
-    upd[e.w] = e.sp ^ (A & valid);
+    return A & valid;
+}
+
+__device__ __forceinline__ void heat_finish(const JobDev *__restrict__ jb, const HeatPending &e,
+                                            uint32_t *__restrict__ upd, uint32_t valid,
+                                            uint32_t c1, uint32_t c3, const uint32_t (&rk)[20],
+                                            const int (*hl)[33], unsigned int &calls)
+{
+    upd[e.w] = e.sp ^ heat_word_flips(jb, e.w, e.b2, e.b1, e.b0, e.c2, valid, c1, c3, rk, hl,
+                                      calls);
 }
 
 template <bool COUNT, int MAXJ>
@@ -1191,6 +1203,224 @@ __global__ void __launch_bounds__(kSweepThreads, 8)
     }
 }
 
+// Heat bath for a table whose jobs all have side GL = 64 or 128: the tiles
+// of the Metropolis tile kernel (2 x 2 word-sites times a segment of rows),
+// one main call per word.  A queued word holds (word-site, spins before the
+// update); its rare path counts its classes again from the neighbour area,
+// which this half-step does not write, and draws its main call again.
+template <int GL>
+__device__ __forceinline__ void heat_tile_finish(const JobDev *__restrict__ jb, const uint4 &e,
+                                                 uint32_t *__restrict__ upd,
+                                                 const uint32_t *__restrict__ nb,
+                                                 const uint32_t *__restrict__ Jx,
+                                                 const uint32_t *__restrict__ Jy,
+                                                 const uint32_t *__restrict__ Jz, int h,
+                                                 uint32_t c1, uint32_t c2h, uint32_t c3,
+                                                 const uint32_t (&rk)[20], const int (*hl)[33],
+                                                 unsigned int &calls)
+{
+    constexpr int SLOG = GL == 128 ? 7 : 6;
+    constexpr int N2 = GL / 32, SZ = GL * GL;
+    const int w = (int)e.x;
+    const uint32_t s = e.y;
+    const int x = w & (GL - 1), y = (w >> SLOG) & (GL - 1), z = w >> (2 * SLOG);
+    const uint32_t c2 = c2h | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
+    const int wxp = x == GL - 1 ? w - (GL - 1) : w + 1;
+    const int wxm = x == 0 ? w + (GL - 1) : w - 1;
+    const int wyp = y == GL - 1 ? w - (GL - 1) * GL : w + GL;
+    const int wym = y == 0 ? w + (GL - 1) * GL : w - GL;
+    const int wzp = z == N2 - 1 ? w - (N2 - 1) * SZ : w + SZ;
+    const int wzm = z == 0 ? w + (N2 - 1) * SZ : w - SZ;
+    uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
+    if (z == N2 - 1)
+        nzp = rot_zp(nzp);
+    if (z == 0) {
+        nzm = rot_zm(nzm);
+        jzm = rot_zm(jzm);
+    }
+    const Count c = count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nb[wyp] ^ Jy[w],
+                           s ^ nb[wym] ^ Jy[wym], s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
+    upd[w] = s ^ heat_word_flips(jb, (uint32_t)w, c.b2, c.b1, c.b0, c2, 0xffffffffu, c1, c3, rk,
+                                 hl, calls);
+}
+
+template <bool COUNT, int MAXJ, int GL>
+__global__ void __launch_bounds__(kSweepThreads, 7)
+    heat_tile_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
+{
+    constexpr int N2 = GL / 32, SZ = GL * GL;
+    constexpr int XP = GL / 2, ZP = N2 / 2;
+    constexpr int XPLOG = GL == 128 ? 6 : 5;
+    constexpr uint32_t W = (uint32_t)SZ * N2;
+    int j = 0;
+    {
+        int lo = 0, hi = P.n_jobs - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.block_begin[mid] <= b)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    const MetroJob &J = P.job[j];
+    const MetroGeo &G = P.geo[(J.meta >> 8) & 0xFFu];
+    const JobDev *__restrict__ jb = P.jobs_dev + j;
+    uint32_t rk[20];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = J.key0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = J.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    __shared__ int s_hl[3][33];
+    __shared__ uint4 s_q[kSweepThreads / 32][kTileQueue];
+    __shared__ int s_qn[kSweepThreads / 32];
+    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x) {
+        const int u = i / 33, g = i % 33;
+        const bool live = ((J.meta >> u) & 1u) != 0 && g > 0;
+        (&s_hl[0][0])[i] = live ? (int)((&jb->gC_hi[0][0])[i] >> 16) : -1;
+    }
+    if (threadIdx.x < kSweepThreads / 32)
+        s_qn[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t t = jb->t + P.sweep_offset;
+    if (t >= jb->t_end)
+        return;
+
+    const int h = P.h;
+    const int lane = threadIdx.x & 31;
+    uint4 *q = s_q[threadIdx.x >> 5];
+    int *qn = &s_qn[threadIdx.x >> 5];
+    const int Y = G.seg;
+    const int local = (int)blockIdx.x - P.block_begin[j];
+    const int s = local / G.bps;
+    const int tl = (local - s * G.bps) * kSweepThreads + (int)threadIdx.x;
+    const int x0 = 2 * (tl & (XP - 1));
+    const int z0 = 2 * ((tl >> XPLOG) & (ZP - 1));  // uniform over a warp (XP >= 32)
+    const int y0 = (tl >> XPLOG) / ZP * Y;
+    uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
+    const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
+    const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
+    const uint32_t *__restrict__ Jy = Jx + W;
+    const uint32_t *__restrict__ Jz = Jy + W;
+    const uint32_t c3 = (uint32_t)s / J.rng_group;
+    const uint32_t c1 = (uint32_t)t;
+    const uint32_t c2h = dev::kStreamHeat | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
+    const int oz0 = z0 * SZ, oz1 = oz0 + SZ;
+    const int ozm = (z0 == 0 ? N2 - 1 : z0 - 1) * SZ;
+    const int ozp = (z0 + 2 == N2 ? 0 : z0 + 2) * SZ;
+    const bool wrap_m = z0 == 0, wrap_p = z0 + 2 == N2;
+    const int xm = (x0 - 1) & (GL - 1), xq = (x0 + 2) & (GL - 1);
+    unsigned int n_words = 0, n_extra = 0;
+
+    const int rym = ((y0 - 1) & (GL - 1)) * GL;
+    uint2 Nm0 = ld2(nb, x0 + rym + oz0), Nm1 = ld2(nb, x0 + rym + oz1);
+    uint2 Jym0 = ld2(Jy, x0 + rym + oz0), Jym1 = ld2(Jy, x0 + rym + oz1);
+    uint2 Nc0 = ld2(nb, x0 + y0 * GL + oz0), Nc1 = ld2(nb, x0 + y0 * GL + oz1);
+    for (int i = 0; i < Y; ++i) {
+        const int y = y0 + i;
+        const int ry = y * GL, ryp = ((y + 1) & (GL - 1)) * GL;
+        const int w0 = x0 + ry + oz0, w1 = x0 + ry + oz1;  // the even-x words at z0, z0 + 1
+        const uint2 S0 = ld2(upd, w0), S1 = ld2(upd, w1);
+        const uint2 Nn0 = ld2(nb, x0 + ryp + oz0), Nn1 = ld2(nb, x0 + ryp + oz1);
+        uint2 Nzm = ld2(nb, x0 + ry + ozm), Nzp = ld2(nb, x0 + ry + ozp);
+        uint2 Jzm = ld2(Jz, x0 + ry + ozm);
+        const uint32_t Xm0 = nb[xm + ry + oz0], Xm1 = nb[xm + ry + oz1];
+        const uint32_t Xp0 = nb[xq + ry + oz0], Xp1 = nb[xq + ry + oz1];
+        const uint32_t Jxm0 = Jx[xm + ry + oz0], Jxm1 = Jx[xm + ry + oz1];
+        const uint2 Jx0 = ld2(Jx, w0), Jx1 = ld2(Jx, w1);
+        const uint2 Jy0 = ld2(Jy, w0), Jy1 = ld2(Jy, w1);
+        const uint2 Jz0 = ld2(Jz, w0), Jz1 = ld2(Jz, w1);
+        if (wrap_m) {
+            Nzm = make_uint2(rot_zm(Nzm.x), rot_zm(Nzm.y));
+            Jzm = make_uint2(rot_zm(Jzm.x), rot_zm(Jzm.y));
+        }
+        if (wrap_p)
+            Nzp = make_uint2(rot_zp(Nzp.x), rot_zp(Nzp.y));
+        // replica of word (x0, y, z0); the other three alternate with x and z
+        const uint32_t c2a = c2h | ((uint32_t)(h ^ (y & 1)) << 11);
+        const uint32_t c2b = c2a ^ (1u << 11);
+        // words a0 = (x0, z0), a1 = (x0 + 1, z0), b0 = (x0, z0 + 1), b1 = (x0 + 1, z0 + 1)
+        const uint32_t wd[4] = {(uint32_t)w0, (uint32_t)w0 + 1u, (uint32_t)w1, (uint32_t)w1 + 1u};
+        const uint32_t sp[4] = {S0.x, S0.y, S1.x, S1.y};
+        const uint32_t c2w[4] = {c2a, c2b, c2b, c2a};
+        // the six bond inputs of each word (x neighbours inside the pair come
+        // from the other word of the pair, z neighbours from the other z row)
+        const uint32_t in[4][6] = {
+            {Nc0.y ^ Jx0.x, Xm0 ^ Jxm0, Nn0.x ^ Jy0.x, Nm0.x ^ Jym0.x, Nc1.x ^ Jz0.x,
+             Nzm.x ^ Jzm.x},
+            {Xp0 ^ Jx0.y, Nc0.x ^ Jx0.x, Nn0.y ^ Jy0.y, Nm0.y ^ Jym0.y, Nc1.y ^ Jz0.y,
+             Nzm.y ^ Jzm.y},
+            {Nc1.y ^ Jx1.x, Xm1 ^ Jxm1, Nn1.x ^ Jy1.x, Nm1.x ^ Jym1.x, Nzp.x ^ Jz1.x,
+             Nc0.x ^ Jz0.x},
+            {Xp1 ^ Jx1.y, Nc1.x ^ Jx1.x, Nn1.y ^ Jy1.y, Nm1.y ^ Jym1.y, Nzp.y ^ Jz1.y,
+             Nc0.y ^ Jz0.y}};
+        Nm0 = Nc0;
+        Nm1 = Nc1;
+        Nc0 = Nn0;
+        Nc1 = Nn1;
+        Jym0 = Jy0;
+        Jym1 = Jy1;
+        uint32_t out[4];
+        bool hit[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t v = sp[k];
+            const Count c = count6(v ^ in[k][0], v ^ in[k][1], v ^ in[k][2], v ^ in[k][3],
+                                   v ^ in[k][4], v ^ in[k][5]);
+            const uint4 R = dev::philox10_rk(make_uint4(wd[k], c1, c2w[k], c3), rk);
+            const HeatMasks m = heat_masks(c.b2, c.b1, c.b0, 0xffffffffu);
+            hit[k] = heat_hit(R, m, s_hl);
+            // without a selection: class 3 by its coin, classes 4-6 flip whole
+            out[k] = v ^ ((m.M[3] & R.x) | c.b2);
+        }
+        // every word is written; a queued word is written again by the rare path
+        *reinterpret_cast<uint2 *>(upd + w0) = make_uint2(out[0], out[1]);
+        *reinterpret_cast<uint2 *>(upd + w1) = make_uint2(out[2], out[3]);
+        if (COUNT)
+            n_words += 4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (hit[k])
+                q[atomicAdd(qn, 1)] = make_uint4(wd[k], sp[k], 0u, 0u);
+        __syncwarp();
+        int q_n = *qn;
+        if (q_n >= 96) {  // full rounds, one queued word per lane, while 32 are queued
+            do {
+                q_n -= 32;
+                const uint4 e = q[q_n + lane];
+                unsigned int extra = 0;
+                heat_tile_finish<GL>(jb, e, upd, nb, Jx, Jy, Jz, h, c1, c2h, c3, rk, s_hl, extra);
+                if (COUNT)
+                    n_extra += extra;
+                __syncwarp();
+            } while (q_n >= 32);
+            if (lane == 0)
+                *qn = q_n;
+            __syncwarp();
+        }
+    }
+    // the words still queued in the block's four warps, pooled
+    __syncthreads();
+    const int n0q = s_qn[0], n1q = n0q + s_qn[1], n2q = n1q + s_qn[2], n3q = n2q + s_qn[3];
+    for (int g = (int)threadIdx.x; g < n3q; g += kSweepThreads) {
+        const int wq = g < n0q ? 0 : g < n1q ? 1 : g < n2q ? 2 : 3;
+        const int off = g - (wq == 0 ? 0 : wq == 1 ? n0q : wq == 2 ? n1q : n2q);
+        unsigned int extra = 0;
+        heat_tile_finish<GL>(jb, s_q[wq][off], upd, nb, Jx, Jy, Jz, h, c1, c2h, c3, rk, s_hl,
+                             extra);
+        if (COUNT)
+            n_extra += extra;
+    }
+    if (COUNT) {
+        atomicAdd(&counters[0], (unsigned long long)n_words);
+        atomicAdd(&counters[1], (unsigned long long)(n_words + n_extra));
+        atomicAdd(&counters[2], (unsigned long long)n_extra);
+    }
+}
+
 __global__ void advance_time_kernel(JobDev *jobs, int n_jobs, uint64_t n)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1339,7 +1569,14 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
         for (int h = 0; h < 2; ++h) {
             p.h = h;
             p.sweep_offset = (uint32_t)k;
-            if constexpr (HEAT) {
+            if constexpr (HEAT && GL != 0) {
+                if (counters)
+                    heat_tile_kernel<true, MAXJ, GL>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                else
+                    heat_tile_kernel<false, MAXJ, GL>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+            } else if constexpr (HEAT) {
                 if (counters)
                     heat_kernel<true, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, counters);
                 else
@@ -1393,7 +1630,17 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
         }
         const JobDev *h = host + first;
         const JobDev *d = dev + first;
-        if (HEAT) {
+        if (HEAT && GLR == 128) {
+            if (c <= 8)
+                launch_metro_chunk<8, 128, true>(h, d, c, n, stream, counters);
+            else
+                launch_metro_chunk<kMetroMaxJobs, 128, true>(h, d, c, n, stream, counters);
+        } else if (HEAT && GLR == 64) {
+            if (c <= 8)
+                launch_metro_chunk<8, 64, true>(h, d, c, n, stream, counters);
+            else
+                launch_metro_chunk<kMetroMaxJobs, 64, true>(h, d, c, n, stream, counters);
+        } else if (HEAT) {
             if (c <= 1)
                 launch_metro_chunk<1, 0, true>(h, d, c, n, stream, counters);
             else if (c <= 8)
@@ -1426,33 +1673,28 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
     }
 }
 
-cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
-                               const JobDev *host1, const JobDev *dev1, int n_jobs1,
-                               uint64_t n, cudaStream_t stream, unsigned long long *counters,
-                               const SideStreams *side)
+// A table read as up to three runs: jobs of sides other than 64 and 128 (the
+// column kernels), then side 64, then side 128 (the tile kernels).  A table
+// in any other order is one run for the column kernel.
+struct Run {
+    int first, cnt, GLR;
+};
+
+static int split_runs(const JobDev *host, int n_jobs, Run runs[3])
 {
-    // The Metropolis table is read as up to three runs: jobs of sides other
-    // than 64 and 128 (the column kernel), then side 64, then side 128 (the
-    // tile kernel).  A table in any other order runs whole on the column
-    // kernel.  Runs hold different jobs, so they need no order between them:
-    // given side streams, the second and third run are forked from `stream`
-    // and joined back after their n sweeps, so the runs share the GPU.
     int a = 0;
-    while (a < n_jobs0 && host0[a].geo.L != 64 && host0[a].geo.L != 128)
+    while (a < n_jobs && host[a].geo.L != 64 && host[a].geo.L != 128)
         ++a;
     int b = a;
-    while (b < n_jobs0 && host0[b].geo.L == 64)
+    while (b < n_jobs && host[b].geo.L == 64)
         ++b;
     int e = b;
-    while (e < n_jobs0 && host0[e].geo.L == 128)
+    while (e < n_jobs && host[e].geo.L == 128)
         ++e;
-    struct Run {
-        int first, cnt, GLR;
-    } runs[3];
     int n_runs = 0;
-    if (e != n_jobs0) {  // not in run order
-        if (n_jobs0 > 0)
-            runs[n_runs++] = {0, n_jobs0, 0};
+    if (e != n_jobs) {  // not in run order
+        if (n_jobs > 0)
+            runs[n_runs++] = {0, n_jobs, 0};
     } else {
         if (a > 0)
             runs[n_runs++] = {0, a, 0};
@@ -1461,6 +1703,20 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
         if (e > b)
             runs[n_runs++] = {b, e - b, 128};
     }
+    return n_runs;
+}
+
+cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
+                               const JobDev *host1, const JobDev *dev1, int n_jobs1,
+                               uint64_t n, cudaStream_t stream, unsigned long long *counters,
+                               const SideStreams *side)
+{
+    // Runs of the Metropolis table hold different jobs, so they need no order
+    // between them: given side streams, the second and third run are forked
+    // from `stream` and joined back after their n sweeps, so the runs share
+    // the GPU.  The heat-bath runs follow on `stream`.
+    Run runs[3];
+    const int n_runs = split_runs(host0, n_jobs0, runs);
     const bool fork = side != nullptr && n_runs > 1;
     if (fork) {
         cudaError_t err = cudaEventRecord(side->fork, stream);
@@ -1482,8 +1738,11 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
         if (err != cudaSuccess)
             return err;
     }
-    if (n_jobs1 > 0)
-        launch_metro_run<true>(host1, dev1, n_jobs1, 0, n, stream, counters);
+    Run hruns[3];
+    const int n_hruns = split_runs(host1, n_jobs1, hruns);
+    for (int r = 0; r < n_hruns; ++r)
+        launch_metro_run<true>(host1 + hruns[r].first, dev1 + hruns[r].first, hruns[r].cnt,
+                               hruns[r].GLR, n, stream, counters);
     return cudaGetLastError();
 }
 
