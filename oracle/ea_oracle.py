@@ -10,6 +10,8 @@ with ctypes and computes the observables from int8 spin arrays with numpy:
 
 * overlap            q = (1/N) sum_i S^a_i S^b_i                  (Sec. II, Eq. 2)
 * four-point         C4(r, t_w) = (1/N) sum_i q_i q_{i+r}         (Sec. II, Eq. 3)
+                     along the axes, and over every displacement vector binned by
+                     r^2 (the larger point set of the Sec. IV error bars)
 * integral estimator I_k = int_0^{L/2} r^k C4 dr, xi_k = I_{k+1}/I_k, k = 1
                                                                   (Sec. II, Eqs. 5-6)
 * autocorrelation    C(t, t_w) = (1/N) sum_i S_i(t_w) S_i(t_w+t)  (Sec. II, Eq. 7)
@@ -190,6 +192,49 @@ def c4_sums(S):
         for r in range(L // 2 + 1):
             G[d, r] = np.sum(q * np.roll(q, -r, axis=_AXIS[d]))
     return G
+
+
+def c4_full_sums(S):
+    """G[dz, dy, dx] = sum_i q_i q_{i + (dx, dy, dz)} for every displacement vector of the
+    periodic lattice (Eq. 3 with i + r any site at vector distance r from i), by brute
+    force over the vectors."""
+    L = S.shape[1]
+    q = S[0].astype(np.int64) * S[1]
+    G = np.empty((L, L, L), dtype=np.int64)
+    for dz in range(L):
+        qz = np.roll(q, -dz, axis=0)
+        for dy in range(L):
+            qzy = np.roll(qz, -dy, axis=1)
+            for dx in range(L):
+                G[dz, dy, dx] = np.sum(q * np.roll(qzy, -dx, axis=2))
+    return G
+
+
+def c4_at(S, vectors):
+    """sum_i q_i q_{i + v} for a list of displacement vectors v = (dx, dy, dz)."""
+    q = S[0].astype(np.int64) * S[1]
+    return np.array([np.sum(q * np.roll(q, (-dz, -dy, -dx), axis=(0, 1, 2)))
+                     for dx, dy, dz in vectors], dtype=np.int64)
+
+
+def radial_index(L):
+    """r^2 of the shortest periodic image of each displacement vector, [dz, dy, dx]:
+    sum over the axes of min(d, L - d)^2, in 0 .. 3 (L/2)^2."""
+    d = np.arange(L)
+    m2 = np.minimum(d, L - d) ** 2
+    return m2[:, None, None] + m2[None, :, None] + m2[None, None, :]
+
+
+def c4_radial_sums(G):
+    """(sums, counts): the sums G(v) over the vectors of each r^2 = 0 .. 3 (L/2)^2, and
+    how many vectors each r^2 holds."""
+    L = G.shape[0]
+    r2 = radial_index(L).ravel()
+    n_bins = 3 * (L // 2) ** 2 + 1
+    sums = np.zeros(n_bins, dtype=np.int64)
+    np.add.at(sums, r2, G.ravel())
+    counts = np.bincount(r2, minlength=n_bins).astype(np.int64)
+    return sums, counts
 
 
 def energy(S, J):

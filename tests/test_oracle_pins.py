@@ -549,3 +549,68 @@ def test_heatbath_zero_temperature_classes():
         n_zero += int(np.sum(upd & (dE == 0)))
     assert n_zero > 1000
     assert abs(zero - n_zero / 2) < 5 * math.sqrt(n_zero / 4)
+
+
+# ----------------------------------------------------------------------------------
+# four-point sums over every displacement vector
+# ----------------------------------------------------------------------------------
+def _loop_full(S):
+    """Pure-Python loops over sites and vectors with explicit periodic indices."""
+    L = S.shape[1]
+    q = [[[int(S[0, z, y, x]) * int(S[1, z, y, x]) for x in range(L)] for y in range(L)]
+         for z in range(L)]
+    G = np.zeros((L, L, L), dtype=np.int64)
+    for dz in range(L):
+        for dy in range(L):
+            for dx in range(L):
+                tot = 0
+                for z in range(L):
+                    for y in range(L):
+                        for x in range(L):
+                            tot += q[z][y][x] * q[(z + dz) % L][(y + dy) % L][(x + dx) % L]
+                G[dz, dy, dx] = tot
+    return G
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_c4_full_brute_force(L):
+    S = ora.init_spins(L, 40 + L, 0)
+    assert np.array_equal(ora.c4_full_sums(S), _loop_full(S))
+
+
+@pytest.mark.parametrize("L", [6, 8, 12])
+def test_c4_full_identities(L):
+    S = ora.init_spins(L, 50 + L, 1)
+    J = ora.init_couplings(L, 0.5, 50 + L, 1)
+    ora.sweeps(L, 50 + L, 1, S, J, 0.8, 0, 0, 3)
+    G = ora.c4_full_sums(S)
+    N = L ** 3
+    q = S[0].astype(np.int64) * S[1]
+    assert G[0, 0, 0] == N
+    assert int(G.sum()) == int(q.sum()) ** 2  # sum over vectors = (sum_i q_i)^2
+    # G(v) = G(-v)
+    assert np.array_equal(G, np.roll(G[::-1, ::-1, ::-1], 1, axis=(0, 1, 2)))
+    # the axis points are the axis sums
+    ax = ora.c4_sums(S)
+    r = np.arange(L // 2 + 1)
+    assert np.array_equal(G[0, 0, r], ax[0]) and np.array_equal(G[0, r, 0], ax[1])
+    assert np.array_equal(G[r, 0, 0], ax[2])
+    # the correlation theorem with numpy's FFT, rounded
+    F = np.fft.fftn(q)
+    Gf = np.rint(np.fft.ifftn(F * np.conj(F)).real).astype(np.int64)
+    assert np.array_equal(G, Gf)
+    v = [(1, 2, 3), (L - 1, 0, 2), (L // 2, L // 2, L // 2)]
+    assert np.array_equal(ora.c4_at(S, v), [G[dz, dy, dx] for dx, dy, dz in v])
+
+
+@pytest.mark.parametrize("L", [4, 6, 16])
+def test_radial_bins(L):
+    r2 = ora.radial_index(L)
+    n_bins = 3 * (L // 2) ** 2 + 1
+    G = np.ones((L, L, L), dtype=np.int64)
+    sums, counts = ora.c4_radial_sums(G)
+    assert len(counts) == n_bins and counts.sum() == L ** 3 and np.array_equal(sums, counts)
+    assert counts[0] == 1 and counts[1] == 6 and counts[n_bins - 1] == 1
+    # r^2 = 2: the 12 face diagonals; r^2 = 3: the 8 body diagonals (L >= 4)
+    assert counts[2] == 12 and counts[3] == 8
+    assert r2[0, 0, 1] == 1 and r2[0, 0, L - 1] == 1 and r2[L // 2, L // 2, L // 2] == n_bins - 1
