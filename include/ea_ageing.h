@@ -177,6 +177,28 @@ int ea_time(const ea_ctx *ctx, uint64_t *t);
  * a scheduled waiting time, t not a scheduled lag, or t_w + t not reached. */
 int ea_measure(ea_ctx *ctx, uint64_t t_w, uint64_t t, ea_obs *out);
 
+/* Four-point sums over every displacement vector, binned by distance (Eq. 3
+ * with i + r any site at vector distance r from i; Sec. IV fits this larger
+ * point set beside the axis points to size its error bars).
+ * For the snapshot at the scheduled waiting time t_w and every sample s:
+ *   sums[s * n_bins + b] = sum over vectors v with |v|^2 = b of
+ *                          sum_i q_i q_{i+v},   q_i = S^0_i S^1_i,
+ * where |v|^2 = sum over axes of min(d, L - d)^2 (the shortest periodic
+ * image), b = 0 .. n_bins - 1, and counts[b] = the number of vectors with
+ * |v|^2 = b (0 for the values no vector takes).  C4 at distance sqrt(b) is
+ * sums / (counts N).  Exact integers: computed by a transform modulo a prime,
+ * with no rounding.  The caller owns sums[n_samples * n_bins] and
+ * counts[n_bins] (n_bins from ea_c4_radial_bins).  Uses device scratch of up
+ * to 256 MiB while it runs and synchronises the job's stream.  Errors:
+ * EA_ERR_INVALID_ARG (NULL, side above 512), EA_ERR_STATE (before
+ * ea_quench), EA_ERR_NO_SNAPSHOT (t_w not scheduled or not reached),
+ * EA_ERR_OOM. */
+int ea_c4_radial(ea_ctx *ctx, uint64_t t_w, long long *sums, long long *counts);
+
+/* Number of distance bins of ea_c4_radial for side L: 3 (L/2)^2 + 1.
+ * Host only.  EA_ERR_INVALID_ARG for odd L, L < 2 or L > 512. */
+int ea_c4_radial_bins(int L, int *n_bins);
+
 /* Copy spins of sample s, replica a into out[L^3] (int8 +-1, [z][y][x]).
  * Synchronous.  Errors: EA_ERR_INVALID_ARG, EA_ERR_STATE (before quench). */
 int ea_get_spins(ea_ctx *ctx, int s, int a, int8_t *out);

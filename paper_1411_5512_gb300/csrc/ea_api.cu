@@ -763,6 +763,68 @@ int ea_measure(ea_ctx *c, uint64_t t_w, uint64_t t, ea_obs *out)
     return EA_OK;
 }
 
+int ea_c4_radial_bins(int L, int *n_bins)
+{
+    if (!n_bins || L < 2 || (L & 1) || L > ea::kC4FullMaxL)
+        return EA_ERR_INVALID_ARG;
+    *n_bins = 3 * (L / 2) * (L / 2) + 1;
+    return EA_OK;
+}
+
+int ea_c4_radial(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts)
+{
+    if (check_ctx(c) || !sums || !counts)
+        return EA_ERR_INVALID_ARG;
+    if (c->L > ea::kC4FullMaxL)
+        return fail(c, EA_ERR_INVALID_ARG, "ea_c4_radial: side above 512");
+    if (!c->quenched)
+        return fail(c, EA_ERR_STATE, "ea_c4_radial before ea_quench");
+    const int i = idx_of(c->tw, t_w);
+    if (i < 0 || t_w > c->t)
+        return fail(c, EA_ERR_NO_SNAPSHOT, "t_w not scheduled or not reached");
+    const int L = c->L, H = L / 2, n_bins = 3 * H * H + 1;
+    // vectors per r^2: a shortest-image component m stands for d = m and d = L - m,
+    // one vector when they coincide (m = 0 or L/2)
+    std::fill(counts, counts + n_bins, 0LL);
+    for (int mz = 0; mz <= H; ++mz)
+        for (int my = 0; my <= H; ++my)
+            for (int mx = 0; mx <= H; ++mx) {
+                auto f = [H](int m) { return (m == 0 || m == H) ? 1LL : 2LL; };
+                counts[mx * mx + my * my + mz * mz] += f(mx) * f(my) * f(mz);
+            }
+    ea::C4FullTables fwd, inv;
+    if (ea::make_c4full_plan(L, &fwd, &inv) != 0)
+        return fail(c, EA_ERR_INVALID_ARG, "ea_c4_radial: no transform prime for this side");
+    const size_t per = ea::c4full_scratch_words(L);
+    const int chunk = (int)std::max<size_t>(
+        1, std::min<size_t>((size_t)c->S, ((size_t)256 << 20) / (per * sizeof(uint32_t))));
+    const size_t scratch_bytes = (size_t)chunk * per * sizeof(uint32_t);
+    const size_t bins_bytes = (size_t)c->S * n_bins * sizeof(long long);
+    uint32_t *scratch = (uint32_t *)dev_alloc(scratch_bytes, c->stream);
+    long long *bins = (long long *)dev_alloc(bins_bytes, c->stream);
+    auto release = [&]() {
+        dev_free(scratch, scratch_bytes, c->stream);
+        dev_free(bins, bins_bytes, c->stream);
+    };
+    if (!scratch || !bins) {
+        release();
+        return fail(c, EA_ERR_OOM, "ea_c4_radial: scratch allocation failed");
+    }
+    cudaError_t err = cudaMemsetAsync(bins, 0, bins_bytes, c->stream);
+    const uint32_t *snap = c->snaps + (size_t)i * c->area_words();
+    for (int s0 = 0; s0 < c->S && err == cudaSuccess; s0 += chunk)
+        err = ea::launch_c4full(snap, c->geo, s0, std::min(chunk, c->S - s0), scratch, fwd, inv,
+                                bins, n_bins, c->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(sums, bins, bins_bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(c->stream);
+    release();
+    if (err != cudaSuccess)
+        return cuda_fail(c, err, "ea_c4_radial");
+    return EA_OK;
+}
+
 int ea_get_spins(ea_ctx *c, int s, int a, int8_t *out)
 {
     if (check_ctx(c) || !out || s < 0 || s >= c->S || a < 0 || a > 1)

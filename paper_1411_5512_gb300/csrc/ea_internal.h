@@ -170,6 +170,24 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
                                unsigned long long *counters = nullptr,
                                const SideStreams *side = nullptr);
 
+// Four-point sums over every displacement vector (ea_c4full.cu), by an exact
+// transform modulo a prime p = cL + 1 > 2N + 1 below 2^31.
+constexpr int kC4FullMaxL = 512;
+struct C4FullTables {
+    uint32_t p;     // the prime
+    uint32_t pneg;  // -p^-1 mod 2^32 (Montgomery reduction)
+    uint32_t ninv;  // N^-1, Montgomery form
+    uint32_t pad;
+    uint32_t w[kC4FullMaxL];  // w^j, j < L, Montgomery form (w of order L, or its inverse)
+};
+int make_c4full_plan(int L, C4FullTables *fwd, C4FullTables *inv);  // 0 or -1
+size_t c4full_scratch_words(int L);  // per sample
+// Samples s0 .. s0 + n_chunk - 1 of a snapshot [S][2][words]: adds G(v) of each
+// into bins[s][r^2] (zeroed by the caller), with scratch of n_chunk * L^3 words.
+cudaError_t launch_c4full(const uint32_t *snap, const Geo &g, int s0, int n_chunk,
+                          uint32_t *scratch, const C4FullTables &fwd, const C4FullTables &inv,
+                          long long *bins, int n_bins, cudaStream_t stream);
+
 // Add n to the time field of every job of a table, stopping at its t_end
 // (device side, for graphs).
 cudaError_t launch_advance_time(JobDev *jobs_dev, int n_jobs, uint64_t n, cudaStream_t stream);

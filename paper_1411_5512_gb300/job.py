@@ -131,6 +131,25 @@ class EAJob:
         return {"A": A, "Q": Q, "E": E, "G": G, "C4": C4, "C4_sem": sem, "C": obs.C,
                 "q_mean": obs.q_mean, "xi1": obs.xi1, "r_cut": obs.r_cut}
 
+    def c4_radial(self, t_w):
+        """Four-point sums over every displacement vector of the snapshot at t_w,
+        binned by squared distance: {"sums": [S, n_bins], "counts": [n_bins],
+        "r2", "r" (the occupied bins), "C4" (sample mean), "C4_sem" (over samples),
+        "C4_samples" [S, bins]}, C4 = sums / (counts N) over the occupied bins."""
+        nb = ctypes.c_int()
+        _lib.check(self.lib.ea_c4_radial_bins(int(self.L), ctypes.byref(nb)))
+        sums = np.zeros((self.n_samples, nb.value), dtype=np.int64)
+        counts = np.zeros(nb.value, dtype=np.int64)
+        _lib.check(self.lib.ea_c4_radial(self.h, int(t_w), sums.ctypes.data_as(_lib.i64p),
+                                         counts.ctypes.data_as(_lib.i64p)), self.h)
+        occ = np.nonzero(counts)[0]
+        N = float(self.L) ** 3
+        per = sums[:, occ] / (counts[occ] * N)
+        S = self.n_samples
+        sem = per.std(axis=0, ddof=1) / np.sqrt(S) if S > 1 else np.zeros(len(occ))
+        return {"sums": sums, "counts": counts, "r2": occ, "r": np.sqrt(occ.astype(np.float64)),
+                "C4": per.mean(axis=0), "C4_sem": sem, "C4_samples": per}
+
     def spins(self, s, a):
         out = np.zeros((self.L,) * 3, dtype=np.int8)
         _lib.check(self.lib.ea_get_spins(self.h, int(s), int(a), out.ctypes.data_as(_lib.i8p)),

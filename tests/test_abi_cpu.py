@@ -53,6 +53,17 @@ def test_geometry_matches_oracle(lib):
         assert lib.ea_geometry(L, out) == -1
 
 
+def test_c4_radial_bins(lib):
+    nb = ctypes.c_int()
+    for L in [2, 4, 6, 16, 128, 512]:
+        assert lib.ea_c4_radial_bins(L, ctypes.byref(nb)) == 0
+        assert nb.value == 3 * (L // 2) ** 2 + 1
+        if L <= 16:  # the oracle's binning has as many bins
+            assert nb.value == len(ora.c4_radial_sums(np.zeros((L, L, L), dtype=np.int64))[1])
+    for L in [0, 3, 514, 1024]:
+        assert lib.ea_c4_radial_bins(L, ctypes.byref(nb)) == -1
+
+
 @pytest.mark.parametrize("rule", [0, 1])
 def test_thresholds_match_oracle(lib, rule):
     from paper_1411_5512_gb300 import job

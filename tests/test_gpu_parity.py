@@ -220,6 +220,57 @@ def test_heat_bath_late_time(J, L, t0):
     j.close()
 
 
+@pytest.mark.parametrize("L,S,n,T", [(2, 3, 4, 0.8), (4, 2, 6, 0.7), (6, 2, 5, 0.9), (8, 3, 4, 0.7),
+                                     (12, 2, 3, 1.2), (16, 2, 4, 0.7), (32, 1, 3, 0.7)])
+def test_c4_radial_matches_oracle(J, L, S, n, T):
+    """Every bin of the four-point sums over all displacement vectors, exact, against
+    the oracle's brute force on its own spins (multi-lane words for L < 64)."""
+    seed, p_neg = 80 + L, 0.5
+    j = J.EAJob(L, p_neg, seed, S)
+    j.set_schedule([0, n], [0])
+    j.quench(T)
+    j.sweep(n)
+    out = j.c4_radial(n)
+    ref = ora.run_job(L, p_neg, seed, S, T, 0, [], [], n, keep_spins=True)
+    for s in range(S):
+        sums, counts = ora.c4_radial_sums(ora.c4_full_sums(ref["spins"][s]))
+        assert np.array_equal(out["counts"], counts)
+        assert np.array_equal(out["sums"][s], sums), s
+    # the quenched state, from the snapshot at t_w = 0
+    out0 = j.c4_radial(0)
+    for s in range(S):
+        S0 = np.stack([ora.init_spins(L, seed, s)[a] for a in range(2)])
+        assert np.array_equal(out0["sums"][s], ora.c4_radial_sums(ora.c4_full_sums(S0))[0])
+    j.close()
+
+
+@pytest.mark.parametrize("L", [64, 128])
+def test_c4_radial_full_size(J, L):
+    """Sides 64 and 128: every vector at once through sum_v G(v) = Q^2, the r = 0 bin, and
+    the shells of up to 12 vectors against the oracle on its own spins."""
+    seed, p_neg, T, n, S = 90 + L, 0.5, 0.7, 2, 2
+    j = J.EAJob(L, p_neg, seed, S)
+    j.set_schedule([n], [0])
+    j.quench(T)
+    j.sweep(n)
+    out = j.c4_radial(n)
+    Q = j.measure(n, 0)["Q"]
+    ref = ora.run_job(L, p_neg, seed, S, T, 0, [], [], n, keep_spins=True)
+    N = L ** 3
+    shells = {1: [(1, 0, 0), (L - 1, 0, 0), (0, 1, 0), (0, L - 1, 0), (0, 0, 1), (0, 0, L - 1)],
+              3: [(a, b, c) for a in (1, L - 1) for b in (1, L - 1) for c in (1, L - 1)],
+              2: [v for v in [(a, b, 0) for a in (1, L - 1) for b in (1, L - 1)] +
+                  [(a, 0, c) for a in (1, L - 1) for c in (1, L - 1)] +
+                  [(0, b, c) for b in (1, L - 1) for c in (1, L - 1)]]}
+    for s in range(S):
+        assert out["sums"][s, 0] == N
+        assert int(out["sums"][s].sum()) == int(Q[s]) ** 2
+        for r2, vecs in shells.items():
+            assert out["counts"][r2] == len(vecs)
+            assert out["sums"][s, r2] == int(ora.c4_at(ref["spins"][s], vecs).sum()), (s, r2)
+    j.close()
+
+
 @pytest.mark.parametrize("L,tws,n,pick", [(64, [0, 1, 3], 3, [0, 1]), (128, [0, 2], 2, [1])])
 def test_c4_sums_sides_64_128(J, L, tws, n, pick):
     """The four-point sums of the sides whose lanes all lie along z (their own kernel):
