@@ -337,6 +337,9 @@ def run_ours(args, world, rank, local):
     heat = None
     if not args.no_heat:
         heat = run_heat(args, job, workloads, stream, flush)
+    c4r = None
+    if not args.no_heat:
+        c4r = run_c4_radial(args, job, workloads, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -371,6 +374,8 @@ def run_ours(args, world, rank, local):
         line["mixed_l"] = mixed
     if heat is not None:
         line["heat_bath"] = heat
+    if c4r is not None:
+        line["c4_radial"] = c4r
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -446,6 +451,24 @@ def run_heat(args, job, workloads, stream, flush):
     return {"workload": "L128_p0.5-0.1_S16x5_T0.7 heat bath", "value": flips / (m * 1e6),
             "unit": UNIT, "ms_per_step": m, "cols_per_thread": cfg[0], "graph_sweeps": cfg[1],
             "philox_calls_per_word": prof["philox_calls"] / max(prof["words"], 1)}
+
+
+def run_c4_radial(args, job, workloads, stream):
+    """The four-point sums over every displacement vector of a side-128 job of 16
+    samples (one snapshot): wall time of the synchronous call, per sample."""
+    w = workloads.PAPER_SCALE[0]
+    j = job.EAJob(w["L"], w["p_neg"], w["seed"], w["n_samples"], stream=stream)
+    j.set_schedule([0], [0])
+    j.quench(w["T"])
+    j.c4_radial(0)  # warm-up
+    reps = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        j.c4_radial(0)
+        reps.append(time.perf_counter() - t0)
+    j.close()
+    ms = statistics.median(reps) * 1e3
+    return {"workload": "L128_S16 one snapshot", "ms": ms, "ms_per_sample": ms / w["n_samples"]}
 
 
 def run_serving(args, job, workloads, stream):

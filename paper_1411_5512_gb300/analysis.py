@@ -20,6 +20,10 @@ scipy and runs on the host only.
   decomposition of Sec. II, tested in Sec. IV).
 - overlap_histogram: P(q), the distribution of the replica overlap q = Q / N
   (Eq. 2) over samples and times.
+- multifit_error: the error bars of Sec. IV: the same multifit on the axis
+  points and on every displacement vector with r >= r_min (ea_c4_radial); the
+  error of alpha, beta and each xi is the difference of the two results plus
+  both statistical errors.
 """
 import numpy as np
 
@@ -194,3 +198,18 @@ def overlap_histogram(Q, N, bins=2 * 16):
     q = np.asarray(Q, dtype=np.float64).ravel() / float(N)
     hist, edges = np.histogram(q, bins=bins, range=(-1.0, 1.0), density=True)
     return edges, hist, int(q.size)
+
+
+def multifit_error(axis_curves, all_curves, r_min=3.0):
+    """Sec. IV error estimate: fit the axis curves and the all-vector curves (each a
+    list of (r, C4, err) per waiting time), then
+    err(v) = |v_axis - v_all| + se_axis(v) + se_all(v) for alpha, beta and xi.
+    Returns {"alpha", "beta", "xi": values of the axis fit, and their "*_err"}."""
+    fa = multifit_c4(axis_curves, r_min=r_min)
+    fb = multifit_c4(all_curves, r_min=r_min)
+    out = {"alpha": fa["alpha"], "beta": fa["beta"], "xi": fa["xi"]}
+    for k in ("alpha", "beta"):
+        out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"] + fb[k + "_err"]
+    out["xi_err"] = np.abs(fa["xi"] - fb["xi"]) + fa["xi_err"] + fb["xi_err"]
+    out["fit_axis"], out["fit_all"] = fa, fb
+    return out

@@ -123,4 +123,41 @@ def test_pipeline_on_measured_curves():
     fit = an.multifit_c4(curves, r_min=3)
     assert np.isfinite(fit["alpha"]) and np.isfinite(fit["beta"])
     assert np.all(np.isfinite(fit["xi"])) and np.all(fit["xi"] > 0)
+    # the error bars of Sec. IV from the all-vector point set of the same snapshots
+    allv = []
+    for tw in tws:
+        rad = j.c4_radial(tw)
+        keep = rad["r"] <= L // 2
+        allv.append((rad["r"][keep], rad["C4"][keep], rad["C4_sem"][keep]))
+        # the axis points are among the vectors: the r = 1 shell is the axis r = 1 mean
+        m = j.measure(tw, 0)
+        assert abs(rad["C4"][1] - m["C4"][1]) < 1e-12
+    e = an.multifit_error(curves, allv)
+    assert np.isfinite(e["alpha_err"]) and np.isfinite(e["beta_err"])
+    assert np.all(np.isfinite(e["xi_err"]))
     j.close()
+
+
+def test_multifit_error_combines_both_point_sets():
+    """Both point sets built from the same form: the error is the sum of the two fits'
+    statistical errors (the difference vanishes); a shifted second set adds the shift."""
+    alpha, beta = 0.5, 1.4
+    xis, As = [2.5, 3.5, 5.0], [1.0, 1.0, 1.0]
+    axis = model_curves(alpha, beta, xis, As, rel_err=1e-3)
+    # the all-vector set: irrational distances sqrt(r^2) of the same form
+    r = np.sqrt(np.arange(0, 3 * 32 ** 2 + 1, dtype=np.float64))[:400]
+    allv = []
+    for xi, A in zip(xis, As):
+        c = np.ones_like(r)
+        c[1:] = an.c4_model(r[1:], A, alpha, xi, beta)
+        allv.append((r, c, 1e-3 * np.abs(c) + 1e-12))
+    e = an.multifit_error(axis, allv)
+    assert abs(e["alpha"] - alpha) < 1e-6 and abs(e["beta"] - beta) < 1e-6
+    fa, fb = e["fit_axis"], e["fit_all"]
+    assert abs(e["alpha_err"] - (fa["alpha_err"] + fb["alpha_err"])) < 1e-6
+    # a second set from a different alpha: the error covers the difference
+    allv2 = [(r, an.c4_model(np.maximum(r, 1), A, alpha + 0.05, xi, beta), e_)
+             for (r, _, e_), xi, A in zip(allv, xis, As)]
+    e2 = an.multifit_error(axis, allv2)
+    assert e2["alpha_err"] >= abs(e2["fit_all"]["alpha"] - alpha) - 1e-6
+    assert abs(e2["fit_all"]["alpha"] - (alpha + 0.05)) < 1e-4
