@@ -195,6 +195,22 @@ int ea_measure(ea_ctx *ctx, uint64_t t_w, uint64_t t, ea_obs *out);
  * EA_ERR_OOM. */
 int ea_c4_radial(ea_ctx *ctx, uint64_t t_w, long long *sums, long long *counts);
 
+/* ea_c4_radial for callers that cannot allocate device memory: a host that
+ * has handed all of it to its own pool, or code on a path where cudaMalloc,
+ * which may synchronise the device, is not allowed.  The paper has no
+ * counterpart; this is a property of the library.  Same arguments, results
+ * and errors as ea_c4_radial, but it calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch is a static device array built into the
+ * library, room for one sample of side up to 128 (8.1 MiB, held on every
+ * device the process uses, until exit).  Samples go through it one at a time.
+ * Sides above 128 give EA_ERR_INVALID_ARG.  The first call on a device looks
+ * up the array's address on that device (make it before any stream capture),
+ * with the job's device current.  All calls share the array and it keeps the
+ * last call's contents (each call clears what it sums into first): calls that
+ * overlap on the GPU, from different streams or threads, race, so order them.
+ * Synchronises the job's stream. */
+int ea_c4_radial_noalloc(ea_ctx *ctx, uint64_t t_w, long long *sums, long long *counts);
+
 /* Number of distance bins of ea_c4_radial for side L: 3 (L/2)^2 + 1.
  * Host only.  EA_ERR_INVALID_ARG for odd L, L < 2 or L > 512. */
 int ea_c4_radial_bins(int L, int *n_bins);

@@ -77,6 +77,7 @@ SIGNATURES = {
     "ea_measure": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.POINTER(EaObs)]),
     "ea_c4_radial": (ctypes.c_int, [vp, ctypes.c_uint64, i64p, i64p]),
+    "ea_c4_radial_noalloc": (ctypes.c_int, [vp, ctypes.c_uint64, i64p, i64p]),
     "ea_c4_radial_bins": (ctypes.c_int, [ctypes.c_int, intp]),
     "ea_get_spins": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, i8p]),
     "ea_get_couplings": (ctypes.c_int, [vp, ctypes.c_int, i8p]),

@@ -825,6 +825,56 @@ int ea_c4_radial(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts)
     return EA_OK;
 }
 
+int ea_c4_radial_noalloc(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts)
+{
+    if (check_ctx(c) || !sums || !counts)
+        return EA_ERR_INVALID_ARG;
+    if (c->L > ea::kC4FullNoAllocMaxL)
+        return fail(c, EA_ERR_INVALID_ARG,
+                    "ea_c4_radial_noalloc: side above 128, the size of its static scratch");
+    if (!c->quenched)
+        return fail(c, EA_ERR_STATE, "ea_c4_radial_noalloc before ea_quench");
+    const int i = idx_of(c->tw, t_w);
+    if (i < 0 || t_w > c->t)
+        return fail(c, EA_ERR_NO_SNAPSHOT, "t_w not scheduled or not reached");
+    const int L = c->L, H = L / 2, n_bins = 3 * H * H + 1;
+    std::fill(counts, counts + n_bins, 0LL);
+    for (int mz = 0; mz <= H; ++mz)
+        for (int my = 0; my <= H; ++my)
+            for (int mx = 0; mx <= H; ++mx) {
+                auto f = [H](int m) { return (m == 0 || m == H) ? 1LL : 2LL; };
+                counts[mx * mx + my * my + mz * mz] += f(mx) * f(my) * f(mz);
+            }
+    ea::C4FullTables fwd, inv;
+    if (ea::make_c4full_plan(L, &fwd, &inv) != 0)
+        return fail(c, EA_ERR_INVALID_ARG,
+                    "ea_c4_radial_noalloc: no transform prime for this side");
+    long long *bins = nullptr;
+    uint32_t *residues = nullptr;
+    cudaError_t err = ea::c4full_static_scratch(&bins, &residues);
+    if (err != cudaSuccess)
+        return cuda_fail(c, err, "ea_c4_radial_noalloc: static scratch address");
+    // one sample at a time through the shared scratch, in stream order; the
+    // bins left by the previous sample or call are cleared first
+    const size_t W = (size_t)c->geo.words;
+    const uint32_t *snap = c->snaps + (size_t)i * c->area_words();
+    const size_t row_bytes = (size_t)n_bins * sizeof(long long);
+    for (int s = 0; s < c->S && err == cudaSuccess; ++s) {
+        err = cudaMemsetAsync(bins, 0, row_bytes, c->stream);
+        if (err == cudaSuccess)
+            err = ea::launch_c4full(snap + (size_t)s * 2 * W, c->geo, 0, 1, residues, fwd, inv,
+                                    bins, n_bins, c->stream);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(sums + (size_t)s * n_bins, bins, row_bytes,
+                                  cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(c->stream);
+    if (err != cudaSuccess)
+        return cuda_fail(c, err, "ea_c4_radial_noalloc");
+    return EA_OK;
+}
+
 int ea_get_spins(ea_ctx *c, int s, int a, int8_t *out)
 {
     if (check_ctx(c) || !out || s < 0 || s >= c->S || a < 0 || a > 1)

@@ -18,7 +18,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
-#include <vector>
+#include <mutex>
 
 #include "ea_internal.h"
 
@@ -274,22 +274,24 @@ int make_c4full_plan(int L, C4FullTables *fwd, C4FullTables *inv)
             break;
     }
     const uint32_t P = (uint32_t)p;
-    // a generator of the multiplicative group: g^((p-1)/q) != 1 for each prime q | p - 1
-    std::vector<uint32_t> qs;
+    // a generator of the multiplicative group: g^((p-1)/q) != 1 for each prime
+    // q | p - 1 (fewer than 10 distinct ones below 2^31)
+    uint32_t qs[32];
+    int nq = 0;
     uint32_t m = P - 1;
     for (uint32_t d = 2; (uint64_t)d * d <= m; ++d)
         if (m % d == 0) {
-            qs.push_back(d);
+            qs[nq++] = d;
             while (m % d == 0)
                 m /= d;
         }
     if (m > 1)
-        qs.push_back(m);
+        qs[nq++] = m;
     uint32_t gen = 2;
     for (;; ++gen) {
         bool ok = true;
-        for (uint32_t q : qs)
-            ok = ok && pow_mod(gen, (P - 1) / q, P) != 1u;
+        for (int i = 0; i < nq; ++i)
+            ok = ok && pow_mod(gen, (P - 1) / qs[i], P) != 1u;
         if (ok)
             break;
     }
@@ -311,6 +313,47 @@ int make_c4full_plan(int L, C4FullTables *fwd, C4FullTables *inv)
         b = b * wi % P;
     }
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Scratch without allocation, for ea_c4_radial_noalloc: some callers cannot
+// call cudaMalloc (a host that has handed all device memory to its own pool,
+// or code on a path where an allocation, which may synchronise the device, is
+// not allowed).  They get the transform's scratch from this file-scope array:
+// the radial bins of one sample, then the residues of one sample of side up
+// to kC4FullNoAllocMaxL.  Every process that loads the library holds it on
+// every device it uses, until exit.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocBinsU64 = 12320;  // 3 (128/2)^2 + 1 = 12289 bins, padded to 256 bytes
+constexpr size_t kNoAllocU64 =
+    kNoAllocBinsU64 + (size_t)kC4FullNoAllocMaxL * kC4FullNoAllocMaxL * kC4FullNoAllocMaxL / 2;
+static __device__ __align__(256) unsigned long long g_c4full_scratch[kNoAllocU64];
+
+cudaError_t c4full_static_scratch(long long **bins, uint32_t **residues)
+{
+    // the array's device address, looked up once per device with that device
+    // current (in host code the array's name is only a stand-in)
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static void *addr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess)
+        return err;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_c4full_scratch);
+        if (err != cudaSuccess)
+            return err;
+        addr[dev] = p;
+    }
+    unsigned long long *base = static_cast<unsigned long long *>(addr[dev]);
+    *bins = reinterpret_cast<long long *>(base);
+    *residues = reinterpret_cast<uint32_t *>(base + kNoAllocBinsU64);
+    return cudaSuccess;
 }
 
 size_t c4full_scratch_words(int L)

@@ -187,6 +187,10 @@ size_t c4full_scratch_words(int L);  // per sample
 cudaError_t launch_c4full(const uint32_t *snap, const Geo &g, int s0, int n_chunk,
                           uint32_t *scratch, const C4FullTables &fwd, const C4FullTables &inv,
                           long long *bins, int n_bins, cudaStream_t stream);
+// The static scratch of ea_c4_radial_noalloc on the current device: room for
+// the bins and the residues of one sample of side up to kC4FullNoAllocMaxL.
+constexpr int kC4FullNoAllocMaxL = 128;
+cudaError_t c4full_static_scratch(long long **bins, uint32_t **residues);
 
 // Add n to the time field of every job of a table, stopping at its t_end
 // (device side, for graphs).
