@@ -34,6 +34,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #define ORA_OK 0
@@ -193,6 +194,50 @@ int ora_init_couplings(int L, double p_neg, uint64_t seed, uint32_t s, int8_t *J
         for (int d = 0; d < 3; d++)
             J[d * N + i] = ((uint64_t)out[d] < thr) ? (int8_t)-1 : (int8_t)1;
     }
+    return ORA_OK;
+}
+
+/* Couplings with an exact count: K = floor(p_neg * 3N + 1/2) of the 3N bonds
+   are negative, the K-subset drawn uniformly.  Bond b = d N + i gets the
+   64-bit key (out0 << 32) | out1 of Philox(ctr = (i, 1 + d, 0, s)); the
+   negative bonds are the first K in the order of (key, b). */
+struct bond_key {
+    uint64_t key;
+    uint32_t b;
+};
+
+static int bond_key_cmp(const void *pa, const void *pb)
+{
+    const struct bond_key *a = (const struct bond_key *)pa, *b = (const struct bond_key *)pb;
+    if (a->key != b->key)
+        return a->key < b->key ? -1 : 1;
+    return a->b < b->b ? -1 : (a->b > b->b ? 1 : 0);
+}
+
+int ora_init_couplings_exact(int L, double p_neg, uint64_t seed, uint32_t s, int8_t *J)
+{
+    if (L < 2 || L > 1024 || (L & 1) || !(p_neg >= 0.0 && p_neg <= 1.0))
+        return ORA_BAD_ARG;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    int64_t N = (int64_t)L * L * L;
+    uint64_t K = (uint64_t)floor(p_neg * 3.0 * (double)N + 0.5);
+    struct bond_key *keys = (struct bond_key *)malloc((size_t)(3 * N) * sizeof(struct bond_key));
+    if (!keys)
+        return ORA_BAD_ARG;
+    for (int d = 0; d < 3; d++)
+        for (int64_t i = 0; i < N; i++) {
+            uint32_t ctr[4] = {(uint32_t)i, 1u + (uint32_t)d, STREAM_COUPLINGS << 30, s};
+            uint32_t out[4];
+            ora_philox4x32_10(ctr, key, out);
+            keys[d * N + i].key = ((uint64_t)out[0] << 32) | out[1];
+            keys[d * N + i].b = (uint32_t)(d * N + i);
+        }
+    qsort(keys, (size_t)(3 * N), sizeof(struct bond_key), bond_key_cmp);
+    for (int64_t b = 0; b < 3 * N; b++)
+        J[b] = 1;
+    for (uint64_t r = 0; r < K; r++)
+        J[keys[r].b] = -1;
+    free(keys);
     return ORA_OK;
 }
 

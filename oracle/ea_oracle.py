@@ -62,6 +62,9 @@ def lib():
         L.ora_init_couplings.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
                                          ctypes.c_uint32, i8p]
         L.ora_init_couplings.restype = ctypes.c_int
+        L.ora_init_couplings_exact.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                               ctypes.c_uint32, i8p]
+        L.ora_init_couplings_exact.restype = ctypes.c_int
         L.ora_init_spins.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, i8p]
         L.ora_init_spins.restype = ctypes.c_int
         L.ora_sweeps.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, i8p, i8p,
@@ -126,6 +129,14 @@ def init_couplings(L, p_neg, seed, s):
     J = np.zeros((3, L, L, L), dtype=np.int8)
     _check(lib().ora_init_couplings(L, float(p_neg), seed, s, _ptr(J, ctypes.c_int8)),
            "init_couplings")
+    return J
+
+
+def init_couplings_exact(L, p_neg, seed, s):
+    """Couplings with exactly floor(p_neg 3N + 1/2) negative bonds, the subset uniform."""
+    J = np.zeros((3, L, L, L), dtype=np.int8)
+    _check(lib().ora_init_couplings_exact(L, float(p_neg), seed, s, _ptr(J, ctypes.c_int8)),
+           "init_couplings_exact")
     return J
 
 

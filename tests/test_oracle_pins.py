@@ -614,3 +614,57 @@ def test_radial_bins(L):
     # r^2 = 2: the 12 face diagonals; r^2 = 3: the 8 body diagonals (L >= 4)
     assert counts[2] == 12 and counts[3] == 8
     assert r2[0, 0, 1] == 1 and r2[0, 0, L - 1] == 1 and r2[L // 2, L // 2, L // 2] == n_bins - 1
+
+
+# ----------------------------------------------------------------------------------
+# couplings with an exact count of negative bonds
+# ----------------------------------------------------------------------------------
+def _exact_by_sorting(L, p_neg, seed, s):
+    """The K first bonds in the order of (key, bond index), with Python's sort."""
+    N = L ** 3
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    keys = []
+    for d in range(3):
+        for i in range(N):
+            o = ora.philox4x32_10([i, 1 + d, 0, s], key)
+            keys.append(((int(o[0]) << 32) | int(o[1]), d * N + i))
+    K = int(math.floor(p_neg * 3 * N + 0.5))
+    J = np.ones(3 * N, dtype=np.int8)
+    for _, b in sorted(keys)[:K]:
+        J[b] = -1
+    return J.reshape(3, L, L, L)
+
+
+@pytest.mark.parametrize("L,p_neg", [(2, 0.5), (4, 0.3), (4, 0.0), (4, 1.0), (6, 0.137)])
+def test_exact_couplings_count_and_order(L, p_neg):
+    J = ora.init_couplings_exact(L, p_neg, 11, 2)
+    N = L ** 3
+    assert int(np.sum(J == -1)) == int(math.floor(p_neg * 3 * N + 0.5))
+    assert np.array_equal(J, _exact_by_sorting(L, p_neg, 11, 2))
+
+
+def test_exact_couplings_nested_and_sample_dependent():
+    L = 8
+    a = ora.init_couplings_exact(L, 0.2, 5, 0)
+    b = ora.init_couplings_exact(L, 0.3, 5, 0)
+    assert np.all(b[a == -1] == -1)  # the selection grows with K
+    assert np.any(a != ora.init_couplings_exact(L, 0.2, 5, 1))
+
+
+def test_exact_couplings_hypergeometric():
+    """At L = 2 (n = 24 bonds), K = 12: every bond is negative with probability 1/2,
+    and the count X in a fixed half of the bonds is hypergeometric, with variance
+    12 (1/2)(1/2)(12/23) = 1.565, not the binomial 3 of independent bonds."""
+    n, K, reps = 24, 12, 4000
+    one = np.zeros(n)
+    xs = []
+    for s in range(reps):
+        J = (ora.init_couplings_exact(2, 0.5, 1234, s).ravel() == -1)
+        one += J
+        xs.append(int(J[:12].sum()))
+    p1 = K / n
+    assert np.all(np.abs(one / reps - p1) < 5 * math.sqrt(p1 * (1 - p1) / reps))
+    var = float(np.var(xs, ddof=1))
+    expect = 12 * 0.5 * 0.5 * (n - 12) / (n - 1)
+    assert abs(var - expect) < 5 * expect * math.sqrt(2.0 / reps), var
+    assert abs(float(np.mean(xs)) - 6.0) < 5 * math.sqrt(expect / reps)
