@@ -145,6 +145,17 @@ uint64_t ea_launch_count(void);
 int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_samples,
                       int rng_group_G, void *cuda_stream);
 
+/* As ea_create_samples, but every sample has exactly K = floor(p_neg 3N + 1/2)
+ * negative bonds, the K-subset uniform among all of them, instead of
+ * independent bonds.  Sec. II draws every bond independently from P(J); this
+ * variant fixes the concentration of each sample instead, which removes its
+ * sample-to-sample fluctuation.  Bond b = d N + i (d = x, y, z; i the site) gets the 64-bit key
+ * (out0 << 32) | out1 of Philox4x32-10 with counter (i, 1 + d, 0, s) and key
+ * (lo32(seed), hi32(seed)); the negative bonds are the first K in the order
+ * of (key, b).  Synchronises the stream.  Errors as ea_create_samples. */
+int ea_create_samples_exact(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_samples,
+                            int rng_group_G, void *cuda_stream);
+
 /* Set the measurement schedule: waiting times t_w[0..n_tw) and time lags
  * t[0..n_t) (Sec. II: C(t, t_w) and C4(r, t_w) are measured at waiting times
  * counted in sweeps from the quench).  At every t_w the state is snapshotted

@@ -70,6 +70,8 @@ SIGNATURES = {
     "ea_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, vp]),
     "ea_create_samples": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
                                          ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp]),
+    "ea_create_samples_exact": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp]),
     "ea_set_schedule": (ctypes.c_int, [vp, u64p, ctypes.c_int, u64p, ctypes.c_int]),
     "ea_quench": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
     "ea_sweep": (ctypes.c_int, [vp, ctypes.c_uint64]),

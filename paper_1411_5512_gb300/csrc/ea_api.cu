@@ -576,6 +576,35 @@ int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_sa
     return EA_OK;
 }
 
+int ea_create_samples_exact(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_samples,
+                            int rng_group_G, void *cuda_stream)
+{
+    const int rc = ea_create_samples(out, L, p_neg, seed, n_samples, rng_group_G, cuda_stream);
+    if (rc != EA_OK)
+        return rc;
+    ea_ctx *c = *out;
+    // the i.i.d. couplings just drawn are replaced by the exact-count draw
+    const size_t scratch_bytes = (size_t)n_samples * 260 * sizeof(uint32_t);
+    uint32_t *scratch = (uint32_t *)dev_alloc(scratch_bytes, c->stream);
+    if (!scratch) {
+        ea_destroy(c);
+        *out = nullptr;
+        return EA_ERR_OOM;
+    }
+    cudaError_t e = ea::launch_init_couplings_exact(c->J, c->geo, n_samples, p_neg, seed,
+                                                    scratch, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    dev_free(scratch, scratch_bytes, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ea_destroy(c);
+        *out = nullptr;
+        return EA_ERR_CUDA;
+    }
+    return EA_OK;
+}
+
 int ea_set_schedule(ea_ctx *c, const uint64_t *t_w, int n_tw, const uint64_t *t, int n_t)
 {
     if (check_ctx(c))

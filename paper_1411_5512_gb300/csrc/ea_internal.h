@@ -199,6 +199,10 @@ cudaError_t launch_advance_time(JobDev *jobs_dev, int n_jobs, uint64_t n, cudaSt
 // kernels (ea_kernels.cu); all enqueue on `stream` and return cudaGetLastError()
 cudaError_t launch_init_couplings(uint32_t *J, const Geo &g, int n_samples, double p_neg,
                                   uint64_t seed, cudaStream_t stream);
+// Couplings with exactly floor(p_neg 3N + 1/2) negative bonds per sample (the
+// K-subset uniform); scratch holds n_samples * 260 words.
+cudaError_t launch_init_couplings_exact(uint32_t *J, const Geo &g, int n_samples, double p_neg,
+                                        uint64_t seed, uint32_t *scratch, cudaStream_t stream);
 cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int n_samples, uint64_t seed,
                               cudaStream_t stream);
 

@@ -5,7 +5,9 @@
 // (Geo in ea_internal.h), so a per-sample reduction is a plain popcount of
 // words: sum_i S_i S'_i = N - 2 * (number of differing bits).
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "ea_device.cuh"
 #include "ea_internal.h"
@@ -52,6 +54,121 @@ __global__ void init_couplings_kernel(uint32_t *__restrict__ J, Geo g, uint64_t 
         jw[0] |= (uint32_t)((uint64_t)o.x < thr_p) << b;
         jw[1] |= (uint32_t)((uint64_t)o.y < thr_p) << b;
         jw[2] |= (uint32_t)((uint64_t)o.z < thr_p) << b;
+    }
+    const size_t W = (size_t)g.words;
+    uint32_t *Js = J + (size_t)s * 3 * W;
+    Js[w] = jw[0];
+    Js[W + w] = jw[1];
+    Js[2 * W + w] = jw[2];
+}
+
+// ---------------------------------------------------------------------------
+// Couplings with an exact count: the negative bonds are the first K in the
+// order of (key, b), b = d N + i, key = (out0 << 32) | out1 of
+// Philox(ctr = (i, 1 + d, 0, s)).  The K-th element of that order is found
+// by a radix select over the 96-bit composite (key, b), 8 bits per pass, most
+// significant first: a pass counts the bonds whose higher digits match the
+// prefix found so far, and a one-block step picks the digit where the count
+// reaches the remaining rank.  Per sample, state = {prefix[3], rank left}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bond_key(uint32_t i, int d, uint32_t s, uint32_t k0, uint32_t k1,
+                                        uint32_t &hi, uint32_t &lo)
+{
+    const uint4 o = philox10(make_uint4(i, 1u + (uint32_t)d, kStreamCouplings, s), k0, k1);
+    hi = o.x;
+    lo = o.y;
+}
+
+__global__ void exact_hist_kernel(int L, int pass, const uint32_t *__restrict__ state,
+                                  uint32_t *__restrict__ hist, uint32_t k0, uint32_t k1)
+{
+    __shared__ uint32_t h[256];
+    const uint32_t s = blockIdx.y;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        h[i] = 0u;
+    __syncthreads();
+    const uint64_t N = (uint64_t)L * L * L;
+    const int wsel = pass >> 2, shift = 24 - 8 * (pass & 3);
+    const uint32_t *st = state + (size_t)s * 4;
+    const uint32_t P[3] = {st[0], st[1], st[2]};
+    // bits of word wsel above the digit must match; words before it too
+    const uint32_t above = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < 3 * N;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(b / N);
+        const uint32_t i = (uint32_t)(b - (uint64_t)d * N);
+        uint32_t c[3];
+        bond_key(i, d, s, k0, k1, c[0], c[1]);
+        c[2] = (uint32_t)b;
+        bool match = true;
+        for (int w = 0; w < wsel; ++w)
+            match = match && c[w] == P[w];
+        match = match && ((c[wsel] ^ P[wsel]) & above) == 0u;
+        if (match)
+            atomicAdd(&h[(c[wsel] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i])
+            atomicAdd(&hist[(size_t)s * 256 + i], h[i]);
+}
+
+// One block of 256 threads per sample: the digit where the running count
+// reaches the rank left; clears the histogram for the next pass.
+__global__ void exact_select_kernel(int pass, uint32_t *__restrict__ state,
+                                    uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t cum[256];
+    const uint32_t s = blockIdx.x;
+    uint32_t *st = state + (size_t)s * 4;
+    uint32_t *hs = hist + (size_t)s * 256;
+    const int t = threadIdx.x;
+    const uint32_t cnt = hs[t];
+    cum[t] = cnt;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {  // inclusive scan
+        const uint32_t v = t >= off ? cum[t - off] : 0u;
+        __syncthreads();
+        cum[t] += v;
+        __syncthreads();
+    }
+    const uint32_t krem = st[3];
+    const uint32_t before = cum[t] - cnt;
+    if (cnt > 0u && before < krem && krem <= cum[t]) {
+        const int wsel = pass >> 2, shift = 24 - 8 * (pass & 3);
+        st[wsel] |= (uint32_t)t << shift;
+        st[3] = krem - before;
+    }
+    hs[t] = 0u;
+}
+
+// J words from the K-th composite P: a bond is negative iff (key, b) <= P.
+__global__ void exact_mark_kernel(uint32_t *__restrict__ J, Geo g, const uint32_t *__restrict__ state,
+                                  int none, uint32_t k0, uint32_t k1)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (w >= g.words)
+        return;
+    int xw, yw, zw;
+    word_coords(g, w, xw, yw, zw);
+    const uint32_t *st = state + (size_t)s * 4;
+    const uint32_t P0 = st[0], P1 = st[1], P2 = st[2];
+    const uint64_t N = (uint64_t)g.L * g.L * g.L;
+    uint32_t jw[3] = {0u, 0u, 0u};
+    if (!none) {
+        for (int b = 0; b < g.lanes; ++b) {
+            const int bx = b % g.k[0], by = (b / g.k[0]) % g.k[1], bz = b / (g.k[0] * g.k[1]);
+            const uint32_t x = bx * g.n[0] + xw, y = by * g.n[1] + yw, z = bz * g.n[2] + zw;
+            const uint32_t i = x + (uint32_t)g.L * (y + (uint32_t)g.L * z);
+            for (int d = 0; d < 3; ++d) {
+                uint32_t hi, lo;
+                bond_key(i, d, (uint32_t)s, k0, k1, hi, lo);
+                const uint32_t bi = (uint32_t)((uint64_t)d * N + i);
+                const bool le = hi != P0 ? hi < P0 : (lo != P1 ? lo < P1 : bi <= P2);
+                jw[d] |= (uint32_t)le << b;
+            }
+        }
     }
     const size_t W = (size_t)g.words;
     uint32_t *Js = J + (size_t)s * 3 * W;
@@ -428,6 +545,41 @@ cudaError_t launch_init_couplings(uint32_t *J, const Geo &g, int n_samples, doub
         p_neg >= 1.0 ? ((uint64_t)1 << 32) : (uint64_t)floor(ldexp(p_neg, 32));
     init_couplings_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(
         J, g, thr_p, (uint32_t)seed, (uint32_t)(seed >> 32));
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_couplings_exact(uint32_t *J, const Geo &g, int n_samples, double p_neg,
+                                        uint64_t seed, uint32_t *scratch, cudaStream_t stream)
+{
+    const uint64_t N = (uint64_t)g.L * g.L * g.L;
+    const uint64_t K = (uint64_t)std::floor(p_neg * 3.0 * (double)N + 0.5);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    uint32_t *state = scratch;                          // [S][4]
+    uint32_t *hist = scratch + (size_t)n_samples * 4;  // [S][256]
+    // prefix 0, rank K; histograms zero
+    std::vector<uint32_t> init((size_t)n_samples * 4, 0u);
+    for (int s = 0; s < n_samples; ++s)
+        init[(size_t)s * 4 + 3] = (uint32_t)K;
+    cudaError_t err = cudaMemcpyAsync(state, init.data(), init.size() * sizeof(uint32_t),
+                                      cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(hist, 0, (size_t)n_samples * 256 * sizeof(uint32_t), stream);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(stream);  // init is host memory that goes away
+    if (err != cudaSuccess)
+        return err;
+    if (K > 0) {
+        const uint64_t per = (3 * N + kBlock - 1) / kBlock;
+        const dim3 gh((unsigned)std::min<uint64_t>(per, 512), (unsigned)n_samples);
+        for (int pass = 0; pass < 12; ++pass) {
+            exact_hist_kernel<<<gh, kBlock, 0, stream>>>(g.L, pass, state, hist, k0, k1);
+            exact_select_kernel<<<n_samples, 256, 0, stream>>>(pass, state, hist);
+        }
+        count_launches(24);
+    }
+    exact_mark_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(J, g, state, K == 0 ? 1 : 0,
+                                                                      k0, k1);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -82,7 +82,10 @@ def footprint(L, n_samples, n_tw, n_t):
 class EAJob:
     """n_samples disorder samples x 2 replicas of an L^3 +-J EA lattice."""
 
-    def __init__(self, L, p_neg, seed, n_samples, rng_group=1, stream=None, _handle=None):
+    def __init__(self, L, p_neg, seed, n_samples, rng_group=1, stream=None, _handle=None,
+                 exact_count=False):
+        """exact_count: exactly floor(p_neg 3N + 1/2) negative bonds per sample instead of
+        independent bonds."""
         self.lib = _lib.load()
         self.L = int(L)
         self.n_samples = int(n_samples)
@@ -91,9 +94,9 @@ class EAJob:
             self.h = _handle
             return
         h = ctypes.c_void_p()
-        _lib.check(self.lib.ea_create_samples(ctypes.byref(h), self.L, float(p_neg),
-                                              int(seed), self.n_samples, int(rng_group),
-                                              _stream_handle(stream)))
+        create = self.lib.ea_create_samples_exact if exact_count else self.lib.ea_create_samples
+        _lib.check(create(ctypes.byref(h), self.L, float(p_neg), int(seed), self.n_samples,
+                          int(rng_group), _stream_handle(stream)))
         self.h = h
 
     # -- lifecycle ---------------------------------------------------------------

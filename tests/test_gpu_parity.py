@@ -482,3 +482,33 @@ def test_torch_allocator_route(J):
         assert torch.cuda.memory_allocated() == before
     finally:
         J.use_cuda_allocator()
+
+
+# ----------------------------------------------------------------------------------
+# couplings with an exact count of negative bonds
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("L,p_neg,S", [(2, 0.5, 3), (4, 0.3, 2), (6, 0.137, 2), (16, 0.5, 3),
+                                       (16, 0.0, 1), (16, 1.0, 1), (32, 0.21, 2), (128, 0.1, 1)])
+def test_exact_count_couplings(J, L, p_neg, S):
+    seed = 300 + L
+    j = J.EAJob(L, p_neg, seed, S, exact_count=True)
+    K = int(math.floor(p_neg * 3 * L ** 3 + 0.5))
+    for s in range(S):
+        Jg = j.couplings(s)
+        assert int(np.sum(Jg == -1)) == K
+        assert np.array_equal(Jg, ora.init_couplings_exact(L, p_neg, seed, s)), s
+    j.close()
+
+
+def test_exact_count_job_runs_like_the_oracle(J):
+    """A job on exact-count couplings sweeps as the oracle does on the same couplings."""
+    L, p_neg, seed, S, T, n = 16, 0.5, 77, 2, 0.7, 10
+    j = J.EAJob(L, p_neg, seed, S, exact_count=True)
+    j.quench(T)
+    j.sweep(n)
+    for s in range(S):
+        Jc = ora.init_couplings_exact(L, p_neg, seed, s)
+        Sref = ora.init_spins(L, seed, s)
+        ora.sweeps(L, seed, s, Sref, Jc, T, 0, 0, n)
+        assert np.array_equal(j.all_spins(s), Sref), s
+    j.close()
