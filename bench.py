@@ -179,7 +179,9 @@ N_SM = 152
 # dram__bytes_write.sum, one pass, caches flushed before each captured launch;
 # profiles/launches_bench_L128_S16x5.md, mean of three launches).  Take them
 # again (or set None) when the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 2.17e6, 2: 108.41e6 + 3.49e6, 4: 110.52e6 + 5.54e6}
+TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.01e6, 2: 108.34e6 + 3.39e6, 4: 110.50e6 + 5.60e6}
+# The same for the heat-bath tile kernel on the heat-bath leg, shape 1 (4 rows).
+HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.13e6}
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
@@ -450,7 +452,10 @@ def run_heat(args, job, workloads, stream, flush):
     m = statistics.median(ms)
     return {"workload": "L128_p0.5-0.1_S16x5_T0.7 heat bath", "value": flips / (m * 1e6),
             "unit": UNIT, "ms_per_step": m, "cols_per_thread": cfg[0], "graph_sweeps": cfg[1],
-            "philox_calls_per_word": prof["philox_calls"] / max(prof["words"], 1)}
+            "philox_calls_per_word": prof["philox_calls"] / max(prof["words"], 1),
+            "hbm_frac_of_measured": flips / (m * 1e6) * 0.75 / peaks()[0]["hbm_gbs"],
+            "traffic_per_launch": HEAT_TRAFFIC_BYTES_PER_LAUNCH.get(cfg[0]),
+            "algorithmic_bytes_per_launch": 0.75 * sum(w["n_samples"] * w["L"] ** 3 for w in specs)}
 
 
 def run_c4_radial(args, job, workloads, stream):

@@ -1244,7 +1244,7 @@ __device__ __forceinline__ void heat_tile_finish(const JobDev *__restrict__ jb, 
                                  hl, calls);
 }
 
-template <bool COUNT, int MAXJ, int GL>
+template <bool COUNT, int MAXJ, int GL, bool LOWT>
 __global__ void __launch_bounds__(kSweepThreads, 7)
     heat_tile_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
 {
@@ -1285,6 +1285,7 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
     if (threadIdx.x < kSweepThreads / 32)
         s_qn[threadIdx.x] = 0;
     __syncthreads();
+    const int B1 = s_hl[1][32], B0 = s_hl[0][32];  // 32-lane bounds of the pairs (1, 5), (0, 6)
     const uint64_t t = jb->t + P.sweep_offset;
     if (t >= jb->t_end)
         return;
@@ -1371,10 +1372,27 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
             const Count c = count6(v ^ in[k][0], v ^ in[k][1], v ^ in[k][2], v ^ in[k][3],
                                    v ^ in[k][4], v ^ in[k][5]);
             const uint4 R = dev::philox10_rk(make_uint4(wd[k], c1, c2w[k], c3), rk);
-            const HeatMasks m = heat_masks(c.b2, c.b1, c.b0, 0xffffffffu);
-            hit[k] = heat_hit(R, m, s_hl);
+            uint32_t m3;
+            if (LOWT) {
+                // the pairs (1, 5) and (0, 6) against their 32-lane bounds: a superset
+                // of the per-count test that needs neither their masks nor popcounts
+                const uint32_t lo = ~c.b2;
+                const uint32_t m2 = lo & c.b1 & ~c.b0, m4 = c.b2 & ~(c.b1 | c.b0);
+                m3 = lo & c.b1 & c.b0;
+                bool h = (int)(R.y >> 16) <= s_hl[2][__popc(m2)];
+                h |= (int)(R.y & 0xFFFFu) <= s_hl[2][__popc(m4)];
+                h |= (int)(R.z >> 16) <= B1;
+                h |= (int)(R.z & 0xFFFFu) <= B1;
+                h |= (int)(R.w >> 16) <= B0;
+                h |= (int)(R.w & 0xFFFFu) <= B0;
+                hit[k] = h;
+            } else {
+                const HeatMasks m = heat_masks(c.b2, c.b1, c.b0, 0xffffffffu);
+                hit[k] = heat_hit(R, m, s_hl);
+                m3 = m.M[3];
+            }
             // without a selection: class 3 by its coin, classes 4-6 flip whole
-            out[k] = v ^ ((m.M[3] & R.x) | c.b2);
+            out[k] = v ^ ((m3 & R.x) | c.b2);
         }
         // every word is written; a queued word is written again by the rare path
         *reinterpret_cast<uint2 *>(upd + w0) = make_uint2(out[0], out[1]);
@@ -1570,12 +1588,20 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
             p.h = h;
             p.sweep_offset = (uint32_t)k;
             if constexpr (HEAT && GL != 0) {
-                if (counters)
-                    heat_tile_kernel<true, MAXJ, GL>
-                        <<<grid, kSweepThreads, 0, stream>>>(p, counters);
-                else
-                    heat_tile_kernel<false, MAXJ, GL>
+                if (counters) {
+                    if (lowt)
+                        heat_tile_kernel<true, MAXJ, GL, true>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                    else
+                        heat_tile_kernel<true, MAXJ, GL, false>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                } else if (lowt) {
+                    heat_tile_kernel<false, MAXJ, GL, true>
                         <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                } else {
+                    heat_tile_kernel<false, MAXJ, GL, false>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                }
             } else if constexpr (HEAT) {
                 if (counters)
                     heat_kernel<true, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, counters);

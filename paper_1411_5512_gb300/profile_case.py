@@ -2,6 +2,7 @@
 
   python -m paper_1411_5512_gb300.profile_case [--L 128] [--samples 128] [--sweeps 4]
                                                [--rule 0] [--batch] [--cpt N] [--T 0.7]
+                                               [--measure | --c4-radial]
 
 One job of `samples` samples at side L (p_neg = 0.5, T = 0.7), quenched and swept
 `sweeps` times through the plain path (or through a one-job batch with --batch,
@@ -23,6 +24,8 @@ def main(argv=None):
     ap.add_argument("--cpt", type=int, default=0, help="batch launch shape (0 = default)")
     ap.add_argument("--T", type=float, default=0.7)
     ap.add_argument("--measure", action="store_true", help="schedule t_w = t = {0, 1, 2, 4}")
+    ap.add_argument("--c4-radial", action="store_true",
+                    help="then the four-point sums over every vector of the last snapshot")
     a = ap.parse_args(argv)
     import torch
 
@@ -31,6 +34,8 @@ def main(argv=None):
     j = job.EAJob(a.L, 0.5, 100, a.samples)
     if a.measure:
         j.set_schedule([0, 1, 2, 4], [0, 1, 2, 4])
+    elif a.c4_radial:
+        j.set_schedule([a.sweeps], [0])
     j.quench(a.T, a.rule)
     if a.batch:
         b = job.EABatch()
@@ -40,6 +45,8 @@ def main(argv=None):
         b.close()
     else:
         j.sweep(a.sweeps)
+    if a.c4_radial:
+        j.c4_radial(a.sweeps)
     torch.cuda.synchronize()
     print("ok", j.time)
     j.close()
