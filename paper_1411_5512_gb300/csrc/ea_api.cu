@@ -1235,8 +1235,8 @@ struct ea_batch {
     uint64_t graph_kernels = 0;  // kernels per replay
     const void *graph_key[2] = {nullptr, nullptr};
     int graph_blocks[2] = {0, 0};
-    // side streams: the runs of a mixed table (column kernel, side 64, side
-    // 128) are enqueued concurrently
+    // side streams: the runs of a mixed table (column kernel, general tiles,
+    // side 64, side 128) are enqueued concurrently
     ea::SideStreams side{};
     bool have_side = false;
     std::string err;
@@ -1293,7 +1293,11 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
     }
     // equal sides next to each other, sides 64 and 128 last: they form the
     // runs that the tile kernel takes (the order of rows changes no result)
-    auto run_key = [](int L) { return (L == 64 || L == 128) ? (1 << 20) + L : L; };
+    // the sides of the general tile kernel next, sides 64 and 128 last (their
+    // own tile kernels)
+    auto run_key = [](int L) {
+        return (L == 64 || L == 128) ? (2 << 20) + L : ea::general_tile_side(L) ? (1 << 20) + L : L;
+    };
     for (int r = 0; r < 2; ++r)
         std::stable_sort(b->tab_host[r].begin(), b->tab_host[r].end(),
                          [&](const ea::JobDev &a, const ea::JobDev &c) {
@@ -1410,11 +1414,11 @@ int ea_batch_create(ea_batch **out, void *cuda_stream)
     b->stream = (cudaStream_t)cuda_stream;
     // without side streams a mixed table runs its parts one after another
     bool ok = true;
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < ea::kSideStreams; ++i)
         ok = ok && cudaStreamCreateWithFlags(&b->side.stream[i], cudaStreamNonBlocking) ==
                        cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < ea::kSideStreams; ++i)
         ok = ok && cudaEventCreateWithFlags(&b->side.join[i], cudaEventDisableTiming) == cudaSuccess;
     cudaGetLastError();
     b->have_side = ok;
@@ -1702,7 +1706,7 @@ int ea_batch_destroy(ea_batch *b)
         dev_free(b->tab_dev[r], b->cap[r] * sizeof(ea::JobDev), b->stream);
         dev_free(b->bb_dev[r], (b->cap[r] + 1) * sizeof(int), b->stream);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < ea::kSideStreams; ++i) {
         if (b->side.stream[i])
             cudaStreamDestroy(b->side.stream[i]);
         if (b->side.join[i])

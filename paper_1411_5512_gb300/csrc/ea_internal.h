@@ -114,6 +114,8 @@ struct MetroGeo {
     uint32_t fix;          // bit 0: lanes realign across the x wrap, bit 1: y wrap
     int zsA[2], zsB[2];    // lane realignment across the periodic wrap along z
     uint32_t zmA[2], zmB[2];
+    int ysA[2], ysB[2];    // and along y
+    uint32_t ymA[2], ymB[2];
 };
 
 struct MetroJob {
@@ -154,10 +156,19 @@ uint64_t launches_total();
 
 // Two side streams and the events that fork them from a launching stream and
 // join them back: independent runs of a table then share the GPU.
+// Sides whose Metropolis half-steps take the general tile kernel: every lane
+// along y and z (L divisible by 16), enough tiles per sample to fill a block
+// (L >= 32), and not the sides with their own tile kernels (64, 128).
+inline bool general_tile_side(int L)
+{
+    return L % 16 == 0 && L >= 32 && L != 64 && L != 128;
+}
+
+constexpr int kSideStreams = 3;
 struct SideStreams {
-    cudaStream_t stream[2];
+    cudaStream_t stream[kSideStreams];
     cudaEvent_t fork;
-    cudaEvent_t join[2];
+    cudaEvent_t join[kSideStreams];
 };
 
 // Enqueue n sweeps of every job of a table: one launch per half-step per rule

@@ -557,6 +557,7 @@ __device__ __forceinline__ uint2 ld2(const uint32_t *__restrict__ p, int i)
     return *reinterpret_cast<const uint2 *>(p + i);
 }
 
+constexpr int kGeneralTile = 1;  // run code of the general tile kernel (sides divisible by 16)
 constexpr int kTileQueue = 224;  // entries per warp: up to 95 left over + 128 added per row
 constexpr int kTileMinSMs = 152;  // SMs of a GB300: launches below 4 blocks per SM take shorter rows
 
@@ -575,26 +576,19 @@ struct TileTables {
 // class's 32-lane bound (T1x, T0) are the word's classes counted again from
 // the neighbour area, which this half-step does not write, and decided
 // exactly, with calls 64 and 65 as needed.
-template <int GL>
-__device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const TileTables &tb,
-                                            const uint4 &e, uint32_t *__restrict__ upd,
-                                            const uint32_t *__restrict__ nb,
-                                            const uint32_t *__restrict__ Jx,
-                                            const uint32_t *__restrict__ Jy,
-                                            const uint32_t *__restrict__ Jz, int h, uint32_t live0,
-                                            uint32_t live1, uint32_t live2, uint32_t always3,
-                                            uint32_t T1x, uint32_t T0, uint32_t c1, uint32_t c2m,
-                                            uint32_t c3, const uint32_t (&rk)[20],
-                                            unsigned int &calls)
+// The rare path of one queued word at word-site w with counter word c2, spins
+// s, main bits M and class-2 lanes M2; `recount` counts the word's classes
+// again from the neighbour area.
+template <class Recount>
+__device__ __forceinline__ void tile_finish_at(const JobDev *__restrict__ jb, const TileTables &tb,
+                                               int w, uint32_t s, uint32_t M, uint32_t M2,
+                                               uint32_t c2, uint32_t *__restrict__ upd,
+                                               uint32_t live0, uint32_t live1, uint32_t live2,
+                                               uint32_t always3, uint32_t T1x, uint32_t T0,
+                                               uint32_t c1, uint32_t c3, const uint32_t (&rk)[20],
+                                               unsigned int &calls, const Recount &recount)
 {
-    constexpr int SLOG = GL == 128 ? 7 : 6;
-    constexpr int N2 = GL / 32, SZ = GL * GL;
-    const int w = (int)e.x;
-    const uint32_t s = e.y, M = e.z;
-    uint32_t M2 = e.w;
     const uint32_t base = upd[w];  // s with its outright flips
-    const int x = w & (GL - 1), y = (w >> SLOG) & (GL - 1), z = w >> (2 * SLOG);
-    const uint32_t c2 = c2m | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
     uint32_t A = 0u;
     if (always3 & 4u) {  // accepted outright (exp(-dE/T) rounds to 1)
         A = M2;
@@ -657,21 +651,7 @@ __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const
         }
     }
     if ((M & 0xFFC00u) <= T1x || (M & 0x3FFu) <= T0) {
-        const int wxp = x == GL - 1 ? w - (GL - 1) : w + 1;
-        const int wxm = x == 0 ? w + (GL - 1) : w - 1;
-        const int wyp = y == GL - 1 ? w - (GL - 1) * GL : w + GL;
-        const int wym = y == 0 ? w + (GL - 1) * GL : w - GL;
-        const int wzp = z == N2 - 1 ? w - (N2 - 1) * SZ : w + SZ;
-        const int wzm = z == 0 ? w + (N2 - 1) * SZ : w - SZ;
-        uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
-        if (z == N2 - 1)
-            nzp = rot_zp(nzp);
-        if (z == 0) {
-            nzm = rot_zm(nzm);
-            jzm = rot_zm(jzm);
-        }
-        const Count c = count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nb[wyp] ^ Jy[w],
-                               s ^ nb[wym] ^ Jy[wym], s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
+        const Count c = recount();
         const uint32_t alw = c.b2 | (c.b1 & c.b0);
         const Classes k = classes(c, alw, 0xffffffffu, live0, live1, live2);
         uint32_t M1 = k.M1, M0 = k.M0;
@@ -697,6 +677,45 @@ __device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const
         }
     }
     upd[w] = base ^ A;
+}
+
+template <int GL>
+__device__ __forceinline__ void tile_finish(const JobDev *__restrict__ jb, const TileTables &tb,
+                                            const uint4 &e, uint32_t *__restrict__ upd,
+                                            const uint32_t *__restrict__ nb,
+                                            const uint32_t *__restrict__ Jx,
+                                            const uint32_t *__restrict__ Jy,
+                                            const uint32_t *__restrict__ Jz, int h, uint32_t live0,
+                                            uint32_t live1, uint32_t live2, uint32_t always3,
+                                            uint32_t T1x, uint32_t T0, uint32_t c1, uint32_t c2m,
+                                            uint32_t c3, const uint32_t (&rk)[20],
+                                            unsigned int &calls)
+{
+    constexpr int SLOG = GL == 128 ? 7 : 6;
+    constexpr int N2 = GL / 32, SZ = GL * GL;
+    const int w = (int)e.x;
+    const uint32_t s = e.y, M = e.z, M2 = e.w;
+    const int x = w & (GL - 1), y = (w >> SLOG) & (GL - 1), z = w >> (2 * SLOG);
+    const uint32_t c2 = c2m | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
+    const auto recount = [&]() -> Count {
+        const int wxp = x == GL - 1 ? w - (GL - 1) : w + 1;
+        const int wxm = x == 0 ? w + (GL - 1) : w - 1;
+        const int wyp = y == GL - 1 ? w - (GL - 1) * GL : w + GL;
+        const int wym = y == 0 ? w + (GL - 1) * GL : w - GL;
+        const int wzp = z == N2 - 1 ? w - (N2 - 1) * SZ : w + SZ;
+        const int wzm = z == 0 ? w + (N2 - 1) * SZ : w - SZ;
+        uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
+        if (z == N2 - 1)
+            nzp = rot_zp(nzp);
+        if (z == 0) {
+            nzm = rot_zm(nzm);
+            jzm = rot_zm(jzm);
+        }
+        return count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nb[wyp] ^ Jy[w],
+                      s ^ nb[wym] ^ Jy[wym], s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
+    };
+    tile_finish_at(jb, tb, w, s, M, M2, c2, upd, live0, live1, live2, always3, T1x, T0, c1, c3, rk,
+                   calls, recount);
 }
 
 // Full adders of three bits: sum and carry.
@@ -919,6 +938,284 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
         unsigned int extra = 0;
         tile_finish<GL>(jb, tb, s_q[wq][off], upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3,
                         T1x, T0, c1, c2m, c3, rk, extra);
+        if (COUNT)
+            n_extra += extra;
+    }
+    if (COUNT) {
+        atomicAdd(&counters[0], (unsigned long long)n_words);
+        atomicAdd(&counters[1], (unsigned long long)(n_calls + n_extra));
+        atomicAdd(&counters[2], (unsigned long long)n_extra);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Metropolis half-step for jobs whose 32 lanes all lie along y and z (kx = 1:
+// the sides divisible by 16) other than 64 and 128.  The tiles, window and
+// queue of metro_tile_kernel, with the word lattice n0 x n1 x n2 read at run
+// time: a thread owns (x0, x0 + 1) x (z0, z0 + 1) over a segment of Y rows
+// (Y divides n1, so a segment never crosses the y wrap); the neighbour word
+// read across the y or z wrap is realigned lane by lane, the x wrap needs no
+// realignment.  Threads past the sample's last tile run on a valid tile and
+// write nothing.
+// ---------------------------------------------------------------------------
+struct GTileGeo {
+    int n0, n1, n2;
+    Axis ay, az;
+};
+
+__device__ __forceinline__ void gtile_finish(const JobDev *__restrict__ jb, const TileTables &tb,
+                                             const uint4 &e, uint32_t *__restrict__ upd,
+                                             const uint32_t *__restrict__ nb,
+                                             const uint32_t *__restrict__ Jx,
+                                             const uint32_t *__restrict__ Jy,
+                                             const uint32_t *__restrict__ Jz, const GTileGeo &gg,
+                                             int h, uint32_t live0, uint32_t live1, uint32_t live2,
+                                             uint32_t always3, uint32_t T1x, uint32_t T0,
+                                             uint32_t c1, uint32_t c2m, uint32_t c3,
+                                             const uint32_t (&rk)[20], unsigned int &calls)
+{
+    const int n0 = gg.n0, n1 = gg.n1, n2 = gg.n2, sz = n0 * n1;
+    const int w = (int)e.x;
+    const uint32_t s = e.y, M = e.z, M2 = e.w;
+    const int x = w % n0, r = w / n0, y = r % n1, z = r / n1;
+    const uint32_t c2 = c2m | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
+    const auto recount = [&]() -> Count {
+        const int wxp = x == n0 - 1 ? w - (n0 - 1) : w + 1;
+        const int wxm = x == 0 ? w + (n0 - 1) : w - 1;
+        const int wyp = y == n1 - 1 ? w - (n1 - 1) * n0 : w + n0;
+        const int wym = y == 0 ? w + (n1 - 1) * n0 : w - n0;
+        const int wzp = z == n2 - 1 ? w - (n2 - 1) * sz : w + sz;
+        const int wzm = z == 0 ? w + (n2 - 1) * sz : w - sz;
+        uint32_t nyp = nb[wyp], nym = nb[wym], jym = Jy[wym];
+        uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
+        if (y == n1 - 1)
+            nyp = fixup(nyp, gg.ay, 0);
+        if (y == 0) {
+            nym = fixup(nym, gg.ay, 1);
+            jym = fixup(jym, gg.ay, 1);
+        }
+        if (z == n2 - 1)
+            nzp = fixup(nzp, gg.az, 0);
+        if (z == 0) {
+            nzm = fixup(nzm, gg.az, 1);
+            jzm = fixup(jzm, gg.az, 1);
+        }
+        return count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nyp ^ Jy[w], s ^ nym ^ jym,
+                      s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
+    };
+    tile_finish_at(jb, tb, w, s, M, M2, c2, upd, live0, live1, live2, always3, T1x, T0, c1, c3, rk,
+                   calls, recount);
+}
+
+template <bool COUNT, int MAXJ, bool LOWT>
+__global__ void __launch_bounds__(kSweepThreads, 8)
+    metro_gtile_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
+{
+    int j = 0;
+    {
+        int lo = 0, hi = P.n_jobs - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.block_begin[mid] <= b)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    const MetroJob &J = P.job[j];
+    const MetroGeo &G = P.geo[(J.meta >> 8) & 0xFFu];
+    const JobDev *__restrict__ jb = P.jobs_dev + j;
+    uint32_t rk[20];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = J.key0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = J.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    __shared__ TileTables tb;
+    __shared__ uint4 s_q[kSweepThreads / 32][kTileQueue];
+    __shared__ int s_qn[kSweepThreads / 32];
+    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x) {
+        const int u = i / 33, n = i - 33 * u;
+        const uint32_t hi = jb->gC_hi[u][n];
+        tb.hi[u][n] = hi;
+        tb.lead[u][n] = u == 2 ? lead2(hi) : u == 1 ? lead1(hi) : lead0(hi);
+    }
+    if (threadIdx.x < kSweepThreads / 32)
+        s_qn[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t t = jb->t + P.sweep_offset;
+    if (t >= jb->t_end)
+        return;
+
+    const int h = P.h;
+    const int lane = threadIdx.x & 31;
+    uint4 *q = s_q[threadIdx.x >> 5];
+    int *qn = &s_qn[threadIdx.x >> 5];
+    GTileGeo gg;
+    gg.n0 = G.n0;
+    gg.n1 = G.n1;
+    gg.n2 = G.n2;
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+        gg.ay.sA[dir] = G.ysA[dir];
+        gg.ay.sB[dir] = G.ysB[dir];
+        gg.ay.mA[dir] = G.ymA[dir];
+        gg.ay.mB[dir] = G.ymB[dir];
+        gg.az.sA[dir] = G.zsA[dir];
+        gg.az.sB[dir] = G.zsB[dir];
+        gg.az.mA[dir] = G.zmA[dir];
+        gg.az.mB[dir] = G.zmB[dir];
+    }
+    const int n0 = gg.n0, n1 = gg.n1, n2 = gg.n2, SZ = n0 * n1;
+    const int XP = n0 >> 1, ZP = n2 >> 1, Y = G.seg;
+    const int local = (int)blockIdx.x - P.block_begin[j];
+    const int s = local / G.bps;
+    int tl = (local - s * G.bps) * kSweepThreads + (int)threadIdx.x;
+    const bool act = tl < XP * ZP * (n1 / Y);
+    if (!act)
+        tl = 0;
+    const int x0 = 2 * (tl % XP);
+    const int z0 = 2 * ((tl / XP) % ZP);
+    const int y0 = tl / XP / ZP * Y;
+    const bool all_always = (J.meta >> 3) & 1u, none_random = (J.meta >> 4) & 1u;
+    const uint32_t live0 = 0u - (J.meta & 1u), live1 = 0u - ((J.meta >> 1) & 1u),
+                   live2 = 0u - ((J.meta >> 2) & 1u);
+    const uint32_t always3 = jb->always_u & 7u;
+    const uint32_t T1x = lead1(jb->gC_hi[1][32]), T0 = lead0(jb->gC_hi[0][32]);
+    const uint32_t W = G.words;
+    uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
+    const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
+    const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
+    const uint32_t *__restrict__ Jy = Jx + W;
+    const uint32_t *__restrict__ Jz = Jy + W;
+    const uint32_t c3 = (uint32_t)s / J.rng_group;
+    const uint32_t c1 = (uint32_t)t;
+    const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
+    const int oz0 = z0 * SZ, oz1 = oz0 + SZ;
+    const int ozm = (z0 == 0 ? n2 - 1 : z0 - 1) * SZ;
+    const int ozp = (z0 + 2 == n2 ? 0 : z0 + 2) * SZ;
+    const bool wrap_m = z0 == 0, wrap_p = z0 + 2 == n2;
+    const int xm = x0 == 0 ? n0 - 1 : x0 - 1, xq = x0 + 2 == n0 ? 0 : x0 + 2;
+    unsigned int n_words = 0, n_calls = 0, n_extra = 0;
+
+    // the window: neighbour rows y - 1 (m) and y (c), y bonds of row y - 1; the
+    // row above a segment that starts at y = 0 lies across the y wrap
+    const int rym = (y0 == 0 ? n1 - 1 : y0 - 1) * n0;
+    uint2 Nm0 = ld2(nb, x0 + rym + oz0), Nm1 = ld2(nb, x0 + rym + oz1);
+    uint2 Jym0 = ld2(Jy, x0 + rym + oz0), Jym1 = ld2(Jy, x0 + rym + oz1);
+    if (y0 == 0) {
+        Nm0 = make_uint2(fixup(Nm0.x, gg.ay, 1), fixup(Nm0.y, gg.ay, 1));
+        Nm1 = make_uint2(fixup(Nm1.x, gg.ay, 1), fixup(Nm1.y, gg.ay, 1));
+        Jym0 = make_uint2(fixup(Jym0.x, gg.ay, 1), fixup(Jym0.y, gg.ay, 1));
+        Jym1 = make_uint2(fixup(Jym1.x, gg.ay, 1), fixup(Jym1.y, gg.ay, 1));
+    }
+    uint2 Nc0 = ld2(nb, x0 + y0 * n0 + oz0), Nc1 = ld2(nb, x0 + y0 * n0 + oz1);
+    for (int i = 0; i < Y; ++i) {
+        const int y = y0 + i;
+        const bool wrap_y = y + 1 == n1;  // only on a segment's last row
+        const int ry = y * n0, ryp = wrap_y ? 0 : ry + n0;
+        const int w0 = x0 + ry + oz0, w1 = x0 + ry + oz1;  // the even-x words at z0, z0 + 1
+        const uint2 S0 = ld2(upd, w0), S1 = ld2(upd, w1);
+        uint2 Nn0 = ld2(nb, x0 + ryp + oz0), Nn1 = ld2(nb, x0 + ryp + oz1);
+        if (wrap_y) {
+            Nn0 = make_uint2(fixup(Nn0.x, gg.ay, 0), fixup(Nn0.y, gg.ay, 0));
+            Nn1 = make_uint2(fixup(Nn1.x, gg.ay, 0), fixup(Nn1.y, gg.ay, 0));
+        }
+        uint2 Nzm = ld2(nb, x0 + ry + ozm), Nzp = ld2(nb, x0 + ry + ozp);
+        uint2 Jzm = ld2(Jz, x0 + ry + ozm);
+        const uint32_t Xm0 = nb[xm + ry + oz0], Xm1 = nb[xm + ry + oz1];
+        const uint32_t Xp0 = nb[xq + ry + oz0], Xp1 = nb[xq + ry + oz1];
+        const uint32_t Jxm0 = Jx[xm + ry + oz0], Jxm1 = Jx[xm + ry + oz1];
+        const uint2 Jx0 = ld2(Jx, w0), Jx1 = ld2(Jx, w1);
+        const uint2 Jy0 = ld2(Jy, w0), Jy1 = ld2(Jy, w1);
+        const uint2 Jz0 = ld2(Jz, w0), Jz1 = ld2(Jz, w1);
+        if (wrap_m) {
+            Nzm = make_uint2(fixup(Nzm.x, gg.az, 1), fixup(Nzm.y, gg.az, 1));
+            Jzm = make_uint2(fixup(Jzm.x, gg.az, 1), fixup(Jzm.y, gg.az, 1));
+        }
+        if (wrap_p)
+            Nzp = make_uint2(fixup(Nzp.x, gg.az, 0), fixup(Nzp.y, gg.az, 0));
+        const uint32_t c2A = c2m | ((uint32_t)(h ^ (y & 1)) << 11);
+        uint4 R = make_uint4(0u, 0u, 0u, 0u);
+        if (!(all_always || none_random))  // the quad's main call
+            R = dev::philox10_rk(make_uint4((uint32_t)w0, c1, c2A, c3), rk);
+        uint32_t alwa0, alwa1, alwb0, alwb1, m2a0, m2a1, m2b0, m2b1;
+        uint32_t sp = S0.x;
+        const bool draw = act && !(all_always || none_random);
+        bool ha0 = tile_word<LOWT>(sp ^ Nc0.y ^ Jx0.x, sp ^ Xm0 ^ Jxm0, sp ^ Nn0.x ^ Jy0.x,
+                                   sp ^ Nm0.x ^ Jym0.x, sp ^ Nc1.x ^ Jz0.x, sp ^ Nzm.x ^ Jzm.x,
+                                   R.x, tb, T1x, T0, live0, live1, live2, alwa0, m2a0);
+        sp = S0.y;
+        bool ha1 = tile_word<LOWT>(sp ^ Xp0 ^ Jx0.y, sp ^ Nc0.x ^ Jx0.x, sp ^ Nn0.y ^ Jy0.y,
+                                   sp ^ Nm0.y ^ Jym0.y, sp ^ Nc1.y ^ Jz0.y, sp ^ Nzm.y ^ Jzm.y,
+                                   R.y, tb, T1x, T0, live0, live1, live2, alwa1, m2a1);
+        sp = S1.x;
+        bool hb0 = tile_word<LOWT>(sp ^ Nc1.y ^ Jx1.x, sp ^ Xm1 ^ Jxm1, sp ^ Nn1.x ^ Jy1.x,
+                                   sp ^ Nm1.x ^ Jym1.x, sp ^ Nzp.x ^ Jz1.x, sp ^ Nc0.x ^ Jz0.x,
+                                   R.z, tb, T1x, T0, live0, live1, live2, alwb0, m2b0);
+        sp = S1.y;
+        bool hb1 = tile_word<LOWT>(sp ^ Xp1 ^ Jx1.y, sp ^ Nc1.x ^ Jx1.x, sp ^ Nn1.y ^ Jy1.y,
+                                   sp ^ Nm1.y ^ Jym1.y, sp ^ Nzp.y ^ Jz1.y, sp ^ Nc0.y ^ Jz0.y,
+                                   R.w, tb, T1x, T0, live0, live1, live2, alwb1, m2b1);
+        ha0 = ha0 && draw;
+        ha1 = ha1 && draw;
+        hb0 = hb0 && draw;
+        hb1 = hb1 && draw;
+        Nm0 = Nc0;
+        Nm1 = Nc1;
+        Nc0 = Nn0;
+        Nc1 = Nn1;
+        Jym0 = Jy0;
+        Jym1 = Jy1;
+        const uint32_t fx = all_always ? 0xffffffffu : 0u;
+        if (act) {
+            *reinterpret_cast<uint2 *>(upd + w0) =
+                make_uint2(S0.x ^ (alwa0 | fx), S0.y ^ (alwa1 | fx));
+            *reinterpret_cast<uint2 *>(upd + w1) =
+                make_uint2(S1.x ^ (alwb0 | fx), S1.y ^ (alwb1 | fx));
+            if (COUNT)
+                n_words += 4;
+        }
+        if (all_always || none_random)
+            continue;
+        if (COUNT && act)
+            n_calls += 1;
+        if (ha0)
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0, S0.x, R.x, m2a0);
+        if (ha1)
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w0 + 1u, S0.y, R.y, m2a1);
+        if (hb0)
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1, S1.x, R.z, m2b0);
+        if (hb1)
+            q[atomicAdd(qn, 1)] = make_uint4((uint32_t)w1 + 1u, S1.y, R.w, m2b1);
+        __syncwarp();
+        int q_n = *qn;
+        if (q_n >= 96) {  // full rounds, one queued word per lane, while 32 are queued
+            do {
+                q_n -= 32;
+                const uint4 e = q[q_n + lane];
+                unsigned int extra = 0;
+                gtile_finish(jb, tb, e, upd, nb, Jx, Jy, Jz, gg, h, live0, live1, live2, always3,
+                             T1x, T0, c1, c2m, c3, rk, extra);
+                if (COUNT)
+                    n_extra += extra;
+                __syncwarp();
+            } while (q_n >= 32);
+            if (lane == 0)
+                *qn = q_n;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    const int n0q = s_qn[0], n1q = n0q + s_qn[1], n2q = n1q + s_qn[2], n3q = n2q + s_qn[3];
+    for (int g = (int)threadIdx.x; g < n3q; g += kSweepThreads) {
+        const int wq = g < n0q ? 0 : g < n1q ? 1 : g < n2q ? 2 : 3;
+        const int off = g - (wq == 0 ? 0 : wq == 1 ? n0q : wq == 2 ? n1q : n2q);
+        unsigned int extra = 0;
+        gtile_finish(jb, tb, s_q[wq][off], upd, nb, Jx, Jy, Jz, gg, h, live0, live1, live2,
+                     always3, T1x, T0, c1, c2m, c3, rk, extra);
         if (COUNT)
             n_extra += extra;
     }
@@ -1515,6 +1812,10 @@ static void metro_geo(MetroGeo &g, const JobDev &jd)
         g.zsB[dir] = jd.geo.sB[2][dir];
         g.zmA[dir] = jd.geo.mA[2][dir];
         g.zmB[dir] = jd.geo.mB[2][dir];
+        g.ysA[dir] = jd.geo.sA[1][dir];
+        g.ysB[dir] = jd.geo.sB[1][dir];
+        g.ymA[dir] = jd.geo.mA[1][dir];
+        g.ymB[dir] = jd.geo.mB[1][dir];
     }
 }
 
@@ -1546,11 +1847,11 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
     // while the launch would hold fewer than four blocks per SM
     int y_max = 16;
     if (GL != 0) {
-        long samples = 0;
+        long tiles = 0;  // tiles of one row, 2 x 2 word-sites each
         for (int i = 0; i < cnt; ++i)
-            samples += host[i].n_samples;
-        const long per_row = (long)(GL / 2) * (GL / 64) * GL / kSweepThreads;  // blocks x rows
-        while (y_max > 2 && samples * per_row / y_max < 4L * kTileMinSMs)
+            tiles += (long)host[i].n_samples * (host[i].geo.n[0] / 2) * (host[i].geo.n[2] / 2) *
+                     host[i].geo.n[1];
+        while (y_max > 2 && tiles / y_max / kSweepThreads < 4L * kTileMinSMs)
             y_max >>= 1;
     }
     for (int i = 0; i < cnt; ++i) {
@@ -1564,10 +1865,14 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
             metro_geo(p.geo[gi], jd);
             if (GL != 0) {
                 // tiles of 2 x 2 word-sites times a segment of Y = 4, 8 or 16 rows
-                const int Y = std::min(
-                    y_max, jd.cols_per_thread >= 4 ? 16 : jd.cols_per_thread >= 2 ? 8 : 4);
+                // (fewer where the row count n1 of the word lattice needs it)
+                int Y = std::min(y_max,
+                                 jd.cols_per_thread >= 4 ? 16 : jd.cols_per_thread >= 2 ? 8 : 4);
+                while (jd.geo.n[1] % Y != 0)
+                    Y >>= 1;
+                const int threads = (jd.geo.n[0] / 2) * (jd.geo.n[2] / 2) * (jd.geo.n[1] / Y);
                 p.geo[gi].seg = Y;
-                p.geo[gi].bps = (GL / 2) * (GL / 64) * (GL / Y) / kSweepThreads;
+                p.geo[gi].bps = (threads + kSweepThreads - 1) / kSweepThreads;
             }
             ++n_geo;
         }
@@ -1607,6 +1912,21 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
                     heat_kernel<true, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, counters);
                 else
                     heat_kernel<false, MAXJ><<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+            } else if constexpr (GL == kGeneralTile) {
+                if (counters) {
+                    if (lowt)
+                        metro_gtile_kernel<true, MAXJ, true>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                    else
+                        metro_gtile_kernel<true, MAXJ, false>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                } else if (lowt) {
+                    metro_gtile_kernel<false, MAXJ, true>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                } else {
+                    metro_gtile_kernel<false, MAXJ, false>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                }
             } else if constexpr (GL != 0) {
                 if (counters) {
                     if (lowt)
@@ -1675,6 +1995,13 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
                 launch_metro_chunk<128, 0, true>(h, d, c, n, stream, counters);
             else
                 launch_metro_chunk<kMetroMaxJobs, 0, true>(h, d, c, n, stream, counters);
+        } else if (GLR == kGeneralTile) {
+            if (c <= 8)
+                launch_metro_chunk<8, kGeneralTile>(h, d, c, n, stream, counters);
+            else if (c <= 128)
+                launch_metro_chunk<128, kGeneralTile>(h, d, c, n, stream, counters);
+            else
+                launch_metro_chunk<kMetroMaxJobs, kGeneralTile>(h, d, c, n, stream, counters);
         } else if (GLR == 128) {
             if (c <= 8)
                 launch_metro_chunk<8, 128>(h, d, c, n, stream, counters);
@@ -1699,36 +2026,37 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
     }
 }
 
-// A table read as up to three runs: jobs of sides other than 64 and 128 (the
-// column kernels), then side 64, then side 128 (the tile kernels).  A table
-// in any other order is one run for the column kernel.
+// A table read as runs, in this order: the jobs for the column kernels, then
+// (with `general`) those of the general tile kernel, then side 64, then side
+// 128 (their own tile kernels).  A table in any other order is one run for the
+// column kernel.
 struct Run {
     int first, cnt, GLR;
 };
 
-static int split_runs(const JobDev *host, int n_jobs, Run runs[3])
+static int split_runs(const JobDev *host, int n_jobs, bool general, Run runs[4])
 {
-    int a = 0;
-    while (a < n_jobs && host[a].geo.L != 64 && host[a].geo.L != 128)
-        ++a;
-    int b = a;
-    while (b < n_jobs && host[b].geo.L == 64)
-        ++b;
-    int e = b;
-    while (e < n_jobs && host[e].geo.L == 128)
-        ++e;
-    int n_runs = 0;
-    if (e != n_jobs) {  // not in run order
-        if (n_jobs > 0)
-            runs[n_runs++] = {0, n_jobs, 0};
-    } else {
-        if (a > 0)
-            runs[n_runs++] = {0, a, 0};
-        if (b > a)
-            runs[n_runs++] = {a, b - a, 64};
-        if (e > b)
-            runs[n_runs++] = {b, e - b, 128};
+    constexpr int kCode[4] = {0, kGeneralTile, 64, 128};
+    auto cls = [&](int L) {
+        return L == 64 ? 2 : L == 128 ? 3 : (general && general_tile_side(L)) ? 1 : 0;
+    };
+    int count[4] = {0, 0, 0, 0};
+    int prev = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        const int c = cls(host[i].geo.L);
+        if (c < prev) {  // not in run order
+            runs[0] = {0, n_jobs, 0};
+            return 1;
+        }
+        prev = c;
+        ++count[c];
     }
+    int n_runs = 0, first = 0;
+    for (int c = 0; c < 4; ++c)
+        if (count[c] > 0) {
+            runs[n_runs++] = {first, count[c], kCode[c]};
+            first += count[c];
+        }
     return n_runs;
 }
 
@@ -1738,11 +2066,11 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
                                const SideStreams *side)
 {
     // Runs of the Metropolis table hold different jobs, so they need no order
-    // between them: given side streams, the second and third run are forked
-    // from `stream` and joined back after their n sweeps, so the runs share
-    // the GPU.  The heat-bath runs follow on `stream`.
-    Run runs[3];
-    const int n_runs = split_runs(host0, n_jobs0, runs);
+    // between them: given side streams, every run after the first is forked
+    // from `stream` and joined back after its n sweeps, so the runs share the
+    // GPU.  The heat-bath runs follow on `stream`.
+    Run runs[4];
+    const int n_runs = split_runs(host0, n_jobs0, true, runs);
     const bool fork = side != nullptr && n_runs > 1;
     if (fork) {
         cudaError_t err = cudaEventRecord(side->fork, stream);
@@ -1764,8 +2092,8 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
         if (err != cudaSuccess)
             return err;
     }
-    Run hruns[3];
-    const int n_hruns = split_runs(host1, n_jobs1, hruns);
+    Run hruns[4];
+    const int n_hruns = split_runs(host1, n_jobs1, false, hruns);
     for (int r = 0; r < n_hruns; ++r)
         launch_metro_run<true>(host1 + hruns[r].first, dev1 + hruns[r].first, hruns[r].cnt,
                                hruns[r].GLR, n, stream, counters);

@@ -173,6 +173,37 @@ def test_tile_kernel_late_time(J, t0):
     j.close()
 
 
+GTILE_CASES = [
+    # L, p_neg, T, cols_per_thread, S, sweeps: the general tile kernel (L divisible by
+    # 16, lanes along y and z, realigned across the y and z wraps)
+    (48, 0.5, 0.7, 1, 3, 3),
+    (96, 0.4, 1.2, 2, 2, 2),
+    (32, 0.5, 0.9, 4, 5, 3),
+    (80, 0.5, 0.7, 2, 2, 2),     # 20 rows of words: segments of 4
+    (160, 0.3, 2.0, 1, 1, 2),
+    (48, 0.5, 0.0, 2, 2, 3),     # T = 0: no random numbers
+    (48, 0.5, 1e17, 1, 2, 2),    # dE = 4 accepted outright
+    (32, 0.5, float("inf"), 1, 2, 2),
+]
+
+
+@pytest.mark.parametrize("L,p_neg,T,cpt,S,n", GTILE_CASES)
+def test_general_tile_kernel_bit_exact(J, L, p_neg, T, cpt, S, n):
+    seed = 600 + L + cpt
+    j = J.EAJob(L, p_neg, seed, S)
+    j.quench(T)
+    b = J.EABatch()
+    b.configure(cpt, 0)
+    b.add(j)
+    b.sweep(n)
+    pick = [0, S - 1] if S > 1 else [0]
+    ref = ora.run_job(L, p_neg, seed, S, T, 0, [], [], n, samples=pick, keep_spins=True)
+    for i, s in enumerate(pick):
+        assert np.array_equal(j.all_spins(s), ref["spins"][i]), s
+    b.close()
+    j.close()
+
+
 HEAT_CASES = [
     # L, p_neg, T, cols_per_thread, S, sweeps: the heat bath through a batch
     (128, 0.5, 0.7, 1, 3, 2),
