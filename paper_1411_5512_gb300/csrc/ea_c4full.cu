@@ -44,6 +44,11 @@ __device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t p)
     return s >= p ? s - p : s;
 }
 
+__device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b, uint32_t p)
+{
+    return a >= b ? a - b : a + (p - b);
+}
+
 // q bit (1 <=> q = -1) of site (x, y, z) of a sample whose two areas start at
 // a0 and a0 + words: the areas hold the two replicas at every word-site.
 __device__ __forceinline__ uint32_t q_bit(const uint32_t *__restrict__ a0, const Geo &g, int x,
@@ -105,6 +110,22 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Power-of-two sides: the +-1 field itself in Montgomery form (one = R mod p),
+// for the transform pass along x that follows.
+__global__ void c4f_expand_kernel(const uint32_t *__restrict__ snap, Geo g, int s0,
+                                  uint32_t *__restrict__ R, uint32_t one, uint32_t p)
+{
+    const int L = g.L;
+    const size_t N = (size_t)L * L * L;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N)
+        return;
+    const int c = blockIdx.y;
+    const uint32_t *a0 = snap + (size_t)(s0 + c) * 2 * g.words;
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / ((size_t)L * L));
+    R[(size_t)c * N + i] = q_bit(a0, g, x, y, z) ? p - one : one;
+}
+
 // Address of element e of line g along an axis (0 x, 1 y, 2 z) of one sample.
 __device__ __forceinline__ size_t line_addr(int axis, int L, int g, int e)
 {
@@ -119,7 +140,11 @@ __device__ __forceinline__ size_t line_addr(int axis, int L, int g, int e)
 // A DFT pass along one axis, in place, for kLines lines per block.  With bins
 // (the last inverse pass, along x) the results are read out of Montgomery
 // form and added into the radial bins of the sample instead of written back.
-template <bool BIN>
+// With RADIX2 (L a power of two) the lines are transformed in place by the
+// iterative radix-2 scheme: elements loaded in bit-reversed order, log2 L
+// stages of butterflies (u, v w) -> (u + v w, u - v w) with w = w^(j L / len),
+// the result in natural order; O is then T itself.
+template <bool BIN, bool RADIX2>
 __global__ void __launch_bounds__(kThreads)
     c4f_axis_kernel(uint32_t *__restrict__ R, int L, int axis,
                     const __grid_constant__ C4FullTables tw, long long *__restrict__ bins,
@@ -129,7 +154,7 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int P = kLines + 1;  // tile pitch
     uint32_t *sw = sm;             // [L]
     uint32_t *T = sm + L;          // [L][P] input
-    uint32_t *O = T + L * P;       // [L][P] output
+    uint32_t *O = RADIX2 ? T : T + L * P;  // [L][P] output
     const int c = blockIdx.y;
     const size_t N = (size_t)L * L * L;
     uint32_t *Rs = R + (size_t)c * N;
@@ -149,23 +174,41 @@ __global__ void __launch_bounds__(kThreads)
             l = i - e * kLines;
         }
         const int g = g0 + l;
-        T[e * P + l] = g < lines ? Rs[line_addr(axis, L, g, e)] : 0u;
+        int et = e;
+        if (RADIX2)
+            et = (int)(__brev((uint32_t)e) >> (32 - (__ffs(L) - 1)));
+        T[et * P + l] = g < lines ? Rs[line_addr(axis, L, g, e)] : 0u;
     }
     __syncthreads();
     const uint32_t p = tw.p, pneg = tw.pneg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = warp; k < L; k += kThreads / 32) {
-        uint32_t acc = 0u;
-        int idx = 0;  // e k mod L
-        for (int e = 0; e < L; ++e) {
-            acc = madd(acc, mmul(T[e * P + lane], sw[idx], p, pneg), p);
-            idx += k;
-            if (idx >= L)
-                idx -= L;
+    if (RADIX2) {
+        for (int len = 2; len <= L; len <<= 1) {
+            const int half = len >> 1, step = L / len;
+            for (int k = warp; k < L / 2; k += kThreads / 32) {
+                const int j = k & (half - 1);
+                const int i0 = (k - j) * 2 + j, i1 = i0 + half;
+                const uint32_t u = T[i0 * P + lane];
+                const uint32_t v = mmul(T[i1 * P + lane], sw[j * step], p, pneg);
+                T[i0 * P + lane] = madd(u, v, p);
+                T[i1 * P + lane] = msub(u, v, p);
+            }
+            __syncthreads();
         }
-        O[k * P + lane] = acc;
+    } else {
+        for (int k = warp; k < L; k += kThreads / 32) {
+            uint32_t acc = 0u;
+            int idx = 0;  // e k mod L
+            for (int e = 0; e < L; ++e) {
+                acc = madd(acc, mmul(T[e * P + lane], sw[idx], p, pneg), p);
+                idx += k;
+                if (idx >= L)
+                    idx -= L;
+            }
+            O[k * P + lane] = acc;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (!BIN) {
         for (int i = threadIdx.x; i < kLines * L; i += blockDim.x) {
             int l, e;
@@ -225,9 +268,9 @@ __global__ void c4f_pointwise_kernel(uint32_t *__restrict__ R, int L, uint32_t p
     Rs[j] = v;
 }
 
-size_t axis_smem(int L)
+size_t axis_smem(int L, bool radix2)
 {
-    return ((size_t)L + 2 * (size_t)L * (kLines + 1)) * sizeof(uint32_t);
+    return ((size_t)L + (radix2 ? 1 : 2) * (size_t)L * (kLines + 1)) * sizeof(uint32_t);
 }
 
 bool is_prime(uint32_t n)
@@ -361,34 +404,67 @@ size_t c4full_scratch_words(int L)
     return (size_t)L * L * L;
 }
 
-cudaError_t launch_c4full(const uint32_t *snap, const Geo &g, int s0, int n_chunk,
-                          uint32_t *scratch, const C4FullTables &fwd, const C4FullTables &inv,
-                          long long *bins, int n_bins, cudaStream_t stream)
+template <bool RADIX2>
+cudaError_t launch_c4full_passes(const uint32_t *snap, const Geo &g, int s0, int n_chunk,
+                                 uint32_t *scratch, const C4FullTables &fwd,
+                                 const C4FullTables &inv, long long *bins, int n_bins,
+                                 cudaStream_t stream)
 {
     const int L = g.L;
-    const size_t sm = axis_smem(L);
-    cudaError_t err = cudaFuncSetAttribute(c4f_axis_kernel<false>,
+    const size_t sm = axis_smem(L, RADIX2);
+    cudaError_t err = cudaFuncSetAttribute(c4f_axis_kernel<false, RADIX2>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(c4f_axis_kernel<true>,
+        err = cudaFuncSetAttribute(c4f_axis_kernel<true, RADIX2>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess)
         return err;
     const int lines = L * L;
-    const dim3 g_load((lines + kLoadRows - 1) / kLoadRows, n_chunk);
-    const size_t sm_load = ((size_t)L + kLoadRows * (size_t)((L + 31) / 32)) * sizeof(uint32_t);
-    c4f_load_x_kernel<<<g_load, kThreads, sm_load, stream>>>(snap, g, s0, scratch, fwd);
-    const dim3 g_axis((lines + kLines - 1) / kLines, n_chunk);
-    c4f_axis_kernel<false><<<g_axis, kThreads, sm, stream>>>(scratch, L, 1, fwd, nullptr, 0, s0);
-    c4f_axis_kernel<false><<<g_axis, kThreads, sm, stream>>>(scratch, L, 2, fwd, nullptr, 0, s0);
     const size_t N = (size_t)L * L * L;
+    const dim3 g_axis((lines + kLines - 1) / kLines, n_chunk);
+    int launches = 0;
+    if (RADIX2) {
+        // the +-1 field, then its transform along x
+        const dim3 g_ex((unsigned)((N + 255) / 256), n_chunk);
+        c4f_expand_kernel<<<g_ex, 256, 0, stream>>>(snap, g, s0, scratch,
+                                                    (uint32_t)(((uint64_t)1 << 32) % fwd.p),
+                                                    fwd.p);
+        c4f_axis_kernel<false, RADIX2>
+            <<<g_axis, kThreads, sm, stream>>>(scratch, L, 0, fwd, nullptr, 0, s0);
+        launches += 2;
+    } else {
+        const dim3 g_load((lines + kLoadRows - 1) / kLoadRows, n_chunk);
+        const size_t sm_load =
+            ((size_t)L + kLoadRows * (size_t)((L + 31) / 32)) * sizeof(uint32_t);
+        c4f_load_x_kernel<<<g_load, kThreads, sm_load, stream>>>(snap, g, s0, scratch, fwd);
+        launches += 1;
+    }
+    c4f_axis_kernel<false, RADIX2><<<g_axis, kThreads, sm, stream>>>(scratch, L, 1, fwd, nullptr, 0,
+                                                                     s0);
+    c4f_axis_kernel<false, RADIX2><<<g_axis, kThreads, sm, stream>>>(scratch, L, 2, fwd, nullptr, 0,
+                                                                     s0);
     const dim3 g_pw((unsigned)((N + 255) / 256), n_chunk);
     c4f_pointwise_kernel<<<g_pw, 256, 0, stream>>>(scratch, L, fwd.p, fwd.pneg, fwd.ninv);
-    c4f_axis_kernel<false><<<g_axis, kThreads, sm, stream>>>(scratch, L, 2, inv, nullptr, 0, s0);
-    c4f_axis_kernel<false><<<g_axis, kThreads, sm, stream>>>(scratch, L, 1, inv, nullptr, 0, s0);
-    c4f_axis_kernel<true><<<g_axis, kThreads, sm, stream>>>(scratch, L, 0, inv, bins, n_bins, s0);
-    count_launches(7);
+    c4f_axis_kernel<false, RADIX2><<<g_axis, kThreads, sm, stream>>>(scratch, L, 2, inv, nullptr, 0,
+                                                                     s0);
+    c4f_axis_kernel<false, RADIX2><<<g_axis, kThreads, sm, stream>>>(scratch, L, 1, inv, nullptr, 0,
+                                                                     s0);
+    c4f_axis_kernel<true, RADIX2><<<g_axis, kThreads, sm, stream>>>(scratch, L, 0, inv, bins,
+                                                                    n_bins, s0);
+    count_launches((uint64_t)launches + 6);
     return cudaGetLastError();
+}
+
+cudaError_t launch_c4full(const uint32_t *snap, const Geo &g, int s0, int n_chunk,
+                          uint32_t *scratch, const C4FullTables &fwd, const C4FullTables &inv,
+                          long long *bins, int n_bins, cudaStream_t stream)
+{
+    // power-of-two sides by the radix-2 transform, the others by direct DFTs
+    if ((g.L & (g.L - 1)) == 0)
+        return launch_c4full_passes<true>(snap, g, s0, n_chunk, scratch, fwd, inv, bins, n_bins,
+                                          stream);
+    return launch_c4full_passes<false>(snap, g, s0, n_chunk, scratch, fwd, inv, bins, n_bins,
+                                       stream);
 }
 
 }  // namespace ea
