@@ -248,8 +248,6 @@ struct ea_ctx {
     uint32_t *snaps = nullptr;
     ea::JobDev jd;                 // host copy of the job's sweep-table entry
     ea::JobDev *jd_dev = nullptr;  // one-entry table for the plain path
-    int *bb_dev = nullptr;         // its block_begin = {0, blocks}
-    int blocks = 0;
     unsigned long long *res = nullptr;
     size_t spins_bytes = 0, J_bytes = 0, snaps_bytes = 0, res_bytes = 0;
     // host copy of res, valid while res_gen == res_host_gen; res_gen moves on
@@ -542,8 +540,7 @@ int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_sa
     c->spins = (uint32_t *)dev_alloc(c->spins_bytes, c->stream);
     c->J = (uint32_t *)dev_alloc(c->J_bytes, c->stream);
     c->jd_dev = (ea::JobDev *)dev_alloc(sizeof(ea::JobDev), c->stream);
-    c->bb_dev = (int *)dev_alloc(2 * sizeof(int), c->stream);
-    if (!c->spins || !c->J || !c->jd_dev || !c->bb_dev) {
+    if (!c->spins || !c->J || !c->jd_dev) {
         ea_destroy(c);
         return EA_ERR_OOM;
     }
@@ -555,15 +552,6 @@ int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_sa
     c->jd.rng_group = (uint32_t)rng_group_G;
     ea::fill_job_keys(&c->jd, seed);
     ea::fill_job_layout(&c->jd, default_cols_per_thread(g));
-    c->blocks = n_samples * c->jd.blocks_per_sample;
-    {
-        const int bb[2] = {0, c->blocks};
-        if (cudaMemcpy(c->bb_dev, bb, sizeof(bb), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaGetLastError();
-            ea_destroy(c);
-            return EA_ERR_CUDA;
-        }
-    }
     cudaError_t e = ea::launch_init_couplings(c->J, g, n_samples, p_neg, seed, c->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c->spins, 0, c->spins_bytes, c->stream);
@@ -1199,7 +1187,6 @@ int ea_destroy(ea_ctx *c)
     dev_free(c->spins, c->spins_bytes, c->stream);
     dev_free(c->J, c->J_bytes, c->stream);
     dev_free(c->jd_dev, sizeof(ea::JobDev), c->stream);
-    dev_free(c->bb_dev, 2 * sizeof(int), c->stream);
     delete c;
     return EA_OK;
 }
@@ -1223,18 +1210,16 @@ struct ea_batch {
     int graph_sweeps = 0;  // sweeps per captured graph (0 = direct launches)
     // device job tables, one per update rule
     ea::JobDev *tab_dev[2] = {nullptr, nullptr};
-    int *bb_dev[2] = {nullptr, nullptr};
     size_t cap[2] = {0, 0};
     int n_jobs[2] = {0, 0};
-    int blocks[2] = {0, 0};
     std::vector<ea::JobDev> tab_host[2];
-    std::vector<int> bb_host[2];
+    uint64_t tab_sig = 0;  // what the launches take from the host tables (table_signature)
     // captured graph of graph_sweeps sweeps over the current tables
     cudaGraphExec_t graph = nullptr;
     int graph_K = 0;
     uint64_t graph_kernels = 0;  // kernels per replay
     const void *graph_key[2] = {nullptr, nullptr};
-    int graph_blocks[2] = {0, 0};
+    uint64_t graph_sig = 0;
     // side streams: the runs of a mixed table (column kernel, general tiles,
     // side 64, side 128) are enqueued concurrently
     ea::SideStreams side{};
@@ -1268,15 +1253,44 @@ void drop_graph(ea_batch *b)
     b->graph_K = 0;
 }
 
+// A hash of everything a captured graph's launches take from the host tables
+// at capture time (order, pointers, keys, geometry, launch shape, class flags
+// and the kernel variant chosen from the tables), not the times, which the
+// launches read from the device rows.  A graph is replayed only while it
+// matches.
+uint64_t table_signature(const std::vector<ea::JobDev> (&tab)[2])
+{
+    uint64_t h = 1469598103934665603ull;  // FNV-1a, 64 bit
+    auto mix = [&h](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xFFu;
+            h *= 1099511628211ull;
+        }
+    };
+    for (int r = 0; r < 2; ++r) {
+        mix(0xA5A5u + (uint64_t)r);
+        mix(tab[r].size());
+        for (const ea::JobDev &jd : tab[r]) {
+            mix((uint64_t)(uintptr_t)jd.spins);
+            mix((uint64_t)(uintptr_t)jd.J);
+            mix(((uint64_t)jd.rk[0] << 32) | jd.rk[1]);
+            mix(((uint64_t)(uint32_t)jd.geo.L << 32) | (uint32_t)jd.n_samples);
+            mix(((uint64_t)jd.rng_group << 32) | (uint32_t)jd.cols_per_thread);
+            mix(((uint64_t)jd.geo_live << 32) | jd.always_u);
+            mix(((uint64_t)(uint32_t)jd.all_always << 32) | (uint32_t)jd.none_random);
+            mix(((uint64_t)jd.gC_hi[1][32] << 32) | jd.gC_hi[0][32]);
+        }
+    }
+    return h;
+}
+
 // Rebuild both rule tables from the members' current state and upload them;
 // member i may run up to min(n, limits[i]) more sweeps (limits may be NULL).
 int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits = nullptr)
 {
     size_t mi = 0;
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < 2; ++r)
         b->tab_host[r].clear();
-        b->bb_host[r].assign(1, 0);
-    }
     for (ea_ctx *m : b->members) {
         const int r = m->rule == EA_RULE_HEATBATH ? 1 : 0;
         ea::JobDev jd = m->jd;
@@ -1289,12 +1303,10 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
         if (b->cpt > 0)
             ea::fill_job_layout(&jd, b->cpt);
         b->tab_host[r].push_back(jd);
-        b->bb_host[r].push_back(b->bb_host[r].back() + m->S * jd.blocks_per_sample);
     }
-    // equal sides next to each other, sides 64 and 128 last: they form the
-    // runs that the tile kernel takes (the order of rows changes no result)
-    // the sides of the general tile kernel next, sides 64 and 128 last (their
-    // own tile kernels)
+    // equal sides next to each other: the sides of the column kernels first,
+    // those of the general tile kernel next, sides 64 and 128 last (their own
+    // tile kernels); the order of rows changes no result
     auto run_key = [](int L) {
         return (L == 64 || L == 128) ? (2 << 20) + L : ea::general_tile_side(L) ? (1 << 20) + L : L;
     };
@@ -1303,25 +1315,21 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
                          [&](const ea::JobDev &a, const ea::JobDev &c) {
                              return run_key(a.geo.L) < run_key(c.geo.L);
                          });
+    b->tab_sig = table_signature(b->tab_host);
     for (int r = 0; r < 2; ++r) {
         const size_t n = b->tab_host[r].size();
         b->n_jobs[r] = (int)n;
-        b->blocks[r] = b->bb_host[r].back();
         if (n == 0)
             continue;
         if (n > b->cap[r]) {
             size_t cap = std::max<size_t>(n, 2 * b->cap[r]);
             dev_free(b->tab_dev[r], b->cap[r] * sizeof(ea::JobDev), b->stream);
-            dev_free(b->bb_dev[r], (b->cap[r] + 1) * sizeof(int), b->stream);
             b->tab_dev[r] = (ea::JobDev *)dev_alloc(cap * sizeof(ea::JobDev), b->stream);
-            b->bb_dev[r] = (int *)dev_alloc((cap + 1) * sizeof(int), b->stream);
             b->cap[r] = cap;
-            if (!b->tab_dev[r] || !b->bb_dev[r])
+            if (!b->tab_dev[r])
                 return bfail(b, EA_ERR_OOM, "batch table allocation failed");
         }
         EA_BCUDA(b, cudaMemcpyAsync(b->tab_dev[r], b->tab_host[r].data(), n * sizeof(ea::JobDev),
-                                    cudaMemcpyHostToDevice, b->stream));
-        EA_BCUDA(b, cudaMemcpyAsync(b->bb_dev[r], b->bb_host[r].data(), (n + 1) * sizeof(int),
                                     cudaMemcpyHostToDevice, b->stream));
     }
     return EA_OK;
@@ -1341,8 +1349,7 @@ int ensure_graph(ea_batch *b)
 {
     const int K = b->graph_sweeps;
     if (b->graph && b->graph_K == K && b->graph_key[0] == b->tab_dev[0] &&
-        b->graph_key[1] == b->tab_dev[1] && b->graph_blocks[0] == b->blocks[0] &&
-        b->graph_blocks[1] == b->blocks[1])
+        b->graph_key[1] == b->tab_dev[1] && b->graph_sig == b->tab_sig)
         return EA_OK;
     drop_graph(b);
     cudaGraph_t g = nullptr;
@@ -1368,15 +1375,14 @@ int ensure_graph(ea_batch *b)
     b->graph_kernels = kernels;
     b->graph_key[0] = b->tab_dev[0];
     b->graph_key[1] = b->tab_dev[1];
-    b->graph_blocks[0] = b->blocks[0];
-    b->graph_blocks[1] = b->blocks[1];
+    b->graph_sig = b->tab_sig;
     return EA_OK;
 }
 
 // n sweeps of every member on the tables as uploaded (no measurements).
 int run_sweeps(ea_batch *b, uint64_t n)
 {
-    if (n == 0 || (b->blocks[0] == 0 && b->blocks[1] == 0))
+    if (n == 0 || (b->n_jobs[0] == 0 && b->n_jobs[1] == 0))
         return EA_OK;
     uint64_t rem = n;
     if (b->graph_sweeps > 0 && b->stream != nullptr && n >= (uint64_t)b->graph_sweeps) {
@@ -1704,7 +1710,6 @@ int ea_batch_destroy(ea_batch *b)
     drop_graph(b);
     for (int r = 0; r < 2; ++r) {
         dev_free(b->tab_dev[r], b->cap[r] * sizeof(ea::JobDev), b->stream);
-        dev_free(b->bb_dev[r], (b->cap[r] + 1) * sizeof(int), b->stream);
     }
     for (int i = 0; i < ea::kSideStreams; ++i) {
         if (b->side.stream[i])

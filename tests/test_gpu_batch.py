@@ -216,3 +216,38 @@ def test_launch_count(J):
     assert J.launch_count() - n0 == 2 * (2 * 4 + 1)
     b.close()
     j.close()
+
+
+def test_graph_follows_member_swaps_and_requench(J):
+    """A captured graph holds the members' pointers and class flags in its launches:
+    swapping a member for another of the same shape, or quenching one again at another
+    temperature, must take a new graph.  Every job equals the same job run alone."""
+    import torch
+    stream = torch.cuda.Stream()
+    b = J.EABatch(stream=stream)
+    b.configure(1, 4)
+    L, S = 32, 2
+    a = J.EAJob(L, 0.5, 901, S, stream=stream)
+    c = J.EAJob(L, 0.5, 902, S, stream=stream)  # the same shape as a
+    a.quench(0.7)
+    c.quench(0.7)
+    b.add(a)
+    b.sweep(8)                  # a graph with a's pointers
+    b.remove(a)
+    b.add(c)
+    b.sweep(8)                  # the same table size and shape: a new graph all the same
+    c.quench(0.0)               # again at T = 0: other class flags (no random numbers)
+    b.sweep(8)
+    b.close()
+    ra = J.EAJob(L, 0.5, 901, S)
+    ra.quench(0.7)
+    ra.sweep(8)
+    rc = J.EAJob(L, 0.5, 902, S)
+    rc.quench(0.0)
+    rc.sweep(8)
+    for s in range(S):
+        assert np.array_equal(a.all_spins(s), ra.all_spins(s)), s
+        assert np.array_equal(c.all_spins(s), rc.all_spins(s)), s
+    assert a.time == 8 and c.time == 8
+    for j in (a, c, ra, rc):
+        j.close()

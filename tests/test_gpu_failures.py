@@ -49,7 +49,7 @@ class FailingAllocator:
 
 def test_create_reports_oom_and_frees_partial_allocations(J):
     from paper_1411_5512_gb300 import _lib
-    for budget in range(0, 4):
+    for budget in range(0, 3):  # a job holds three allocations: spins, couplings, its table row
         fa = FailingAllocator(budget)
         try:
             with pytest.raises(_lib.EAError) as e:
@@ -59,7 +59,7 @@ def test_create_reports_oom_and_frees_partial_allocations(J):
         finally:
             fa.close()
     # a schedule that cannot get its snapshot memory fails cleanly too
-    fa = FailingAllocator(4)
+    fa = FailingAllocator(3)
     try:
         j = J.EAJob(16, 0.5, 1, 2)
         with pytest.raises(_lib.EAError) as e:
