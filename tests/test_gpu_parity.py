@@ -442,10 +442,17 @@ def test_infinite_temperature_full_size(J):
 # ----------------------------------------------------------------------------------
 # state handling and errors
 # ----------------------------------------------------------------------------------
-def test_checkpoint_restore_continues_bit_exact(J, tmp_path):
-    L, S = 16, 2
+@pytest.mark.parametrize("L,rule,exact", [(16, 0, False), (64, 1, False), (32, 0, True)])
+def test_checkpoint_restore_continues_bit_exact(J, tmp_path, L, rule, exact):
+    S = 2
     t_w, t = [0, 4, 8], [0, 2, 8]
-    a = gpu_run(J, L, 0.5, 12, S, 0.7, 0, t_w, t, 10)
+    if exact:  # couplings with an exact count, which the restore must carry over
+        a = J.EAJob(L, 0.5, 12, S, exact_count=True)
+        a.set_schedule(t_w, t)
+        a.quench(0.7, rule)
+        a.sweep(10)
+    else:
+        a = gpu_run(J, L, 0.5, 12, S, 0.7, rule, t_w, t, 10)
     path = str(tmp_path / "job.ckpt")
     a.checkpoint(path)
     a.sweep(9)
@@ -459,6 +466,9 @@ def test_checkpoint_restore_continues_bit_exact(J, tmp_path):
             ma, mb = a.measure(tw, lag), b.measure(tw, lag)
             for k in ("A", "Q", "E", "G"):
                 assert np.array_equal(ma[k], mb[k])
+        assert np.array_equal(a.c4_radial(tw)["sums"], b.c4_radial(tw)["sums"])
+    for s in range(S):
+        assert np.array_equal(a.couplings(s), b.couplings(s))
     a.close()
     b.close()
 

@@ -19,6 +19,8 @@ STREAM = [
     (8, 0.5, 108, 1, 0.7, 0, 0, [0], [0]),          # zero sweeps
     (16, 0.5, 109, 1, 0.7, 0, 17, [0, 16], [0, 1]),
     (24, 0.25, 110, 2, 0.55, 0, 12, [0, 4], [0, 8]),
+    (48, 0.5, 111, 1, 0.7, 0, 9, [0, 8], [0, 1]),   # the general tile kernel
+    (64, 0.3, 112, 1, 0.8, 1, 7, [0], [0, 4]),      # the heat-bath tile kernel
 ]
 
 
