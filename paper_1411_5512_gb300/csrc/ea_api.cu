@@ -19,6 +19,8 @@
 #include <vector>
 
 #include "../../include/ea_ageing.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "ea_internal.h"
 
 using ea::Geo;
@@ -28,6 +30,15 @@ namespace {
 ea_alloc_fn g_alloc = nullptr;
 ea_free_fn g_free = nullptr;
 void *g_alloc_user = nullptr;
+
+// An NVTX range over a call that enqueues work: named spans on a profiler's
+// timeline (nsys, ncu --nvtx); without a tool attached it costs a branch.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 void *dev_alloc(size_t bytes, cudaStream_t stream)
 {
@@ -517,6 +528,7 @@ int ea_set_allocator(ea_alloc_fn alloc, ea_free_fn release, void *user)
 int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_samples,
                       int rng_group_G, void *cuda_stream)
 {
+    NvtxRange nvtx_range("ea_create_samples");
     if (!out)
         return EA_ERR_INVALID_ARG;
     *out = nullptr;
@@ -613,6 +625,7 @@ int ea_set_schedule(ea_ctx *c, const uint64_t *t_w, int n_tw, const uint64_t *t,
 
 int ea_quench(ea_ctx *c, double T, int rule)
 {
+    NvtxRange nvtx_range("ea_quench");
     if (check_ctx(c))
         return EA_ERR_INVALID_ARG;
     uint64_t thr[7];
@@ -639,6 +652,7 @@ int ea_quench(ea_ctx *c, double T, int rule)
 
 int ea_sweep(ea_ctx *c, uint64_t n)
 {
+    NvtxRange nvtx_range("ea_sweep");
     if (check_ctx(c))
         return EA_ERR_INVALID_ARG;
     if (!c->quenched)
@@ -673,6 +687,7 @@ int ea_time(const ea_ctx *c, uint64_t *t)
 
 int ea_measure(ea_ctx *c, uint64_t t_w, uint64_t t, ea_obs *out)
 {
+    NvtxRange nvtx_range("ea_measure");
     if (check_ctx(c) || !out)
         return EA_ERR_INVALID_ARG;
     if (!c->quenched)
@@ -790,6 +805,7 @@ int ea_c4_radial_bins(int L, int *n_bins)
 
 int ea_c4_radial(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts)
 {
+    NvtxRange nvtx_range("ea_c4_radial");
     if (check_ctx(c) || !sums || !counts)
         return EA_ERR_INVALID_ARG;
     if (c->L > ea::kC4FullMaxL)
@@ -1069,6 +1085,7 @@ bool read_dev(FILE *f, void *dev, size_t bytes, cudaStream_t s)
 
 int ea_checkpoint(ea_ctx *c, const char *path)
 {
+    NvtxRange nvtx_range("ea_checkpoint");
     if (check_ctx(c) || !path)
         return EA_ERR_INVALID_ARG;
     if (!c->quenched)
@@ -1553,6 +1570,7 @@ extern "C" {
 
 int ea_batch_sweep(ea_batch *b, uint64_t n)
 {
+    NvtxRange nvtx_range("ea_batch_sweep");
     if (!b)
         return EA_ERR_INVALID_ARG;
     return batch_sweep_impl(b, n, nullptr);
@@ -1646,6 +1664,7 @@ int ea_batch_profile(ea_batch *b, int sweeps, uint64_t out[4])
 
 int ea_batch_autotune(ea_batch *b, int trial_sweeps)
 {
+    NvtxRange nvtx_range("ea_batch_autotune");
     if (!b || trial_sweeps < 1)
         return EA_ERR_INVALID_ARG;
     if (b->members.empty())
@@ -1854,6 +1873,7 @@ int ea_server_submit(ea_server *srv, const ea_job_spec *spec, int64_t *job_id)
 
 int ea_server_step(ea_server *srv, int *n_finished)
 {
+    NvtxRange nvtx_range("ea_server_step");
     if (!srv)
         return EA_ERR_INVALID_ARG;
     if (n_finished)
