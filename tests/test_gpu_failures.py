@@ -2,6 +2,7 @@
 cancelled jobs, calls out of order.  The library must return clean status codes,
 leak nothing, and leave other jobs' results unchanged."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -96,3 +97,25 @@ def test_server_keeps_unadmittable_jobs_queued_and_cancels(J):
     with pytest.raises(_lib.EAError):
         srv.cancel(c)
     srv.close()
+
+
+def test_library_job_continues_from_its_checkpoint(J, tmp_path):
+    """The recovery runner on the library: a job stopped after its first chunk and
+    continued from its checkpoint gives every scheduled sum of an uninterrupted run."""
+    import torch.distributed as dist
+    from paper_1411_5512_gb300 import recovery
+    spec = dict(L=32, p_neg=0.5, seed=5, n_samples=2, T=0.7, rule=0, sweeps=20,
+                t_w=[0, 8], t=[0, 4, 12])
+    with pytest.raises(RuntimeError):
+        recovery._run_job(0, spec, recovery.LibraryRunner, str(tmp_path), 8, lambda: None,
+                          resume=False, fail_after=1)
+    resumed = recovery._run_job(0, spec, recovery.LibraryRunner, str(tmp_path), 8,
+                                lambda: None, resume=True)
+    fresh = recovery._run_job(1, spec, recovery.LibraryRunner, str(tmp_path), 20,
+                              lambda: None, resume=False)
+    assert resumed == fresh and len(fresh) == 6
+    # one rank, the whole list through the coordinator
+    os.makedirs(str(tmp_path / "all"))
+    res = recovery.run_jobs([spec, dict(spec, seed=6, rule=1)], 0, 1, dist.HashStore(),
+                            str(tmp_path / "all"), chunk=7)
+    assert sorted(res) == [0, 1] and res[0] == fresh
