@@ -1843,7 +1843,7 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
     p.block_begin[0] = 0;
     int n_geo = 0;
     int geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
-    // tile kernel: rows per thread from the launch shape, halved (down to 2)
+    // tile kernels: rows per thread from the launch shape, halved (down to 2)
     // while the launch would hold fewer than four blocks per SM
     int y_max = 16;
     if (GL != 0) {
@@ -1853,6 +1853,10 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
                      host[i].geo.n[1];
         while (y_max > 2 && tiles / y_max / kSweepThreads < 4L * kTileMinSMs)
             y_max >>= 1;
+        // a launch that would not even give every SM a block takes single rows:
+        // the lone samples of a serving tail run at the latency of short rows
+        if (y_max == 2 && tiles / 2 / kSweepThreads < kTileMinSMs)
+            y_max = 1;
     }
     for (int i = 0; i < cnt; ++i) {
         const JobDev &jd = host[i];

@@ -126,11 +126,12 @@ def test_sweeps_bit_exact(J, L, p_neg, T, rule, G, S, n):
 # including temperatures where many words take the rare path and its later draws
 TILE_CASES = [
     # L, p_neg, T, cols_per_thread (segments of 4, 8, 16 rows; launches of fewer than
-    # four blocks per SM take shorter segments, down to 2 rows), S, sweeps
+    # four blocks per SM take shorter segments, down to 2 rows, and launches of fewer
+    # than one block per SM single rows), S, sweeps
     (128, 0.5, 0.7, 4, 80, 2),  # 16 rows
     (128, 0.4, 1.2, 2, 40, 2),  # 8 rows
     (64, 0.5, 0.9, 1, 160, 2),  # 4 rows
-    (64, 0.5, 0.7, 1, 2, 4),    # the small cases: 2 rows
+    (64, 0.5, 0.7, 1, 2, 4),    # the small cases: 1 row
     (64, 0.3, 2.0, 2, 2, 3),
     (64, 0.5, 5.0, 4, 2, 3),
     (64, 0.5, 0.0, 2, 1, 3),   # T = 0: no random numbers
