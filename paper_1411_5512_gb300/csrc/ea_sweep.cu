@@ -1,27 +1,35 @@
 // ea_sweep.cu -- the checkerboard half-step kernels (Sec. III) over a table of jobs.
 //
-// One thread updates a column of word-sites (x', y', z' = 0..n2-1) of one
-// sample in half-step h.  Every word-site of area h is updated (it holds the
-// replica whose colour is due in half-step h, Fig. 1), so a column is a run of
-// contiguous work with its z-neighbours in a register window.
+// In half-step h every word-site of area h is updated (it holds the replica
+// whose colour is due in half-step h, Fig. 1); its neighbours are read from
+// area 1 - h.  The kernels differ in how threads share that work:
+//   metro_kernel, heat_kernel      a column of word-sites along z per thread,
+//                                  any side, z-neighbours in a register window;
+//   metro_tile_kernel,             2 x 2 word tiles over a segment of rows per
+//   heat_tile_kernel               thread, sides 64 and 128 (all lanes along z);
+//   metro_gtile_kernel             the same tiles for the other sides divisible
+//                                  by 16 (lanes along y and z).
 //
 // Per word (32 sites of one sample):
 //   u_j = s ^ n_j ^ J_j for the six bonds (1 = unsatisfied)         6 LOP3
 //   bit-sliced count (b2 b1 b0) = u                                 8 LOP3
-//   dE = 12 - 4u (Eq. 9): u >= 3 (dE <= 0) flips outright.
-//   Metropolis (metro_kernel): the lanes of class u = 0, 1, 2 (dE = 12, 8,
-//     4) flip independently with p_u = exp(-dE/T); taken in lane order they
-//     form a Bernoulli sequence whose first acceptance rank is geometric, so
-//     one 64-bit draw V per class decides: no flip when V >= C_u[n] (n lanes
-//     in the class), else the lane of rank min{g : V < C_u[g+1]}, after which
-//     the remaining lanes take the next draw.  One Philox call per pair of
-//     words holds the leading 32 (class 2) and 16 (classes 1, 0) bits of
-//     their first draws, enough to settle ~97% of words at T = 0.7 without a
-//     branch; the rest of a draw is fetched only when the test hits.
-//   Heat bath (heat_kernel): one Philox call per word holds a coin word for
-//     dE = 0 and the leading bits of the first gap draws of the other six
-//     classes; classes dE > 0 flip the lanes the gaps select, classes dE < 0
-//     keep them (P(dE) + P(-dE) = 1).
+//   dE = 12 - 4u (Eq. 9).
+//   Metropolis: u >= 3 (dE <= 0) flips outright.  The lanes of class u = 0, 1,
+//     2 (dE = 12, 8, 4) flip independently with p_u = exp(-dE/T); taken in lane
+//     order they form a Bernoulli sequence whose first acceptance rank is
+//     geometric, so one 64-bit draw V per class decides: no flip when
+//     V >= C_u[n] (n lanes in the class), else the lane of rank
+//     min{g : V < C_u[g+1]}, after which the remaining lanes take the next
+//     draw.  One Philox call per 2 x 2 quad of words holds the leading 12
+//     (class 2) and 10 (classes 1, 0) bits of their first draws, enough to
+//     settle ~97% of words at T = 0.7 without a branch; the rest of a draw is
+//     fetched only when the test hits.
+//   Heat bath: one Philox call per word holds a coin word for dE = 0 and the
+//     leading bits of the first gap draws of the other six classes; classes
+//     dE > 0 flip the lanes the gaps select, classes dE < 0 keep them
+//     (P(dE) + P(-dE) = 1).
+// Words whose leading bits might select a lane wait in a per-warp queue and
+// are finished 32 at a time (the rare path), so it runs converged.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
