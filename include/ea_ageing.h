@@ -244,6 +244,19 @@ int ea_set_spins(ea_ctx *ctx, int s, int a, const int8_t *in);
 int ea_set_couplings(ea_ctx *ctx, int s, const int8_t *in);
 int ea_set_time(ea_ctx *ctx, uint64_t t);
 
+/* The couplings of every sample in the library's packed layout, moved in one
+ * copy: words J[s][d][w], s < n_samples, d = x, y, z, w < words (the word
+ * lattice of ea_geometry); bit b of J[s][d][w] is 1 when the bond from the
+ * site at word-site w, lane b, to its +e_d neighbour is J = -1.  Lanes past
+ * the word's sites (fewer than 32 lanes, small L) are 0.  n_words =
+ * n_samples * 3 * words.  get copies device to host; set copies host to
+ * device (bits outside the lanes: EA_ERR_INVALID_ARG) and replaces the
+ * couplings drawn by ea_create_samples.  Both synchronise the job's stream;
+ * pinned host memory makes the copy a single DMA. */
+int ea_coupling_words(const ea_ctx *ctx, size_t *n_words);
+int ea_get_coupling_words(ea_ctx *ctx, uint32_t *host_words);
+int ea_set_coupling_words(ea_ctx *ctx, const uint32_t *host_words);
+
 /* Thresholds in use (as ea_thresholds).  EA_ERR_STATE before ea_quench. */
 int ea_get_thresholds(const ea_ctx *ctx, uint64_t thr[7], uint8_t always[7]);
 

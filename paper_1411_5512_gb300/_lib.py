@@ -86,6 +86,9 @@ SIGNATURES = {
     "ea_set_spins": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, i8p]),
     "ea_set_couplings": (ctypes.c_int, [vp, ctypes.c_int, i8p]),
     "ea_set_time": (ctypes.c_int, [vp, ctypes.c_uint64]),
+    "ea_coupling_words": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "ea_get_coupling_words": (ctypes.c_int, [vp, vp]),
+    "ea_set_coupling_words": (ctypes.c_int, [vp, vp]),
     "ea_get_thresholds": (ctypes.c_int, [vp, u64p, u8p]),
     "ea_checkpoint": (ctypes.c_int, [vp, ctypes.c_char_p]),
     "ea_restore": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_char_p, vp]),

@@ -1018,6 +1018,39 @@ int ea_set_couplings(ea_ctx *c, int s, const int8_t *in)
     return EA_OK;
 }
 
+int ea_coupling_words(const ea_ctx *c, size_t *n_words)
+{
+    if (!c || !n_words)
+        return EA_ERR_INVALID_ARG;
+    *n_words = (size_t)c->S * 3 * c->geo.words;
+    return EA_OK;
+}
+
+int ea_get_coupling_words(ea_ctx *c, uint32_t *host_words)
+{
+    if (check_ctx(c) || !host_words)
+        return EA_ERR_INVALID_ARG;
+    EA_CUDA(c, cudaMemcpyAsync(host_words, c->J, c->J_bytes, cudaMemcpyDeviceToHost, c->stream));
+    EA_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EA_OK;
+}
+
+int ea_set_coupling_words(ea_ctx *c, const uint32_t *host_words)
+{
+    if (check_ctx(c) || !host_words)
+        return EA_ERR_INVALID_ARG;
+    const uint32_t valid = c->geo.valid;
+    if (valid != 0xffffffffu) {  // lanes past the word's sites must stay 0
+        const size_t n = (size_t)c->S * 3 * c->geo.words;
+        for (size_t i = 0; i < n; ++i)
+            if (host_words[i] & ~valid)
+                return fail(c, EA_ERR_INVALID_ARG, "coupling word with bits outside its lanes");
+    }
+    EA_CUDA(c, cudaMemcpyAsync(c->J, host_words, c->J_bytes, cudaMemcpyHostToDevice, c->stream));
+    EA_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EA_OK;
+}
+
 int ea_set_time(ea_ctx *c, uint64_t t)
 {
     if (check_ctx(c))

@@ -52,6 +52,16 @@ def use_cuda_allocator():
     _torch_alloc_refs = None
 
 
+def _host_ptr(buf, n_words):
+    """Address of a host buffer of n_words 32-bit words (numpy array or torch tensor)."""
+    if hasattr(buf, "data_ptr"):  # torch
+        assert not buf.is_cuda and buf.element_size() == 4 and buf.numel() == n_words
+        assert buf.is_contiguous()
+        return buf.data_ptr()
+    assert buf.dtype.itemsize == 4 and buf.size == n_words and buf.flags["C_CONTIGUOUS"]
+    return buf.ctypes.data
+
+
 def launch_count():
     """Kernel launches the library has issued in this process (a replayed graph
     counts the kernels it holds)."""
@@ -178,6 +188,26 @@ class EAJob:
         arr = np.ascontiguousarray(J, dtype=np.int8)
         assert arr.shape == (3,) + (self.L,) * 3
         _lib.check(self.lib.ea_set_couplings(self.h, int(s), arr.ctypes.data_as(_lib.i8p)),
+                   self.h)
+
+    def coupling_words(self, out=None):
+        """All samples' couplings in the packed layout (uint32 words, see the C header);
+        `out` may be a numpy array or a (pinned) torch tensor of that many 32-bit words."""
+        n = ctypes.c_size_t()
+        _lib.check(self.lib.ea_coupling_words(self.h, ctypes.byref(n)), self.h)
+        if out is None:
+            out = np.zeros(n.value, dtype=np.uint32)
+        _lib.check(self.lib.ea_get_coupling_words(self.h, ctypes.c_void_p(_host_ptr(out, n.value))),
+                   self.h)
+        return out
+
+    def set_coupling_words(self, words):
+        """Replace the couplings by packed words from host memory (numpy array or
+        torch tensor, 32-bit)."""
+        n = ctypes.c_size_t()
+        _lib.check(self.lib.ea_coupling_words(self.h, ctypes.byref(n)), self.h)
+        _lib.check(self.lib.ea_set_coupling_words(self.h,
+                                                  ctypes.c_void_p(_host_ptr(words, n.value))),
                    self.h)
 
     def set_time(self, t):

@@ -554,3 +554,24 @@ def test_exact_count_job_runs_like_the_oracle(J):
         ora.sweeps(L, seed, s, Sref, Jc, T, 0, 0, n)
         assert np.array_equal(j.all_spins(s), Sref), s
     j.close()
+
+
+def test_coupling_words_move_whole_disorder(J):
+    """The packed couplings of one job set into another reproduce every bond; words with
+    bits outside their lanes (side 6: one site per word) are refused."""
+    from paper_1411_5512_gb300 import _lib
+    a = J.EAJob(16, 0.3, 5, 2)
+    b = J.EAJob(16, 0.3, 99, 2)
+    words = a.coupling_words()
+    assert words.size == 2 * 3 * (16 ** 3 // 32)
+    b.set_coupling_words(words)
+    for s in range(2):
+        assert np.array_equal(a.couplings(s), b.couplings(s))
+        assert np.array_equal(b.couplings(s), ora.init_couplings(16, 0.3, 5, s))
+    c = J.EAJob(6, 0.5, 1, 1)
+    w6 = c.coupling_words()
+    w6[3] |= np.uint32(2)
+    with pytest.raises(_lib.EAError):
+        c.set_coupling_words(w6)
+    for j in (a, b, c):
+        j.close()
