@@ -179,9 +179,9 @@ N_SM = 152
 # dram__bytes_write.sum, one pass, caches flushed before each captured launch;
 # profiles/launches_bench_L128_S16x5.md, mean of three launches).  Take them
 # again (or set None) when the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.01e6, 2: 108.34e6 + 3.39e6, 4: 110.50e6 + 5.60e6}
-# The same for the heat-bath tile kernel on the heat-bath leg, shape 1 (4 rows).
-HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.14e6}
+TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.12e6, 2: 108.77e6 + 3.54e6, 4: 110.37e6 + 5.53e6}
+# The same for the heat-bath tile kernel on the heat-bath leg, shapes 1 and 2.
+HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.14e6, 2: 106.37e6 + 3.18e6}
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
