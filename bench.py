@@ -166,7 +166,7 @@ def run_reference(args, world, rank):
 # ----------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------
-# integer ops per word update of the Metropolis sweep (see DESIGN.md):
+# integer ops per word update of the Metropolis sweep:
 # 6 LOP3 bond bits + 8 LOP3 count + 4 accept/flip/store + 5 class masks
 # + 3 class tests x (popc, table load, compare, branch)
 OPS_FIXED_PER_WORD = 35
@@ -177,8 +177,8 @@ N_SM = 152
 # per launch shape (rows per thread 4, 8, 16 <-> --cpt 1, 2, 4), from an ncu
 # capture of this command with that fixed shape (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass, caches flushed before each captured launch;
-# profiles/launches_bench_L128_S16x5.md, mean of three launches).  Take them
-# again (or set None) when the kernel changes.
+# mean of three launches).  Take them again (or set None) when the kernel
+# changes.
 TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.12e6, 2: 108.77e6 + 3.54e6, 4: 110.37e6 + 5.53e6}
 # The same for the heat-bath tile kernel on the heat-bath leg, shapes 1 and 2.
 HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.14e6, 2: 106.37e6 + 3.18e6}
