@@ -152,8 +152,11 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "L128_p0.5-0.1_S16x5_T0.7 (CPU oracle, bounded sample)",
-                       "L": 128, "samples": 1, "sweeps_per_step": per_step},
+            "config": {"workload": "L128_p0.5-0.1_S16x5_T0.7", "L": 128,
+                       "jobs": [0.5, 0.4, 0.3, 0.2, 0.1], "samples": 80, "replicas": 2,
+                       "rule": "metropolis", "rng_group": 1, "sweeps_per_step": per_step,
+                       "path": "the CPU oracle on one host thread, each step a bounded sample "
+                               "of the workload (cpu_baseline.sample)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d steps x sample 0 of the L=128 p_neg=0.5 job x %d "
                                        "sweeps x 2 replicas" % (args.steps, per_step)},
