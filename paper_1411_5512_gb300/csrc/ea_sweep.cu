@@ -43,15 +43,6 @@ namespace {
 
 using dev::maj3;
 using dev::realign;
-using dev::sel;
-
-// bitwise 8-way select on (b2 b1 b0) of f[0..6], f[7] = 0
-__device__ __forceinline__ uint32_t mux7(uint32_t b2, uint32_t b1, uint32_t b0, const uint32_t f[7])
-{
-    const uint32_t m0 = sel(b0, f[1], f[0]), m1 = sel(b0, f[3], f[2]), m2 = sel(b0, f[5], f[4]),
-                   m3 = ~b0 & f[6];
-    return sel(b2, sel(b1, m3, m2), sel(b1, m1, m0));
-}
 
 struct Axis {
     int sA[2], sB[2];
@@ -72,21 +63,6 @@ __device__ __forceinline__ void load_axis(Axis &a, const Geo &g, int d)
         a.mA[dir] = g.mA[d][dir];
         a.mB[dir] = g.mB[d][dir];
     }
-}
-
-// Block -> job of the table (the last j with block_begin[j] <= blockIdx.x).
-__device__ __forceinline__ int find_job(const int *__restrict__ block_begin, int n_jobs)
-{
-    int lo = 0, hi = n_jobs - 1;
-    const int b = (int)blockIdx.x;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (block_begin[mid] <= b)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
 }
 
 // The bit-sliced count u = 4 b2 + 2 b1 + b0 of six unsatisfied-bond bits.
@@ -971,6 +947,39 @@ struct GTileGeo {
     Axis ay, az;
 };
 
+// The class count of word w (spins s, at (x, y, z)) from the neighbour area,
+// with the y and z wraps realigned.
+__device__ __forceinline__ Count gtile_count(int w, uint32_t s, int x, int y, int z,
+                                             const uint32_t *__restrict__ nb,
+                                             const uint32_t *__restrict__ Jx,
+                                             const uint32_t *__restrict__ Jy,
+                                             const uint32_t *__restrict__ Jz, const GTileGeo &gg)
+{
+    const int n0 = gg.n0, n1 = gg.n1, n2 = gg.n2, sz = n0 * n1;
+    const int wxp = x == n0 - 1 ? w - (n0 - 1) : w + 1;
+    const int wxm = x == 0 ? w + (n0 - 1) : w - 1;
+    const int wyp = y == n1 - 1 ? w - (n1 - 1) * n0 : w + n0;
+    const int wym = y == 0 ? w + (n1 - 1) * n0 : w - n0;
+    const int wzp = z == n2 - 1 ? w - (n2 - 1) * sz : w + sz;
+    const int wzm = z == 0 ? w + (n2 - 1) * sz : w - sz;
+    uint32_t nyp = nb[wyp], nym = nb[wym], jym = Jy[wym];
+    uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
+    if (y == n1 - 1)
+        nyp = fixup(nyp, gg.ay, 0);
+    if (y == 0) {
+        nym = fixup(nym, gg.ay, 1);
+        jym = fixup(jym, gg.ay, 1);
+    }
+    if (z == n2 - 1)
+        nzp = fixup(nzp, gg.az, 0);
+    if (z == 0) {
+        nzm = fixup(nzm, gg.az, 1);
+        jzm = fixup(jzm, gg.az, 1);
+    }
+    return count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nyp ^ Jy[w], s ^ nym ^ jym,
+                  s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
+}
+
 __device__ __forceinline__ void gtile_finish(const JobDev *__restrict__ jb, const TileTables &tb,
                                              const uint4 &e, uint32_t *__restrict__ upd,
                                              const uint32_t *__restrict__ nb,
@@ -982,35 +991,12 @@ __device__ __forceinline__ void gtile_finish(const JobDev *__restrict__ jb, cons
                                              uint32_t c1, uint32_t c2m, uint32_t c3,
                                              const uint32_t (&rk)[20], unsigned int &calls)
 {
-    const int n0 = gg.n0, n1 = gg.n1, n2 = gg.n2, sz = n0 * n1;
+    const int n0 = gg.n0, n1 = gg.n1;
     const int w = (int)e.x;
     const uint32_t s = e.y, M = e.z, M2 = e.w;
     const int x = w % n0, r = w / n0, y = r % n1, z = r / n1;
     const uint32_t c2 = c2m | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
-    const auto recount = [&]() -> Count {
-        const int wxp = x == n0 - 1 ? w - (n0 - 1) : w + 1;
-        const int wxm = x == 0 ? w + (n0 - 1) : w - 1;
-        const int wyp = y == n1 - 1 ? w - (n1 - 1) * n0 : w + n0;
-        const int wym = y == 0 ? w + (n1 - 1) * n0 : w - n0;
-        const int wzp = z == n2 - 1 ? w - (n2 - 1) * sz : w + sz;
-        const int wzm = z == 0 ? w + (n2 - 1) * sz : w - sz;
-        uint32_t nyp = nb[wyp], nym = nb[wym], jym = Jy[wym];
-        uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
-        if (y == n1 - 1)
-            nyp = fixup(nyp, gg.ay, 0);
-        if (y == 0) {
-            nym = fixup(nym, gg.ay, 1);
-            jym = fixup(jym, gg.ay, 1);
-        }
-        if (z == n2 - 1)
-            nzp = fixup(nzp, gg.az, 0);
-        if (z == 0) {
-            nzm = fixup(nzm, gg.az, 1);
-            jzm = fixup(jzm, gg.az, 1);
-        }
-        return count6(s ^ nb[wxp] ^ Jx[w], s ^ nb[wxm] ^ Jx[wxm], s ^ nyp ^ Jy[w], s ^ nym ^ jym,
-                      s ^ nzp ^ Jz[w], s ^ nzm ^ jzm);
-    };
+    const auto recount = [&]() -> Count { return gtile_count(w, s, x, y, z, nb, Jx, Jy, Jz, gg); };
     tile_finish_at(jb, tb, w, s, M, M2, c2, upd, live0, live1, live2, always3, T1x, T0, c1, c3, rk,
                    calls, recount);
 }
@@ -1508,9 +1494,10 @@ __global__ void __launch_bounds__(kSweepThreads, 8)
     }
 }
 
-// Heat bath for a table whose jobs all have side GL = 64 or 128: the tiles
-// of the Metropolis tile kernel (2 x 2 word-sites times a segment of rows),
-// one main call per word.  A queued word holds (word-site, spins before the
+// Heat bath for a table whose jobs all have side GL = 64 or 128, or (GL =
+// kGeneralTile) the other sides of the general tile kernel, with the word
+// lattice read at run time: the tiles of the Metropolis tile kernels (2 x 2
+// word-sites times a segment of rows), one main call per word.  A queued word holds (word-site, spins before the
 // update); its rare path counts its classes again from the neighbour area,
 // which this half-step does not write, and draws its main call again.
 template <int GL>
@@ -1549,14 +1536,35 @@ __device__ __forceinline__ void heat_tile_finish(const JobDev *__restrict__ jb, 
                                  hl, calls);
 }
 
+// The rare path of a queued heat-bath word of a run-time lattice.
+__device__ __forceinline__ void heat_gtile_finish(const JobDev *__restrict__ jb, const uint4 &e,
+                                                  uint32_t *__restrict__ upd,
+                                                  const uint32_t *__restrict__ nb,
+                                                  const uint32_t *__restrict__ Jx,
+                                                  const uint32_t *__restrict__ Jy,
+                                                  const uint32_t *__restrict__ Jz,
+                                                  const GTileGeo &gg, int h, uint32_t c1,
+                                                  uint32_t c2h, uint32_t c3,
+                                                  const uint32_t (&rk)[20], const int (*hl)[33],
+                                                  unsigned int &calls)
+{
+    const int w = (int)e.x;
+    const uint32_t s = e.y;
+    const int x = w % gg.n0, r = w / gg.n0, y = r % gg.n1, z = r / gg.n1;
+    const uint32_t c2 = c2h | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
+    const Count c = gtile_count(w, s, x, y, z, nb, Jx, Jy, Jz, gg);
+    upd[w] = s ^ heat_word_flips(jb, (uint32_t)w, c.b2, c.b1, c.b0, c2, 0xffffffffu, c1, c3, rk,
+                                 hl, calls);
+}
+
 template <bool COUNT, int MAXJ, int GL, bool LOWT>
 __global__ void __launch_bounds__(kSweepThreads, 7)
     heat_tile_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
 {
+    constexpr bool GEN = GL == kGeneralTile;  // the word lattice read at run time
     constexpr int N2 = GL / 32, SZ = GL * GL;
     constexpr int XP = GL / 2, ZP = N2 / 2;
     constexpr int XPLOG = GL == 128 ? 6 : 5;
-    constexpr uint32_t W = (uint32_t)SZ * N2;
     int j = 0;
     {
         int lo = 0, hi = P.n_jobs - 1;
@@ -1602,10 +1610,41 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
     const int Y = G.seg;
     const int local = (int)blockIdx.x - P.block_begin[j];
     const int s = local / G.bps;
-    const int tl = (local - s * G.bps) * kSweepThreads + (int)threadIdx.x;
-    const int x0 = 2 * (tl & (XP - 1));
-    const int z0 = 2 * ((tl >> XPLOG) & (ZP - 1));  // uniform over a warp (XP >= 32)
-    const int y0 = (tl >> XPLOG) / ZP * Y;
+    int tl = (local - s * G.bps) * kSweepThreads + (int)threadIdx.x;
+    // lattice of words n0 x n1 x n2, compile-time for sides 64 and 128
+    const int n0 = GEN ? G.n0 : GL, n1 = GEN ? G.n1 : GL, n2 = GEN ? G.n2 : N2;
+    const int sz = n0 * n1;
+    const uint32_t W = GEN ? G.words : (uint32_t)SZ * N2;
+    GTileGeo gg;
+    bool act = true;  // threads past the sample's last tile run on a valid tile, write nothing
+    int x0, z0, y0;
+    if constexpr (GEN) {
+        gg.n0 = n0;
+        gg.n1 = n1;
+        gg.n2 = n2;
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            gg.ay.sA[dir] = G.ysA[dir];
+            gg.ay.sB[dir] = G.ysB[dir];
+            gg.ay.mA[dir] = G.ymA[dir];
+            gg.ay.mB[dir] = G.ymB[dir];
+            gg.az.sA[dir] = G.zsA[dir];
+            gg.az.sB[dir] = G.zsB[dir];
+            gg.az.mA[dir] = G.zmA[dir];
+            gg.az.mB[dir] = G.zmB[dir];
+        }
+        const int xp = n0 >> 1, zp = n2 >> 1;
+        act = tl < xp * zp * (n1 / Y);
+        if (!act)
+            tl = 0;
+        x0 = 2 * (tl % xp);
+        z0 = 2 * ((tl / xp) % zp);
+        y0 = tl / xp / zp * Y;
+    } else {
+        x0 = 2 * (tl & (XP - 1));
+        z0 = 2 * ((tl >> XPLOG) & (ZP - 1));  // uniform over a warp (XP >= 32)
+        y0 = (tl >> XPLOG) / ZP * Y;
+    }
     uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
     const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
@@ -1614,23 +1653,44 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
     const uint32_t c3 = (uint32_t)s / J.rng_group;
     const uint32_t c1 = (uint32_t)t;
     const uint32_t c2h = dev::kStreamHeat | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
-    const int oz0 = z0 * SZ, oz1 = oz0 + SZ;
-    const int ozm = (z0 == 0 ? N2 - 1 : z0 - 1) * SZ;
-    const int ozp = (z0 + 2 == N2 ? 0 : z0 + 2) * SZ;
-    const bool wrap_m = z0 == 0, wrap_p = z0 + 2 == N2;
-    const int xm = (x0 - 1) & (GL - 1), xq = (x0 + 2) & (GL - 1);
+    const int oz0 = z0 * sz, oz1 = oz0 + sz;
+    const int ozm = (z0 == 0 ? n2 - 1 : z0 - 1) * sz;
+    const int ozp = (z0 + 2 == n2 ? 0 : z0 + 2) * sz;
+    const bool wrap_m = z0 == 0, wrap_p = z0 + 2 == n2;
+    int xm, xq;
+    if constexpr (GEN) {
+        xm = x0 == 0 ? n0 - 1 : x0 - 1;
+        xq = x0 + 2 == n0 ? 0 : x0 + 2;
+    } else {
+        xm = (x0 - 1) & (GL - 1);
+        xq = (x0 + 2) & (GL - 1);
+    }
     unsigned int n_words = 0, n_extra = 0;
 
-    const int rym = ((y0 - 1) & (GL - 1)) * GL;
+    // the window; with a run-time lattice the row above a segment that starts
+    // at y = 0 lies across the y wrap
+    const int rym = GEN ? (y0 == 0 ? n1 - 1 : y0 - 1) * n0 : ((y0 - 1) & (GL - 1)) * GL;
     uint2 Nm0 = ld2(nb, x0 + rym + oz0), Nm1 = ld2(nb, x0 + rym + oz1);
     uint2 Jym0 = ld2(Jy, x0 + rym + oz0), Jym1 = ld2(Jy, x0 + rym + oz1);
-    uint2 Nc0 = ld2(nb, x0 + y0 * GL + oz0), Nc1 = ld2(nb, x0 + y0 * GL + oz1);
+    if (GEN && y0 == 0) {
+        Nm0 = make_uint2(fixup(Nm0.x, gg.ay, 1), fixup(Nm0.y, gg.ay, 1));
+        Nm1 = make_uint2(fixup(Nm1.x, gg.ay, 1), fixup(Nm1.y, gg.ay, 1));
+        Jym0 = make_uint2(fixup(Jym0.x, gg.ay, 1), fixup(Jym0.y, gg.ay, 1));
+        Jym1 = make_uint2(fixup(Jym1.x, gg.ay, 1), fixup(Jym1.y, gg.ay, 1));
+    }
+    uint2 Nc0 = ld2(nb, x0 + y0 * n0 + oz0), Nc1 = ld2(nb, x0 + y0 * n0 + oz1);
     for (int i = 0; i < Y; ++i) {
         const int y = y0 + i;
-        const int ry = y * GL, ryp = ((y + 1) & (GL - 1)) * GL;
+        const bool wrap_y = GEN && y + 1 == n1;  // only on a segment's last row
+        const int ry = y * n0;
+        const int ryp = GEN ? (wrap_y ? 0 : ry + n0) : ((y + 1) & (GL - 1)) * GL;
         const int w0 = x0 + ry + oz0, w1 = x0 + ry + oz1;  // the even-x words at z0, z0 + 1
         const uint2 S0 = ld2(upd, w0), S1 = ld2(upd, w1);
-        const uint2 Nn0 = ld2(nb, x0 + ryp + oz0), Nn1 = ld2(nb, x0 + ryp + oz1);
+        uint2 Nn0 = ld2(nb, x0 + ryp + oz0), Nn1 = ld2(nb, x0 + ryp + oz1);
+        if (wrap_y) {
+            Nn0 = make_uint2(fixup(Nn0.x, gg.ay, 0), fixup(Nn0.y, gg.ay, 0));
+            Nn1 = make_uint2(fixup(Nn1.x, gg.ay, 0), fixup(Nn1.y, gg.ay, 0));
+        }
         uint2 Nzm = ld2(nb, x0 + ry + ozm), Nzp = ld2(nb, x0 + ry + ozp);
         uint2 Jzm = ld2(Jz, x0 + ry + ozm);
         const uint32_t Xm0 = nb[xm + ry + oz0], Xm1 = nb[xm + ry + oz1];
@@ -1639,12 +1699,21 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
         const uint2 Jx0 = ld2(Jx, w0), Jx1 = ld2(Jx, w1);
         const uint2 Jy0 = ld2(Jy, w0), Jy1 = ld2(Jy, w1);
         const uint2 Jz0 = ld2(Jz, w0), Jz1 = ld2(Jz, w1);
-        if (wrap_m) {
-            Nzm = make_uint2(rot_zm(Nzm.x), rot_zm(Nzm.y));
-            Jzm = make_uint2(rot_zm(Jzm.x), rot_zm(Jzm.y));
+        if constexpr (GEN) {
+            if (wrap_m) {
+                Nzm = make_uint2(fixup(Nzm.x, gg.az, 1), fixup(Nzm.y, gg.az, 1));
+                Jzm = make_uint2(fixup(Jzm.x, gg.az, 1), fixup(Jzm.y, gg.az, 1));
+            }
+            if (wrap_p)
+                Nzp = make_uint2(fixup(Nzp.x, gg.az, 0), fixup(Nzp.y, gg.az, 0));
+        } else {
+            if (wrap_m) {
+                Nzm = make_uint2(rot_zm(Nzm.x), rot_zm(Nzm.y));
+                Jzm = make_uint2(rot_zm(Jzm.x), rot_zm(Jzm.y));
+            }
+            if (wrap_p)
+                Nzp = make_uint2(rot_zp(Nzp.x), rot_zp(Nzp.y));
         }
-        if (wrap_p)
-            Nzp = make_uint2(rot_zp(Nzp.x), rot_zp(Nzp.y));
         // replica of word (x0, y, z0); the other three alternate with x and z
         const uint32_t c2a = c2h | ((uint32_t)(h ^ (y & 1)) << 11);
         const uint32_t c2b = c2a ^ (1u << 11);
@@ -1700,13 +1769,15 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
             out[k] = v ^ ((m3 & R.x) | c.b2);
         }
         // every word is written; a queued word is written again by the rare path
-        *reinterpret_cast<uint2 *>(upd + w0) = make_uint2(out[0], out[1]);
-        *reinterpret_cast<uint2 *>(upd + w1) = make_uint2(out[2], out[3]);
-        if (COUNT)
-            n_words += 4;
+        if (act) {
+            *reinterpret_cast<uint2 *>(upd + w0) = make_uint2(out[0], out[1]);
+            *reinterpret_cast<uint2 *>(upd + w1) = make_uint2(out[2], out[3]);
+            if (COUNT)
+                n_words += 4;
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (hit[k])
+            if (act && hit[k])
                 q[atomicAdd(qn, 1)] = make_uint4(wd[k], sp[k], 0u, 0u);
         __syncwarp();
         int q_n = *qn;
@@ -1715,7 +1786,12 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
                 q_n -= 32;
                 const uint4 e = q[q_n + lane];
                 unsigned int extra = 0;
-                heat_tile_finish<GL>(jb, e, upd, nb, Jx, Jy, Jz, h, c1, c2h, c3, rk, s_hl, extra);
+                if constexpr (GEN)
+                    heat_gtile_finish(jb, e, upd, nb, Jx, Jy, Jz, gg, h, c1, c2h, c3, rk, s_hl,
+                                      extra);
+                else
+                    heat_tile_finish<GL>(jb, e, upd, nb, Jx, Jy, Jz, h, c1, c2h, c3, rk, s_hl,
+                                         extra);
                 if (COUNT)
                     n_extra += extra;
                 __syncwarp();
@@ -1732,8 +1808,12 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
         const int wq = g < n0q ? 0 : g < n1q ? 1 : g < n2q ? 2 : 3;
         const int off = g - (wq == 0 ? 0 : wq == 1 ? n0q : wq == 2 ? n1q : n2q);
         unsigned int extra = 0;
-        heat_tile_finish<GL>(jb, s_q[wq][off], upd, nb, Jx, Jy, Jz, h, c1, c2h, c3, rk, s_hl,
-                             extra);
+        if constexpr (GEN)
+            heat_gtile_finish(jb, s_q[wq][off], upd, nb, Jx, Jy, Jz, gg, h, c1, c2h, c3, rk,
+                              s_hl, extra);
+        else
+            heat_tile_finish<GL>(jb, s_q[wq][off], upd, nb, Jx, Jy, Jz, h, c1, c2h, c3, rk,
+                                 s_hl, extra);
         if (COUNT)
             n_extra += extra;
     }
@@ -1993,6 +2073,14 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
                 launch_metro_chunk<8, 128, true>(h, d, c, n, stream, counters);
             else
                 launch_metro_chunk<kMetroMaxJobs, 128, true>(h, d, c, n, stream, counters);
+        } else if (HEAT && GLR == kGeneralTile) {
+            if (c <= 8)
+                launch_metro_chunk<8, kGeneralTile, true>(h, d, c, n, stream, counters);
+            else if (c <= 128)
+                launch_metro_chunk<128, kGeneralTile, true>(h, d, c, n, stream, counters);
+            else
+                launch_metro_chunk<kMetroMaxJobs, kGeneralTile, true>(h, d, c, n, stream,
+                                                                      counters);
         } else if (HEAT && GLR == 64) {
             if (c <= 8)
                 launch_metro_chunk<8, 64, true>(h, d, c, n, stream, counters);
@@ -2105,7 +2193,7 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
             return err;
     }
     Run hruns[4];
-    const int n_hruns = split_runs(host1, n_jobs1, false, hruns);
+    const int n_hruns = split_runs(host1, n_jobs1, true, hruns);
     for (int r = 0; r < n_hruns; ++r)
         launch_metro_run<true>(host1 + hruns[r].first, dev1 + hruns[r].first, hruns[r].cnt,
                                hruns[r].GLR, n, stream, counters);

@@ -211,7 +211,12 @@ HEAT_CASES = [
     (128, 0.1, 0.7, 4, 2, 2),
     (64, 0.3, 1.0, 2, 5, 3),
     (64, 0.5, 6.0, 1, 2, 2),
-    (48, 0.5, 0.7, 2, 2, 3),
+    (48, 0.5, 0.7, 2, 2, 3),     # the general tiles (run-time lattice)
+    (96, 0.4, 1.5, 1, 2, 2),
+    (32, 0.5, 0.7, 4, 5, 3),
+    (80, 0.5, 3.0, 2, 2, 2),     # many rare paths
+    (16, 0.5, 0.7, 1, 3, 3),     # the column kernel
+    (24, 0.3, 0.9, 2, 2, 3),
 ]
 
 
