@@ -116,14 +116,21 @@ __global__ void c4f_expand_kernel(const uint32_t *__restrict__ snap, Geo g, int 
                                   uint32_t *__restrict__ R, uint32_t one, uint32_t p)
 {
     const int L = g.L;
-    const size_t N = (size_t)L * L * L;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lg = __ffs(L) - 1;  // L = 2^lg here, N < 2^31
+    const uint32_t N = (uint32_t)L * L * L;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N)
         return;
     const int c = blockIdx.y;
     const uint32_t *a0 = snap + (size_t)(s0 + c) * 2 * g.words;
-    const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / ((size_t)L * L));
-    R[(size_t)c * N + i] = q_bit(a0, g, x, y, z) ? p - one : one;
+    const int x = (int)(i & (L - 1)), y = (int)((i >> lg) & (L - 1)), z = (int)(i >> (2 * lg));
+    // the word-site and lane of (x, y, z): every extent here is a power of two
+    const int sx = __ffs(g.n[0]) - 1, sy = __ffs(g.n[1]) - 1, sz = __ffs(g.n[2]) - 1;
+    const int kx = __ffs(g.k[0]) - 1, ky = __ffs(g.k[1]) - 1;
+    const int w = (x & (g.n[0] - 1)) | ((y & (g.n[1] - 1)) << sx) | ((z & (g.n[2] - 1)) << (sx + sy));
+    const int lane = (x >> sx) | ((y >> sy) << kx) | ((z >> sz) << (kx + ky));
+    const uint32_t b = ((a0[w] ^ a0[g.words + w]) >> lane) & 1u;
+    R[(size_t)c * N + i] = b ? p - one : one;
 }
 
 // Address of element e of line g along an axis (0 x, 1 y, 2 z) of one sample.
