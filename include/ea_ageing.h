@@ -7,11 +7,12 @@
  * One context ("job") holds n_samples disorder samples of an L^3 periodic
  * lattice, each with two replicas that share the couplings (Sec. II, Eq. 2),
  * quenched from a random start (Sec. II) and evolved by single-spin-flip
- * Metropolis sweeps in checkerboard order (Sec. III, Eq. 9).  Measurements of
- * the autocorrelation C(t, t_w) (Eq. 7), the replica overlap q (Eq. 2), the
- * four-point correlation C4(r, t_w) (Eq. 3) along the lattice axes and the
- * integral estimator xi_1 (Eqs. 5-6) are taken on the device at the times of a
- * schedule.
+ * Metropolis sweeps in checkerboard order (Sec. III, Eq. 9), or by the
+ * heat-bath rule.  Measurements of the autocorrelation C(t, t_w) (Eq. 7), the
+ * replica overlap q (Eq. 2), the four-point correlation C4(r, t_w) (Eq. 3)
+ * along the lattice axes and the integral estimator xi_1 (Eqs. 5-6) are taken
+ * on the device at the times of a schedule; C4 over every displacement vector
+ * is computed on request from the snapshots (ea_c4_radial).
  *
  * Conventions shared by every call:
  *   - Every function returns an int status: EA_OK (0) or a negative EA_ERR_*.
@@ -90,21 +91,26 @@ const char *ea_status_string(int status);
  * kx = min(32/(kz*ky), p2).  EA_ERR_INVALID_ARG for odd L or L outside [2,1024]. */
 int ea_geometry(int L, int out[6]);
 
-/* Acceptance thresholds for dE = 4k - 12, k = 0..6.  A move is accepted when
- * always[k] != 0 or when the 64-bit uniform random number r < thr[k], so with
- * probability floor(2^64 P(dE)) / 2^64, where P is min(1, exp(-dE/T)) for
+/* Flip probabilities for dE = 4k - 12, k = 0..6, as 64-bit fixed point:
+ * thr[k] = floor(2^64 P(dE)), where P is min(1, exp(-dE/T)) for
  * EA_RULE_METROPOLIS (Eq. 9) and 1/(1 + exp(dE/T)) for EA_RULE_HEATBATH;
- * P = 1 sets always[k].  T = 0 and T = +inf give the limits.  Both arrays are
- * caller-owned.  EA_ERR_INVALID_ARG for T < 0, NaN T or an unknown rule. */
+ * P = 1 sets always[k] (and thr[k] = 0).  T = 0 and T = +inf give the limits.
+ * The sweeps realise these probabilities class by class: the sites of a
+ * word-site with one dE are decided by geometric gaps (ea_geo_table; for the
+ * heat bath with dE < 0 the gaps select the sites that keep their spin), and
+ * the heat bath's dE = 0 sites by a fair coin.  Both arrays are caller-owned.
+ * EA_ERR_INVALID_ARG for T < 0, NaN T or an unknown rule. */
 int ea_thresholds(double T, int rule, uint64_t thr[7], uint8_t always[7]);
 
-/* Geometric-gap table of the Metropolis update: C[g] = floor(2^64 (1 - (1 -
- * p)^g)) for g = 0..32 (clamped to 2^64 - 1), computed as floor(ldexp(-expm1(g
+/* Geometric-gap table of the updates: C[g] = floor(2^64 (1 - (1 - p)^g)) for
+ * g = 0..32 (clamped to 2^64 - 1), computed as floor(ldexp(-expm1(g
  * log1p(-p)), 64)).  Among the n sites of one word-site with the same dE > 0,
- * each flipping independently with p = exp(-dE/T) (Eq. 9), a 64-bit uniform V
- * gives no flip when V >= C[n], else a first flip at rank min{g : V < C[g+1]}
- * in increasing lane order; the sites after it start a fresh gap with the next
- * draw.  EA_ERR_INVALID_ARG unless 0 < p < 1.  Host-only. */
+ * each selected independently with probability p (Metropolis: the flip
+ * probability exp(-dE/T), Eq. 9; heat bath: 1/(1 + exp(dE/T)), which also
+ * selects the sites that keep their spin at -dE), a 64-bit uniform V selects
+ * none when V >= C[n], else the site of rank min{g : V < C[g+1]} in increasing
+ * lane order; the sites after it start a fresh gap with the next draw.
+ * EA_ERR_INVALID_ARG unless 0 < p < 1.  Host-only. */
 int ea_geo_table(double p, uint64_t C[33]);
 
 /* Device bytes a context with this shape and schedule will hold (spins,
