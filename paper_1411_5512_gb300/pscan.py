@@ -12,6 +12,9 @@ measured curves:
 - xi_1(t_w) with the fitted tail;
 - z from both xi series;
 - x from C(t, t_w) on t in [100, t_w / 1000].
+- the error bars of alpha and beta as Sec. IV makes them: the multifit on the
+  axis points against the multifit on every displacement vector with
+  3 <= r <= L/2 (ea_c4_radial), their difference plus both statistical errors.
 The paper's p is 1 - p_neg.  The table is printed, and the raw curves are
 written to --out.
 """
@@ -54,14 +57,19 @@ def run(L, samples, T, log2_sweeps, pnegs, seed0=300):
     curves = []
     for p, j in zip(pnegs, jobs):
         c4 = {}
+        c4_all = {}
         C = {}
         for tw in t_w:
             m = j.measure(tw, 0)
             c4[tw] = (m["C4"], m["C4_sem"], m["r_cut"])
+            if tw >= 10:
+                rad = j.c4_radial(tw)
+                keep = rad["r"] <= L // 2
+                c4_all[tw] = (rad["r"][keep], rad["C4"][keep], rad["C4_sem"][keep])
             for lag in lags:
                 if tw + lag <= total and lag > 0 and tw > 0:
                     C[(tw, lag)] = j.measure(tw, lag)["C"]
-        curves.append({"pneg": p, "c4": c4, "C": C})
+        curves.append({"pneg": p, "c4": c4, "c4_all": c4_all, "C": C})
     b.close()
     for j in jobs:
         j.close()
@@ -82,8 +90,18 @@ def analyse(L, curves, tw_min=10):
         except (ValueError, RuntimeError, np.linalg.LinAlgError):
             rows.append({"pneg": cur["pneg"], "p": 1.0 - cur["pneg"], "alpha": np.nan,
                          "beta": np.nan, "z_fit": np.nan, "z_int": np.nan, "x": np.nan,
-                         "xi_fit_last": np.nan, "xi_int_last": np.nan, "chi2_dof": np.nan})
+                         "xi_fit_last": np.nan, "xi_int_last": np.nan, "chi2_dof": np.nan,
+                         "alpha_err": np.nan, "beta_err": np.nan})
             continue
+        # the error bars of Sec. IV from the axis points and every displacement vector
+        a_err = b_err = np.nan
+        if all(tw in cur.get("c4_all", {}) for tw in tws):
+            try:
+                e = an.multifit_error([(r, cur["c4"][tw][0], cur["c4"][tw][1]) for tw in tws],
+                                      [cur["c4_all"][tw] for tw in tws], r_min=3)
+                a_err, b_err = e["alpha_err"], e["beta_err"]
+            except (ValueError, RuntimeError, np.linalg.LinAlgError):
+                pass
         xi_fit = fit["xi"]
         xi_int = []
         for k, tw in enumerate(tws):
@@ -106,7 +124,7 @@ def analyse(L, curves, tw_min=10):
         rows.append({"pneg": cur["pneg"], "p": 1.0 - cur["pneg"], "alpha": fit["alpha"],
                      "beta": fit["beta"], "z_fit": zf, "z_int": zi, "x": x,
                      "xi_fit_last": float(xi_fit[-1]), "xi_int_last": float(xi_int[-1]),
-                     "chi2_dof": fit["chi2_dof"]})
+                     "chi2_dof": fit["chi2_dof"], "alpha_err": a_err, "beta_err": b_err})
     return rows
 
 
@@ -126,9 +144,9 @@ def main(argv=None):
     print("| p | p_neg | alpha | beta | z (fit) | z (xi_1) | x | xi(t_w max), fit / xi_1 |")
     print("|---|---|---|---|---|---|---|---|")
     for row in rows:
-        print("| %.2f | %.2f | %.3f | %.3f | %.2f | %.2f | %.4f | %.1f / %.1f |" % (
-            row["p"], row["pneg"], row["alpha"], row["beta"], row["z_fit"], row["z_int"],
-            row["x"], row["xi_fit_last"], row["xi_int_last"]))
+        print("| %.2f | %.2f | %.3f(%.3f) | %.3f(%.3f) | %.2f | %.2f | %.4f | %.1f / %.1f |" % (
+            row["p"], row["pneg"], row["alpha"], row["alpha_err"], row["beta"], row["beta_err"],
+            row["z_fit"], row["z_int"], row["x"], row["xi_fit_last"], row["xi_int_last"]))
     if a.out:
         flat = {}
         for cur in curves:
