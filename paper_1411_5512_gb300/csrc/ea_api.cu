@@ -416,8 +416,6 @@ int fire_measurements(ea_ctx *c)
     ++c->res_gen;
     const size_t S = (size_t)c->S, R = (size_t)c->R();
     const size_t area = c->area_words();
-    EA_CUDA(c, ea::launch_obs_state(c->spins, c->J, c->geo, c->S, c->res + c->off_q + mi * S,
-                                    c->res + c->off_u + mi * S * 2, c->stream));
     const int ti = idx_of(c->tw, c->t);
     if (ti >= 0) {
         EA_CUDA(c, cudaMemcpyAsync(c->snaps + ti * area, c->spins, area * sizeof(uint32_t),
@@ -425,14 +423,29 @@ int fire_measurements(ea_ctx *c)
         EA_CUDA(c, ea::launch_obs_c4(c->spins, c->geo, c->S, c->res + c->off_g + ti * S * 3 * R,
                                      c->stream));
     }
+    // the state sums and every autocorrelation due at this time, one pass over
+    // the state per launch of up to kObsMaxSnaps snapshots
+    ea::ObsTimeParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.spins = c->spins;
+    p.J = c->J;
+    p.q_pop = c->res + c->off_q + mi * S;
+    p.u_pop = c->res + c->off_u + mi * S * 2;
     for (size_t i = 0; i < c->tw.size() && c->tw[i] <= c->t; ++i) {
         const int j = idx_of(c->tt, c->t - c->tw[i]);
         if (j < 0)
             continue;
-        const size_t slot = c->off_a + (i * c->tt.size() + (size_t)j) * S * 2;
-        EA_CUDA(c, ea::launch_obs_autocorr(c->snaps + i * area, c->spins, c->geo, c->S,
-                                           c->res + slot, c->stream));
+        p.snap[p.n_snap] = c->snaps + i * area;
+        p.a_pop[p.n_snap] = c->res + c->off_a + (i * c->tt.size() + (size_t)j) * S * 2;
+        if (++p.n_snap == ea::kObsMaxSnaps) {
+            EA_CUDA(c, ea::launch_obs_time(p, c->geo, c->S, c->stream));
+            p.q_pop = nullptr;  // the state sums went with the first launch
+            p.u_pop = nullptr;
+            p.n_snap = 0;
+        }
     }
+    if (p.n_snap > 0 || p.q_pop != nullptr)
+        EA_CUDA(c, ea::launch_obs_time(p, c->geo, c->S, c->stream));
     return EA_OK;
 }
 

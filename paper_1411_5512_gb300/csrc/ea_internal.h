@@ -218,12 +218,21 @@ cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int n_samples, uint
                               cudaStream_t stream);
 
 // observable sums (popcounts) accumulated with integer atomics
-cudaError_t launch_obs_state(const uint32_t *spins, const uint32_t *J, const Geo &g, int n_samples,
-                             unsigned long long *q_pop /*[S]*/, unsigned long long *u_pop /*[S][2]*/,
-                             cudaStream_t stream);
-cudaError_t launch_obs_autocorr(const uint32_t *snap, const uint32_t *spins, const Geo &g,
-                                int n_samples, unsigned long long *a_pop /*[S][2]*/,
-                                cudaStream_t stream);
+// The observables of one measurement time (ea_kernels.cu: obs_time_kernel):
+// the state sums and the comparisons with up to kObsMaxSnaps snapshots.
+constexpr int kObsMaxSnaps = 16;
+constexpr int kObsThreads = 256;
+struct ObsTimeParams {
+    const uint32_t *spins;     // [S][2][words]
+    const uint32_t *J;         // [S][3][words]
+    unsigned long long *q_pop; // [S] (NULL: no state sums in this launch)
+    unsigned long long *u_pop; // [S][2]
+    int n_snap;
+    const uint32_t *snap[kObsMaxSnaps];       // snapshots, [S][2][words] each
+    unsigned long long *a_pop[kObsMaxSnaps];  // [S][2] each
+};
+cudaError_t launch_obs_time(const ObsTimeParams &p, const Geo &g, int n_samples,
+                            cudaStream_t stream);
 cudaError_t launch_obs_c4(const uint32_t *spins, const Geo &g, int n_samples,
                           unsigned long long *g_pop /*[S][3][L/2+1]*/, cudaStream_t stream);
 

@@ -222,75 +222,85 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long v)
     return tot;
 }
 
-// q_pop[s] += popc(area0 ^ area1) (= number of sites where the replicas differ);
-// u_pop[s][a] += unsatisfied bonds of replica a.
-__global__ void obs_state_kernel(const uint32_t *__restrict__ spins, const uint32_t *__restrict__ J,
-                                 Geo g, unsigned long long *q_pop, unsigned long long *u_pop)
+// Everything a measurement time takes from the current state, in one pass over
+// it: q_pop[s] += popc(area0 ^ area1) (the sites where the replicas differ),
+// u_pop[s][a] += the unsatisfied bonds of replica a, and for each listed
+// snapshot a_pop[k][s][a] += the sites where replica a differs from it.  With
+// q_pop NULL only the snapshot comparisons run (a list longer than one
+// launch holds).
+__global__ void __launch_bounds__(kObsThreads)
+    obs_time_kernel(const __grid_constant__ ObsTimeParams P, Geo g)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int kAcc = 3 + 2 * kObsMaxSnaps;
     const int s = blockIdx.y;
     const size_t W = (size_t)g.words;
-    unsigned long long q = 0, ua[2] = {0, 0};
-    if (w < g.words) {
+    const uint32_t *__restrict__ area0 = P.spins + (size_t)s * 2 * W;
+    const uint32_t *__restrict__ area1 = area0 + W;
+    const uint32_t *__restrict__ Js = P.J + (size_t)s * 3 * W;
+    const bool state = P.q_pop != nullptr;
+    uint32_t acc[kAcc];
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i)
+        acc[i] = 0u;
+    const int step[3] = {1, g.n[0], g.n[0] * g.n[1]};
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < g.words;
+         w += gridDim.x * blockDim.x) {
         int xw, yw, zw;
         word_coords(g, w, xw, yw, zw);
-        const int c = (xw + yw + zw) & 1;
-        const uint32_t *area[2] = {spins + (size_t)s * 2 * W, spins + ((size_t)s * 2 + 1) * W};
-        const uint32_t *Js = J + (size_t)s * 3 * W;
-        q = __popc(area[0][w] ^ area[1][w]);
-        const int step[3] = {1, g.n[0], g.n[0] * g.n[1]};
-        const int coord[3] = {xw, yw, zw};
+        const int c = (xw + yw + zw) & 1;  // area h at w holds replica h ^ c
+        const uint32_t cur[2] = {area0[w], area1[w]};
+        if (state) {
+            acc[0] += __popc(cur[0] ^ cur[1]);
+            const int coord[3] = {xw, yw, zw};
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const uint32_t sa = area[a ^ c][w];
-            const uint32_t *nbarea = area[a ^ c ^ 1];  // replica a at the other colour
+            for (int a = 0; a < 2; ++a) {
+                const uint32_t sa = cur[a ^ c];
+                const uint32_t *nbarea = (a ^ c) ? area0 : area1;  // replica a, other colour
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                uint32_t nbw;
-                if (coord[d] + 1 < g.n[d])
-                    nbw = nbarea[w + step[d]];
-                else
-                    nbw = realign(nbarea[w - (g.n[d] - 1) * step[d]], g, d, 0);
-                ua[a] += __popc((sa ^ nbw ^ Js[d * W + w]) & g.valid);
+                for (int d = 0; d < 3; ++d) {
+                    const uint32_t nbw = coord[d] + 1 < g.n[d]
+                                             ? nbarea[w + step[d]]
+                                             : realign(nbarea[w - (g.n[d] - 1) * step[d]], g, d, 0);
+                    acc[1 + a] += __popc((sa ^ nbw ^ Js[d * W + w]) & g.valid);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kObsMaxSnaps; ++k) {
+            if (k < P.n_snap) {
+                const uint32_t *__restrict__ sn = P.snap[k] + (size_t)s * 2 * W;
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+                    acc[3 + 2 * k + a] += __popc(sn[(size_t)(a ^ c) * W + w] ^ cur[a ^ c]);
             }
         }
     }
-    const unsigned long long tq = block_sum(q);
-    if (threadIdx.x == 0 && tq)
-        atomicAdd(&q_pop[s], tq);
-    const unsigned long long t0 = block_sum(ua[0]);
-    if (threadIdx.x == 0 && t0)
-        atomicAdd(&u_pop[2 * s], t0);
-    const unsigned long long t1 = block_sum(ua[1]);
-    if (threadIdx.x == 0 && t1)
-        atomicAdd(&u_pop[2 * s + 1], t1);
-}
-
-// a_pop[s][a] += sites where replica a differs from its snapshot
-__global__ void obs_autocorr_kernel(const uint32_t *__restrict__ snap,
-                                    const uint32_t *__restrict__ spins, Geo g,
-                                    unsigned long long *a_pop)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    const size_t W = (size_t)g.words;
-    unsigned long long d[2] = {0, 0};
-    if (w < g.words) {
-        int xw, yw, zw;
-        word_coords(g, w, xw, yw, zw);
-        const int c = (xw + yw + zw) & 1;
+    // one block reduction for all accumulators: warps first, then one thread each
+    __shared__ unsigned long long s_part[kAcc][kObsThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n_acc = 3 + 2 * P.n_snap;
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const size_t off = ((size_t)s * 2 + (a ^ c)) * W + w;
-            d[a] = __popc(snap[off] ^ spins[off]);
+    for (int i = 0; i < kAcc; ++i) {
+        if (i < n_acc) {
+            unsigned long long v = acc[i];
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                s_part[i][wid] = v;
         }
     }
-    const unsigned long long t0 = block_sum(d[0]);
-    if (threadIdx.x == 0 && t0)
-        atomicAdd(&a_pop[2 * s], t0);
-    const unsigned long long t1 = block_sum(d[1]);
-    if (threadIdx.x == 0 && t1)
-        atomicAdd(&a_pop[2 * s + 1], t1);
+    __syncthreads();
+    const int i = (int)threadIdx.x;
+    if (i < n_acc && (i >= 3 || state)) {
+        unsigned long long tot = 0;
+        for (int k = 0; k < kObsThreads / 32; ++k)
+            tot += s_part[i][k];
+        unsigned long long *dst = i == 0  ? P.q_pop + s
+                                  : i < 3 ? P.u_pop + 2 * s + (i - 1)
+                                          : P.a_pop[(i - 3) / 2] + 2 * s + ((i - 3) & 1);
+        if (tot)
+            atomicAdd(dst, tot);
+    }
 }
 
 __device__ __forceinline__ uint32_t low_bits(int n)
@@ -593,19 +603,11 @@ cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int n_samples, uint
     return cudaGetLastError();
 }
 
-cudaError_t launch_obs_state(const uint32_t *spins, const uint32_t *J, const Geo &g, int n_samples,
-                             unsigned long long *q_pop, unsigned long long *u_pop,
-                             cudaStream_t stream)
+cudaError_t launch_obs_time(const ObsTimeParams &p, const Geo &g, int n_samples,
+                            cudaStream_t stream)
 {
-    obs_state_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(spins, J, g, q_pop, u_pop);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_obs_autocorr(const uint32_t *snap, const uint32_t *spins, const Geo &g,
-                                int n_samples, unsigned long long *a_pop, cudaStream_t stream)
-{
-    obs_autocorr_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(snap, spins, g, a_pop);
+    const unsigned bx = (unsigned)std::max(1, (g.words + 4 * kObsThreads - 1) / (4 * kObsThreads));
+    obs_time_kernel<<<dim3(bx, (unsigned)n_samples), kObsThreads, 0, stream>>>(p, g);
     count_launches(1);
     return cudaGetLastError();
 }

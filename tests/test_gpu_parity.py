@@ -336,6 +336,19 @@ def test_observables_match_oracle(J, L, p_neg, T, S):
     j.close()
 
 
+@pytest.mark.parametrize("L,S", [(8, 2), (64, 1)])
+def test_dense_schedule_more_snapshots_than_one_pass(J, L, S):
+    """Every sweep a waiting time and a lag: up to 23 autocorrelations fall due at one
+    time, more than one pass over the state holds (16), so a time takes two."""
+    t_w = list(range(0, 23))
+    t = list(range(0, 23))
+    n = 22
+    j = gpu_run(J, L, 0.5, 9, S, 0.8, 0, t_w, t, n)
+    out = ora.run_job(L, 0.5, 9, S, 0.8, 0, t_w, t, n)
+    compare_job(j, out, L, list(range(S)), t_w, t, n)
+    j.close()
+
+
 def test_tiny_workload_full_length(J):
     w = workloads.TINY
     j = gpu_run(J, w["L"], w["p_neg"], w["seed"], w["n_samples"], w["T"], 0, w["t_w"], w["t"],
