@@ -453,10 +453,10 @@ int check_ctx(const ea_ctx *c) { return c ? EA_OK : EA_ERR_INVALID_ARG; }
 
 }  // namespace
 
-// Launch shape of the Metropolis kernel: enough blocks to fill the GPU a few
-// times over for one job, fewer per-thread set-ups for large lattices.  Sides
-// 64 and 128 take the tile kernel, whose threads already hold 4 rows of 2 x 2
-// word-sites at the smallest shape.
+// Default launch shape of the sweep kernels: enough blocks to fill the GPU a
+// few times over for one job, fewer per-thread set-ups for large lattices.
+// Sides 64 and 128 take their tile kernels, whose threads already hold 4 rows
+// of 2 x 2 word-sites at the smallest shape.
 static int default_cols_per_thread(const Geo &g)
 {
     if (g.L == 64 || g.L == 128)

@@ -107,7 +107,7 @@ constexpr int kSweepThreads = 128;
 struct MetroGeo {
     int n0, n1, n2, cols;
     int bps, cpt;          // blocks per sample, word columns per thread
-    int seg;               // rows per thread of the side-64/128 tile kernel
+    int seg;               // rows per thread of the tile kernels
     uint32_t words;        // words per area
     uint32_t valid, magic;
     int dshift;
@@ -156,7 +156,7 @@ uint64_t launches_total();
 
 // Two side streams and the events that fork them from a launching stream and
 // join them back: independent runs of a table then share the GPU.
-// Sides whose Metropolis half-steps take the general tile kernel: every lane
+// Sides whose half-steps take the general tiles (both rules): every lane
 // along y and z (L divisible by 16), enough tiles per sample to fill a block
 // (L >= 32), and not the sides with their own tile kernels (64, 128).
 inline bool general_tile_side(int L)
