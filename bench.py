@@ -184,7 +184,7 @@ N_SM = 152
 # changes.
 TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.12e6, 2: 108.77e6 + 3.54e6, 4: 110.37e6 + 5.53e6}
 # The same for the heat-bath tile kernel on the heat-bath leg, shapes 1 and 2.
-HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.14e6, 2: 106.37e6 + 3.18e6}
+HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.16e6, 2: 106.33e6 + 3.12e6}
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
@@ -443,7 +443,11 @@ def run_heat(args, job, workloads, stream, flush):
     b = job.EABatch(stream=stream)
     for j in jobs:
         b.add(j)
-    cfg = b.autotune(trial_sweeps=8)
+    if args.cpt:  # a fixed launch shape (for a traffic capture of that shape)
+        b.configure(args.cpt, args.graph_sweeps)
+        cfg = (args.cpt, args.graph_sweeps)
+    else:
+        cfg = b.autotune(trial_sweeps=8)
     prof = b.profile(sweeps=4)
     n = args.sweeps_per_step
     b.sweep(n)
