@@ -134,13 +134,14 @@ int ora_site_to_word(int L, int x, int y, int z, uint32_t *widx, int *lane)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Acceptance thresholds, one per energy change dE = 4k - 12, k = 0..6.     */
-/* A move with energy change dE is accepted when always[k] is set, or when  */
-/* r < thr[k] for the 64-bit uniform r above, i.e. with probability         */
-/* thr[k] / 2^64 = floor(2^64 P(dE)) / 2^64.                                */
+/* Flip probabilities, one per energy change dE = 4k - 12, k = 0..6, as     */
+/* 64-bit fixed point: thr[k] = floor(2^64 P(dE)), always[k] when P == 1.    */
 /*   rule 0, Metropolis (Eq. 9):  P = min(1, exp(-dE/T))                    */
 /*   rule 1, heat bath:           P = 1 / (1 + exp(dE/T))                   */
-/* P == 1 sets always[k].  T = 0 and T = +inf are the limits of P.          */
+/* T = 0 and T = +inf are the limits of P.  The half-step realises these    */
+/* probabilities class by class (geometric gaps below; the heat bath's      */
+/* dE = 0 by a coin); here always[k] marks the outright Metropolis classes  */
+/* and thr[k] == 0 a class that never flips.                                */
 /* ------------------------------------------------------------------------ */
 int ora_thresholds(double T, int rule, uint64_t thr[7], uint8_t always[7])
 {
