@@ -77,7 +77,8 @@ def _ckpt(ckpt_dir, i):
 
 def _run_job(i, spec, runner_factory, ckpt_dir, chunk, beat, resume, fail_after=None):
     """Run job i to its end in chunks, checkpointing after each; beat() after each
-    chunk.  fail_after: stop (raise) after that many chunks (for tests)."""
+    chunk.  fail_after: stop (raise) once that many chunks are done, 0 before the
+    first (for tests)."""
     r = runner_factory(spec)
     path = _ckpt(ckpt_dir, i)
     try:
@@ -87,13 +88,13 @@ def _run_job(i, spec, runner_factory, ckpt_dir, chunk, beat, resume, fail_after=
             r.start()
         chunks = 0
         while r.time() < spec["sweeps"]:
+            if fail_after is not None and chunks >= fail_after:
+                raise RuntimeError("rank stopped on purpose after %d chunks" % chunks)
             r.advance(min(chunk, spec["sweeps"] - r.time()))
             r.save(path + ".tmp")
             os.replace(path + ".tmp", path)
             chunks += 1
             beat()
-            if fail_after is not None and chunks >= fail_after:
-                raise RuntimeError("rank stopped on purpose after %d chunks" % chunks)
         return r.result()
     finally:
         r.close()

@@ -81,7 +81,9 @@ def _rank(rank, world, port, ckpt_dir, fail_rank, q):
     import torch.distributed as dist
     store = dist.TCPStore("127.0.0.1", port, world, rank == 0,
                           timeout=datetime.timedelta(seconds=60))
-    fail = 1 if rank == fail_rank else None
+    # fail_rank: the rank that stops after its first chunk; with three ranks, rank 2
+    # also stops, before any chunk
+    fail = 1 if rank == fail_rank else (0 if (world == 3 and rank == 2 and fail_rank) else None)
     try:
         res = recovery.run_jobs(JOBS, rank, world, store, ckpt_dir, runner_factory=OracleRunner,
                                 chunk=4, timeout=2.0, fail_after=fail)
@@ -122,3 +124,17 @@ def test_jobs_of_a_stopped_rank_continue_from_their_checkpoints(tmp_path, fail_r
         # chunk; its second job had none and ran from the start on rank 0
         assert os.path.exists(os.path.join(str(tmp_path), "job1.ckpt.resumed"))
         assert not os.path.exists(os.path.join(str(tmp_path), "job3.ckpt.resumed"))
+
+
+def test_two_ranks_stop_one_before_its_first_chunk(tmp_path):
+    """Three ranks: rank 1 stops after one chunk, rank 2 before any.  Rank 0 continues
+    rank 1's job from its checkpoint and runs rank 2's jobs from the start."""
+    ref = _reference()
+    res, codes = _run(3, 1, tmp_path)
+    assert sorted(res) == list(range(len(JOBS)))
+    for i in ref:
+        assert res[i] == ref[i], i
+    assert codes[0] == 0 and codes[1] == 3 and codes[2] == 3
+    assert os.path.exists(os.path.join(str(tmp_path), "job1.ckpt.resumed"))
+    # rank 2 wrote no checkpoint, so rank 0 ran its jobs from the start
+    assert not os.path.exists(os.path.join(str(tmp_path), "job2.ckpt.resumed"))
