@@ -161,3 +161,32 @@ def test_multifit_error_combines_both_point_sets():
     e2 = an.multifit_error(axis, allv2)
     assert e2["alpha_err"] >= abs(e2["fit_all"]["alpha"] - alpha) - 1e-6
     assert abs(e2["fit_all"]["alpha"] - (alpha + 0.05)) < 1e-4
+
+
+def test_pscan_analysis_on_synthetic_curves():
+    """The p-scan's analysis recovers alpha, beta, z and x from curves built from the
+    forms it fits, on the axis points and on every displacement vector."""
+    from paper_1411_5512_gb300 import pscan
+    L = 64
+    alpha, beta, z_true, x_true = 0.45, 1.4, 8.0, 0.02
+    r = np.arange(0, L // 2 + 1, dtype=np.float64)
+    r_all = np.sqrt(np.arange(0, 3 * (L // 2) ** 2 + 1, dtype=np.float64))
+    r_all = r_all[r_all <= L // 2]
+    tws = [2 ** k for k in range(4, 20)]  # x needs t_w / 1000 above 100
+    c4, c4_all, C = {}, {}, {}
+    for tw in tws:
+        xi = 1.1 * tw ** (1.0 / z_true)
+        cur = np.ones_like(r)
+        cur[1:] = an.c4_model(r[1:], 0.9, alpha, xi, beta)
+        c4[tw] = (cur, 1e-3 * cur + 1e-9, L // 2)
+        ca = np.ones_like(r_all)
+        ca[1:] = an.c4_model(r_all[1:], 0.9, alpha, xi, beta)
+        c4_all[tw] = (r_all, ca, 1e-3 * ca + 1e-9)
+        for j in range(0, 20):
+            C[(tw, 2 ** j)] = 0.7 * (2.0 ** j) ** (-x_true)
+    rows = pscan.analyse(L, [{"pneg": 0.5, "c4": c4, "c4_all": c4_all, "C": C}])
+    row = rows[0]
+    assert abs(row["alpha"] - alpha) < 1e-4 and abs(row["beta"] - beta) < 1e-4
+    assert abs(row["z_fit"] - z_true) < 1e-3
+    assert abs(row["x"] - x_true) < 1e-9
+    assert np.isfinite(row["alpha_err"]) and row["alpha_err"] < 1e-2
