@@ -237,6 +237,25 @@ def test_heat_bath_batch_bit_exact(J, L, p_neg, T, cpt, S, n):
     j.close()
 
 
+@pytest.mark.parametrize("L,rule,S", [(64, 0, 4), (64, 1, 4), (48, 0, 3), (96, 1, 2), (128, 0, 2)])
+def test_shared_random_numbers_on_the_tiles(J, L, rule, S):
+    """Pairs of samples sharing their random numbers (G = 2) through the tile kernels of
+    both rules: every sample against the oracle with the same share groups."""
+    seed, p_neg, T, n = 40 + L, 0.5, 0.8, 3
+    j = J.EAJob(L, p_neg, seed, S, rng_group=2)
+    j.quench(T, rule)
+    b = J.EABatch()
+    b.add(j)
+    b.sweep(n)
+    b.close()
+    pick = list(range(S)) if L <= 64 else [0, S - 1]
+    ref = ora.run_job(L, p_neg, seed, S, T, rule, [], [], n, samples=pick, keep_spins=True,
+                      rng_group=2)
+    for i, s in enumerate(pick):
+        assert np.array_equal(j.all_spins(s), ref["spins"][i]), s
+    j.close()
+
+
 @pytest.mark.parametrize("L,t0", [(16, (1 << 32) - 1), (64, (1 << 44) + 77)])
 def test_heat_bath_late_time(J, L, t0):
     """The high bits of the sweep counter in the heat-bath draws, from an oracle-made state."""
