@@ -1,0 +1,147 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake in a copy
+of the oracle (a dropped term, a wrong sign, index, operand or constant), on the CPU,
+and the pin suite run against that copy must fail.  The unchanged copy must pass.
+
+Planted mistakes are chosen in the arithmetic the paper fixes (Eqs. 1-3, 5-7 and 9,
+the checkerboard of Sec. III, the heat-bath rule and the gap construction that
+realises both rules), not in the random-number mapping, which is a definition of
+the library and is pinned by the GPU parity tests instead.  Every copy lives in a
+temporary directory; the oracle itself is never modified.
+"""
+import concurrent.futures
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+# (name, file in oracle/, text, replacement): the text must occur exactly once.
+MUTANTS = [
+    # Philox4x32-10 (SC'11): multiplier, key schedule, round count
+    ("philox_multiplier", "ea_oracle.c", "0xD2511F53u * (uint64_t)c[0]", "0xD2511F55u * (uint64_t)c[0]"),
+    ("philox_key_bump", "ea_oracle.c", "k[1] += 0xBB67AE85u;", "k[1] += 0xBB67AE86u;"),
+    ("philox_nine_rounds", "ea_oracle.c", "for (int r = 0; r < 10; r++)", "for (int r = 0; r < 9; r++)"),
+    # word-site geometry
+    ("geometry_kz_cap", "ea_oracle.c", "int kz = p2 < 32 ? p2 : 32;", "int kz = p2 < 16 ? p2 : 16;"),
+    ("geometry_block_origin", "ea_oracle.c", "sy[b] = ((b / kx) % ky) * Ly + yw;",
+     "sy[b] = ((b / kx) % ky) * Ly + yw + 1;"),
+    # Eq. 9 and the heat-bath rule
+    ("metropolis_sign", "ea_oracle.c", "P = exp(-(double)dE / T);", "P = exp((double)dE / T);"),
+    ("metropolis_temperature_scale", "ea_oracle.c", "P = exp(-(double)dE / T);",
+     "P = exp(-(double)dE / (2.0 * T));"),
+    ("metropolis_dE_zero", "ea_oracle.c", "            if (dE <= 0)\n                P = 1.0;",
+     "            if (dE < 0)\n                P = 1.0;"),
+    ("heatbath_sign", "ea_oracle.c", "P = 1.0 / (1.0 + exp((double)dE / T));",
+     "P = 1.0 / (1.0 + exp(-(double)dE / T));"),
+    ("heatbath_gap_probability", "ea_oracle.c", "p = 1.0 / (1.0 + exp((double)(12 - 4 * u) / T));",
+     "p = 1.0 / (1.0 + exp((double)(12 - 4 * u) / (2.0 * T)));"),
+    # the local field dE = 2 S_i sum_j J_ij S_j
+    ("field_drops_a_bond", "ea_oracle.c", "J[2 * N + izm] * Sa[izm];", "0;"),
+    ("field_backward_bond_index", "ea_oracle.c", "J[0 * N + ixm] * Sa[ixm]", "J[0 * N + i] * Sa[ixm]"),
+    ("field_direction_swap", "ea_oracle.c", "J[1 * N + i] * Sa[iyp]", "J[2 * N + i] * Sa[iyp]"),
+    ("field_sign", "ea_oracle.c", "return 2 * Sa[i] * h_loc;", "return -2 * Sa[i] * h_loc;"),
+    # the checkerboard of Sec. III
+    ("colour_two_axes", "ea_oracle.c", "if (((xw + yw + zw) & 1) != (h ^ a))", "if (((xw + yw) & 1) != (h ^ a))"),
+    # gaps: P(G >= g) = (1 - p)^g and the selection that follows
+    ("gap_table_exponent", "ea_oracle.c", "double q = -expm1((double)g * log1p(-p));",
+     "double q = -expm1((double)(g + 1) * log1p(-p));"),
+    ("gap_skips_a_site", "ea_oracle.c", "start += G + 1;", "start += G + 2;"),
+    ("gap_none_test", "ea_oracle.c", "if (V >= C[rem])", "if (V >= C[rem - 1])"),
+    ("heatbath_coin_always", "ea_oracle.c", "flip[list[i]] = (uint8_t)((coin >> list[i]) & 1u);",
+     "flip[list[i]] = 1;"),
+    ("heatbath_keep_inverted", "ea_oracle.c", "flip[list[i]] = u < 3 ? mark[list[i]] : (uint8_t)!mark[list[i]];",
+     "flip[list[i]] = mark[list[i]];"),
+    ("heatbath_wrong_pair", "ea_oracle.c", "int j = u < 3 ? u : 6 - u;\n                            uint8_t mark",
+     "int j = u < 3 ? u : u - 4;\n                            uint8_t mark"),
+    ("energy_change_sign", "ea_oracle.c", "dE_acc[a] += dE[b];", "dE_acc[a] -= dE[b];"),
+    # initial state
+    ("couplings_inverted", "ea_oracle.c", "J[d * N + i] = ((uint64_t)out[d] < thr) ? (int8_t)-1 : (int8_t)1;",
+     "J[d * N + i] = ((uint64_t)out[d] < thr) ? (int8_t)1 : (int8_t)-1;"),
+    ("exact_count_truncated", "ea_oracle.c", "floor(p_neg * 3.0 * (double)N + 0.5)", "floor(p_neg * 3.0 * (double)N)"),
+    ("replicas_share_start", "ea_oracle.c", "S[a * N + i] = (out[a] >> 31)", "S[a * N + i] = (out[0] >> 31)"),
+    # observables (Eqs. 1-3, 5-7)
+    ("overlap_one_replica", "ea_oracle.py", "np.sum(S[0].astype(np.int64) * S[1]))",
+     "np.sum(S[0].astype(np.int64) * S[0]))"),
+    ("autocorr_other_replica", "ea_oracle.py", "S_tw[a].astype(np.int64) * S_now[a]",
+     "S_tw[a].astype(np.int64) * S_now[1 - a]"),
+    ("axis_map_transposed", "ea_oracle.py", "_AXIS = {0: 2, 1: 1, 2: 0}", "_AXIS = {0: 0, 1: 1, 2: 2}"),
+    ("energy_sign", "ea_oracle.py", "E[a] = -tot", "E[a] = tot"),
+    ("c4_full_shift_axis", "ea_oracle.py", "qzy = np.roll(qz, -dy, axis=1)", "qzy = np.roll(qz, -dy, axis=0)"),
+    ("radial_unfolded", "ea_oracle.py", "m2 = np.minimum(d, L - d) ** 2", "m2 = d ** 2"),
+    ("c4_curve_sample_norm", "ea_oracle.py", "/ (3.0 * N * S)", "/ (3.0 * N)"),
+    ("c4_sem_ddof", "ea_oracle.py", "std(axis=0, ddof=1)", "std(axis=0, ddof=0)"),
+    ("cutoff_two_sigma", "ea_oracle.py", "if c4[r] < 3.0 * sem[r]:", "if c4[r] < 2.0 * sem[r]:"),
+    ("xi1_moment", "ea_oracle.py", "I2 += r * r * c4[r]", "I2 += r * c4[r]"),
+]
+
+_DRIVER = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+import oracle
+assert oracle.__file__.startswith(sys.argv[1]), oracle.__file__
+oracle.lib()
+import pytest
+sys.exit(pytest.main([sys.argv[2], "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]))
+"""
+
+
+def _copy(dst, mutant):
+    os.makedirs(os.path.join(dst, "oracle"))
+    for f in ("__init__.py", "build.py", "ea_oracle.c", "ea_oracle.py"):
+        shutil.copy(os.path.join(ORACLE, f), os.path.join(dst, "oracle", f))
+    if mutant is None:
+        return
+    _, fname, old, new = mutant
+    path = os.path.join(dst, "oracle", fname)
+    with open(path) as f:
+        src = f.read()
+    assert src.count(old) == 1, "the planted text of %s must occur once" % mutant[0]
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+
+
+def _run(dst):
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    try:
+        p = subprocess.run([sys.executable, "-c", _DRIVER, dst, PINS], cwd=dst, env=env,
+                           capture_output=True, text=True, timeout=300)
+    except subprocess.TimeoutExpired:
+        return None, "timed out"
+    return p.returncode, p.stdout + p.stderr
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    base = tmp_path_factory.mktemp("oracle_mutants")
+    cases = [("unchanged", None)] + [(m[0], m) for m in MUTANTS]
+    dirs = {}
+    for name, m in cases:
+        dirs[name] = str(base / name)
+        _copy(dirs[name], m)
+    workers = max(1, min(8, (os.cpu_count() or 1)))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        futs = {name: ex.submit(_run, dirs[name]) for name, _ in cases}
+        return {name: f.result() for name, f in futs.items()}
+
+
+def _failed_tests(log):
+    return [ln.split(" ")[1] for ln in log.splitlines() if ln.startswith("FAILED ")]
+
+
+def test_unchanged_copy_passes_the_pins(outcomes):
+    rc, log = outcomes["unchanged"]
+    assert rc == 0, log[-3000:]
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    rc, log = outcomes[name]
+    assert rc is not None, "%s: the pins did not finish" % name
+    # exit status 1: tests ran and at least one failed (not a collection or usage error)
+    assert rc == 1, "%s survived the pins (status %r)\n%s" % (name, rc, log[-3000:])
+    assert _failed_tests(log), log[-3000:]
