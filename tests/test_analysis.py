@@ -20,6 +20,26 @@ def model_curves(alpha, beta, xis, As, L=64, rel_err=1e-3):
     return curves
 
 
+def test_c4_model_hand_values():
+    """Eq. 4 with a stretched exponential, A r^-alpha exp(-(r / xi)^beta), at points
+    worked by hand."""
+    assert abs(an.c4_model(1.0, 1.0, 0.5, 2.0, 1.0) - np.exp(-0.5)) < 1e-15
+    assert abs(an.c4_model(4.0, 2.0, 0.5, 2.0, 2.0) - np.exp(-4.0)) < 1e-15  # 2 * 4^-1/2 * e^-(2^2)
+    assert abs(an.c4_model(2.0, 3.0, 1.0, 2.0, 1.0) - 1.5 * np.exp(-1.0)) < 1e-15
+
+
+def test_multifit_uses_points_from_r_min_on():
+    """Sec. IV fits r >= 3: a wrong point at r = 2 changes nothing, one at r = 3 does."""
+    alpha, beta = 0.45, 1.45
+    xis, As = [2.0, 3.1, 4.7], [0.9, 0.85, 0.8]
+    for r_bad, moves in ((2, False), (3, True)):
+        curves = model_curves(alpha, beta, xis, As)
+        for r, c, _ in curves:
+            c[r == r_bad] *= 1.5
+        fit = an.multifit_c4(curves, r_min=3)
+        assert (abs(fit["alpha"] - alpha) > 1e-4) == moves, (r_bad, fit["alpha"])
+
+
 def test_multifit_recovers_exact_parameters():
     alpha, beta = 0.45, 1.45
     xis, As = [2.0, 3.1, 4.7, 7.5], [0.9, 0.85, 0.8, 0.78]
@@ -71,11 +91,19 @@ def test_fit_x_and_mean_over_windows():
     curves = [(t_w, t, 0.7 * t ** -0.019) for t_w in (1e6, 4e6, 2e7)]
     assert abs(an.fit_x_mean(curves) - 0.019) < 1e-12
     assert np.isnan(an.fit_x_mean([(1e4, t, t ** -0.1)]))  # window [100, 10] is empty
+    # Sec. IV's window ends at t_w / 1000: a curve that bends right after it still gives x
+    bent = []
+    for t_w in (1e6, 4e6):
+        end = t_w / 1000.0
+        bent.append((t_w, t, 0.7 * t ** -0.019 * np.exp(-np.maximum(t / end - 1.0, 0.0))))
+    assert abs(an.fit_x_mean(bent) - 0.019) < 1e-12
 
 
 def test_collapse_finds_the_exponent():
+    # with a constant term, as Sec. IV fits xi(t_w): then xi(t_w + t) / xi(t_w) is not a
+    # function of t / t_w alone, and only the right scaling variable collapses the curves
     def xi_of_t(t):
-        return 1.2 * np.asarray(t, dtype=np.float64) ** 0.1
+        return 1.2 * np.asarray(t, dtype=np.float64) ** 0.1 + 0.5
 
     x_true = 0.016
     t = np.unique(np.round(np.logspace(0, 6, 60)))
@@ -160,6 +188,15 @@ def test_multifit_error_combines_both_point_sets():
              for (r, _, e_), xi, A in zip(allv, xis, As)]
     e2 = an.multifit_error(axis, allv2)
     assert e2["alpha_err"] >= abs(e2["fit_all"]["alpha"] - alpha) - 1e-6
+    # a second set with 5% longer xi: each xi error covers its difference
+    allv3 = [(r, an.c4_model(np.maximum(r, 1), A, alpha, 1.05 * xi, beta), e_)
+             for (r, _, e_), xi, A in zip(allv, xis, As)]
+    e3 = an.multifit_error(axis, allv3)
+    fa3, fb3 = e3["fit_axis"], e3["fit_all"]
+    dxi = np.abs(fa3["xi"] - fb3["xi"])
+    assert np.allclose(dxi, 0.05 * np.array(xis), rtol=1e-3)
+    assert np.all(dxi > fa3["xi_err"] + fb3["xi_err"])  # the shift dominates the fit errors
+    assert np.allclose(e3["xi_err"], dxi + fa3["xi_err"] + fb3["xi_err"], rtol=1e-12)
     assert abs(e2["fit_all"]["alpha"] - (alpha + 0.05)) < 1e-4
 
 

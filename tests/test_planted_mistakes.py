@@ -1,12 +1,16 @@
-"""The oracle's pins catch plausible mistakes: each case plants one mistake in a copy
-of the oracle (a dropped term, a wrong sign, index, operand or constant), on the CPU,
-and the pin suite run against that copy must fail.  The unchanged copy must pass.
+"""The pins catch plausible mistakes.  Each case plants one mistake in a copy of the
+code under test, on the CPU: a dropped term, a wrong sign, index, operand or
+constant.  The tests that pin that code then run against the copy and must fail;
+the unchanged copy must pass.  Two groups:
 
-Planted mistakes are chosen in the arithmetic the paper fixes (Eqs. 1-3, 5-7 and 9,
-the checkerboard of Sec. III, the heat-bath rule and the gap construction that
-realises both rules), not in the random-number mapping, which is a definition of
-the library and is pinned by the GPU parity tests instead.  Every copy lives in a
-temporary directory; the oracle itself is never modified.
+- the oracle (its C chain and its numpy observables) against the oracle's pins;
+  the mistakes lie in the arithmetic the paper fixes (Eqs. 1-3, 5-7 and 9, the
+  checkerboard of Sec. III, the heat-bath rule and the gap construction that
+  realises both rules), not in the random-number mapping, which is a definition of
+  the library and is pinned by the GPU parity tests instead;
+- the host analysis of Sec. IV (``analysis.py``) against its tests.
+
+Every copy lives in a temporary directory; the files under test are never modified.
 """
 import concurrent.futures
 import os
@@ -19,6 +23,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+ANALYSIS = os.path.join(ROOT, "paper_1411_5512_gb300", "analysis.py")
+ANALYSIS_PINS = os.path.join(ROOT, "tests", "test_analysis.py")
 
 # (name, file in oracle/, text, replacement): the text must occur exactly once.
 MUTANTS = [
@@ -79,12 +85,57 @@ MUTANTS = [
     ("xi1_moment", "ea_oracle.py", "I2 += r * r * c4[r]", "I2 += r * c4[r]"),
 ]
 
+# Mistakes in the analysis of Sec. IV: (name, text, replacement) in analysis.py.
+ANALYSIS_MUTANTS = [
+    ("model_alpha_sign", "r ** (-alpha)", "r ** (alpha)"),
+    ("model_ratio_inverted", "np.exp(-(r / xi) ** beta)", "np.exp(-(xi / r) ** beta)"),
+    ("model_beta_dropped", "np.exp(-(r / xi) ** beta)", "np.exp(-(r / xi))"),
+    ("multifit_r_min_exclusive", "keep = (r >= r_min) & (e > 0)", "keep = (r > r_min) & (e > 0)"),
+    ("multifit_unweighted", "out.append((c4_model(r, A, alpha, xi, beta) - c) / e)",
+     "out.append((c4_model(r, A, alpha, xi, beta) - c))"),
+    ("xi1_second_moment", "I2 = float(np.sum(r[inside] ** 2 * C4[inside]))",
+     "I2 = float(np.sum(r[inside] * C4[inside]))"),
+    ("xi1_tail_repeats_r_c", "rt = np.arange(int(r_c) + 1, L // 2 + 1", "rt = np.arange(int(r_c), L // 2 + 1"),
+    ("xi1_tail_short", "rt = np.arange(int(r_c) + 1, L // 2 + 1", "rt = np.arange(int(r_c) + 1, L // 2"),
+    ("xi1_tail_moment", "I2 += float(np.sum(rt ** 2 * ct))", "I2 += float(np.sum(rt * ct))"),
+    ("z_without_constant", "return a * t ** inv_z + c", "return a * t ** inv_z"),
+    ("z_inverted", 'return {"z": float(1.0 / inv_z)', 'return {"z": float(inv_z)'),
+    ("x_sign", "return float(-slope)", "return float(slope)"),
+    ("x_window", "fit_x(t, C, t_min, t_w / 1000.0)", "fit_x(t, C, t_min, t_w / 100.0)"),
+    ("collapse_sign", "np.log(C) + x * np.log(t)", "np.log(C) - x * np.log(t)"),
+    ("collapse_variable", "u = np.log(xi_of_t(t_w + t[keep]) / xi_of_t(t_w))",
+     "u = np.log(xi_of_t(t[keep]) / xi_of_t(t_w))"),
+    ("overlap_norm", "q = np.asarray(Q, dtype=np.float64).ravel() / float(N)",
+     "q = np.asarray(Q, dtype=np.float64).ravel() / float(2 * N)"),
+    ("error_without_difference", 'out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"] + fb[k + "_err"]',
+     'out[k + "_err"] = fa[k + "_err"] + fb[k + "_err"]'),
+    ("error_one_fit_only", 'out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"] + fb[k + "_err"]',
+     'out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"]'),
+    ("xi_error_without_difference", 'out["xi_err"] = np.abs(fa["xi"] - fb["xi"]) + fa["xi_err"] + fb["xi_err"]',
+     'out["xi_err"] = fa["xi_err"] + fb["xi_err"]'),
+]
+
 _DRIVER = r"""
 import sys
 sys.path.insert(0, sys.argv[1])
 import oracle
 assert oracle.__file__.startswith(sys.argv[1]), oracle.__file__
 oracle.lib()
+import pytest
+sys.exit(pytest.main([sys.argv[2], "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]))
+"""
+
+
+_ANALYSIS_DRIVER = r"""
+import importlib.util
+import sys
+sys.path.insert(0, sys.argv[3])
+import paper_1411_5512_gb300 as pkg
+spec = importlib.util.spec_from_file_location("paper_1411_5512_gb300.analysis", sys.argv[1])
+mod = importlib.util.module_from_spec(spec)
+sys.modules[spec.name] = mod
+spec.loader.exec_module(mod)
+pkg.analysis = mod
 import pytest
 sys.exit(pytest.main([sys.argv[2], "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]))
 """
@@ -105,10 +156,24 @@ def _copy(dst, mutant):
         f.write(src.replace(old, new))
 
 
-def _run(dst):
+def _copy_analysis(dst, mutant):
+    os.makedirs(dst)
+    with open(ANALYSIS) as f:
+        src = f.read()
+    if mutant is not None:
+        _, old, new = mutant
+        assert src.count(old) == 1, "the planted text of %s must occur once" % mutant[0]
+        src = src.replace(old, new)
+    path = os.path.join(dst, "analysis.py")
+    with open(path, "w") as f:
+        f.write(src)
+    return path
+
+
+def _run(args, cwd):
     env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
     try:
-        p = subprocess.run([sys.executable, "-c", _DRIVER, dst, PINS], cwd=dst, env=env,
+        p = subprocess.run([sys.executable, "-c"] + args, cwd=cwd, env=env,
                            capture_output=True, text=True, timeout=300)
     except subprocess.TimeoutExpired:
         return None, "timed out"
@@ -118,27 +183,33 @@ def _run(dst):
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
     base = tmp_path_factory.mktemp("oracle_mutants")
-    cases = [("unchanged", None)] + [(m[0], m) for m in MUTANTS]
-    dirs = {}
-    for name, m in cases:
-        dirs[name] = str(base / name)
-        _copy(dirs[name], m)
+    jobs = {}
+    for name, m in [("unchanged", None)] + [(m[0], m) for m in MUTANTS]:
+        d = str(base / ("oracle_" + name))
+        _copy(d, m)
+        jobs["oracle:" + name] = ([_DRIVER, d, PINS], d)
+    for name, m in [("unchanged", None)] + [(m[0], m) for m in ANALYSIS_MUTANTS]:
+        d = str(base / ("analysis_" + name))
+        path = _copy_analysis(d, m)
+        jobs["analysis:" + name] = ([_ANALYSIS_DRIVER, path, ANALYSIS_PINS, ROOT], d)
     workers = max(1, min(8, (os.cpu_count() or 1)))
     with concurrent.futures.ThreadPoolExecutor(workers) as ex:
-        futs = {name: ex.submit(_run, dirs[name]) for name, _ in cases}
-        return {name: f.result() for name, f in futs.items()}
+        futs = {key: ex.submit(_run, *job) for key, job in jobs.items()}
+        return {key: f.result() for key, f in futs.items()}
 
 
 def _failed_tests(log):
     return [ln.split(" ")[1] for ln in log.splitlines() if ln.startswith("FAILED ")]
 
 
-def test_unchanged_copy_passes_the_pins(outcomes):
-    rc, log = outcomes["unchanged"]
+@pytest.mark.parametrize("group", ["oracle", "analysis"])
+def test_unchanged_copy_passes_the_pins(outcomes, group):
+    rc, log = outcomes[group + ":unchanged"]
     assert rc == 0, log[-3000:]
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+@pytest.mark.parametrize("name", ["oracle:" + m[0] for m in MUTANTS] +
+                         ["analysis:" + m[0] for m in ANALYSIS_MUTANTS])
 def test_planted_mistake_fails_a_pin(outcomes, name):
     rc, log = outcomes[name]
     assert rc is not None, "%s: the pins did not finish" % name
