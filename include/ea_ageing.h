@@ -185,7 +185,8 @@ int ea_quench(ea_ctx *ctx, double T, int rule);
  * EA_ERR_INVALID_ARG (time would pass 2^48), EA_ERR_CUDA. */
 int ea_sweep(ea_ctx *ctx, uint64_t n);
 
-/* Current time (sweeps done since the quench). */
+/* Current time (sweeps done since the quench, counting sweeps still enqueued)
+ * into *t.  Host only.  Errors: EA_ERR_INVALID_ARG (NULL). */
 int ea_time(const ea_ctx *ctx, uint64_t *t);
 
 /* Read back the observables of the pair (t_w, t) into *out and derive the
@@ -236,7 +237,9 @@ int ea_c4_radial_bins(int L, int *n_bins);
  * Synchronous.  Errors: EA_ERR_INVALID_ARG, EA_ERR_STATE (before quench). */
 int ea_get_spins(ea_ctx *ctx, int s, int a, int8_t *out);
 
-/* Copy couplings of sample s into out[3][L^3] (int8 +-1, [d][z][y][x]). */
+/* Copy couplings of sample s into out[3][L^3] (int8 +-1, [d][z][y][x]; J[d] is
+ * the bond to the +e_d neighbour).  Valid from ea_create_samples on.
+ * Synchronous.  Errors: EA_ERR_INVALID_ARG (NULL, s out of range), EA_ERR_CUDA. */
 int ea_get_couplings(ea_ctx *ctx, int s, int8_t *out);
 
 /* Load a configuration (the paper stores whole configurations at its
@@ -304,14 +307,16 @@ int ea_batch_create(ea_batch **out, void *cuda_stream);
 int ea_batch_add(ea_batch *b, ea_ctx *job);
 int ea_batch_remove(ea_batch *b, ea_ctx *job);
 
-/* Number of member jobs. */
+/* Number of member jobs into *n_jobs.  Errors: EA_ERR_INVALID_ARG (NULL). */
 int ea_batch_size(const ea_batch *b, int *n_jobs);
 
 /* Launch shape used by ea_batch_sweep: work per thread of the sweep kernel
  * (1, 2 or 4; 0 = per-job default) and sweeps per captured graph (0 = direct
  * launches).  The work per thread is that many word columns, or for a table
  * whose jobs all have side 64 or 128, segments of 4, 8 or 16 rows of 2 x 2
- * word-sites.  Neither changes any result. */
+ * word-sites.  Neither changes any result.  get reads both back.  Errors:
+ * EA_ERR_INVALID_ARG (NULL, cols_per_thread other than 0, 1, 2, 4, graph_sweeps
+ * outside 0..4096). */
 int ea_batch_configure(ea_batch *b, int cols_per_thread, int graph_sweeps);
 int ea_batch_get_config(const ea_batch *b, int *cols_per_thread, int *graph_sweeps);
 
@@ -323,10 +328,12 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps);
 /* Work counts of the update, for the integer-op roofline: runs `sweeps`
  * sweeps of every member with a counting variant of the sweep kernel and
  * then puts the members' state back (time, spins), so no result changes.
- * out = {word updates, Philox4x32-10 calls, calls that took the general
- * (non-zero threshold) plane path, attempted spin flips}.  The call count is
- * per word with per-word early exit, i.e. what the algorithm needs, not what a
- * SIMT warp issues.  Synchronises the batch stream. */
+ * out = {word updates, Philox4x32-10 calls, the calls among them that the
+ * rare path makes (extension and continuation draws, beyond the main calls),
+ * attempted spin flips}.  The call count is per word with per-word early
+ * exit, i.e. what the algorithm needs, not what a SIMT warp issues.
+ * Synchronises the batch stream.  Errors: EA_ERR_INVALID_ARG (NULL, sweeps
+ * < 1), EA_ERR_CUDA, EA_ERR_OOM. */
 int ea_batch_profile(ea_batch *b, int sweeps, uint64_t out[4]);
 
 /* Run n sweeps of every member, firing each member's scheduled measurements
@@ -336,6 +343,9 @@ int ea_batch_sweep(ea_batch *b, uint64_t n);
 
 /* Destroy the batch; members return to their own streams.  NULL is accepted. */
 int ea_batch_destroy(ea_batch *b);
+
+/* Text of the last error on the batch (empty string if none or NULL); owned by
+ * the batch, valid until its next call.  Never NULL. */
 const char *ea_batch_last_error(const ea_batch *b);
 
 /* ---- serving: continuous batching of ageing jobs ---------------------------
@@ -416,10 +426,16 @@ int ea_server_release(ea_server *srv, int64_t job_id);
  * job is released.  EA_ERR_INVALID_ARG for an unknown id. */
 int ea_server_cancel(ea_server *srv, int64_t job_id);
 
+/* Counts of queued, running and done (unreleased) jobs, bytes in use, flips
+ * and steps so far, into the caller's *out.  Host only.  Errors:
+ * EA_ERR_INVALID_ARG (NULL). */
 int ea_server_get_stats(const ea_server *srv, ea_server_stats *out);
 
 /* Destroy the server and every job it still holds.  NULL is accepted. */
 int ea_server_destroy(ea_server *srv);
+
+/* Text of the last error on the server (empty string if none or NULL); owned
+ * by the server, valid until its next call.  Never NULL. */
 const char *ea_server_last_error(const ea_server *srv);
 
 #ifdef __cplusplus

@@ -286,13 +286,14 @@ class EABatch:
         _lib.check(self.lib.ea_batch_sweep(self.h, int(n)), batch=self.h)
 
     def profile(self, sweeps=4):
-        """{words, philox_calls, general_calls, flips} over `sweeps` counted sweeps
-        (the members' state is put back afterwards)."""
+        """{words, philox_calls, rare_calls, flips} over `sweeps` counted sweeps (the
+        members' state is put back afterwards).  philox_calls counts every call;
+        rare_calls the extension and continuation calls of the rare path among them."""
         out = np.zeros(4, dtype=np.uint64)
         _lib.check(self.lib.ea_batch_profile(self.h, int(sweeps), out.ctypes.data_as(_lib.u64p)),
                    batch=self.h)
         return {"words": int(out[0]), "philox_calls": int(out[1]),
-                "general_calls": int(out[2]), "flips": int(out[3])}
+                "rare_calls": int(out[2]), "flips": int(out[3])}
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h:
