@@ -221,9 +221,11 @@ def test_pscan_analysis_on_synthetic_curves():
         c4_all[tw] = (r_all, ca, 1e-3 * ca + 1e-9)
         for j in range(0, 20):
             C[(tw, 2 ** j)] = 0.7 * (2.0 ** j) ** (-x_true)
-    rows = pscan.analyse(L, [{"pneg": 0.5, "c4": c4, "c4_all": c4_all, "C": C}])
+    rows = pscan.analyse(L, [{"pneg": 0.3, "c4": c4, "c4_all": c4_all, "C": C}])
     row = rows[0]
+    assert row["pneg"] == 0.3 and abs(row["p"] - 0.7) < 1e-15  # the paper's p = 1 - p_neg
     assert abs(row["alpha"] - alpha) < 1e-4 and abs(row["beta"] - beta) < 1e-4
     assert abs(row["z_fit"] - z_true) < 1e-3
+    assert abs(row["xi_fit_last"] - 1.1 * tws[-1] ** (1.0 / z_true)) < 1e-3  # the latest t_w
     assert abs(row["x"] - x_true) < 1e-9
     assert np.isfinite(row["alpha_err"]) and row["alpha_err"] < 1e-2

@@ -8,7 +8,8 @@ the unchanged copy must pass.  Two groups:
   checkerboard of Sec. III, the heat-bath rule and the gap construction that
   realises both rules), not in the random-number mapping, which is a definition of
   the library and is pinned by the GPU parity tests instead;
-- the host analysis of Sec. IV (``analysis.py``) against its tests.
+- the host analysis of Sec. IV (``analysis.py``) and the p-scan table built on it
+  (``pscan.py``) against their tests.
 
 Every copy lives in a temporary directory; the files under test are never modified.
 """
@@ -23,7 +24,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
-ANALYSIS = os.path.join(ROOT, "paper_1411_5512_gb300", "analysis.py")
+PKG = os.path.join(ROOT, "paper_1411_5512_gb300")
 ANALYSIS_PINS = os.path.join(ROOT, "tests", "test_analysis.py")
 
 # (name, file in oracle/, text, replacement): the text must occur exactly once.
@@ -85,34 +86,41 @@ MUTANTS = [
     ("xi1_moment", "ea_oracle.py", "I2 += r * r * c4[r]", "I2 += r * c4[r]"),
 ]
 
-# Mistakes in the analysis of Sec. IV: (name, text, replacement) in analysis.py.
+# Mistakes in the analysis of Sec. IV and the p-scan table built on it:
+# (name, file in the package, text, replacement).
 ANALYSIS_MUTANTS = [
-    ("model_alpha_sign", "r ** (-alpha)", "r ** (alpha)"),
-    ("model_ratio_inverted", "np.exp(-(r / xi) ** beta)", "np.exp(-(xi / r) ** beta)"),
-    ("model_beta_dropped", "np.exp(-(r / xi) ** beta)", "np.exp(-(r / xi))"),
-    ("multifit_r_min_exclusive", "keep = (r >= r_min) & (e > 0)", "keep = (r > r_min) & (e > 0)"),
-    ("multifit_unweighted", "out.append((c4_model(r, A, alpha, xi, beta) - c) / e)",
+    ("model_alpha_sign", "analysis.py", "r ** (-alpha)", "r ** (alpha)"),
+    ("model_ratio_inverted", "analysis.py", "np.exp(-(r / xi) ** beta)", "np.exp(-(xi / r) ** beta)"),
+    ("model_beta_dropped", "analysis.py", "np.exp(-(r / xi) ** beta)", "np.exp(-(r / xi))"),
+    ("multifit_r_min_exclusive", "analysis.py", "keep = (r >= r_min) & (e > 0)", "keep = (r > r_min) & (e > 0)"),
+    ("multifit_unweighted", "analysis.py", "out.append((c4_model(r, A, alpha, xi, beta) - c) / e)",
      "out.append((c4_model(r, A, alpha, xi, beta) - c))"),
-    ("xi1_second_moment", "I2 = float(np.sum(r[inside] ** 2 * C4[inside]))",
+    ("xi1_second_moment", "analysis.py", "I2 = float(np.sum(r[inside] ** 2 * C4[inside]))",
      "I2 = float(np.sum(r[inside] * C4[inside]))"),
-    ("xi1_tail_repeats_r_c", "rt = np.arange(int(r_c) + 1, L // 2 + 1", "rt = np.arange(int(r_c), L // 2 + 1"),
-    ("xi1_tail_short", "rt = np.arange(int(r_c) + 1, L // 2 + 1", "rt = np.arange(int(r_c) + 1, L // 2"),
-    ("xi1_tail_moment", "I2 += float(np.sum(rt ** 2 * ct))", "I2 += float(np.sum(rt * ct))"),
-    ("z_without_constant", "return a * t ** inv_z + c", "return a * t ** inv_z"),
-    ("z_inverted", 'return {"z": float(1.0 / inv_z)', 'return {"z": float(inv_z)'),
-    ("x_sign", "return float(-slope)", "return float(slope)"),
-    ("x_window", "fit_x(t, C, t_min, t_w / 1000.0)", "fit_x(t, C, t_min, t_w / 100.0)"),
-    ("collapse_sign", "np.log(C) + x * np.log(t)", "np.log(C) - x * np.log(t)"),
-    ("collapse_variable", "u = np.log(xi_of_t(t_w + t[keep]) / xi_of_t(t_w))",
+    ("xi1_tail_repeats_r_c", "analysis.py", "rt = np.arange(int(r_c) + 1, L // 2 + 1", "rt = np.arange(int(r_c), L // 2 + 1"),
+    ("xi1_tail_short", "analysis.py", "rt = np.arange(int(r_c) + 1, L // 2 + 1", "rt = np.arange(int(r_c) + 1, L // 2"),
+    ("xi1_tail_moment", "analysis.py", "I2 += float(np.sum(rt ** 2 * ct))", "I2 += float(np.sum(rt * ct))"),
+    ("z_without_constant", "analysis.py", "return a * t ** inv_z + c", "return a * t ** inv_z"),
+    ("z_inverted", "analysis.py", 'return {"z": float(1.0 / inv_z)', 'return {"z": float(inv_z)'),
+    ("x_sign", "analysis.py", "return float(-slope)", "return float(slope)"),
+    ("x_window", "analysis.py", "fit_x(t, C, t_min, t_w / 1000.0)", "fit_x(t, C, t_min, t_w / 100.0)"),
+    ("collapse_sign", "analysis.py", "np.log(C) + x * np.log(t)", "np.log(C) - x * np.log(t)"),
+    ("collapse_variable", "analysis.py", "u = np.log(xi_of_t(t_w + t[keep]) / xi_of_t(t_w))",
      "u = np.log(xi_of_t(t[keep]) / xi_of_t(t_w))"),
-    ("overlap_norm", "q = np.asarray(Q, dtype=np.float64).ravel() / float(N)",
+    ("overlap_norm", "analysis.py", "q = np.asarray(Q, dtype=np.float64).ravel() / float(N)",
      "q = np.asarray(Q, dtype=np.float64).ravel() / float(2 * N)"),
-    ("error_without_difference", 'out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"] + fb[k + "_err"]',
+    ("error_without_difference", "analysis.py", 'out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"] + fb[k + "_err"]',
      'out[k + "_err"] = fa[k + "_err"] + fb[k + "_err"]'),
-    ("error_one_fit_only", 'out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"] + fb[k + "_err"]',
+    ("error_one_fit_only", "analysis.py", 'out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"] + fb[k + "_err"]',
      'out[k + "_err"] = abs(fa[k] - fb[k]) + fa[k + "_err"]'),
-    ("xi_error_without_difference", 'out["xi_err"] = np.abs(fa["xi"] - fb["xi"]) + fa["xi_err"] + fb["xi_err"]',
+    ("xi_error_without_difference", "analysis.py", 'out["xi_err"] = np.abs(fa["xi"] - fb["xi"]) + fa["xi_err"] + fb["xi_err"]',
      'out["xi_err"] = fa["xi_err"] + fb["xi_err"]'),
+    # the p-scan table built on the analysis
+    ("pscan_p_convention", "pscan.py", '"p": 1.0 - cur["pneg"], "alpha": fit["alpha"]',
+     '"p": cur["pneg"], "alpha": fit["alpha"]'),
+    ("pscan_first_xi", "pscan.py", '"xi_fit_last": float(xi_fit[-1])', '"xi_fit_last": float(xi_fit[0])'),
+    ("pscan_z_from_xi1", "pscan.py", 'zf = an.fit_z(np.array(tws, dtype=np.float64), xi_fit)["z"]',
+     'zf = an.fit_z(np.array(tws, dtype=np.float64), xi_int)["z"]'),
 ]
 
 _DRIVER = r"""
@@ -128,14 +136,17 @@ sys.exit(pytest.main([sys.argv[2], "-x", "-q", "-p", "no:cacheprovider", "-m", "
 
 _ANALYSIS_DRIVER = r"""
 import importlib.util
+import os
 import sys
 sys.path.insert(0, sys.argv[3])
 import paper_1411_5512_gb300 as pkg
-spec = importlib.util.spec_from_file_location("paper_1411_5512_gb300.analysis", sys.argv[1])
-mod = importlib.util.module_from_spec(spec)
-sys.modules[spec.name] = mod
-spec.loader.exec_module(mod)
-pkg.analysis = mod
+for name in ("analysis", "pscan"):
+    path = os.path.join(sys.argv[1], name + ".py")
+    spec = importlib.util.spec_from_file_location("paper_1411_5512_gb300." + name, path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod
+    spec.loader.exec_module(mod)
+    setattr(pkg, name, mod)
 import pytest
 sys.exit(pytest.main([sys.argv[2], "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]))
 """
@@ -158,16 +169,16 @@ def _copy(dst, mutant):
 
 def _copy_analysis(dst, mutant):
     os.makedirs(dst)
-    with open(ANALYSIS) as f:
-        src = f.read()
-    if mutant is not None:
-        _, old, new = mutant
-        assert src.count(old) == 1, "the planted text of %s must occur once" % mutant[0]
-        src = src.replace(old, new)
-    path = os.path.join(dst, "analysis.py")
-    with open(path, "w") as f:
-        f.write(src)
-    return path
+    for fname in ("analysis.py", "pscan.py"):
+        with open(os.path.join(PKG, fname)) as f:
+            src = f.read()
+        if mutant is not None and mutant[1] == fname:
+            _, _, old, new = mutant
+            assert src.count(old) == 1, "the planted text of %s must occur once" % mutant[0]
+            src = src.replace(old, new)
+        with open(os.path.join(dst, fname), "w") as f:
+            f.write(src)
+    return dst
 
 
 def _run(args, cwd):
