@@ -33,8 +33,14 @@
  *     runs the opposite colour order (the interlaced layout of Fig. 1).  After
  *     n sweeps the context time is n; measurements at time m see the state
  *     after m sweeps.
- *   - Results are bit-identical to the CPU oracle on the same arguments: the
- *     random numbers depend only on (seed, sample, replica, site, sweep).
+ *   - Results are bit-identical to the CPU oracle on the same arguments.
+ *     The random numbers are keyed by (seed, sample div G, word-site,
+ *     replica, sweep) and by the energy class and draw index inside a
+ *     word-site, never by where a job runs: a word-site groups up to 32 sites
+ *     of one sample (ea_geometry), and the sites of one energy class in a
+ *     word-site are decided together by geometric gaps, so the decision of a
+ *     site depends on which other lanes of its word-site share its class.
+ *     Each site still flips independently with its probability of Eq. 9.
  */
 #ifndef EA_AGEING_H
 #define EA_AGEING_H

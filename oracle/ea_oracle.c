@@ -30,7 +30,7 @@
  * publication.  The mapping from (seed, sample, replica, word-site, sweep) to
  * the 64-bit uniform numbers that decide the flips is a definition of this
  * library (the paper's generator cannot be reproduced); it is restated in
- * full beside metro_draw and heat_draw below.
+ * full beside draw64 below, the one function that cuts every draw.
  */
 #include <math.h>
 #include <stdint.h>
@@ -259,39 +259,20 @@ int ora_init_spins(int L, uint64_t seed, uint32_t s, int8_t *S)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Metropolis acceptance by geometric gaps.                                 */
+/* Acceptance by geometric gaps (both rules).                               */
 /*                                                                          */
-/* Among the sites of one word-site that share the energy change dE > 0     */
-/* (class u = (12 - dE) / 4 unsatisfied bonds, u = 0, 1, 2), each must flip  */
-/* independently with probability p_u = exp(-dE/T) (Eq. 9).  Taken in       */
-/* increasing lane order, they form a Bernoulli(p_u) sequence, and the      */
-/* number G of rejections before the first acceptance is geometric:         */
-/* P(G >= g) = (1 - p_u)^g.  One 64-bit uniform V decides the first         */
-/* acceptance among n remaining sites: none if V >= C_u[n], else the site   */
-/* of rank G = min{g : V < C_u[g+1]}, with                                  */
-/*   C_u[g] = floor(2^64 (1 - (1 - p_u)^g)),  computed as                   */
-/*   floor(ldexp(-expm1(g * log1p(-p_u)), 64)), clamped to 2^64 - 1.         */
-/* The sites after an acceptance start a fresh gap with the next draw.      */
-/*                                                                          */
-/* Draws.  Word-sites group in quads (x' even, x' + 1) x (z' even, z' + 1) */
-/* of the word lattice: one Philox call per quad holds the leading bits of  */
-/* the first draws of all four words:                                       */
-/*   main call of the quad: counter (widx of its word (x' even, z' even),   */
-/*     lo32(t), (3 << 30) | (bits 32..47 of t) << 12 | a_q << 11 | 0, s),     */
-/*     where a_q is the replica updated at that word in this half-step;     */
-/*     output k = (x' mod 2) + 2 (z' mod 2) belongs to word (x', y', z'):    */
-/*     its bits 31..20 are bits 63..52 of draw 0 of class 2 (dE = 4), bits  */
-/*     19..10 bits 63..54 of class 1's (dE = 8), bits 9..0 bits 63..54 of   */
-/*     class 0's (dE = 12).                                                 */
-/*   extension calls of a word: counter (its widx, lo32(t), ... | a << 11 | */
-/*     call, s).  Call 64: (out0 << 32 | out1) >> 12 = bits 51..0 of class */
-/*     2's draw 0, (out2 << 32 | out3) >> 10 = bits 53..0 of class 1's.    */
-/*     Call 65: (out0 << 32 | out1) >> 10 = bits 53..0 of class 0's.        */
-/*   draw d >= 1 of class u of a word: the 64-bit number (out[2e] << 32) |   */
-/*     out[2e + 1] of call 1 + u + 3 (d-1 div 2), e = (d-1) mod 2, with the   */
-/*     word's own widx and replica.                                          */
-#define STREAM_METROPOLIS 3u
-
+/* The sites of one word-site that share a class must each flip             */
+/* independently with the same probability p (for Metropolis, class u =    */
+/* (12 - dE) / 4 unsatisfied bonds with dE > 0 has p_u = exp(-dE/T), Eq. 9). */
+/* Taken in increasing lane order they form a Bernoulli(p) sequence, and    */
+/* the number G of failures before the first success is geometric:          */
+/* P(G >= g) = (1 - p)^g.  One 64-bit uniform V decides the first success   */
+/* among n remaining sites: none if V >= C[n], else the site of rank        */
+/* G = min{g : V < C[g+1]}, with                                            */
+/*   C[g] = floor(2^64 (1 - (1 - p)^g)),  computed as                       */
+/*   floor(ldexp(-expm1(g * log1p(-p)), 64)), clamped to 2^64 - 1.           */
+/* The sites after a success start a fresh gap with the next draw.          */
+/* ------------------------------------------------------------------------ */
 int ora_geo_table(double p, uint64_t C[33])
 {
     if (!(p > 0.0 && p < 1.0))
@@ -305,128 +286,125 @@ int ora_geo_table(double p, uint64_t C[33])
     return ORA_OK;
 }
 
-static void metro_call(uint32_t widx, uint64_t seed, uint32_t s, int a, uint64_t t, int call,
-                       uint32_t out[4])
+/* ------------------------------------------------------------------------ */
+/* The draws.  Every 64-bit uniform V that decides flips, and the heat      */
+/* bath's coin word, is cut from Philox4x32-10 calls with key               */
+/* (lo32(seed), hi32(seed)) and counter                                     */
+/*   (widx, lo32(t), stream << 30 | (bits 32..47 of t) << 12 | a << 11 | call, s) */
+/* where widx = x' + Lx (y' + Ly z') is a word-site of the Lx x Ly x Lz word */
+/* lattice, a the replica updated there, t the sweep and s the sample (or   */
+/* the sample divided by G).  Stream 3 is Metropolis, stream 2 the heat     */
+/* bath.  The assignment of outputs to draws is a definition of this        */
+/* library (the paper's generator cannot be reproduced); draw64 below is    */
+/* the whole of it:                                                          */
+/*                                                                          */
+/* Metropolis, class u in {0, 1, 2}, draw d:                                */
+/*   d = 0: the leading bits come from the main call of the word-site's     */
+/*     quad (x' even, x' + 1) x (z' even, z' + 1): call 0 at the quad's      */
+/*     first word-site (x' even, y', z' even), with the replica updated      */
+/*     there.  Its output k = (x' mod 2) + 2 (z' mod 2) belongs to this      */
+/*     word-site: bits 31..20 lead class 2 (V bits 63..52), bits 19..10     */
+/*     class 1 (63..54), bits 9..0 class 0 (63..54).  The rest of V comes   */
+/*     from the word-site's own extension calls: call 64 gives              */
+/*     (out0:out1) >> 12 to class 2 (V bits 51..0) and (out2:out3) >> 10 to */
+/*     class 1 (53..0); call 65 gives (out0:out1) >> 10 to class 0 (53..0). */
+/*   d >= 1: (out[2e]:out[2e+1]) of call 1 + u + 3 ((d-1) div 2),            */
+/*     e = (d - 1) mod 2.                                                   */
+/* Heat bath, class u != 3, pair index j = min(u, 6 - u):                   */
+/*   d = 0: V bits 63..48 are bits 31..16 (u < 3) or 15..0 (u > 3) of       */
+/*     output 3 - j of call 0; V bits 47..0 are (out0:out1) >> 16 (u < 3)   */
+/*     or (out2:out3) >> 16 (u > 3) of call 128 + (2 - j).                  */
+/*   d >= 1: (out[2e]:out[2e+1]) of call 1 + u + 7 ((d-1) div 2),            */
+/*     e = (d - 1) mod 2 (calls below 128 for d <= 32).                     */
+/*   The coin word of class 3 (dE = 0) is output 0 of call 0: bit b decides  */
+/*   lane b.                                                                */
+/* Why the Metropolis leads are shared per quad: at low T nearly every word  */
+/* is settled by its leading bits alone, so a quarter of a Philox call per  */
+/* word-site decides it; the rest of a draw is needed only when the leading */
+/* bits fall at or below the table.                                          */
+/* ------------------------------------------------------------------------ */
+#define STREAM_METROPOLIS 3u
+
+static void flip_call(uint32_t stream, uint32_t widx, uint64_t seed, uint32_t s, int a,
+                      uint64_t t, int call, uint32_t out[4])
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t ctr[4] = {widx, (uint32_t)t,
-                       (STREAM_METROPOLIS << 30) | ((uint32_t)((t >> 32) & 0xFFFFu) << 12) |
+                       (stream << 30) | ((uint32_t)((t >> 32) & 0xFFFFu) << 12) |
                            ((uint32_t)a << 11) | (uint32_t)call,
                        s};
     ora_philox4x32_10(ctr, key, out);
 }
 
-/* Draw d of class u for the word-site (xw, yw, zw) of a lattice whose word
-   lattice is Lx x Ly x Lz, updated in replica a. */
-static uint64_t metro_draw(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s,
-                           int a, uint64_t t, int u, int d)
+static uint64_t join64(uint32_t hi, uint32_t lo)
 {
-    uint32_t widx = (uint32_t)(xw + Lx * (yw + Ly * zw));
-    if (d >= 1) {
-        uint32_t out[4];
-        int e = (d - 1) % 2;
-        metro_call(widx, seed, s, a, t, 1 + u + 3 * ((d - 1) / 2), out);
-        return ((uint64_t)out[2 * e] << 32) | (uint64_t)out[2 * e + 1];
-    }
-    /* leading bits from the quad's main call */
-    int ox = xw & 1, oz = zw & 1;
-    uint32_t widx_q = (uint32_t)((xw - ox) + Lx * (yw + Ly * (zw - oz)));
-    int a_q = a ^ ox ^ oz; /* the replica updated at the quad's first word */
-    uint32_t m[4], x[4];
-    metro_call(widx_q, seed, s, a_q, t, 0, m);
-    uint32_t lead = m[ox + 2 * oz];
-    if (u == 2) {
-        metro_call(widx, seed, s, a, t, 64, x);
-        return ((uint64_t)(lead >> 20) << 52) | ((((uint64_t)x[0] << 32) | x[1]) >> 12);
-    }
-    if (u == 1) {
-        metro_call(widx, seed, s, a, t, 64, x);
-        return ((uint64_t)((lead >> 10) & 0x3FFu) << 54) | ((((uint64_t)x[2] << 32) | x[3]) >> 10);
-    }
-    metro_call(widx, seed, s, a, t, 65, x);
-    return ((uint64_t)(lead & 0x3FFu) << 54) | ((((uint64_t)x[0] << 32) | x[1]) >> 10);
+    return ((uint64_t)hi << 32) | (uint64_t)lo;
 }
 
-/* ------------------------------------------------------------------------ */
-/* Heat-bath acceptance by geometric gaps.                                  */
-/*                                                                          */
-/* The heat-bath rule flips a site with probability P(dE) = 1/(1+e^(dE/T)), */
-/* and P(dE) + P(-dE) = 1.  With p_j = P(12 - 4j) for j = 0, 1, 2 (dE = 12, */
-/* 8, 4), the sites of a word-site in class u (u unsatisfied bonds, dE =    */
-/* 12 - 4u) are decided as follows:                                          */
-/*   u = 0, 1, 2: the sites that flip are chosen by geometric gaps with     */
-/*     probability p_u, exactly as the Metropolis classes are;              */
-/*   u = 3 (dE = 0, P = 1/2): lane b flips when bit b of the coin word is 1; */
-/*   u = 4, 5, 6: a site keeps its spin with probability 1 - P(dE) =        */
-/*     p_(6-u); the sites that keep are chosen by geometric gaps with that   */
-/*     probability, and every other site of the class flips.                */
-/* The gap table of p_j serves classes j and 6 - j.  p_j = 0 (T = 0, or     */
-/* e^((12-4j)/T) beyond the double range) leaves class j unflipped and flips */
-/* all of class 6 - j.                                                       */
-/*                                                                          */
-/* Draws, per word-site, from Philox4x32-10 with counter                    */
-/*   (widx, lo32(t), (2 << 30) | (bits 32..47 of t) << 12 | a << 11 | call, s): */
-/*   call 0: out0 is the coin word; out1 holds bits 63..48 of draw 0 of     */
-/*     class 2 in its bits 31..16 and those of class 4 in bits 15..0; out2  */
-/*     the same for classes 1 and 5; out3 for classes 0 and 6.              */
-/*   call 128 + (2 - j) for the pair (j, 6 - j): (out0 << 32 | out1) >> 16 */
-/*     is bits 47..0 of draw 0 of class j, (out2 << 32 | out3) >> 16 that of */
-/*     class 6 - j.                                                         */
-/*   draw d >= 1 of class u: (out[2e] << 32) | out[2e + 1] of call          */
-/*     1 + u + 7 (d-1 div 2), e = (d-1) mod 2 (calls below 128 for d <= 32). */
-/* ------------------------------------------------------------------------ */
-static void heat_call(uint32_t widx, uint64_t seed, uint32_t s, int a, uint64_t t, int call,
-                      uint32_t out[4])
-{
-    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t ctr[4] = {widx, (uint32_t)t,
-                       (STREAM_HEAT << 30) | ((uint32_t)((t >> 32) & 0xFFFFu) << 12) |
-                           ((uint32_t)a << 11) | (uint32_t)call,
-                       s};
-    ora_philox4x32_10(ctr, key, out);
-}
-
-/* Draw d of class u (u != 3) for the word-site (xw, yw, zw), replica a. */
-static uint64_t heat_draw(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s,
-                          int a, uint64_t t, int u, int d)
+/* Draw d of class u at word-site (xw, yw, zw), replica a, sweep t. */
+static uint64_t draw64(int rule, int Lx, int Ly, int xw, int yw, int zw, uint64_t seed,
+                       uint32_t s, int a, uint64_t t, int u, int d)
 {
     uint32_t widx = (uint32_t)(xw + Lx * (yw + Ly * zw));
     uint32_t out[4];
+    if (rule == 0) {
+        if (d >= 1) {
+            int e = (d - 1) % 2;
+            flip_call(STREAM_METROPOLIS, widx, seed, s, a, t, 1 + u + 3 * ((d - 1) / 2), out);
+            return join64(out[2 * e], out[2 * e + 1]);
+        }
+        int ox = xw & 1, oz = zw & 1;
+        uint32_t widx_q = (uint32_t)((xw - ox) + Lx * (yw + Ly * (zw - oz)));
+        flip_call(STREAM_METROPOLIS, widx_q, seed, s, a ^ ox ^ oz, t, 0, out);
+        uint32_t lead = out[ox + 2 * oz];
+        if (u == 2) {
+            flip_call(STREAM_METROPOLIS, widx, seed, s, a, t, 64, out);
+            return ((uint64_t)(lead >> 20) << 52) | (join64(out[0], out[1]) >> 12);
+        }
+        if (u == 1) {
+            flip_call(STREAM_METROPOLIS, widx, seed, s, a, t, 64, out);
+            return ((uint64_t)((lead >> 10) & 0x3FFu) << 54) | (join64(out[2], out[3]) >> 10);
+        }
+        flip_call(STREAM_METROPOLIS, widx, seed, s, a, t, 65, out);
+        return ((uint64_t)(lead & 0x3FFu) << 54) | (join64(out[0], out[1]) >> 10);
+    }
     if (d >= 1) {
         int e = (d - 1) % 2;
-        heat_call(widx, seed, s, a, t, 1 + u + 7 * ((d - 1) / 2), out);
-        return ((uint64_t)out[2 * e] << 32) | (uint64_t)out[2 * e + 1];
+        flip_call(STREAM_HEAT, widx, seed, s, a, t, 1 + u + 7 * ((d - 1) / 2), out);
+        return join64(out[2 * e], out[2 * e + 1]);
     }
-    int j = u < 3 ? u : 6 - u;      /* the pair (j, 6 - j) */
-    heat_call(widx, seed, s, a, t, 0, out);
-    uint32_t word = out[3 - j];     /* j = 2 -> out1, 1 -> out2, 0 -> out3 */
+    int pair = u < 3 ? u : 6 - u;
+    flip_call(STREAM_HEAT, widx, seed, s, a, t, 0, out);
+    uint32_t word = out[3 - pair];
     uint64_t lead = u < 3 ? (word >> 16) : (word & 0xFFFFu);
-    heat_call(widx, seed, s, a, t, 128 + (2 - j), out);
-    uint64_t low = u < 3 ? ((((uint64_t)out[0] << 32) | out[1]) >> 16)
-                         : ((((uint64_t)out[2] << 32) | out[3]) >> 16);
+    flip_call(STREAM_HEAT, widx, seed, s, a, t, 128 + (2 - pair), out);
+    uint64_t low = u < 3 ? (join64(out[0], out[1]) >> 16) : (join64(out[2], out[3]) >> 16);
     return (lead << 48) | low;
 }
 
-/* The coin word of the word-site: bit b decides lane b of class 3. */
-static uint32_t heat_coin(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s,
+/* The heat bath's coin word of a word-site. */
+static uint32_t coin_word(int Lx, int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s,
                           int a, uint64_t t)
 {
     uint32_t out[4];
-    heat_call((uint32_t)(xw + Lx * (yw + Ly * zw)), seed, s, a, t, 0, out);
+    flip_call(STREAM_HEAT, (uint32_t)(xw + Lx * (yw + Ly * zw)), seed, s, a, t, 0, out);
     return out[0];
 }
 
-/* Gap selection over the lanes lane_list[0..n) (increasing lane order) of
-   one class: sets mark[lane] = 1 for the selected ones.  rule 0 draws with
-   metro_draw, rule 1 with heat_draw. */
-static void gap_class(const uint64_t C[33], const int *lane_list, int n, int rule, int Lx,
-                      int Ly, int xw, int yw, int zw, uint64_t seed, uint32_t s, int a,
-                      uint64_t t, int u, uint8_t *mark)
+/* The lanes of the mask `lanes` (ranked in increasing lane order) that the
+   geometric gaps of table C select, with the draws d = 0, 1, ... of class u. */
+static uint32_t gap_select(const uint64_t C[33], uint32_t lanes, int rule, int Lx, int Ly,
+                           int xw, int yw, int zw, uint64_t seed, uint32_t s, int a,
+                           uint64_t t, int u)
 {
+    int list[32], n = 0;
+    for (int b = 0; b < 32; b++)
+        if ((lanes >> b) & 1u)
+            list[n++] = b;
+    uint32_t selected = 0;
     int start = 0, d = 0;
     while (n - start > 0) {
-        uint64_t V = rule == 0 ? metro_draw(Lx, Ly, xw, yw, zw, seed, s, a, t, u, d)
-                               : heat_draw(Lx, Ly, xw, yw, zw, seed, s, a, t, u, d);
+        uint64_t V = draw64(rule, Lx, Ly, xw, yw, zw, seed, s, a, t, u, d);
         d++;
         int rem = n - start;
         if (V >= C[rem])
@@ -434,9 +412,135 @@ static void gap_class(const uint64_t C[33], const int *lane_list, int n, int rul
         int G = 0;
         while (!(V < C[G + 1]))
             G++;
-        mark[lane_list[start + G]] = 1;
+        selected |= 1u << list[start + G];
         start += G + 1;
     }
+    return selected;
+}
+
+/* What one temperature and rule fix for every word-site: always[k] (k =
+   (dE + 12) / 4) marks the Metropolis classes accepted outright; live[u] the
+   classes u = 0, 1, 2 decided by the gap table C[u] (for the heat bath, table
+   u also serves class 6 - u). */
+struct flip_rule {
+    int rule;
+    uint8_t always[7];
+    int live[3];
+    uint64_t C[3][33];
+};
+
+static int flip_rule_init(double T, int rule, struct flip_rule *f)
+{
+    uint64_t thr[7];
+    if (ora_thresholds(T, rule, thr, f->always) != ORA_OK)
+        return ORA_BAD_ARG;
+    f->rule = rule;
+    for (int u = 0; u < 3; u++) {
+        double p;
+        f->live[u] = 0;
+        if (rule == 0) {
+            int k = 6 - u;
+            if (f->always[k] || thr[k] == 0)
+                continue;
+            p = exp(-(double)(12 - 4 * u) / T);
+        } else {
+            if (T == 0.0)
+                continue;
+            p = 1.0 / (1.0 + exp((double)(12 - 4 * u) / T));
+            if (!(p > 0.0))
+                continue;
+        }
+        f->live[u] = 1;
+        ora_geo_table(p, f->C[u]);
+    }
+    return ORA_OK;
+}
+
+/* The lanes of class u (the mask `lanes`) of one word-site that flip:
+     rule 0 (Metropolis): a class accepted outright (dE <= 0, or e^(-dE/T)
+       rounding to 1) flips whole; a class with a gap table flips the lanes
+       the gaps select; a class with threshold 0 never flips.
+     rule 1 (heat bath), P(dE) = 1/(1+e^(dE/T)) and P(dE) + P(-dE) = 1:
+       u = 0, 1, 2: the lanes the gaps of table u select flip;
+       u = 3 (dE = 0, P = 1/2): lane b flips when bit b of the coin word is 1;
+       u = 4, 5, 6: a lane keeps its spin with probability 1 - P(dE) =
+         P(-dE), so the gaps of table 6 - u select the lanes that keep, and
+         every other lane of the class flips.
+       A table that is not live (p = 0: T = 0 or e^(dE/T) beyond the double
+       range) leaves class u < 3 unflipped and flips all of class 6 - u. */
+static uint32_t class_flips(const struct flip_rule *f, uint32_t lanes, int Lx, int Ly, int xw,
+                            int yw, int zw, uint64_t seed, uint32_t s, int a, uint64_t t, int u)
+{
+    if (lanes == 0)
+        return 0;
+    if (f->rule == 0) {
+        if (f->always[6 - u])
+            return lanes;
+        if (u >= 3 || !f->live[u])
+            return 0;
+        return gap_select(f->C[u], lanes, 0, Lx, Ly, xw, yw, zw, seed, s, a, t, u);
+    }
+    if (u == 3) {
+        uint32_t coin = coin_word(Lx, Ly, xw, yw, zw, seed, s, a, t);
+        return lanes & coin;
+    }
+    int j = u < 3 ? u : 6 - u;
+    uint32_t mark = f->live[j] ? gap_select(f->C[j], lanes, 1, Lx, Ly, xw, yw, zw, seed, s, a,
+                                            t, u)
+                               : 0;
+    return u < 3 ? mark : (lanes & ~mark);
+}
+
+/* Word-site arguments of the exported draw functions. */
+static int word_site_ok(int L, int xw, int yw, int zw, int g[6])
+{
+    if (ora_geometry(L, g) != ORA_OK)
+        return 0;
+    return xw >= 0 && yw >= 0 && zw >= 0 && xw < g[3] && yw < g[4] && zw < g[5];
+}
+
+/* Draw d of class u (for the pins of the draw contract). */
+int ora_draw64(int rule, int L, uint64_t seed, uint32_t s, int a, uint64_t t, int xw, int yw,
+               int zw, int u, int d, uint64_t *out)
+{
+    int g[6];
+    int u_ok = rule == 0 ? (u >= 0 && u <= 2) : (rule == 1 && u >= 0 && u <= 6 && u != 3);
+    if (!word_site_ok(L, xw, yw, zw, g) || !u_ok || d < 0 || d > 31 || (a != 0 && a != 1) ||
+        t >= ((uint64_t)1 << 48))
+        return ORA_BAD_ARG;
+    *out = draw64(rule, g[3], g[4], xw, yw, zw, seed, s, a, t, u, d);
+    return ORA_OK;
+}
+
+/* The heat bath's coin word (for the pins). */
+int ora_coin_word(int L, uint64_t seed, uint32_t s, int a, uint64_t t, int xw, int yw, int zw,
+                  uint32_t *out)
+{
+    int g[6];
+    if (!word_site_ok(L, xw, yw, zw, g) || (a != 0 && a != 1) || t >= ((uint64_t)1 << 48))
+        return ORA_BAD_ARG;
+    *out = coin_word(g[3], g[4], xw, yw, zw, seed, s, a, t);
+    return ORA_OK;
+}
+
+/* The flips of class u among the lanes `lanes` of word-site (xw, yw, zw) at
+   the sweeps t0, t0 + 1, ..., t0 + n_t - 1 (out[k] for sweep t0 + k): the
+   decision the half-step takes for that class (for the pins). */
+int ora_class_flips(int rule, int L, double T, uint64_t seed, uint32_t s, int a, uint64_t t0,
+                    int n_t, int xw, int yw, int zw, int u, uint32_t lanes, uint32_t *out)
+{
+    int g[6];
+    struct flip_rule f;
+    if (!word_site_ok(L, xw, yw, zw, g) || u < 0 || u > 6 || (a != 0 && a != 1) || n_t < 0 ||
+        t0 + (uint64_t)n_t > ((uint64_t)1 << 48) || (rule != 0 && rule != 1) ||
+        flip_rule_init(T, rule, &f) != ORA_OK)
+        return ORA_BAD_ARG;
+    int lanes_max = g[0] * g[1] * g[2];
+    if (lanes_max < 32 && (lanes >> lanes_max) != 0)
+        return ORA_BAD_ARG;
+    for (int k = 0; k < n_t; k++)
+        out[k] = class_flips(&f, lanes, g[3], g[4], xw, yw, zw, seed, s, a, t0 + (uint64_t)k, u);
+    return ORA_OK;
 }
 
 /* Local field dE = 2 S_i sum_j J_ij S_j at site (x, y, z) of replica Sa. */
@@ -465,44 +569,19 @@ static int delta_E(int L, const int8_t *Sa, const int8_t *J, int x, int y, int z
 /* one colour do not neighbour each other, so the sites of a colour are     */
 /* decided from the same configuration and may be taken in any order; here  */
 /* they are taken word-site by word-site.  Each site gets dE = 2 S_i sum_j  */
-/* J_ij S_j (Eq. 9) and class u = (12 - dE) / 4;                           */
-/*   rule 0 (Metropolis): dE <= 0 flips (always[k], k = (dE + 12) / 4), as  */
-/*     does a class whose e^(-dE/T) rounds to 1; the other classes are      */
-/*     decided by geometric gaps (metro_draw); a class with threshold 0     */
-/*     never flips.                                                         */
-/*   rule 1 (heat bath): every class is decided by heat_draw's coin word or */
-/*     gaps (above).                                                        */
-/* dE_acc[a] accumulates the energy change of accepted flips of replica a.  */
-/* s keys the random numbers (counter word 3): the sample index, or the     */
-/* sample index divided by G when G samples share their random numbers.     */
+/* J_ij S_j (Eq. 9) and class u = (12 - dE) / 4, and each class of the      */
+/* word-site flips as class_flips decides.  dE_acc[a] accumulates the       */
+/* energy change of accepted flips of replica a.  s keys the random numbers */
+/* (counter word 3): the sample index, or the sample index divided by G     */
+/* when G samples share their random numbers.                               */
 /* ------------------------------------------------------------------------ */
 int ora_half_step(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, double T, int rule,
                   uint64_t t, int h, int64_t dE_acc[2])
 {
-    uint64_t thr[7];
-    uint8_t always[7];
+    struct flip_rule f;
     if (L < 2 || L > 1024 || (L & 1) || t >= ((uint64_t)1 << 48) || (h != 0 && h != 1) ||
-        ora_thresholds(T, rule, thr, always) != ORA_OK)
+        (rule != 0 && rule != 1) || flip_rule_init(T, rule, &f) != ORA_OK)
         return ORA_BAD_ARG;
-    uint64_t C[3][33];
-    int live[3] = {0, 0, 0};
-    for (int u = 0; u < 3; u++) {
-        double p;
-        if (rule == 0) {
-            int k = 6 - u;
-            if (always[k] || thr[k] == 0)
-                continue;
-            p = exp(-(double)(12 - 4 * u) / T);
-        } else {
-            if (T == 0.0)
-                continue;
-            p = 1.0 / (1.0 + exp((double)(12 - 4 * u) / T));
-            if (!(p > 0.0))
-                continue;
-        }
-        live[u] = 1;
-        ora_geo_table(p, C[u]);
-    }
     int g[6];
     ora_geometry(L, g);
     int kx = g[0], ky = g[1], kz = g[2], Lx = g[3], Ly = g[4], Lz = g[5];
@@ -516,51 +595,20 @@ int ora_half_step(int L, uint64_t seed, uint32_t s, int8_t *S, const int8_t *J, 
                     if (((xw + yw + zw) & 1) != (h ^ a))
                         continue;
                     int dE[32], sx[32], sy[32], sz[32];
-                    uint8_t flip[32];
+                    uint32_t in_class[7] = {0, 0, 0, 0, 0, 0, 0};
                     for (int b = 0; b < lanes; b++) {
                         sx[b] = (b % kx) * Lx + xw;
                         sy[b] = ((b / kx) % ky) * Ly + yw;
                         sz[b] = (b / (kx * ky)) * Lz + zw;
                         dE[b] = delta_E(L, Sa, J, sx[b], sy[b], sz[b]);
-                        flip[b] = rule == 0 ? always[(dE[b] + 12) / 4] : 0;
+                        in_class[(12 - dE[b]) / 4] |= 1u << b;
                     }
-                    if (rule == 0) {
-                        for (int u = 0; u < 3; u++) {
-                            if (!live[u])
-                                continue;
-                            int list[32], n = 0;
-                            for (int b = 0; b < lanes; b++)
-                                if (dE[b] == 12 - 4 * u)
-                                    list[n++] = b;
-                            if (n > 0)
-                                gap_class(C[u], list, n, 0, Lx, Ly, xw, yw, zw, seed, s, a, t,
-                                          u, flip);
-                        }
-                    } else {
-                        uint32_t coin = heat_coin(Lx, Ly, xw, yw, zw, seed, s, a, t);
-                        for (int u = 0; u <= 6; u++) {
-                            int list[32], n = 0;
-                            for (int b = 0; b < lanes; b++)
-                                if (dE[b] == 12 - 4 * u)
-                                    list[n++] = b;
-                            if (n == 0)
-                                continue;
-                            if (u == 3) {
-                                for (int i = 0; i < n; i++)
-                                    flip[list[i]] = (uint8_t)((coin >> list[i]) & 1u);
-                                continue;
-                            }
-                            int j = u < 3 ? u : 6 - u;
-                            uint8_t mark[32] = {0};
-                            if (live[j])
-                                gap_class(C[j], list, n, 1, Lx, Ly, xw, yw, zw, seed, s, a, t,
-                                          u, mark);
-                            for (int i = 0; i < n; i++)
-                                flip[list[i]] = u < 3 ? mark[list[i]] : (uint8_t)!mark[list[i]];
-                        }
-                    }
+                    uint32_t flips = 0;
+                    for (int u = 0; u <= 6; u++)
+                        flips |= class_flips(&f, in_class[u], Lx, Ly, xw, yw, zw, seed, s, a, t,
+                                             u);
                     for (int b = 0; b < lanes; b++)
-                        if (flip[b]) {
+                        if ((flips >> b) & 1u) {
                             int64_t i = sx[b] + (int64_t)L * (sy[b] + (int64_t)L * sz[b]);
                             Sa[i] = (int8_t)-Sa[i];
                             dE_acc[a] += dE[b];

@@ -77,6 +77,17 @@ def lib():
         L.ora_half_step.restype = ctypes.c_int
         L.ora_geo_table.argtypes = [ctypes.c_double, u64p]
         L.ora_geo_table.restype = ctypes.c_int
+        L.ora_draw64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                 ctypes.c_int, ctypes.c_uint64] + [ctypes.c_int] * 5 + [u64p]
+        L.ora_draw64.restype = ctypes.c_int
+        L.ora_coin_word.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                    ctypes.c_uint64] + [ctypes.c_int] * 3 + [u32p]
+        L.ora_coin_word.restype = ctypes.c_int
+        L.ora_class_flips.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                      ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_uint32, u32p]
+        L.ora_class_flips.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -175,6 +186,35 @@ def geo_table(p):
     C = np.zeros(33, dtype=np.uint64)
     _check(lib().ora_geo_table(float(p), _ptr(C, ctypes.c_uint64)), "geo_table(p=%r)" % p)
     return C
+
+
+def draw64(rule, L, seed, s, a, t, word_site, u, d):
+    """The 64-bit uniform number of draw d of class u at word-site (x', y', z'),
+    replica a, sweep t (the draw contract stated beside draw64 in ea_oracle.c)."""
+    xw, yw, zw = word_site
+    out = ctypes.c_uint64()
+    _check(lib().ora_draw64(int(rule), L, seed, s, int(a), t, xw, yw, zw, int(u), int(d),
+                            ctypes.byref(out)), "draw64")
+    return out.value
+
+
+def coin_word(L, seed, s, a, t, word_site):
+    """The heat bath's coin word of a word-site: bit b decides lane b of class dE = 0."""
+    xw, yw, zw = word_site
+    out = ctypes.c_uint32()
+    _check(lib().ora_coin_word(L, seed, s, int(a), t, xw, yw, zw, ctypes.byref(out)),
+           "coin_word")
+    return out.value
+
+
+def class_flips(rule, L, T, seed, s, a, t0, n_t, word_site, u, lanes):
+    """The lanes (bit mask) of class u that flip, among the lanes `lanes` of one
+    word-site, at sweeps t0 .. t0 + n_t - 1: the half-step's decision for that class."""
+    xw, yw, zw = word_site
+    out = np.zeros(n_t, dtype=np.uint32)
+    _check(lib().ora_class_flips(int(rule), L, float(T), seed, s, int(a), t0, n_t, xw, yw, zw,
+                                 int(u), int(lanes), _ptr(out, ctypes.c_uint32)), "class_flips")
+    return out
 
 
 # ----------------------------------------------------------------------------------

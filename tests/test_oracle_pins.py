@@ -668,3 +668,215 @@ def test_exact_couplings_hypergeometric():
     expect = 12 * 0.5 * 0.5 * (n - 12) / (n - 1)
     assert abs(var - expect) < 5 * expect * math.sqrt(2.0 / reps), var
     assert abs(float(np.mean(xs)) - 6.0) < 5 * math.sqrt(expect / reps)
+
+
+# ----------------------------------------------------------------------------------
+# the draw contract: the joint law of the flips it produces
+#
+# Eq. 9 asks each site of a class to flip independently with its probability.
+# The oracle spends the random bits word-site by word-site (draw64 in
+# ea_oracle.c): leads shared by the four words of a quad, extension and
+# continuation calls, a coin word.  Whatever the layout, the result must be
+# independent fair bits in every draw and independent Bernoulli flips in every
+# class, between the classes of a word-site and between the words of a quad.
+# These pins hold one configuration fixed and vary only the sweep t.
+# ----------------------------------------------------------------------------------
+from scipy import stats  # noqa: E402
+
+DRAW_L = 32  # word lattice 32 x 16 x 2, 32 lanes (kx, ky, kz = 1, 2, 16)
+# the four word-sites of the quad (x' 0..1) x (z' 0..1) at y' = 3, with the replica
+# that half-step 0 updates there (colour (x' + y' + z') mod 2 = h XOR a)
+QUAD = [((0, 3, 0), 1), ((1, 3, 0), 0), ((0, 3, 1), 0), ((1, 3, 1), 1)]
+DRAW_SEED, DRAW_S = 0x5EED1234ABCDEF, 3
+N_SWEEPS = 10_000
+METRO_CLASSES = (0, 1, 2)
+HEAT_CLASSES = (0, 1, 2, 4, 5, 6)
+
+
+def _draw_table(rule, n_t=1024):
+    """V[(u, d)] -> uint64 array over (quad word, sweep t)."""
+    classes = METRO_CLASSES if rule == 0 else HEAT_CLASSES
+    out = {}
+    for u in classes:
+        for d in (0, 1, 2):
+            v = np.zeros((len(QUAD), n_t), dtype=np.uint64)
+            for k, (ws, a) in enumerate(QUAD):
+                for t in range(n_t):
+                    v[k, t] = ora.draw64(rule, DRAW_L, DRAW_SEED, DRAW_S, a, 7000 + t, ws, u, d)
+            out[(u, d)] = v
+    return out
+
+
+_DRAWS = {}
+
+
+def _draws(rule):
+    if rule not in _DRAWS:
+        _DRAWS[rule] = _draw_table(rule)
+    return _DRAWS[rule]
+
+
+def _bits(v):
+    """[..., 64] 0/1 array of the bits of uint64 values (bit 63 first)."""
+    b = np.unpackbits(v.astype(">u8").view(np.uint8).reshape(v.shape + (8,)), axis=-1)
+    return b.astype(np.int64)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_draw_bits_are_fair(rule):
+    """Each of the 64 bits of every draw is a fair coin (a bit stuck, or two
+    sources OR-ed into one bit, shows at once)."""
+    for key, v in _draws(rule).items():
+        b = _bits(v.ravel())
+        n = b.shape[0]
+        z = np.abs(b.sum(axis=0) - n / 2) / math.sqrt(n / 4)
+        assert z.max() < 5.0, (rule, key, int(np.argmax(z)), float(z.max()))
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_draws_share_no_bits(rule):
+    """Two different draws of a word-site (other class or other draw index) agree on
+    each bit half of the time: no lead, extension or continuation is shared."""
+    tab = _draws(rule)
+    keys = sorted(tab)
+    bits = {k: _bits(tab[k]) for k in keys}  # [word][t][64]
+    for k1, k2 in itertools.combinations(keys, 2):
+        agree = (bits[k1] == bits[k2]).reshape(-1, 64)
+        n = agree.shape[0]
+        z = np.abs(agree.sum(axis=0) - n / 2) / math.sqrt(n / 4)
+        assert z.max() < 5.5, (rule, k1, k2, int(np.argmax(z)), float(z.max()))
+
+
+def test_quad_words_share_no_bits():
+    """The four words of a quad take their leads from one Philox call; each must
+    get bits of its own."""
+    tab = _draws(0)
+    for u in METRO_CLASSES:
+        b = _bits(tab[(u, 0)])  # [word][t][64]
+        for w1, w2 in itertools.combinations(range(len(QUAD)), 2):
+            agree = b[w1] == b[w2]
+            n = agree.shape[0]
+            z = np.abs(agree.sum(axis=0) - n / 2) / math.sqrt(n / 4)
+            assert z.max() < 5.0, (u, w1, w2, int(np.argmax(z)), float(z.max()))
+
+
+def _flip_p(rule, u, T):
+    dE = 12 - 4 * u
+    if rule == 0:
+        return min(1.0, math.exp(-dE / T))
+    return 1.0 / (1.0 + math.exp(dE / T))
+
+
+def _lanes(lst):
+    return sum(1 << b for b in lst)
+
+
+def _patterns(masks, lane_lists):
+    """Pack the flips of the listed lanes of each mask into one integer pattern per
+    sweep: bit i of the pattern is lane lane_lists[...][i] (in the order given)."""
+    pat = np.zeros(masks[0].shape[0], dtype=np.int64)
+    i = 0
+    for m, lst in zip(masks, lane_lists):
+        for b in lst:
+            pat |= ((m.astype(np.int64) >> b) & 1) << i
+            i += 1
+    return pat, i
+
+
+def _chi2_product_law(pat, probs):
+    """chi^2 p-value of observed patterns against independent bits, bit i set with
+    probability probs[i]; cells expected below 5 are pooled."""
+    n_bits = len(probs)
+    n = pat.shape[0]
+    obs = np.bincount(pat, minlength=1 << n_bits).astype(np.float64)
+    exp = np.ones(1 << n_bits)
+    for i, p in enumerate(probs):
+        on = ((np.arange(1 << n_bits) >> i) & 1).astype(bool)
+        exp *= np.where(on, p, 1.0 - p)
+    exp *= n
+    small = exp < 5.0
+    o = np.append(obs[~small], obs[small].sum())
+    e = np.append(exp[~small], exp[small].sum())
+    if e[-1] == 0.0:
+        o, e = o[:-1], e[:-1]
+    assert o.sum() == n
+    chi2 = float(np.sum((o - e) ** 2 / e))
+    return float(stats.chi2.sf(chi2, len(e) - 1))
+
+
+JOINT_LANES = [((0, 3, 0), 1, [4, 19]), ((1, 3, 1), 1, [0, 13, 31]),
+               ((1, 3, 0), 0, [2, 9, 10, 22, 27])]
+
+
+@pytest.mark.parametrize("rule,u", [(0, u) for u in METRO_CLASSES] +
+                         [(1, u) for u in range(7)])
+@pytest.mark.parametrize("T", [5.0, 12.0])
+def test_class_flips_joint_law(rule, u, T):
+    """Over 10^4 sweeps, the 2^n flip patterns of n = 2, 3, 5 lanes of one class
+    follow the product law Bernoulli(p)^n, p = min(1, e^(-dE/T)) (Eq. 9) or
+    1/(1 + e^(dE/T)) (heat bath): gap-selected (dE > 0), coin (dE = 0) and
+    complement-selected (dE < 0) classes alike."""
+    p = _flip_p(rule, u, T)
+    for ws, a, lst in JOINT_LANES:
+        m = ora.class_flips(rule, DRAW_L, T, DRAW_SEED, DRAW_S, a, 20_000, N_SWEEPS, ws, u,
+                            _lanes(lst))
+        assert np.all((m & ~np.uint32(_lanes(lst))) == 0)
+        pat, nb = _patterns([m], [lst])
+        pv = _chi2_product_law(pat, [p] * nb)
+        assert pv > 1e-6, (rule, u, T, ws, lst, pv)
+
+
+CROSS_PAIRS = {0: [(2, 1), (2, 0), (1, 0)],
+               1: [(2, 4), (1, 5), (0, 6), (2, 1), (2, 0), (1, 0), (4, 5), (4, 6), (3, 2),
+                   (3, 6)]}
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+@pytest.mark.parametrize("T", [5.0, 12.0])
+def test_classes_of_a_word_site_flip_independently(rule, T):
+    """Lanes of two classes of one word-site, decided at the same sweep (their
+    leads come from one Philox output), flip independently: the joint pattern
+    of 3 + 3 lanes follows the product law."""
+    la, lb = [1, 14, 25], [6, 18, 30]
+    for ws, a, _ in JOINT_LANES[:2]:
+        for ua, ub in CROSS_PAIRS[rule]:
+            ma = ora.class_flips(rule, DRAW_L, T, DRAW_SEED, DRAW_S, a, 40_000, N_SWEEPS, ws,
+                                 ua, _lanes(la))
+            mb = ora.class_flips(rule, DRAW_L, T, DRAW_SEED, DRAW_S, a, 40_000, N_SWEEPS, ws,
+                                 ub, _lanes(lb))
+            pat, nb = _patterns([ma, mb], [la, lb])
+            probs = [_flip_p(rule, ua, T)] * 3 + [_flip_p(rule, ub, T)] * 3
+            pv = _chi2_product_law(pat, probs)
+            assert pv > 1e-6, (rule, T, ws, ua, ub, pv)
+
+
+@pytest.mark.parametrize("T", [5.0, 12.0])
+def test_words_of_a_quad_flip_independently(T):
+    """The four words of a quad share one main Philox call; the same-rank lanes of
+    one class in the four words flip independently (4 x 2 lanes, product law)."""
+    lst = [3, 17]
+    for u in METRO_CLASSES:
+        masks = [ora.class_flips(0, DRAW_L, T, DRAW_SEED, DRAW_S, a, 60_000, N_SWEEPS, ws, u,
+                                 _lanes(lst)) for ws, a in QUAD]
+        pat, nb = _patterns(masks, [lst] * 4)
+        pv = _chi2_product_law(pat, [_flip_p(0, u, T)] * nb)
+        assert pv > 1e-6, (u, T, pv)
+
+
+def test_coin_word_lanes_are_fair_and_independent():
+    """Class dE = 0 of the heat bath flips lane b by bit b of the coin word: every
+    lane at rate 1/2, and the lanes independent (nibble patterns uniform)."""
+    all_lanes = (1 << 32) - 1
+    for ws, a in QUAD[:2]:
+        m = ora.class_flips(1, DRAW_L, 3.0, DRAW_SEED, DRAW_S, a, 80_000, N_SWEEPS, ws, 3,
+                            all_lanes)
+        b = ((m[:, None].astype(np.int64) >> np.arange(32)) & 1)
+        n = b.shape[0]
+        z = np.abs(b.sum(axis=0) - n / 2) / math.sqrt(n / 4)
+        assert z.max() < 5.0, (ws, int(np.argmax(z)), float(z.max()))
+        for shift in range(0, 32, 4):
+            nib = (m.astype(np.int64) >> shift) & 0xF
+            assert _chi2_product_law(nib, [0.5] * 4) > 1e-6, (ws, shift)
+        assert np.array_equal(
+            m, [ora.coin_word(DRAW_L, DRAW_SEED, DRAW_S, a, 80_000 + t, ws)
+                for t in range(N_SWEEPS)])

@@ -6,8 +6,9 @@ the unchanged copy must pass.  Two groups:
 - the oracle (its C chain and its numpy observables) against the oracle's pins;
   the mistakes lie in the arithmetic the paper fixes (Eqs. 1-3, 5-7 and 9, the
   checkerboard of Sec. III, the heat-bath rule and the gap construction that
-  realises both rules), not in the random-number mapping, which is a definition of
-  the library and is pinned by the GPU parity tests instead;
+  realises both rules) and in the way the random-number mapping spends its bits
+  (a lead shared by two classes or two words, overlapping bit fields, colliding
+  or reused calls, a shifted coin), which must still give independent flips;
 - the host analysis of Sec. IV (``analysis.py``) and the p-scan table built on it
   (``pscan.py``) against their tests.
 
@@ -59,12 +60,29 @@ MUTANTS = [
      "double q = -expm1((double)(g + 1) * log1p(-p));"),
     ("gap_skips_a_site", "ea_oracle.c", "start += G + 1;", "start += G + 2;"),
     ("gap_none_test", "ea_oracle.c", "if (V >= C[rem])", "if (V >= C[rem - 1])"),
-    ("heatbath_coin_always", "ea_oracle.c", "flip[list[i]] = (uint8_t)((coin >> list[i]) & 1u);",
-     "flip[list[i]] = 1;"),
-    ("heatbath_keep_inverted", "ea_oracle.c", "flip[list[i]] = u < 3 ? mark[list[i]] : (uint8_t)!mark[list[i]];",
-     "flip[list[i]] = mark[list[i]];"),
-    ("heatbath_wrong_pair", "ea_oracle.c", "int j = u < 3 ? u : 6 - u;\n                            uint8_t mark",
-     "int j = u < 3 ? u : u - 4;\n                            uint8_t mark"),
+    ("heatbath_coin_always", "ea_oracle.c", "return lanes & coin;", "return lanes;"),
+    ("heatbath_keep_inverted", "ea_oracle.c", "return u < 3 ? mark : (lanes & ~mark);", "return mark;"),
+    ("heatbath_wrong_pair", "ea_oracle.c", "int j = u < 3 ? u : 6 - u;", "int j = u < 3 ? u : u - 4;"),
+    # the draw contract (draw64): how the random bits are spent must still give
+    # independent fair bits and independent flips
+    ("draw_lead_shared", "ea_oracle.c", "((uint64_t)((lead >> 10) & 0x3FFu) << 54)",
+     "((uint64_t)((lead >> 22) & 0x3FFu) << 54)"),
+    ("draw_quad_output", "ea_oracle.c", "uint32_t lead = out[ox + 2 * oz];", "uint32_t lead = out[ox + oz];"),
+    ("draw_extension_overlap", "ea_oracle.c", "(join64(out[0], out[1]) >> 12)",
+     "(join64(out[0], out[1]) >> 11)"),
+    ("draw_continuation_off_by_one", "ea_oracle.c", "t, 1 + u + 3 * ((d - 1) / 2), out);",
+     "t, u + 3 * ((d - 1) / 2), out);"),
+    ("draw_continuation_drops_class", "ea_oracle.c", "t, 1 + u + 3 * ((d - 1) / 2), out);",
+     "t, 1 + 3 * ((d - 1) / 2), out);"),
+    ("draw_continuation_reused", "ea_oracle.c",
+     "int e = (d - 1) % 2;\n            flip_call(STREAM_METROPOLIS",
+     "int e = 0;\n            flip_call(STREAM_METROPOLIS"),
+    ("coin_lane_shift", "ea_oracle.c", "return lanes & coin;", "return lanes & (coin >> 1);"),
+    ("heat_pair_shared_lead", "ea_oracle.c", "uint32_t word = out[3 - pair];",
+     "uint32_t word = out[1 + (pair & 1)];"),
+    ("heat_keep_same_half", "ea_oracle.c", "uint64_t lead = u < 3 ? (word >> 16) : (word & 0xFFFFu);",
+     "uint64_t lead = word >> 16;"),
+    ("heat_continuation_drops_class", "ea_oracle.c", "1 + u + 7 * ((d - 1) / 2)", "1 + 7 * ((d - 1) / 2)"),
     ("energy_change_sign", "ea_oracle.c", "dE_acc[a] += dE[b];", "dE_acc[a] -= dE[b];"),
     # initial state
     ("couplings_inverted", "ea_oracle.c", "J[d * N + i] = ((uint64_t)out[d] < thr) ? (int8_t)-1 : (int8_t)1;",
