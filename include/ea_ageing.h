@@ -143,6 +143,16 @@ int ea_set_allocator(ea_alloc_fn alloc, ea_free_fn release, void *user);
  * enqueued in it. */
 uint64_t ea_launch_count(void);
 
+/* The integer throughput of the current device, measured by three short
+ * kernels of independent dependency chains that fill every SM: out[0] =
+ * three-input logic ops (lop3.b32) per second, out[1] = 32-bit multiply-adds
+ * (mad.lo.u32) per second, out[2] = Philox4x32-10 calls per second, each the
+ * best of five timed launches.  The paper has no counterpart: these are the
+ * denominators of the integer-ALU roofline that the sweep is reported
+ * against.  Allocates nothing; synchronises the stream.  Errors:
+ * EA_ERR_INVALID_ARG (NULL out), EA_ERR_CUDA. */
+int ea_int_throughput(void *cuda_stream, double out[3]);
+
 /* ---- job lifecycle ------------------------------------------------------- */
 
 /* Create a job of n_samples samples of side L and generate their couplings on
@@ -167,6 +177,20 @@ int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_sa
  * of (key, b).  Synchronises the stream.  Errors as ea_create_samples. */
 int ea_create_samples_exact(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_samples,
                             int rng_group_G, void *cuda_stream);
+
+/* Samples first_sample .. first_sample + n_samples - 1 of the job
+ * (L, p_neg, seed, G): the context's sample s is the job's sample
+ * first_sample + s, with that index in every random number (couplings,
+ * initial spins, sweeps; its share group is (first_sample + s) div G).  So
+ * disjoint ranges of one job, run in different processes or on different
+ * GPUs, give bit for bit the samples that ea_create_samples would give for the
+ * whole job, and their integer sums add up to the whole job's (Sec. III: the
+ * paper ran independent sample batches on each GPU).  ea_create_samples is
+ * the range starting at 0.  Errors as ea_create_samples, and
+ * EA_ERR_INVALID_ARG for first_sample < 0 or first_sample + n_samples above
+ * 65535. */
+int ea_create_samples_range(ea_ctx **out, int L, double p_neg, uint64_t seed, int first_sample,
+                            int n_samples, int rng_group_G, void *cuda_stream);
 
 /* Set the measurement schedule: waiting times t_w[0..n_tw) and time lags
  * t[0..n_t) (Sec. II: C(t, t_w) and C4(r, t_w) are measured at waiting times
@@ -209,15 +233,20 @@ int ea_measure(ea_ctx *ctx, uint64_t t_w, uint64_t t, ea_obs *out);
  *                          sum_i q_i q_{i+v},   q_i = S^0_i S^1_i,
  * where |v|^2 = sum over axes of min(d, L - d)^2 (the shortest periodic
  * image), b = 0 .. n_bins - 1, and counts[b] = the number of vectors with
- * |v|^2 = b (0 for the values no vector takes).  C4 at distance sqrt(b) is
- * sums / (counts N).  Exact integers: computed by a transform modulo a prime,
- * with no rounding.  The caller owns sums[n_samples * n_bins] and
- * counts[n_bins] (n_bins from ea_c4_radial_bins).  Uses device scratch of up
- * to 256 MiB while it runs and synchronises the job's stream.  Errors:
- * EA_ERR_INVALID_ARG (NULL, side above 512), EA_ERR_STATE (before
- * ea_quench), EA_ERR_NO_SNAPSHOT (t_w not scheduled or not reached),
- * EA_ERR_OOM. */
-int ea_c4_radial(ea_ctx *ctx, uint64_t t_w, long long *sums, long long *counts);
+ * |v|^2 = b (0 for the values no vector takes).  Exact integers: computed by
+ * a transform modulo a prime, with no rounding.  The caller owns
+ * sums[n_samples * n_bins] and counts[n_bins] (n_bins from
+ * ea_c4_radial_bins).  The FP64 curve goes to C4[n_bins] and
+ * C4_sem[n_bins] when they are not NULL: for a bin b with counts[b] > 0,
+ *   C4[b]     = sum_s sums[s][b] / (counts[b] N n_samples)  (one rounding),
+ *   C4_sem[b] = the standard error over samples of sums[s][b] / (counts[b] N)
+ *               (NaN with one sample);
+ * both NaN where counts[b] = 0.  Uses device scratch of up to 256 MiB while
+ * it runs and synchronises the job's stream.  Errors: EA_ERR_INVALID_ARG
+ * (NULL sums or counts, side above 512), EA_ERR_STATE (before ea_quench),
+ * EA_ERR_NO_SNAPSHOT (t_w not scheduled or not reached), EA_ERR_OOM. */
+int ea_c4_radial(ea_ctx *ctx, uint64_t t_w, long long *sums, long long *counts, double *C4,
+                 double *C4_sem);
 
 /* ea_c4_radial for callers that cannot allocate device memory: a host that
  * has handed all of it to its own pool, or code on a path where cudaMalloc,
@@ -233,7 +262,8 @@ int ea_c4_radial(ea_ctx *ctx, uint64_t t_w, long long *sums, long long *counts);
  * last call's contents (each call clears what it sums into first): calls that
  * overlap on the GPU, from different streams or threads, race, so order them.
  * Synchronises the job's stream. */
-int ea_c4_radial_noalloc(ea_ctx *ctx, uint64_t t_w, long long *sums, long long *counts);
+int ea_c4_radial_noalloc(ea_ctx *ctx, uint64_t t_w, long long *sums, long long *counts,
+                         double *C4, double *C4_sem);
 
 /* Number of distance bins of ea_c4_radial for side L: 3 (L/2)^2 + 1.
  * Host only.  EA_ERR_INVALID_ARG for odd L, L < 2 or L > 512. */

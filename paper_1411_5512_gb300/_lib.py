@@ -68,18 +68,22 @@ SIGNATURES = {
     "ea_footprint": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_size_t)]),
     "ea_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, vp]),
+    "ea_int_throughput": (ctypes.c_int, [vp, dblp]),
     "ea_create_samples": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
                                          ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp]),
     "ea_create_samples_exact": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
                                                ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp]),
+    "ea_create_samples_range": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, vp]),
     "ea_set_schedule": (ctypes.c_int, [vp, u64p, ctypes.c_int, u64p, ctypes.c_int]),
     "ea_quench": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
     "ea_sweep": (ctypes.c_int, [vp, ctypes.c_uint64]),
     "ea_time": (ctypes.c_int, [vp, u64p]),
     "ea_measure": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.POINTER(EaObs)]),
-    "ea_c4_radial": (ctypes.c_int, [vp, ctypes.c_uint64, i64p, i64p]),
-    "ea_c4_radial_noalloc": (ctypes.c_int, [vp, ctypes.c_uint64, i64p, i64p]),
+    "ea_c4_radial": (ctypes.c_int, [vp, ctypes.c_uint64, i64p, i64p, dblp, dblp]),
+    "ea_c4_radial_noalloc": (ctypes.c_int, [vp, ctypes.c_uint64, i64p, i64p, dblp, dblp]),
     "ea_c4_radial_bins": (ctypes.c_int, [ctypes.c_int, intp]),
     "ea_get_spins": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, i8p]),
     "ea_get_couplings": (ctypes.c_int, [vp, ctypes.c_int, i8p]),

@@ -250,6 +250,7 @@ struct ea_ctx {
     double p_neg = 0;
     uint64_t seed = 0;
     int S = 0;
+    int first = 0;  // the job-local index of sample 0 (ea_create_samples_range)
     int G = 1;
     cudaStream_t stream = nullptr;
     Geo geo;
@@ -528,6 +529,17 @@ int ea_footprint(int L, int n_samples, int n_tw, int n_t, size_t *bytes)
     return EA_OK;
 }
 
+int ea_int_throughput(void *cuda_stream, double out[3])
+{
+    if (!out)
+        return EA_ERR_INVALID_ARG;
+    if (ea::probe_int_throughput((cudaStream_t)cuda_stream, out) != cudaSuccess) {
+        cudaGetLastError();
+        return EA_ERR_CUDA;
+    }
+    return EA_OK;
+}
+
 int ea_set_allocator(ea_alloc_fn alloc, ea_free_fn release, void *user)
 {
     if ((alloc == nullptr) != (release == nullptr))
@@ -541,13 +553,19 @@ int ea_set_allocator(ea_alloc_fn alloc, ea_free_fn release, void *user)
 int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_samples,
                       int rng_group_G, void *cuda_stream)
 {
+    return ea_create_samples_range(out, L, p_neg, seed, 0, n_samples, rng_group_G, cuda_stream);
+}
+
+int ea_create_samples_range(ea_ctx **out, int L, double p_neg, uint64_t seed, int first_sample,
+                            int n_samples, int rng_group_G, void *cuda_stream)
+{
     NvtxRange nvtx_range("ea_create_samples");
     if (!out)
         return EA_ERR_INVALID_ARG;
     *out = nullptr;
     Geo g;
     if (ea::make_geo(L, &g) != 0 || !(p_neg >= 0.0 && p_neg <= 1.0) || n_samples < 1 ||
-        n_samples > ea::kMaxSamples || rng_group_G < 1)
+        first_sample < 0 || n_samples > ea::kMaxSamples - first_sample || rng_group_G < 1)
         return EA_ERR_INVALID_ARG;
     ea_ctx *c = new (std::nothrow) ea_ctx();
     if (!c)
@@ -556,6 +574,7 @@ int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_sa
     c->p_neg = p_neg;
     c->seed = seed;
     c->S = n_samples;
+    c->first = first_sample;
     c->G = rng_group_G;
     c->stream = (cudaStream_t)cuda_stream;
     c->own_stream = c->stream;
@@ -574,10 +593,12 @@ int ea_create_samples(ea_ctx **out, int L, double p_neg, uint64_t seed, int n_sa
     c->jd.J = c->J;
     c->jd.geo = g;
     c->jd.n_samples = n_samples;
+    c->jd.first_sample = first_sample;
     c->jd.rng_group = (uint32_t)rng_group_G;
     ea::fill_job_keys(&c->jd, seed);
     ea::fill_job_layout(&c->jd, default_cols_per_thread(g));
-    cudaError_t e = ea::launch_init_couplings(c->J, g, n_samples, p_neg, seed, c->stream);
+    cudaError_t e =
+        ea::launch_init_couplings(c->J, g, first_sample, n_samples, p_neg, seed, c->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c->spins, 0, c->spins_bytes, c->stream);
     if (e != cudaSuccess) {
@@ -604,8 +625,8 @@ int ea_create_samples_exact(ea_ctx **out, int L, double p_neg, uint64_t seed, in
         *out = nullptr;
         return EA_ERR_OOM;
     }
-    cudaError_t e = ea::launch_init_couplings_exact(c->J, c->geo, n_samples, p_neg, seed,
-                                                    scratch, c->stream);
+    cudaError_t e = ea::launch_init_couplings_exact(c->J, c->geo, c->first, n_samples, p_neg,
+                                                    seed, scratch, c->stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(c->stream);
     dev_free(scratch, scratch_bytes, c->stream);
@@ -651,7 +672,7 @@ int ea_quench(ea_ctx *c, double T, int rule)
     std::memcpy(c->always_k, alw, sizeof(alw));
     c->thr = make_thr(rule, T, thr, alw);
     ea::fill_job_thresholds(&c->jd, c->thr);
-    EA_CUDA(c, ea::launch_init_spins(c->spins, c->geo, c->S, c->seed, c->stream));
+    EA_CUDA(c, ea::launch_init_spins(c->spins, c->geo, c->first, c->S, c->seed, c->stream));
     if (c->res)
         EA_CUDA(c, cudaMemsetAsync(c->res, 0, c->res_bytes, c->stream));
     ++c->res_gen;
@@ -816,7 +837,65 @@ int ea_c4_radial_bins(int L, int *n_bins)
     return EA_OK;
 }
 
-int ea_c4_radial(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts)
+// Vectors per squared distance r^2 of side L: a shortest-image component m
+// stands for d = m and d = L - m, one vector when they coincide (m = 0 or L/2).
+static void c4_radial_counts(int L, long long *counts)
+{
+    const int H = L / 2, n_bins = 3 * H * H + 1;
+    std::fill(counts, counts + n_bins, 0LL);
+    auto images = [H](int m) { return (m == 0 || m == H) ? 1LL : 2LL; };
+    for (int mz = 0; mz <= H; ++mz)
+        for (int my = 0; my <= H; ++my)
+            for (int mx = 0; mx <= H; ++mx)
+                counts[mx * mx + my * my + mz * mz] += images(mx) * images(my) * images(mz);
+}
+
+// The FP64 curve of the all-vector sums (Eq. 3 over every displacement vector
+// of length r): for a bin with vectors, C4 = sum_s sums[s][b] / (counts[b] N S)
+// and sem the standard error over samples of sums[s][b] / (counts[b] N) (NaN
+// for one sample); a bin with no vector gets NaN in both.  Either output may
+// be NULL.
+static void c4_radial_curve(const long long *sums, const long long *counts, int S, int n_bins,
+                            double N, double *C4, double *sem)
+{
+    if (!C4 && !sem)
+        return;
+    std::vector<double> ps((size_t)S);
+    for (int b = 0; b < n_bins; ++b) {
+        if (counts[b] == 0) {
+            if (C4)
+                C4[b] = NAN;
+            if (sem)
+                sem[b] = NAN;
+            continue;
+        }
+        const double norm = (double)counts[b] * N;
+        long long tot = 0;
+        for (int s = 0; s < S; ++s)
+            tot += sums[(size_t)s * n_bins + b];
+        if (C4)
+            C4[b] = (double)tot / (norm * (double)S);
+        if (!sem)
+            continue;
+        if (S < 2) {
+            sem[b] = NAN;
+            continue;
+        }
+        double mean = 0.0;
+        for (int s = 0; s < S; ++s) {
+            ps[s] = (double)sums[(size_t)s * n_bins + b] / norm;
+            mean += ps[s];
+        }
+        mean /= (double)S;
+        double ss = 0.0;
+        for (int s = 0; s < S; ++s)
+            ss += (ps[s] - mean) * (ps[s] - mean);
+        sem[b] = std::sqrt(ss / (double)(S - 1)) / std::sqrt((double)S);
+    }
+}
+
+int ea_c4_radial(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts, double *C4,
+                 double *C4_sem)
 {
     NvtxRange nvtx_range("ea_c4_radial");
     if (check_ctx(c) || !sums || !counts)
@@ -829,15 +908,7 @@ int ea_c4_radial(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts)
     if (i < 0 || t_w > c->t)
         return fail(c, EA_ERR_NO_SNAPSHOT, "t_w not scheduled or not reached");
     const int L = c->L, H = L / 2, n_bins = 3 * H * H + 1;
-    // vectors per r^2: a shortest-image component m stands for d = m and d = L - m,
-    // one vector when they coincide (m = 0 or L/2)
-    std::fill(counts, counts + n_bins, 0LL);
-    for (int mz = 0; mz <= H; ++mz)
-        for (int my = 0; my <= H; ++my)
-            for (int mx = 0; mx <= H; ++mx) {
-                auto f = [H](int m) { return (m == 0 || m == H) ? 1LL : 2LL; };
-                counts[mx * mx + my * my + mz * mz] += f(mx) * f(my) * f(mz);
-            }
+    c4_radial_counts(L, counts);
     ea::C4FullTables fwd, inv;
     if (ea::make_c4full_plan(L, &fwd, &inv) != 0)
         return fail(c, EA_ERR_INVALID_ARG, "ea_c4_radial: no transform prime for this side");
@@ -868,11 +939,14 @@ int ea_c4_radial(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts)
     release();
     if (err != cudaSuccess)
         return cuda_fail(c, err, "ea_c4_radial");
+    c4_radial_curve(sums, counts, c->S, n_bins, (double)L * L * L, C4, C4_sem);
     return EA_OK;
 }
 
-int ea_c4_radial_noalloc(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts)
+int ea_c4_radial_noalloc(ea_ctx *c, uint64_t t_w, long long *sums, long long *counts, double *C4,
+                         double *C4_sem)
 {
+    NvtxRange nvtx_range("ea_c4_radial_noalloc");
     if (check_ctx(c) || !sums || !counts)
         return EA_ERR_INVALID_ARG;
     if (c->L > ea::kC4FullNoAllocMaxL)
@@ -884,13 +958,7 @@ int ea_c4_radial_noalloc(ea_ctx *c, uint64_t t_w, long long *sums, long long *co
     if (i < 0 || t_w > c->t)
         return fail(c, EA_ERR_NO_SNAPSHOT, "t_w not scheduled or not reached");
     const int L = c->L, H = L / 2, n_bins = 3 * H * H + 1;
-    std::fill(counts, counts + n_bins, 0LL);
-    for (int mz = 0; mz <= H; ++mz)
-        for (int my = 0; my <= H; ++my)
-            for (int mx = 0; mx <= H; ++mx) {
-                auto f = [H](int m) { return (m == 0 || m == H) ? 1LL : 2LL; };
-                counts[mx * mx + my * my + mz * mz] += f(mx) * f(my) * f(mz);
-            }
+    c4_radial_counts(L, counts);
     ea::C4FullTables fwd, inv;
     if (ea::make_c4full_plan(L, &fwd, &inv) != 0)
         return fail(c, EA_ERR_INVALID_ARG,
@@ -918,6 +986,7 @@ int ea_c4_radial_noalloc(ea_ctx *c, uint64_t t_w, long long *sums, long long *co
         err = cudaStreamSynchronize(c->stream);
     if (err != cudaSuccess)
         return cuda_fail(c, err, "ea_c4_radial_noalloc");
+    c4_radial_curve(sums, counts, c->S, n_bins, (double)L * L * L, C4, C4_sem);
     return EA_OK;
 }
 
@@ -1089,11 +1158,11 @@ int ea_get_thresholds(const ea_ctx *c, uint64_t thr[7], uint8_t always[7])
 
 // ---- checkpoint -----------------------------------------------------------
 namespace {
-constexpr char kMagic[8] = {'E', 'A', 'G', 'B', '3', '0', '0', '\1'};
+constexpr char kMagic[8] = {'E', 'A', 'G', 'B', '3', '0', '0', '\2'};
 
 struct CkptHeader {
     char magic[8];
-    int32_t L, S, G, rule;
+    int32_t L, S, G, rule, first, pad;
     double p_neg, T;
     uint64_t seed, t;
     uint64_t n_tw, n_t;
@@ -1142,6 +1211,7 @@ int ea_checkpoint(ea_ctx *c, const char *path)
     h.L = c->L;
     h.S = c->S;
     h.G = c->G;
+    h.first = c->first;
     h.rule = c->rule;
     h.p_neg = c->p_neg;
     h.T = c->T;
@@ -1190,7 +1260,7 @@ int ea_restore(ea_ctx **out, const char *path, void *cuda_stream)
         return EA_ERR_IO;
     }
     ea_ctx *c = nullptr;
-    int rc = ea_create_samples(&c, h.L, h.p_neg, h.seed, h.S, h.G, cuda_stream);
+    int rc = ea_create_samples_range(&c, h.L, h.p_neg, h.seed, h.first, h.S, h.G, cuda_stream);
     if (rc != EA_OK) {
         fclose(f);
         return rc;

@@ -88,6 +88,8 @@ struct alignas(16) JobDev {
     int div_n0_shift;
     int blocks_per_sample;
     int cols_per_thread;
+    int first_sample;         // the job-local index of the context's sample 0
+    int pad_[3];
 };
 
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev tables are arrays of 16-byte aligned rows");
@@ -123,7 +125,8 @@ struct MetroJob {
     const uint32_t *J;
     uint32_t key0, key1;   // Philox key (the seed); round keys are derived per block
     uint32_t rng_group;
-    uint32_t meta;         // bits 0-2 live classes, 3 all_always, 4 none_random, 8-15 geometry
+    uint32_t meta;         // bits 0-2 live classes, 3 all_always, 4 none_random, 8-15 geometry,
+                           // 16-31 the job-local index of the context's sample 0
 };
 
 constexpr int kMetroMaxGeo = 8;
@@ -203,19 +206,26 @@ cudaError_t launch_c4full(const uint32_t *snap, const Geo &g, int s0, int n_chun
 constexpr int kC4FullNoAllocMaxL = 128;
 cudaError_t c4full_static_scratch(long long **bins, uint32_t **residues);
 
+// The integer throughput of the current device (ea_probe.cu): out[0] lop3.b32
+// thread-ops/s, out[1] mad.lo.u32 thread-ops/s, out[2] Philox4x32-10 calls/s.
+cudaError_t probe_int_throughput(cudaStream_t stream, double out[3]);
+
 // Add n to the time field of every job of a table, stopping at its t_end
 // (device side, for graphs).
 cudaError_t launch_advance_time(JobDev *jobs_dev, int n_jobs, uint64_t n, cudaStream_t stream);
 
 // kernels (ea_kernels.cu); all enqueue on `stream` and return cudaGetLastError()
-cudaError_t launch_init_couplings(uint32_t *J, const Geo &g, int n_samples, double p_neg,
-                                  uint64_t seed, cudaStream_t stream);
+// Samples first_sample .. first_sample + n_samples - 1 of a job: the context's
+// sample s draws as the job's sample first_sample + s.
+cudaError_t launch_init_couplings(uint32_t *J, const Geo &g, int first_sample, int n_samples,
+                                  double p_neg, uint64_t seed, cudaStream_t stream);
 // Couplings with exactly floor(p_neg 3N + 1/2) negative bonds per sample (the
 // K-subset uniform); scratch holds n_samples * 260 words.
-cudaError_t launch_init_couplings_exact(uint32_t *J, const Geo &g, int n_samples, double p_neg,
-                                        uint64_t seed, uint32_t *scratch, cudaStream_t stream);
-cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int n_samples, uint64_t seed,
-                              cudaStream_t stream);
+cudaError_t launch_init_couplings_exact(uint32_t *J, const Geo &g, int first_sample,
+                                        int n_samples, double p_neg, uint64_t seed,
+                                        uint32_t *scratch, cudaStream_t stream);
+cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int first_sample, int n_samples,
+                              uint64_t seed, cudaStream_t stream);
 
 // observable sums (popcounts) accumulated with integer atomics
 // The observables of one measurement time (ea_kernels.cu: obs_time_kernel):

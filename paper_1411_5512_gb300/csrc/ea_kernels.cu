@@ -37,10 +37,10 @@ __device__ __forceinline__ void word_coords(const Geo &g, int w, int &xw, int &y
 // initial state
 // ---------------------------------------------------------------------------
 __global__ void init_couplings_kernel(uint32_t *__restrict__ J, Geo g, uint64_t thr_p, uint32_t k0,
-                                      uint32_t k1)
+                                      uint32_t k1, uint32_t s0)
 {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y;  // the context's sample s is the job's sample s0 + s
     if (w >= g.words)
         return;
     int xw, yw, zw;
@@ -50,7 +50,7 @@ __global__ void init_couplings_kernel(uint32_t *__restrict__ J, Geo g, uint64_t 
         const int bx = b % g.k[0], by = (b / g.k[0]) % g.k[1], bz = b / (g.k[0] * g.k[1]);
         const uint32_t x = bx * g.n[0] + xw, y = by * g.n[1] + yw, z = bz * g.n[2] + zw;
         const uint32_t i = x + (uint32_t)g.L * (y + (uint32_t)g.L * z);
-        const uint4 o = philox10(make_uint4(i, 0u, kStreamCouplings, (uint32_t)s), k0, k1);
+        const uint4 o = philox10(make_uint4(i, 0u, kStreamCouplings, s0 + (uint32_t)s), k0, k1);
         jw[0] |= (uint32_t)((uint64_t)o.x < thr_p) << b;
         jw[1] |= (uint32_t)((uint64_t)o.y < thr_p) << b;
         jw[2] |= (uint32_t)((uint64_t)o.z < thr_p) << b;
@@ -80,7 +80,8 @@ __device__ __forceinline__ void bond_key(uint32_t i, int d, uint32_t s, uint32_t
 }
 
 __global__ void exact_hist_kernel(int L, int pass, const uint32_t *__restrict__ state,
-                                  uint32_t *__restrict__ hist, uint32_t k0, uint32_t k1)
+                                  uint32_t *__restrict__ hist, uint32_t k0, uint32_t k1,
+                                  uint32_t s0)
 {
     __shared__ uint32_t h[256];
     const uint32_t s = blockIdx.y;
@@ -98,7 +99,7 @@ __global__ void exact_hist_kernel(int L, int pass, const uint32_t *__restrict__ 
         const int d = (int)(b / N);
         const uint32_t i = (uint32_t)(b - (uint64_t)d * N);
         uint32_t c[3];
-        bond_key(i, d, s, k0, k1, c[0], c[1]);
+        bond_key(i, d, s0 + s, k0, k1, c[0], c[1]);
         c[2] = (uint32_t)b;
         bool match = true;
         for (int w = 0; w < wsel; ++w)
@@ -144,7 +145,7 @@ __global__ void exact_select_kernel(int pass, uint32_t *__restrict__ state,
 
 // J words from the K-th composite P: a bond is negative iff (key, b) <= P.
 __global__ void exact_mark_kernel(uint32_t *__restrict__ J, Geo g, const uint32_t *__restrict__ state,
-                                  int none, uint32_t k0, uint32_t k1)
+                                  int none, uint32_t k0, uint32_t k1, uint32_t s0)
 {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = blockIdx.y;
@@ -163,7 +164,7 @@ __global__ void exact_mark_kernel(uint32_t *__restrict__ J, Geo g, const uint32_
             const uint32_t i = x + (uint32_t)g.L * (y + (uint32_t)g.L * z);
             for (int d = 0; d < 3; ++d) {
                 uint32_t hi, lo;
-                bond_key(i, d, (uint32_t)s, k0, k1, hi, lo);
+                bond_key(i, d, s0 + (uint32_t)s, k0, k1, hi, lo);
                 const uint32_t bi = (uint32_t)((uint64_t)d * N + i);
                 const bool le = hi != P0 ? hi < P0 : (lo != P1 ? lo < P1 : bi <= P2);
                 jw[d] |= (uint32_t)le << b;
@@ -177,7 +178,8 @@ __global__ void exact_mark_kernel(uint32_t *__restrict__ J, Geo g, const uint32_
     Js[2 * W + w] = jw[2];
 }
 
-__global__ void init_spins_kernel(uint32_t *__restrict__ spins, Geo g, uint32_t k0, uint32_t k1)
+__global__ void init_spins_kernel(uint32_t *__restrict__ spins, Geo g, uint32_t k0, uint32_t k1,
+                                  uint32_t s0)
 {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = blockIdx.y;
@@ -190,7 +192,7 @@ __global__ void init_spins_kernel(uint32_t *__restrict__ spins, Geo g, uint32_t 
         const int bx = b % g.k[0], by = (b / g.k[0]) % g.k[1], bz = b / (g.k[0] * g.k[1]);
         const uint32_t x = bx * g.n[0] + xw, y = by * g.n[1] + yw, z = bz * g.n[2] + zw;
         const uint32_t i = x + (uint32_t)g.L * (y + (uint32_t)g.L * z);
-        const uint4 o = philox10(make_uint4(i, 0u, kStreamSpins, (uint32_t)s), k0, k1);
+        const uint4 o = philox10(make_uint4(i, 0u, kStreamSpins, s0 + (uint32_t)s), k0, k1);
         rep[0] |= (o.x >> 31) << b;
         rep[1] |= (o.y >> 31) << b;
     }
@@ -548,19 +550,20 @@ inline dim3 grid_for(const Geo &g, int n_samples, int z = 1)
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_init_couplings(uint32_t *J, const Geo &g, int n_samples, double p_neg,
-                                  uint64_t seed, cudaStream_t stream)
+cudaError_t launch_init_couplings(uint32_t *J, const Geo &g, int first_sample, int n_samples,
+                                  double p_neg, uint64_t seed, cudaStream_t stream)
 {
     const uint64_t thr_p =
         p_neg >= 1.0 ? ((uint64_t)1 << 32) : (uint64_t)floor(ldexp(p_neg, 32));
     init_couplings_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(
-        J, g, thr_p, (uint32_t)seed, (uint32_t)(seed >> 32));
+        J, g, thr_p, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)first_sample);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_couplings_exact(uint32_t *J, const Geo &g, int n_samples, double p_neg,
-                                        uint64_t seed, uint32_t *scratch, cudaStream_t stream)
+cudaError_t launch_init_couplings_exact(uint32_t *J, const Geo &g, int first_sample,
+                                        int n_samples, double p_neg, uint64_t seed,
+                                        uint32_t *scratch, cudaStream_t stream)
 {
     const uint64_t N = (uint64_t)g.L * g.L * g.L;
     const uint64_t K = (uint64_t)std::floor(p_neg * 3.0 * (double)N + 0.5);
@@ -583,22 +586,24 @@ cudaError_t launch_init_couplings_exact(uint32_t *J, const Geo &g, int n_samples
         const uint64_t per = (3 * N + kBlock - 1) / kBlock;
         const dim3 gh((unsigned)std::min<uint64_t>(per, 512), (unsigned)n_samples);
         for (int pass = 0; pass < 12; ++pass) {
-            exact_hist_kernel<<<gh, kBlock, 0, stream>>>(g.L, pass, state, hist, k0, k1);
+            exact_hist_kernel<<<gh, kBlock, 0, stream>>>(g.L, pass, state, hist, k0, k1,
+                                                         (uint32_t)first_sample);
             exact_select_kernel<<<n_samples, 256, 0, stream>>>(pass, state, hist);
         }
         count_launches(24);
     }
     exact_mark_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(J, g, state, K == 0 ? 1 : 0,
-                                                                      k0, k1);
+                                                                      k0, k1,
+                                                                      (uint32_t)first_sample);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int n_samples, uint64_t seed,
-                              cudaStream_t stream)
+cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int first_sample, int n_samples,
+                              uint64_t seed, cudaStream_t stream)
 {
-    init_spins_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(spins, g, (uint32_t)seed,
-                                                                     (uint32_t)(seed >> 32));
+    init_spins_kernel<<<grid_for(g, n_samples), kBlock, 0, stream>>>(
+        spins, g, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)first_sample);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kSweepThreads, 10)
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
     const uint32_t *__restrict__ Jy = Jx + W;
     const uint32_t *__restrict__ Jz = Jy + W;
-    const uint32_t c3 = (uint32_t)s / J.rng_group;
+    const uint32_t c3 = ((uint32_t)s + (J.meta >> 16)) / J.rng_group;
     const uint32_t c1 = (uint32_t)t;
     const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
     const int sz = n0 * n1;
@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
     const uint32_t *__restrict__ Jy = Jx + W;
     const uint32_t *__restrict__ Jz = Jy + W;
-    const uint32_t c3 = (uint32_t)s / J.rng_group;
+    const uint32_t c3 = ((uint32_t)s + (J.meta >> 16)) / J.rng_group;
     const uint32_t c1 = (uint32_t)t;
     const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
     const int oz0 = z0 * SZ, oz1 = oz0 + SZ;
@@ -1084,7 +1084,7 @@ __global__ void __launch_bounds__(kSweepThreads, 8)
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
     const uint32_t *__restrict__ Jy = Jx + W;
     const uint32_t *__restrict__ Jz = Jy + W;
-    const uint32_t c3 = (uint32_t)s / J.rng_group;
+    const uint32_t c3 = ((uint32_t)s + (J.meta >> 16)) / J.rng_group;
     const uint32_t c1 = (uint32_t)t;
     const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
     const int oz0 = z0 * SZ, oz1 = oz0 + SZ;
@@ -1388,7 +1388,7 @@ __global__ void __launch_bounds__(kSweepThreads, 8)
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
     const uint32_t *__restrict__ Jy = Jx + W;
     const uint32_t *__restrict__ Jz = Jy + W;
-    const uint32_t c3 = (uint32_t)s / J.rng_group;
+    const uint32_t c3 = ((uint32_t)s + (J.meta >> 16)) / J.rng_group;
     const uint32_t c1 = (uint32_t)t;
     const uint32_t c2h = dev::kStreamHeat | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
     const int sz = n0 * n1;
@@ -1650,7 +1650,7 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
     const uint32_t *__restrict__ Jy = Jx + W;
     const uint32_t *__restrict__ Jz = Jy + W;
-    const uint32_t c3 = (uint32_t)s / J.rng_group;
+    const uint32_t c3 = ((uint32_t)s + (J.meta >> 16)) / J.rng_group;
     const uint32_t c1 = (uint32_t)t;
     const uint32_t c2h = dev::kStreamHeat | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
     const int oz0 = z0 * sz, oz1 = oz0 + sz;
@@ -1915,7 +1915,7 @@ static void metro_job(MetroJob &m, const JobDev &jd, int geo_index)
     m.key1 = jd.rk[1];
     m.rng_group = jd.rng_group;
     m.meta = (jd.geo_live & 7u) | (jd.all_always ? 8u : 0u) | (jd.none_random ? 16u : 0u) |
-             ((uint32_t)geo_index << 8);
+             ((uint32_t)geo_index << 8) | ((uint32_t)jd.first_sample << 16);
 }
 
 // Jobs host[0..cnt) in one launch sequence; all of them share at most

@@ -68,6 +68,13 @@ def launch_count():
     return int(_lib.load().ea_launch_count())
 
 
+def int_throughput(stream=None):
+    """{"lop3", "imad", "philox"}: measured thread-ops/s (Philox: calls/s) of this GPU."""
+    out = (ctypes.c_double * 3)()
+    _lib.check(_lib.load().ea_int_throughput(_stream_handle(stream), out))
+    return {"lop3": out[0], "imad": out[1], "philox": out[2]}
+
+
 def geometry(L):
     out = (ctypes.c_int * 6)()
     _lib.check(_lib.load().ea_geometry(L, out))
@@ -93,20 +100,28 @@ class EAJob:
     """n_samples disorder samples x 2 replicas of an L^3 +-J EA lattice."""
 
     def __init__(self, L, p_neg, seed, n_samples, rng_group=1, stream=None, _handle=None,
-                 exact_count=False):
+                 exact_count=False, first_sample=0):
         """exact_count: exactly floor(p_neg 3N + 1/2) negative bonds per sample instead of
-        independent bonds."""
+        independent bonds.  first_sample: this context holds the job's samples
+        first_sample .. first_sample + n_samples - 1 (ea_create_samples_range)."""
         self.lib = _lib.load()
         self.L = int(L)
         self.n_samples = int(n_samples)
+        self.first_sample = int(first_sample)
         self._stream = stream
         if _handle is not None:
             self.h = _handle
             return
         h = ctypes.c_void_p()
-        create = self.lib.ea_create_samples_exact if exact_count else self.lib.ea_create_samples
-        _lib.check(create(ctypes.byref(h), self.L, float(p_neg), int(seed), self.n_samples,
-                          int(rng_group), _stream_handle(stream)))
+        if exact_count:
+            assert self.first_sample == 0, "exact-count couplings cover whole jobs"
+            _lib.check(self.lib.ea_create_samples_exact(
+                ctypes.byref(h), self.L, float(p_neg), int(seed), self.n_samples, int(rng_group),
+                _stream_handle(stream)))
+        else:
+            _lib.check(self.lib.ea_create_samples_range(
+                ctypes.byref(h), self.L, float(p_neg), int(seed), self.first_sample,
+                self.n_samples, int(rng_group), _stream_handle(stream)))
         self.h = h
 
     # -- lifecycle ---------------------------------------------------------------
@@ -144,24 +159,24 @@ class EAJob:
         return {"A": A, "Q": Q, "E": E, "G": G, "C4": C4, "C4_sem": sem, "C": obs.C,
                 "q_mean": obs.q_mean, "xi1": obs.xi1, "r_cut": obs.r_cut}
 
-    def c4_radial(self, t_w):
+    def c4_radial(self, t_w, noalloc=False):
         """Four-point sums over every displacement vector of the snapshot at t_w,
         binned by squared distance: {"sums": [S, n_bins], "counts": [n_bins],
-        "r2", "r" (the occupied bins), "C4" (sample mean), "C4_sem" (over samples),
-        "C4_samples" [S, bins]}, C4 = sums / (counts N) over the occupied bins."""
+        "r2", "r" (the occupied bins), "C4", "C4_sem" (the library's FP64 curve
+        over the occupied bins)}.  noalloc: through ea_c4_radial_noalloc."""
         nb = ctypes.c_int()
         _lib.check(self.lib.ea_c4_radial_bins(int(self.L), ctypes.byref(nb)))
         sums = np.zeros((self.n_samples, nb.value), dtype=np.int64)
         counts = np.zeros(nb.value, dtype=np.int64)
-        _lib.check(self.lib.ea_c4_radial(self.h, int(t_w), sums.ctypes.data_as(_lib.i64p),
-                                         counts.ctypes.data_as(_lib.i64p)), self.h)
+        c4 = np.zeros(nb.value, dtype=np.float64)
+        sem = np.zeros(nb.value, dtype=np.float64)
+        fn = self.lib.ea_c4_radial_noalloc if noalloc else self.lib.ea_c4_radial
+        _lib.check(fn(self.h, int(t_w), sums.ctypes.data_as(_lib.i64p),
+                      counts.ctypes.data_as(_lib.i64p), c4.ctypes.data_as(_lib.dblp),
+                      sem.ctypes.data_as(_lib.dblp)), self.h)
         occ = np.nonzero(counts)[0]
-        N = float(self.L) ** 3
-        per = sums[:, occ] / (counts[occ] * N)
-        S = self.n_samples
-        sem = per.std(axis=0, ddof=1) / np.sqrt(S) if S > 1 else np.zeros(len(occ))
         return {"sums": sums, "counts": counts, "r2": occ, "r": np.sqrt(occ.astype(np.float64)),
-                "C4": per.mean(axis=0), "C4_sem": sem, "C4_samples": per}
+                "C4": c4[occ], "C4_sem": sem[occ]}
 
     def spins(self, s, a):
         out = np.zeros((self.L,) * 3, dtype=np.int8)

@@ -288,10 +288,22 @@ def test_c4_radial_matches_oracle(J, L, S, n, T):
     j.sweep(n)
     out = j.c4_radial(n)
     ref = ora.run_job(L, p_neg, seed, S, T, 0, [], [], n, keep_spins=True)
+    ref_sums = []
     for s in range(S):
         sums, counts = ora.c4_radial_sums(ora.c4_full_sums(ref["spins"][s]))
         assert np.array_equal(out["counts"], counts)
         assert np.array_equal(out["sums"][s], sums), s
+        ref_sums.append(sums)
+    # the library's FP64 curve against the oracle's sums normalised here (Eq. 3 over
+    # every vector of length r): C4 = sum / (count N S), the error over samples
+    occ = np.nonzero(counts)[0]
+    ref_sums = np.stack(ref_sums)[:, occ]
+    norm = counts[occ] * float(L) ** 3
+    assert close(out["C4"], ref_sums.sum(axis=0) / (norm * S))
+    if S > 1:
+        assert close(out["C4_sem"], (ref_sums / norm).std(axis=0, ddof=1) / math.sqrt(S))
+    else:
+        assert np.all(np.isnan(out["C4_sem"]))
     # the quenched state, from the snapshot at t_w = 0
     out0 = j.c4_radial(0)
     for s in range(S):
@@ -612,3 +624,52 @@ def test_coupling_words_move_whole_disorder(J):
         c.set_coupling_words(w6)
     for j in (a, b, c):
         j.close()
+
+
+# ----------------------------------------------------------------------------------
+# sample ranges: a context holding samples [lo, hi) of a job
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("L,S,lo,hi,G,rule,batch",
+                         [(16, 5, 2, 5, 1, 0, False), (32, 6, 1, 4, 2, 0, True),
+                          (64, 4, 1, 3, 1, 1, True), (128, 5, 3, 5, 1, 0, True),
+                          (128, 4, 1, 3, 2, 1, False)])
+def test_sample_range_matches_whole_job(J, L, S, lo, hi, G, rule, batch):
+    """Samples lo .. hi-1 of a job created on their own (their job-local indices key
+    every random number, share groups included) equal those samples of the whole job
+    bit for bit: spins, couplings and every integer sum; one of them also equals the
+    oracle."""
+    seed, p_neg, T, n = 40 + L, 0.4, 0.8, 4
+    t_w, t = [0, 2], [0, 1, 2]
+    whole = J.EAJob(L, p_neg, seed, S, rng_group=G)
+    part = J.EAJob(L, p_neg, seed, hi - lo, rng_group=G, first_sample=lo)
+    for j in (whole, part):
+        j.set_schedule(t_w, t)
+        j.quench(T, rule)
+        if batch:
+            b = J.EABatch()
+            b.add(j)
+            b.sweep(n)
+            b.close()
+        else:
+            j.sweep(n)
+    for i, s in enumerate(range(lo, hi)):
+        assert np.array_equal(part.couplings(i), whole.couplings(s)), s
+        assert np.array_equal(part.all_spins(i), whole.all_spins(s)), s
+    for tw in t_w:
+        for lag in t:
+            a, b_ = part.measure(tw, lag), whole.measure(tw, lag)
+            for k in ("A", "Q", "E", "G"):
+                assert np.array_equal(a[k], b_[k][lo:hi]), (k, tw, lag)
+    ref = ora.run_job(L, p_neg, seed, S, T, rule, [], [], n, samples=[hi - 1], keep_spins=True,
+                      rng_group=G)
+    assert np.array_equal(part.all_spins(hi - lo - 1), ref["spins"][0])
+    whole.close()
+    part.close()
+
+
+def test_sample_range_rejects_bad_ranges(J):
+    from paper_1411_5512_gb300 import _lib
+    for first, n in ((-1, 2), (65534, 2), (0, 0)):
+        with pytest.raises(_lib.EAError) as e:
+            J.EAJob(16, 0.5, 1, n, first_sample=first)
+        assert e.value.status == _lib.EA_ERR_INVALID_ARG
