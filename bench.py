@@ -25,6 +25,7 @@ if ROOT not in sys.path:
 
 METRIC = "spin flips/ns (ps/flip) at L=128 + % of roofline; batched vs plain; p50/p99"
 UNIT = "flips/ns"
+WORKLOAD = "L128_p0.5-0.1_S16x5_T0.7"
 
 
 # ----------------------------------------------------------------------------------
@@ -114,52 +115,161 @@ def dist_setup():
 
 
 # ----------------------------------------------------------------------------------
-# reference arm: the CPU oracle
+# the CPU oracle on the host's cores (reference arm and cpu_baseline leg)
 # ----------------------------------------------------------------------------------
-def cpu_oracle_sample(n_sweeps=4, L=128):
-    """Oracle on sample 0 of the first side-128 job: flips/ns on one host thread."""
+def host_cpu():
+    """(cores this process may use, CPU model name)."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return n, model
+
+
+def _oracle_worker(conn, cases):
+    """One host process: the oracle's state of its samples, swept on request."""
+    sys.path.insert(0, ROOT)
     import oracle as ora
+    state = []
+    for L, p_neg, seed, s, T, rule in cases:
+        state.append([L, seed, s, ora.init_spins(L, seed, s), ora.init_couplings(L, p_neg, seed, s),
+                      T, rule, 0])
+    conn.send("ready")
+    while True:
+        n = conn.recv()
+        if n is None:
+            break
+        for st in state:
+            L, seed, s, S, J, T, rule, t = st
+            ora.sweeps(L, seed, s, S, J, T, rule, t, n)
+            st[7] = t + n
+        conn.send(True)
+    conn.close()
+
+
+class OraclePool:
+    """The oracle's samples spread over `procs` host processes (spawned), each
+    sweeping its own samples; sweep(n) returns the wall time of the slowest."""
+
+    def __init__(self, cases, procs):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        procs = max(1, min(procs, len(cases)))
+        self.flips_per_sweep = sum(2 * c[0] ** 3 for c in cases)
+        self.procs = procs
+        self.conns, self.workers = [], []
+        for k in range(procs):
+            a, b = ctx.Pipe()
+            w = ctx.Process(target=_oracle_worker, args=(b, cases[k::procs]), daemon=True)
+            w.start()
+            self.conns.append(a)
+            self.workers.append(w)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    def sweep(self, n):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(n)
+        for c in self.conns:
+            c.recv()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for w in self.workers:
+            w.join(timeout=30)
+
+
+def _oracle_rate(cases, procs, sweeps):
+    """flips/ns of the oracle over `cases` on `procs` processes: one untimed sweep,
+    then `sweeps` timed ones."""
+    pool = OraclePool(cases, procs)
+    try:
+        pool.sweep(1)
+        dt = pool.sweep(sweeps)
+    finally:
+        pool.close()
+    flips = pool.flips_per_sweep * sweeps
+    return {"value": flips / (dt * 1e9), "ps_per_flip": dt * 1e12 / flips, "flips": flips,
+            "seconds": dt, "cores": pool.procs}
+
+
+def cpu_oracle_baseline(l128_sweeps=10, c2_sweeps=100):
+    """The oracle timed on the host: single-thread and one process per sample on all
+    cores, at side 128 (the 16 samples of the p_neg = 0.5 job) and at side 32 (the
+    64 samples of the T = 0.6 job)."""
     from paper_1411_5512_gb300 import workloads
 
+    n_cores, model = host_cpu()
     w = workloads.PAPER_SCALE[0]
-    J = ora.init_couplings(L, w["p_neg"], w["seed"], 0)
-    S = ora.init_spins(L, w["seed"], 0)
-    ora.sweeps(L, w["seed"], 0, S, J, w["T"], 0, 0, 1)  # warm the library
-    t0 = time.perf_counter()
-    ora.sweeps(L, w["seed"], 0, S, J, w["T"], 0, 1, n_sweeps)
-    dt = time.perf_counter() - t0
-    flips = n_sweeps * 2 * L ** 3
-    return {"value": flips / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "sample 0 of the L=128 p_neg=0.5 job, %d sweeps x 2 replicas "
-                      "(%.3g flips, %.1f s), one host thread" % (n_sweeps, flips, dt)}
+    l128 = [(w["L"], w["p_neg"], w["seed"], s, w["T"], 0) for s in range(w["n_samples"])]
+    c = workloads.SMALL[0]
+    c2 = [(c["L"], c["p_neg"], c["seed"], s, c["T"], 0) for s in range(c["n_samples"])]
+    all_128 = _oracle_rate(l128, n_cores, l128_sweeps)
+    one_128 = _oracle_rate(l128, 1, l128_sweeps)
+    all_c2 = _oracle_rate(c2, n_cores, c2_sweeps)
+    one_c2 = _oracle_rate(c2[:8], 1, c2_sweeps)
+    desc = "%d samples x 2 replicas of the L=%d p_neg=%.1f job (T=%.1f), %d sweeps"
+    return {"value": all_128["value"], "unit": UNIT, "cores": all_128["cores"], "kind": "oracle",
+            "ps_per_flip": all_128["ps_per_flip"],
+            "sample": (desc % (w["n_samples"], w["L"], w["p_neg"], w["T"], l128_sweeps)) +
+                      ", one process per sample on all host cores",
+            "host": {"nproc": n_cores, "model": model},
+            "single_thread": dict(one_128, sample=desc % (w["n_samples"], w["L"], w["p_neg"],
+                                                           w["T"], l128_sweeps)),
+            "c2": {"all_cores": dict(all_c2, sample=desc % (c["n_samples"], c["L"], c["p_neg"],
+                                                            c["T"], c2_sweeps)),
+                   "single_thread": dict(one_c2, sample=desc % (8, c["L"], c["p_neg"], c["T"],
+                                                                c2_sweeps))}}
 
 
 def run_reference(args, world, rank):
+    """The oracle as it stands on the host's cores: each step one sweep of the 16
+    samples of the side-128 p_neg = 0.5 job, one process per sample."""
     if rank != 0:
         return 0
+    from paper_1411_5512_gb300 import workloads
+
+    n_cores, model = host_cpu()
+    w = workloads.PAPER_SCALE[0]
+    cases = [(w["L"], w["p_neg"], w["seed"], s, w["T"], 0) for s in range(w["n_samples"])]
     per_step = max(1, args.ref_sweeps)
-    for _ in range(args.warmup):
-        cpu_oracle_sample(1)
-    times = []
-    flips = 0
-    for _ in range(args.steps):
-        r = cpu_oracle_sample(per_step)
-        times.append(per_step * 2 * 128 ** 3 / (r["value"] * 1e9))
-        flips += per_step * 2 * 128 ** 3
+    pool = OraclePool(cases, n_cores)
+    try:
+        for _ in range(args.warmup):
+            pool.sweep(per_step)
+        times = [pool.sweep(per_step) for _ in range(args.steps)]
+    finally:
+        pool.close()
     tot = sum(times)
+    flips = pool.flips_per_sweep * per_step * args.steps
     value = flips / (tot * 1e9)
+    sample = ("%d steps x %d sweep(s) of the %d samples x 2 replicas of the L=128 p_neg=0.5 "
+              "job, one process per sample on %d host cores" %
+              (args.steps, per_step, w["n_samples"], pool.procs))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "L128_p0.5-0.1_S16x5_T0.7", "L": 128,
-                       "jobs": [0.5, 0.4, 0.3, 0.2, 0.1], "samples": 80, "replicas": 2,
-                       "rule": "metropolis", "rng_group": 1, "sweeps_per_step": per_step,
-                       "path": "the CPU oracle on one host thread, each step a bounded sample "
+            "config": {"workload": WORKLOAD, "L": 128,
+                       "jobs": [x["p_neg"] for x in workloads.PAPER_SCALE], "samples": 80,
+                       "replicas": 2, "rule": "metropolis", "rng_group": 1,
+                       "sweeps_per_step": per_step,
+                       "path": "the CPU oracle on the host's cores, each step a bounded sample "
                                "of the workload (cpu_baseline.sample)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d steps x sample 0 of the L=128 p_neg=0.5 job x %d "
-                                       "sweeps x 2 replicas" % (args.steps, per_step)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+                             "sample": sample, "host": {"nproc": n_cores, "model": model}},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -169,13 +279,21 @@ def run_reference(args, world, rank):
 # ----------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------
-# integer ops per word update of the Metropolis sweep:
-# 6 LOP3 bond bits + 8 LOP3 count + 4 accept/flip/store + 5 class masks
-# + 3 class tests x (popc, table load, compare, branch)
-OPS_FIXED_PER_WORD = 35
-OPS_PER_PHILOX = 60        # 10 rounds x (2 mul.lo + 2 mul.hi + 2 three-input XOR)
-INT_LANES_PER_SM = 128     # int32-capable lanes per SM (4 SMSP x 32)
-N_SM = 152
+# The roofline of the method, per flip (one attempted update of one site of one
+# replica of one sample):
+# - memory: a sweep must move the state across memory at least once: read 2
+#   spin bits and 3 coupling bits, write 2 spin bits per site and sample, 7
+#   bits per 2 flips = 0.4375 B/flip.  A pair of half-step kernels moves 12 bits
+#   per 2 flips (0.75 B/flip); reported beside it.
+# - integer ops: about 20 bit-logic ops per 32-site word (bond bits, bit-sliced
+#   count, accept mask, flip) and about 90 per Philox4x32-10 call (ten rounds of
+#   two wide multiplies, two three-input XORs and the key schedule), with the
+#   calls per word counted on the live state; every op is priced at the measured
+#   lop3.b32 rate of this GPU (ea_int_throughput).
+BYTES_PER_FLIP = 7.0 / 16.0
+BYTES_PER_FLIP_HALF_STEPS = 12.0 / 16.0
+OPS_LOGIC_PER_WORD = 20
+OPS_PER_PHILOX = 90
 # DRAM bytes (read + write) of one batched half-step launch of this workload
 # per launch shape (rows per thread 4, 8, 16 <-> --cpt 1, 2, 4), from an ncu
 # capture of this command with that fixed shape (dram__bytes_read.sum +
@@ -207,6 +325,56 @@ def pct(v, q):
         return None
     i = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
     return v[i]
+
+
+def value_per_launch(flips_per_launch, kernel_ms):
+    """flips per launch and seconds per launch of the timed half-step kernel."""
+    return flips_per_launch, kernel_ms * 1e-3
+
+
+def traffic_bytes(args, batch_cfg):
+    if args.traffic_bytes is not None:
+        return args.traffic_bytes
+    return TRAFFIC_BYTES_PER_LAUNCH.get(batch_cfg[0])
+
+
+def roofline(per_launch, ops_per_flip, ipk, traffic, calls_per_word):
+    """The binding roof of the half-step kernel and the others beside it.  HBM at the
+    algorithmic 0.4375 B/flip against the measured copy bandwidth; integer ALU at
+    the algorithmic ops per flip against the measured lop3.b32 rate."""
+    flips, launch_s = per_launch
+    pk, pk_kind = peaks()
+    rate = flips / launch_s  # flips/s
+    hbm_roof = pk["hbm_gbs"] * 1e9 / BYTES_PER_FLIP
+    alu_peak = ipk["lop3"]
+    alu_roof = alu_peak / ops_per_flip
+    hbm = {"bound": "hbm", "achieved": rate * BYTES_PER_FLIP / 1e9, "peak": pk["hbm_gbs"],
+           "unit": "GB/s", "frac": rate / hbm_roof, "roof_flips_per_ns": hbm_roof / 1e9,
+           "bytes_per_flip": BYTES_PER_FLIP,
+           "peak_kind": "%s copy bandwidth (MEASURED_PEAKS.json)" % pk_kind}
+    alu = {"bound": "alu", "achieved": rate * ops_per_flip / 1e12, "peak": alu_peak / 1e12,
+           "unit": "Tops/s", "frac": rate / alu_roof, "roof_flips_per_ns": alu_roof / 1e9,
+           "ops_per_flip": ops_per_flip, "philox_calls_per_word": calls_per_word,
+           "peak_kind": "measured lop3.b32 rate of this GPU (ea_int_throughput)",
+           "measured_rates": {"lop3_tops": ipk["lop3"] / 1e12, "imad_tops": ipk["imad"] / 1e12,
+                              "philox_gcalls": ipk["philox"] / 1e9}}
+    half = {"bound": "hbm", "bytes_per_flip": BYTES_PER_FLIP_HALF_STEPS,
+            "achieved": rate * BYTES_PER_FLIP_HALF_STEPS / 1e9, "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": rate * BYTES_PER_FLIP_HALF_STEPS / 1e9 / pk["hbm_gbs"],
+            "roof_flips_per_ns": pk["hbm_gbs"] / BYTES_PER_FLIP_HALF_STEPS,
+            "what": "the traffic of a pair of half-step kernels, for comparison"}
+    primary, other = (hbm, alu) if hbm_roof <= alu_roof else (alu, hbm)
+    roof = dict(primary)
+    roof.update({"kernel": "metro_tile_kernel", "flips_per_launch": flips,
+                 "traffic": traffic,
+                 "traffic_over_algorithmic": (None if traffic is None else
+                                              traffic / (flips * BYTES_PER_FLIP)),
+                 "binding": "%s roof %.0f flips/ns (HBM %.0f, integer ALU %.0f); the 105 MB "
+                            "state stays in the 126 MB L2 within a step" %
+                            (primary["bound"], min(hbm_roof, alu_roof) / 1e9, hbm_roof / 1e9,
+                             alu_roof / 1e9),
+                 "other": other, "half_step_traffic": half})
+    return roof
 
 
 def run_ours(args, world, rank, local):
@@ -290,45 +458,25 @@ def run_ours(args, world, rank, local):
     plain_ms = timed_steps(stream, args.steps, plain_step, flush)
     plain_value = flips_per_step * args.steps / (sum(plain_ms) * 1e6)
 
-    # algorithmic integer work of the update, counted on the live state
+    # Philox calls per word, counted on the live state by the counting variant
     batch = job.EABatch(stream=stream)
     for j in jobs:
         batch.add(j)
     prof = batch.profile(sweeps=4)
     batch.close()
-    words = max(1, prof["words"])
-    ops_per_word = OPS_FIXED_PER_WORD + OPS_PER_PHILOX * prof["philox_calls"] / words
-    # word updates and flips are both counted over the same sweeps (32 sites per word)
-    ops_per_flip = ops_per_word * words / prof["flips"]
+    calls_per_word = prof["philox_calls"] / max(1, prof["words"])
+    ops_per_flip = (OPS_LOGIC_PER_WORD + OPS_PER_PHILOX * calls_per_word) / 32.0
+    ipk = job.int_throughput(stream)  # measured integer rates of this GPU
+    roof = roofline(value_per_launch(samples * N, kernel_ms), ops_per_flip, ipk,
+                    traffic_bytes(args, batch_cfg), calls_per_word)
+    roof["kernel_us_per_launch"] = kernel_ms * 1e3
 
-    pk, pk_kind = peaks()
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak_tops = N_SM * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    flips_per_launch = samples * N  # one half-step updates every site of one replica
-    launch_s = kernel_ms * 1e-3
-    achieved_tops = flips_per_launch * ops_per_flip / launch_s / 1e12
-    bytes_per_flip = 6.0 / 8.0
-    achieved_gbs = flips_per_launch * bytes_per_flip / launch_s / 1e9
-    # the two roofs in flips/ns; the slower one bounds the kernel
-    hbm_roof = pk["hbm_gbs"] / bytes_per_flip
-    alu_roof = peak_tops * 1e3 / ops_per_flip
-    alu = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
-           "frac": achieved_tops / peak_tops, "roof_flips_per_ns": alu_roof,
-           "peak_basis": "152 SMs x 128 int32 lanes x %.0f MHz (max SM clock)" % sm_mhz,
-           "ops_per_flip": ops_per_flip,
-           "philox_calls_per_word": prof["philox_calls"] / words}
-    hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-           "frac": achieved_gbs / pk["hbm_gbs"], "roof_flips_per_ns": hbm_roof,
-           "bytes_per_flip": bytes_per_flip, "peak_kind": pk_kind + " (copy bandwidth)"}
-    primary, other = (hbm, alu) if hbm_roof <= alu_roof else (alu, hbm)
-    roof = dict(primary)
-    traffic = (args.traffic_bytes if args.traffic_bytes is not None
-               else TRAFFIC_BYTES_PER_LAUNCH.get(batch_cfg[0]))
-    roof.update({"traffic": traffic, "kernel": "metro_tile_kernel",
-                 "traffic_over_algorithmic": (None if traffic is None else
-                                              traffic / (flips_per_launch * bytes_per_flip)),
-                 "kernel_us_per_launch": kernel_ms * 1e3,
-                 "flips_per_launch": flips_per_launch, "other": other})
+    # the paper's plain path: one sample per launch sequence, two launches per
+    # sweep, over every sample of the workload
+    plain1 = None
+    if not args.no_plain_single:
+        plain1 = run_plain_single(args, job, workloads, stream, flush, t_w, t_lag,
+                                  jobs[0].time)
 
     e2e = None
     if not args.no_e2e:
@@ -347,8 +495,8 @@ def run_ours(args, world, rank, local):
         c4r = run_c4_radial(args, job, workloads, stream)
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
-        cpu = cpu_oracle_sample(args.cpu_sweeps)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_baseline(args.cpu_l128_sweeps, args.cpu_c2_sweeps)
 
     for j in jobs:
         j.close()
@@ -357,7 +505,7 @@ def run_ours(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "ps_per_flip": 1e3 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "L128_p0.5-0.1_S16x5_T0.7", "L": L,
+            "config": {"workload": WORKLOAD, "L": L,
                        "jobs": [w["p_neg"] for w in specs], "samples": samples, "replicas": 2,
                        "sweeps_per_step": sps, "rule": "metropolis", "rng_group": 1,
                        "path": "batched (one launch per half-step for all 5 jobs)",
@@ -367,10 +515,14 @@ def run_ours(args, world, rank, local):
                              "L2-sized, so sweeps inside a step see it cache-warm"},
             "step_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99)},
             "plain": {"value": plain_value, "unit": UNIT,
-                      "path": "per-job launches, 2 per sweep per job",
+                      "path": "per-job launch sequences (16 samples per launch), 2 launches "
+                              "per sweep per job",
                       "step_ms": {"p50": pct(plain_ms, 50), "p99": pct(plain_ms, 99)}},
             "batched_over_plain": value / plain_value,
             "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches, "wall_s": wall}
+    if plain1 is not None:
+        line["plain_single"] = plain1
+        line["batched_over_plain_single"] = value / plain1["value"]
     if e2e is not None:
         line["e2e"] = e2e
     if serving is not None:
@@ -388,6 +540,40 @@ def run_ours(args, world, rank, local):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_plain_single(args, job, workloads, stream, flush, t_w, t_lag, t_now):
+    """Every sample of the workload in a context of its own (its job's sample s,
+    ea_create_samples_range), each swept by its own launch sequence, two launches per
+    sweep: the paper's plain path.  The contexts are first brought to the batched
+    jobs' time, so both see a lattice of the same age."""
+    specs = workloads.PAPER_SCALE
+    ctxs = []
+    for w in specs:
+        for s in range(w["n_samples"]):
+            j = job.EAJob(w["L"], w["p_neg"], w["seed"], 1, stream=stream, first_sample=s)
+            j.set_schedule(t_w, t_lag)
+            j.quench(w["T"])
+            ctxs.append(j)
+    b = job.EABatch(stream=stream)
+    for j in ctxs:
+        b.add(j)
+    b.sweep(t_now)
+    b.close()
+    sps = args.sweeps_per_step
+
+    def step():
+        for j in ctxs:
+            j.sweep(sps)
+
+    step()
+    ms = timed_steps(stream, 3, step, flush)
+    for j in ctxs:
+        j.close()
+    flips = sps * sum(2 * w["n_samples"] * w["L"] ** 3 for w in specs)
+    m = statistics.median(ms)
+    return {"value": flips / (m * 1e6), "unit": UNIT, "ms_per_step": m,
+            "path": "one sample per launch sequence (80 contexts), 2 launches per sweep each"}
 
 
 def run_mixed(args, job, workloads, stream, flush):
@@ -496,7 +682,9 @@ def run_serving(args, job, workloads, stream):
                        chunk_sweeps=args.serve_chunk, stream=stream)
     t_sched = [0, 1, 2, 4, 8, 16, 32, 64, 128, 256, 512]
     arrival = {}
+    sweeps_of = {}
     lat = []
+    lat_k = []  # completion latency per 10^3 sweeps of the job
     flips = 0
     nxt = 0
     open_ids = []
@@ -508,6 +696,7 @@ def run_serving(args, job, workloads, stream):
             jid = srv.submit(sp["L"], sp["p_neg"], sp["seed"], sp["n_samples"], sp["T"],
                              sp["sweeps"], t_w=t_sched, t=t_sched)
             arrival[jid] = sp["arrival"]
+            sweeps_of[jid] = sp["sweeps"]
             flips += sp["sweeps"] * 2 * sp["n_samples"] * sp["L"] ** 3
             open_ids.append(jid)
             nxt += 1
@@ -523,6 +712,7 @@ def run_serving(args, job, workloads, stream):
             if state == 2:
                 srv.job(jid).measure(0, 512)  # reads the results back (synchronises)
                 lat.append(time.perf_counter() - t0 - arrival[jid])
+                lat_k.append(lat[-1] / (sweeps_of[jid] / 1e3))
                 srv.release(jid)
             else:
                 still.append(jid)
@@ -531,11 +721,14 @@ def run_serving(args, job, workloads, stream):
     wall = time.perf_counter() - t0
     srv.close()
     lat = np.array(lat)
+    lat_k = np.array(lat_k)
     return {"workload": workloads.SERVING["name"], "jobs": len(specs),
             "rate_per_s": workloads.SERVING["rate"], "chunk_sweeps": args.serve_chunk,
             "latency_s": {"p50": float(np.percentile(lat, 50)),
                           "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max())},
+            "latency_s_per_1e3_sweeps": {"p50": float(np.percentile(lat_k, 50)),
+                                         "p99": float(np.percentile(lat_k, 99))},
             "flips": int(flips), "wall_s": wall, "value": flips / (wall * 1e9), "unit": UNIT}
 
 
@@ -606,6 +799,38 @@ def run_e2e(args, job, workloads, stream, rank, world):
                         "batched sweeps, all observables D2H, destroy"}
 
 
+def run_case(args):
+    """A small, self-contained run of the sweep kernels, for profiling: one job of
+    --case-samples samples at side --case-L (p_neg = 0.5, T = --case-T), quenched
+    and swept --case-sweeps times through a one-job batch with launch shape --cpt
+    (or the plain path with --case-plain).  At side 128 and 128 samples the state
+    is 168 MB, above the 126 MB L2, so DRAM counters stay meaningful while the
+    device footprint stays small."""
+    import torch
+
+    from paper_1411_5512_gb300 import job
+
+    torch.cuda.set_device(0)
+    j = job.EAJob(args.case_L, 0.5, 100, args.case_samples)
+    if args.case_c4_radial:
+        j.set_schedule([args.case_sweeps], [0])
+    j.quench(args.case_T, args.case_rule)
+    if args.case_plain:
+        j.sweep(args.case_sweeps)
+    else:
+        b = job.EABatch()
+        b.configure(args.cpt, 0)
+        b.add(j)
+        b.sweep(args.case_sweeps)
+        b.close()
+    if args.case_c4_radial:
+        j.c4_radial(args.case_sweeps)
+    torch.cuda.synchronize()
+    print("case ok: L=%d S=%d t=%d" % (args.case_L, args.case_samples, j.time))
+    j.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -615,8 +840,10 @@ def main():
     ap.add_argument("--sweeps-per-step", type=int, default=64)
     ap.add_argument("--e2e-sweeps", type=int, default=1024)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-sweeps", type=int, default=4)
-    ap.add_argument("--ref-sweeps", type=int, default=2)
+    ap.add_argument("--cpu-l128-sweeps", type=int, default=10)
+    ap.add_argument("--cpu-c2-sweeps", type=int, default=100)
+    ap.add_argument("--ref-sweeps", type=int, default=1)
+    ap.add_argument("--no-plain-single", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpt", type=int, default=0, choices=[0, 1, 2, 4],
                     help="fixed launch shape of the batched path instead of the autotuned one")
@@ -627,11 +854,22 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-heat", action="store_true")
     ap.add_argument("--mixed-sweeps", type=int, default=64)
-    ap.add_argument("--serve-jobs", type=int, default=40)
+    ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-chunk", type=int, default=1024)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", action="store_true",
+                    help="a small profiling run of the sweep kernels instead of the benchmark")
+    ap.add_argument("--case-L", type=int, default=128)
+    ap.add_argument("--case-samples", type=int, default=128)
+    ap.add_argument("--case-sweeps", type=int, default=4)
+    ap.add_argument("--case-rule", type=int, default=0)
+    ap.add_argument("--case-T", type=float, default=0.7)
+    ap.add_argument("--case-plain", action="store_true")
+    ap.add_argument("--case-c4-radial", action="store_true")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()
