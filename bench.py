@@ -820,6 +820,10 @@ def run_case(args):
     else:
         b = job.EABatch()
         b.configure(args.cpt, 0)
+        if args.case_variant >= 0:
+            b.set_variant(args.case_variant)
+        if args.case_resident >= 0:
+            b.set_resident(args.case_resident)
         b.add(j)
         b.sweep(args.case_sweeps)
         b.close()
@@ -867,6 +871,10 @@ def main():
     ap.add_argument("--case-T", type=float, default=0.7)
     ap.add_argument("--case-plain", action="store_true")
     ap.add_argument("--case-c4-radial", action="store_true")
+    ap.add_argument("--case-variant", type=int, default=-1,
+                    help="side-128 Metropolis kernel: 0 tile, 1 staged (-1: the default)")
+    ap.add_argument("--case-resident", type=int, default=-1,
+                    help="largest side run sample-resident (-1: the default)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

@@ -153,6 +153,23 @@ uint64_t ea_launch_count(void);
  * EA_ERR_INVALID_ARG (NULL out), EA_ERR_CUDA. */
 int ea_int_throughput(void *cuda_stream, double out[3]);
 
+/* Bounded waits on the device.  Every wait of a kernel on a barrier (the
+ * staged kernel waits for its bulk copies) polls at most `polls` times; when a
+ * wait runs out, the block waits for its own copies still in flight, sets
+ * bit 0 of the device status word and returns, leaving its rows of that
+ * half-step unfinished, so the context stays usable and the host learns of it
+ * from ea_device_status.  The default is 2^22 polls.  wait_for_nothing = 1 is
+ * for tests of that path only: the waits are then on a barrier that no copy
+ * ever completes, so each runs out after `polls` polls.  Process-wide; applies
+ * to launches enqueued afterwards.  Errors: EA_ERR_INVALID_ARG
+ * (wait_for_nothing not 0 or 1). */
+int ea_debug_set_wait(uint32_t polls, int wait_for_nothing);
+
+/* Synchronises the stream, reads and clears the device status word: *status
+ * bit 0 = a bounded wait ran out since the last read.  Returns EA_ERR_TIMEOUT
+ * when bit 0 is set, EA_ERR_CUDA when the read fails, else EA_OK. */
+int ea_device_status(void *cuda_stream, uint32_t *status);
+
 /* ---- job lifecycle ------------------------------------------------------- */
 
 /* Create a job of n_samples samples of side L and generate their couplings on
@@ -355,6 +372,28 @@ int ea_batch_size(const ea_batch *b, int *n_jobs);
  * outside 0..4096). */
 int ea_batch_configure(ea_batch *b, int cols_per_thread, int graph_sweeps);
 int ea_batch_get_config(const ea_batch *b, int *cols_per_thread, int *graph_sweeps);
+
+/* Metropolis members of side up to max_side (and at most 64) run sample-
+ * resident: one block per sample holds the sample's spins and couplings in
+ * shared memory and runs every sweep of a launch there (up to 1024), instead
+ * of one launch per half-step over memory (Sec. III: each half-step its own
+ * kernel with a global synchronisation between them).  0 turns it off.  The
+ * results do not change.  New batches use 32, and so does a context swept on
+ * its own (ea_sweep): up to side 32 one block per sample beats a launch per
+ * half-step.  The autotuner chooses among 32, 64 and 0.  get reads it back.
+ * Errors: EA_ERR_INVALID_ARG (NULL, max_side < 0). */
+int ea_batch_set_resident(ea_batch *b, int max_side);
+int ea_batch_get_resident(const ea_batch *b, int *max_side);
+
+/* The kernel of side-128 Metropolis members: 0 (the default) the
+ * register-window tile kernel; 1 the staged kernel, whose blocks bring each
+ * row of the state into shared memory with bulk asynchronous copies while the
+ * previous row is computed.  Both give the same results; the staged
+ * kernel applies when the tables of dE = 8 and 12 are small (T below about
+ * 1), the tile kernel otherwise.  The autotuner also chooses between them.
+ * Errors: EA_ERR_INVALID_ARG (NULL, variant not 0 or 1). */
+int ea_batch_set_variant(ea_batch *b, int variant);
+int ea_batch_get_variant(const ea_batch *b, int *variant);
 
 /* Try the launch shapes on the members' current state for trial_sweeps sweeps
  * each, keep the fastest and put the state back as it was (time, spins): the

@@ -69,6 +69,8 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_size_t)]),
     "ea_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, vp]),
     "ea_int_throughput": (ctypes.c_int, [vp, dblp]),
+    "ea_debug_set_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int]),
+    "ea_device_status": (ctypes.c_int, [vp, u32p]),
     "ea_create_samples": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
                                          ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp]),
     "ea_create_samples_exact": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
@@ -104,6 +106,10 @@ SIGNATURES = {
     "ea_batch_size": (ctypes.c_int, [vp, intp]),
     "ea_batch_configure": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
     "ea_batch_get_config": (ctypes.c_int, [vp, intp, intp]),
+    "ea_batch_set_resident": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ea_batch_get_resident": (ctypes.c_int, [vp, intp]),
+    "ea_batch_set_variant": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ea_batch_get_variant": (ctypes.c_int, [vp, intp]),
     "ea_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int]),
     "ea_batch_profile": (ctypes.c_int, [vp, ctypes.c_int, u64p]),
     "ea_batch_sweep": (ctypes.c_int, [vp, ctypes.c_uint64]),

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -529,6 +530,25 @@ int ea_footprint(int L, int n_samples, int n_tw, int n_t, size_t *bytes)
     return EA_OK;
 }
 
+int ea_debug_set_wait(uint32_t polls, int wait_for_nothing)
+{
+    if (wait_for_nothing != 0 && wait_for_nothing != 1)
+        return EA_ERR_INVALID_ARG;
+    ea::set_wait_policy(polls, (uint32_t)wait_for_nothing);
+    return EA_OK;
+}
+
+int ea_device_status(void *cuda_stream, uint32_t *status)
+{
+    if (!status)
+        return EA_ERR_INVALID_ARG;
+    if (ea::read_sweep_status((cudaStream_t)cuda_stream, status) != cudaSuccess) {
+        cudaGetLastError();
+        return EA_ERR_CUDA;
+    }
+    return (*status & 1u) ? EA_ERR_TIMEOUT : EA_OK;
+}
+
 int ea_int_throughput(void *cuda_stream, double out[3])
 {
     if (!out)
@@ -594,6 +614,24 @@ int ea_create_samples_range(ea_ctx **out, int L, double p_neg, uint64_t seed, in
     c->jd.geo = g;
     c->jd.n_samples = n_samples;
     c->jd.first_sample = first_sample;
+    c->jd.resident = L <= ea::kResDefaultMaxL && ea::res_side_fits(L) ? 1 : 0;
+    c->jd.variant = 0;  // side 128: the register-window tile kernel
+    if (c->jd.resident) {
+        // the kernel's shared-memory opt-in, per device, outside any capture
+        int dev = 0;
+        static std::mutex mu;
+        static std::vector<int> ready;
+        std::lock_guard<std::mutex> lock(mu);
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            std::find(ready.begin(), ready.end(), dev) == ready.end()) {
+            if (ea::prepare_resident_kernels() != cudaSuccess) {
+                cudaGetLastError();
+                ea_destroy(c);
+                return EA_ERR_CUDA;
+            }
+            ready.push_back(dev);
+        }
+    }
     c->jd.rng_group = (uint32_t)rng_group_G;
     ea::fill_job_keys(&c->jd, seed);
     ea::fill_job_layout(&c->jd, default_cols_per_thread(g));
@@ -1341,6 +1379,8 @@ struct ea_batch {
     std::vector<ea_ctx *> members;
     int cpt = 0;           // word columns per thread (0 = per-job default)
     int graph_sweeps = 0;  // sweeps per captured graph (0 = direct launches)
+    int res_max_L = ea::kResDefaultMaxL;  // Metropolis sides up to this run sample-resident
+    int variant = 0;                      // bit 0: side 128 on the staged kernel
     // device job tables, one per update rule
     ea::JobDev *tab_dev[2] = {nullptr, nullptr};
     size_t cap[2] = {0, 0};
@@ -1412,6 +1452,7 @@ uint64_t table_signature(const std::vector<ea::JobDev> (&tab)[2])
             mix(((uint64_t)jd.geo_live << 32) | jd.always_u);
             mix(((uint64_t)(uint32_t)jd.all_always << 32) | (uint32_t)jd.none_random);
             mix(((uint64_t)jd.gC_hi[1][32] << 32) | jd.gC_hi[0][32]);
+            mix(((uint64_t)(uint32_t)jd.resident << 32) | (uint32_t)jd.variant);
         }
     }
     return h;
@@ -1435,18 +1476,26 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
         jd.t_end = m->t + allow;
         if (b->cpt > 0)
             ea::fill_job_layout(&jd, b->cpt);
+        jd.resident = (r == 0 && jd.geo.L <= b->res_max_L && ea::res_side_fits(jd.geo.L)) ? 1 : 0;
+        jd.variant = b->variant;
         b->tab_host[r].push_back(jd);
     }
-    // equal sides next to each other: the sides of the column kernels first,
-    // those of the general tile kernel next, sides 64 and 128 last (their own
-    // tile kernels); the order of rows changes no result
-    auto run_key = [](int L) {
-        return (L == 64 || L == 128) ? (2 << 20) + L : ea::general_tile_side(L) ? (1 << 20) + L : L;
+    // equal sides next to each other: the sample-resident jobs first, then the
+    // sides of the column kernels, those of the general tile kernel next, sides
+    // 64 and 128 last (their own tile kernels); the order of rows changes no
+    // result
+    auto run_key = [](const ea::JobDev &jd) {
+        const int L = jd.geo.L;
+        if (jd.resident)
+            return L;
+        return (L == 64 || L == 128) ? (3 << 20) + L
+               : ea::general_tile_side(L) ? (2 << 20) + L
+                                          : (1 << 20) + L;
     };
     for (int r = 0; r < 2; ++r)
         std::stable_sort(b->tab_host[r].begin(), b->tab_host[r].end(),
                          [&](const ea::JobDev &a, const ea::JobDev &c) {
-                             return run_key(a.geo.L) < run_key(c.geo.L);
+                             return run_key(a) < run_key(c);
                          });
     b->tab_sig = table_signature(b->tab_host);
     for (int r = 0; r < 2; ++r) {
@@ -1778,6 +1827,40 @@ int ea_batch_profile(ea_batch *b, int sweeps, uint64_t out[4])
     return EA_OK;
 }
 
+int ea_batch_set_resident(ea_batch *b, int max_side)
+{
+    if (!b || max_side < 0)
+        return EA_ERR_INVALID_ARG;
+    b->res_max_L = max_side;
+    drop_graph(b);
+    return EA_OK;
+}
+
+int ea_batch_get_resident(const ea_batch *b, int *max_side)
+{
+    if (!b || !max_side)
+        return EA_ERR_INVALID_ARG;
+    *max_side = b->res_max_L;
+    return EA_OK;
+}
+
+int ea_batch_set_variant(ea_batch *b, int variant)
+{
+    if (!b || variant < 0 || variant > 1)
+        return EA_ERR_INVALID_ARG;
+    b->variant = variant;
+    drop_graph(b);
+    return EA_OK;
+}
+
+int ea_batch_get_variant(const ea_batch *b, int *variant)
+{
+    if (!b || !variant)
+        return EA_ERR_INVALID_ARG;
+    *variant = b->variant;
+    return EA_OK;
+}
+
 int ea_batch_autotune(ea_batch *b, int trial_sweeps)
 {
     NvtxRange nvtx_range("ea_batch_autotune");
@@ -1790,15 +1873,32 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
     int rc = save_state(b, st);
     const int cpts[3] = {1, 2, 4};
     const int graphs[2] = {0, 16};
+    // the sample-resident kernel is a candidate when a Metropolis member fits
+    bool any_res = false;
+    for (ea_ctx *m : b->members)
+        any_res = any_res || (m->rule == EA_RULE_METROPOLIS && ea::res_side_fits(m->L));
+    const int res_opts[3] = {ea::kResDefaultMaxL, ea::kResMaxL, 0};
+    const int n_res = any_res ? 3 : 1;
+    // and the staged kernel against the register-window tiles at side 128
+    bool any_128 = false;
+    for (ea_ctx *m : b->members)
+        any_128 = any_128 || (m->rule == EA_RULE_METROPOLIS && m->L == 128);
+    const int var_opts[2] = {0, 1};
+    const int n_var = any_128 ? 2 : 1;
     float best = 1e30f;
-    int best_cpt = b->cpt, best_graph = b->graph_sweeps;
+    int best_cpt = b->cpt, best_graph = b->graph_sweeps, best_res = b->res_max_L;
+    int best_var = b->variant;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == EA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         rc = bfail(b, EA_ERR_CUDA, "event creation failed");
+    for (int vi = 0; vi < n_var && rc == EA_OK; ++vi)
+    for (int ri = 0; ri < n_res && rc == EA_OK; ++ri)
     for (int ci = 0; ci < 3 && rc == EA_OK; ++ci) {
         for (int gi = 0; gi < 2 && rc == EA_OK; ++gi) {
             if (graphs[gi] > 0 && b->stream == nullptr)
                 continue;
+            b->res_max_L = any_res ? res_opts[ri] : b->res_max_L;
+            b->variant = any_128 ? var_opts[vi] : b->variant;
             b->cpt = cpts[ci];
             b->graph_sweeps = graphs[gi] > 0 ? std::min(graphs[gi], trial_sweeps) : 0;
             rc = upload_tables(b, ea::kMaxTime);
@@ -1819,6 +1919,8 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
                 best = ms;
                 best_cpt = b->cpt;
                 best_graph = b->graph_sweeps;
+                best_res = b->res_max_L;
+                best_var = b->variant;
             }
         }
     }
@@ -1829,6 +1931,8 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
         cudaEventDestroy(e1);
     b->cpt = best_cpt;
     b->graph_sweeps = best_graph;
+    b->res_max_L = best_res;
+    b->variant = best_var;
     drop_graph(b);
     return rc;
 }

@@ -57,6 +57,82 @@ __device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t (&rk)[20])
     return c;
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (the TMA engine's cp.async.bulk) into shared memory,
+// completed on an mbarrier that counts the bytes still in flight.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+// Make the initialised barriers visible to the async proxy.
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of copies to complete this phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+// Has the phase of the given parity completed?  (Does not block.)
+__device__ __forceinline__ bool mbar_test_parity(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase of the given parity, at most `limit` polls (with a short
+// sleep between them); false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_test_parity(bar, parity))
+            return true;
+        if (it >= limit)
+            return false;
+        __nanosleep(32);
+    }
+}
+
+// Order this thread's earlier shared-memory accesses before later async-proxy
+// writes to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Copy `bytes` (a multiple of 16, both addresses 16-byte aligned) from global
+// to shared memory; the barrier's transaction count drops by `bytes` on arrival.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 constexpr uint32_t kStreamCouplings = 0u << 30;
 constexpr uint32_t kStreamSpins = 1u << 30;
 constexpr uint32_t kStreamHeat = 2u << 30;         // heat-bath coin words and gaps

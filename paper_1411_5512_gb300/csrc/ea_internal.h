@@ -89,7 +89,10 @@ struct alignas(16) JobDev {
     int blocks_per_sample;
     int cols_per_thread;
     int first_sample;         // the job-local index of the context's sample 0
-    int pad_[3];
+    int resident;             // Metropolis: run every sweep of a launch out of shared
+                              // memory, one block per sample (res_side_fits)
+    int variant;              // bit 0: Metropolis side 128 on the staged kernel
+    int pad_;
 };
 
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev tables are arrays of 16-byte aligned rows");
@@ -141,6 +144,8 @@ struct MetroParams {
     int n_jobs;
     int h;
     uint32_t sweep_offset;
+    uint32_t wait_limit;     // polls of a bounded barrier wait before it gives up
+    uint32_t wait_mode;      // bit 0: wait on a barrier nothing completes (tests)
     MetroGeo geo[kMetroMaxGeo];
     int block_begin[MAXJ + 1];
     MetroJob job[MAXJ];
@@ -167,7 +172,35 @@ inline bool general_tile_side(int L)
     return L % 16 == 0 && L >= 32 && L != 64 && L != 128;
 }
 
-constexpr int kSideStreams = 3;
+// Sides whose Metropolis samples fit whole in one block's shared memory (the
+// sample-resident kernel): both spin areas, the three coupling arrays and a
+// queue of one entry per word, at most kResMaxL.
+constexpr int kResMaxL = 64;
+inline bool res_side_fits(int L)
+{
+    return L >= 2 && L <= kResMaxL;
+}
+// The default limit: up to side 32 one block per sample is faster than a launch
+// per half-step; at 48 and 64 the per-half-step kernels win unless the samples
+// are few (the autotuner tries both).
+constexpr int kResDefaultMaxL = 32;
+// The bounded waits of the staged kernel: polls before giving up, and (tests
+// of the timeout path only) a mode in which the wait is on a barrier that no
+// copy completes.  Process-wide; applies to launches enqueued afterwards.
+void set_wait_policy(uint32_t limit, uint32_t mode);
+// Read and clear the device status word (bit 0: a bounded wait ran out),
+// after the work on `stream` has finished.
+cudaError_t read_sweep_status(cudaStream_t stream, uint32_t *status);
+
+// Opt the sample-resident kernel into its shared memory (above the default
+// 48 KB) on the current device; done when a context that may use it is
+// created, outside any stream capture.
+cudaError_t prepare_resident_kernels();
+// Sweeps per launch of the sample-resident kernel (a longer request takes
+// several launches), so no single launch runs for long.
+constexpr uint64_t kResSweepsPerLaunch = 1024;
+
+constexpr int kSideStreams = 4;
 struct SideStreams {
     cudaStream_t stream[kSideStreams];
     cudaEvent_t fork;

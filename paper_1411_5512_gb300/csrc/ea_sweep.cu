@@ -31,6 +31,7 @@
 // Words whose leading bits might select a lane wait in a per-warp queue and
 // are finished 32 at a time (the rare path), so it runs converged.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -542,6 +543,7 @@ __device__ __forceinline__ uint2 ld2(const uint32_t *__restrict__ p, int i)
 }
 
 constexpr int kGeneralTile = 1;  // run code of the general tile kernel (sides divisible by 16)
+constexpr int kResidentRun = 2;  // run code of the sample-resident kernel
 constexpr int kTileQueue = 224;  // entries per warp: up to 95 left over + 128 added per row
 constexpr int kTileMinSMs = 152;  // SMs of a GB300: launches below 4 blocks per SM take shorter rows
 
@@ -922,6 +924,384 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
         unsigned int extra = 0;
         tile_finish<GL>(jb, tb, s_q[wq][off], upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3,
                         T1x, T0, c1, c2m, c3, rk, extra);
+        if (COUNT)
+            n_extra += extra;
+    }
+    if (COUNT) {
+        atomicAdd(&counters[0], (unsigned long long)n_words);
+        atomicAdd(&counters[1], (unsigned long long)(n_calls + n_extra));
+        atomicAdd(&counters[2], (unsigned long long)n_extra);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Metropolis half-step for side 128 with the rows staged in shared memory.
+// A block of 128 threads owns the whole xz plane of the word lattice (128 x 4
+// words, thread (x pair, z pair) as in metro_tile_kernel) over a segment of Y
+// rows along y.  One warp's lanes bring each row's words into shared memory
+// with bulk asynchronous copies (cp.async.bulk, the TMA engine): row y + 1 of
+// the updated area and of the three coupling arrays and row y + 2 of the
+// neighbour area are in flight while row y is computed, and complete on an
+// mbarrier.  The threads then read every word with shared-memory loads:
+// no global-memory latency on the stencil.  Ring buffers: 4 neighbour rows
+// (y - 1, y, y + 1 in use, y + 2 in flight), 3 rows of y bonds, 2 of the
+// updated area and of the x and z bonds.
+// The rare path is split: words whose class dE = 4 alone might flip (nearly
+// all) are finished by a short routine on the full 64-bit draws; words whose
+// classes dE = 8 or 12 might flip go to tile_finish_at.  The draws are those
+// of every other Metropolis kernel.
+// Every wait on a barrier is bounded (P.wait_limit polls); when one runs out
+// the block waits for its own copies still in flight, records the timeout in
+// the device status word and returns.
+// ---------------------------------------------------------------------------
+constexpr int kStageRow = 512;     // words of one row of the xz plane at side 128
+constexpr int kStageQueue = 160;   // entries per warp: up to 31 left + 128 per row
+constexpr int kStageHeavy = 64;    // entries per warp whose dE = 8 or 12 leads hit
+constexpr uint32_t kStageGroupBytes = 5 * kStageRow * 4;  // one row of five arrays
+constexpr uint32_t kStageFirstBytes = 8 * kStageRow * 4;  // the first group: 8 rows
+constexpr uint32_t kDrainPolls = 1u << 24;
+
+__device__ unsigned int g_sweep_status;  // bit 0: a bounded wait ran out
+
+struct StageSmem {
+    uint32_t nb[4][kStageRow];
+    uint32_t jy[3][kStageRow];
+    uint32_t up[2][kStageRow];
+    uint32_t jx[2][kStageRow];
+    uint32_t jz[2][kStageRow];
+    uint64_t bar[2];
+    uint64_t bar_never;  // nothing ever arrives on it (the timeout test waits on it)
+    uint4 q[kSweepThreads / 32][kStageQueue];
+    uint4 hq[kSweepThreads / 32][kStageHeavy];
+    int qn[kSweepThreads / 32], hn[kSweepThreads / 32];
+    uint32_t c2hi[33], c2lo[33];  // C_2[g] (class dE = 4), full 64 bits
+    TileTables tb;
+};
+
+__device__ __forceinline__ uint2 lds2(const uint32_t *p)
+{
+    return *reinterpret_cast<const uint2 *>(p);
+}
+
+// The short rare path of a queued word e = (word-site, spins, main bits M,
+// class-2 lanes) whose classes dE = 8 and 12 select nothing: class dE = 4 by
+// geometric gaps on full 64-bit draws (draw 0 completed by extension call 64,
+// draws d >= 1 from calls 3 + 3 ((d - 1) div 2)).  The word was stored with its
+// outright flips; that value is read back and the accepted lanes added.
+__device__ __forceinline__ void stage_finish(const StageSmem &S, const uint4 &e,
+                                             uint32_t *__restrict__ upd, int h, uint32_t c1,
+                                             uint32_t c2m, uint32_t c3,
+                                             const uint32_t (&rk)[20], unsigned int &calls)
+{
+    const int w = (int)e.x;
+    const uint32_t M = e.z;
+    const int x = w & 127, y = (w >> 7) & 127, z = w >> 14;
+    const uint32_t c2 = c2m | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
+    const uint32_t base = upd[w];
+    const uint4 X = dev::philox10_rk(make_uint4((uint32_t)w, c1, c2 | 64u, c3), rk);
+    ++calls;
+    auto C = [&S](int g) -> uint64_t { return ((uint64_t)S.c2hi[g] << 32) | S.c2lo[g]; };
+    uint64_t V = first_draw2(M, X);
+    uint32_t Mr = e.w, A = 0u;
+    int rem = __popc(Mr), d = 0;
+    uint4 Q = make_uint4(0u, 0u, 0u, 0u);
+    while (rem > 0 && V < C(rem)) {
+        // G = min{g : V < C[g + 1]} by bisection over the nondecreasing table
+        int lo = 1, hi = rem;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (V < C(mid))
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const int G = lo - 1;
+        const uint32_t bit = nth_bit(Mr, G);
+        A |= bit;
+        Mr &= ~(bit | (bit - 1u));
+        rem -= G + 1;
+        if (rem == 0)
+            break;
+        ++d;
+        if (((d - 1) & 1) == 0) {
+            Q = dev::philox10_rk(
+                make_uint4((uint32_t)w, c1, c2 | (uint32_t)(3 + 3 * ((d - 1) >> 1)), c3), rk);
+            ++calls;
+        }
+        V = ((d - 1) & 1) ? (((uint64_t)Q.z << 32) | Q.w) : (((uint64_t)Q.x << 32) | Q.y);
+    }
+    if (A)
+        upd[w] = base ^ A;
+}
+
+template <bool COUNT, int MAXJ>
+__global__ void __launch_bounds__(kSweepThreads, 5)
+    metro_stage_kernel(const __grid_constant__ MetroParams<MAXJ> P, unsigned long long *counters)
+{
+    constexpr int GL = 128, N2 = 4, SZ = GL * GL;
+    constexpr uint32_t W = (uint32_t)SZ * N2;
+    int j = 0;
+    {
+        int lo = 0, hi = P.n_jobs - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.block_begin[mid] <= b)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    const MetroJob &J = P.job[j];
+    const MetroGeo &G = P.geo[(J.meta >> 8) & 0xFFu];
+    const JobDev *__restrict__ jb = P.jobs_dev + j;
+    __shared__ StageSmem S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t t = jb->t + P.sweep_offset;
+    if (t >= jb->t_end)
+        return;  // this job has stopped (uniform over the block)
+    const int h = P.h;
+    const int Y = G.seg;
+    const int local = (int)blockIdx.x - P.block_begin[j];
+    const int s = local / G.bps;
+    const int y0 = (local - s * G.bps) * Y;
+    uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
+    const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
+    const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
+    const uint32_t *__restrict__ Jy = Jx + W;
+    const uint32_t *__restrict__ Jz = Jy + W;
+
+    // the first group: rows y0 of the updated area and of the x, z bonds, y bonds
+    // of rows y0 - 1 and y0, neighbour rows y0 - 1 .. y0 + 1; one copy per lane
+    // of warp 0 (a row of one array is four 512-byte runs, one per z')
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&S.bar[0], 1);
+        dev::mbar_init(&S.bar[1], 1);
+        dev::mbar_init(&S.bar_never, 1);
+        dev::mbar_init_fence();
+    }
+    __syncthreads();
+    auto row_src = [&](const uint32_t *a, int y, int zq) {
+        return a + (size_t)((y & (GL - 1)) * GL + zq * SZ);
+    };
+    if (warp == 0) {
+        if (lane == 0)
+            dev::mbar_arrive_expect_tx(&S.bar[0], kStageFirstBytes);
+        __syncwarp();
+        const int a = lane >> 2, zq = lane & 3;
+        const uint32_t *src;
+        uint32_t *dst;
+        switch (a) {
+        case 0: src = row_src(upd, y0, zq); dst = S.up[0]; break;
+        case 1: src = row_src(Jx, y0, zq); dst = S.jx[0]; break;
+        case 2: src = row_src(Jz, y0, zq); dst = S.jz[0]; break;
+        case 3: src = row_src(Jy, y0 - 1, zq); dst = S.jy[0]; break;
+        case 4: src = row_src(Jy, y0, zq); dst = S.jy[1]; break;
+        case 5: src = row_src(nb, y0 - 1, zq); dst = S.nb[0]; break;
+        case 6: src = row_src(nb, y0, zq); dst = S.nb[1]; break;
+        default: src = row_src(nb, y0 + 1, zq); dst = S.nb[2]; break;
+        }
+        dev::bulk_g2s(dst + zq * GL, src, GL * 4, &S.bar[0]);
+    }
+
+    uint32_t rk[20];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = J.key0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = J.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x) {
+        const int u = i / 33, n = i - 33 * u;
+        const uint32_t hi = jb->gC_hi[u][n];
+        S.tb.hi[u][n] = hi;
+        S.tb.lead[u][n] = u == 2 ? lead2(hi) : u == 1 ? lead1(hi) : lead0(hi);
+        if (u == 2) {
+            S.c2hi[n] = hi;
+            S.c2lo[n] = jb->gC_lo[2][n];
+        }
+    }
+    if (lane == 0) {
+        S.qn[warp] = 0;
+        S.hn[warp] = 0;
+    }
+    const int xp = threadIdx.x & 63, zp = threadIdx.x >> 6;
+    const int x0 = 2 * xp, z0 = 2 * zp;
+    const int po = z0 * GL + x0, po1 = po + GL;  // the thread's pair at z0, z0 + 1 in a row
+    const bool wrap_m = z0 == 0, wrap_p = z0 + 2 == N2;
+    const int zmo = (wrap_m ? N2 - 1 : z0 - 1) * GL + x0, zpo = (wrap_p ? 0 : z0 + 2) * GL + x0;
+    const int xm = (x0 - 1) & (GL - 1), xq = (x0 + 2) & (GL - 1);
+    const int xmo0 = z0 * GL + xm, xmo1 = xmo0 + GL, xqo0 = z0 * GL + xq, xqo1 = xqo0 + GL;
+    const bool none_random = (J.meta >> 4) & 1u;
+    const uint32_t live0 = 0u - (J.meta & 1u), live1 = 0u - ((J.meta >> 1) & 1u),
+                   live2 = 0u - ((J.meta >> 2) & 1u);
+    const uint32_t always3 = jb->always_u & 7u;
+    const uint32_t T1x = lead1(jb->gC_hi[1][32]), T0 = lead0(jb->gC_hi[0][32]);
+    const uint32_t c3 = ((uint32_t)s + (J.meta >> 16)) / J.rng_group;
+    const uint32_t c1 = (uint32_t)t;
+    const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
+    uint4 *q = S.q[warp];
+    uint4 *hq = S.hq[warp];
+    unsigned int n_words = 0, n_calls = 0, n_extra = 0;
+    // P.wait_mode bit 0 (tests of the timeout path only): wait on a barrier that no
+    // copy completes, so that the bounded wait runs out
+    uint64_t *const wait_bar_test = (P.wait_mode & 1u) ? &S.bar_never : nullptr;
+
+    for (int i = 0; i < Y; ++i) {
+        const int y = y0 + i;
+        // (a) this row's group has landed; (b) every thread is past row i - 1
+        const bool ok = wait_bar_test ? dev::mbar_wait_bounded(wait_bar_test, 0u, P.wait_limit)
+                                      : dev::mbar_wait_bounded(&S.bar[i & 1], (i >> 1) & 1,
+                                                               P.wait_limit);
+        if (__syncthreads_or(!ok)) {
+            dev::mbar_wait_bounded(&S.bar[i & 1], (i >> 1) & 1, kDrainPolls);
+            if (threadIdx.x == 0)
+                atomicOr(&g_sweep_status, 1u);
+            return;
+        }
+        // (c) the next row's group, into the slots row i - 1 has released
+        if (i + 1 < Y && warp == 0) {
+            const int k = (i + 1) & 1;
+            if (lane == 0)
+                dev::mbar_arrive_expect_tx(&S.bar[k], kStageGroupBytes);
+            __syncwarp();
+            if (lane < 20) {
+                dev::fence_proxy_async_smem();
+                const int a = lane >> 2, zq = lane & 3;
+                const uint32_t *src;
+                uint32_t *dst;
+                switch (a) {
+                case 0: src = row_src(upd, y + 1, zq); dst = S.up[k]; break;
+                case 1: src = row_src(Jx, y + 1, zq); dst = S.jx[k]; break;
+                case 2: src = row_src(Jz, y + 1, zq); dst = S.jz[k]; break;
+                case 3: src = row_src(Jy, y + 1, zq); dst = S.jy[(i + 2) % 3]; break;
+                default: src = row_src(nb, y + 2, zq); dst = S.nb[(i + 3) & 3]; break;
+                }
+                dev::bulk_g2s(dst + zq * GL, src, GL * 4, &S.bar[k]);
+            }
+        }
+        // (d) row y from shared memory
+        const uint32_t *nbc = S.nb[(i + 1) & 3], *nbm = S.nb[i & 3], *nbn = S.nb[(i + 2) & 3];
+        const uint32_t *jyc = S.jy[(i + 1) % 3], *jym = S.jy[i % 3];
+        const uint32_t *sup = S.up[i & 1], *sjx = S.jx[i & 1], *sjz = S.jz[i & 1];
+        const uint2 S0 = lds2(sup + po), S1 = lds2(sup + po1);
+        const uint2 Nc0 = lds2(nbc + po), Nc1 = lds2(nbc + po1);
+        const uint2 Nm0 = lds2(nbm + po), Nm1 = lds2(nbm + po1);
+        const uint2 Nn0 = lds2(nbn + po), Nn1 = lds2(nbn + po1);
+        uint2 Nzm = lds2(nbc + zmo), Nzp = lds2(nbc + zpo);
+        const uint32_t Xm0 = nbc[xmo0], Xm1 = nbc[xmo1], Xp0 = nbc[xqo0], Xp1 = nbc[xqo1];
+        const uint2 Jx0 = lds2(sjx + po), Jx1 = lds2(sjx + po1);
+        const uint32_t Jxm0 = sjx[xmo0], Jxm1 = sjx[xmo1];
+        const uint2 Jy0 = lds2(jyc + po), Jy1 = lds2(jyc + po1);
+        const uint2 Jym0 = lds2(jym + po), Jym1 = lds2(jym + po1);
+        const uint2 Jz0 = lds2(sjz + po), Jz1 = lds2(sjz + po1);
+        uint2 Jzm = lds2(sjz + zmo);
+        if (wrap_m) {
+            Nzm = make_uint2(rot_zm(Nzm.x), rot_zm(Nzm.y));
+            Jzm = make_uint2(rot_zm(Jzm.x), rot_zm(Jzm.y));
+        }
+        if (wrap_p)
+            Nzp = make_uint2(rot_zp(Nzp.x), rot_zp(Nzp.y));
+        const int w0 = x0 + y * GL + z0 * SZ, w1 = w0 + SZ;
+        const uint32_t c2A = c2m | ((uint32_t)(h ^ (y & 1)) << 11);
+        uint4 R = make_uint4(0u, 0u, 0u, 0u);
+        if (!none_random)
+            R = dev::philox10_rk(make_uint4((uint32_t)w0, c1, c2A, c3), rk);
+        uint32_t alwa0, alwa1, alwb0, alwb1, m2a0, m2a1, m2b0, m2b1;
+        uint32_t sp = S0.x;
+        bool ha0 = tile_word<true>(sp ^ Nc0.y ^ Jx0.x, sp ^ Xm0 ^ Jxm0, sp ^ Nn0.x ^ Jy0.x,
+                                   sp ^ Nm0.x ^ Jym0.x, sp ^ Nc1.x ^ Jz0.x, sp ^ Nzm.x ^ Jzm.x,
+                                   R.x, S.tb, T1x, T0, live0, live1, live2, alwa0, m2a0);
+        sp = S0.y;
+        bool ha1 = tile_word<true>(sp ^ Xp0 ^ Jx0.y, sp ^ Nc0.x ^ Jx0.x, sp ^ Nn0.y ^ Jy0.y,
+                                   sp ^ Nm0.y ^ Jym0.y, sp ^ Nc1.y ^ Jz0.y, sp ^ Nzm.y ^ Jzm.y,
+                                   R.y, S.tb, T1x, T0, live0, live1, live2, alwa1, m2a1);
+        sp = S1.x;
+        bool hb0 = tile_word<true>(sp ^ Nc1.y ^ Jx1.x, sp ^ Xm1 ^ Jxm1, sp ^ Nn1.x ^ Jy1.x,
+                                   sp ^ Nm1.x ^ Jym1.x, sp ^ Nzp.x ^ Jz1.x, sp ^ Nc0.x ^ Jz0.x,
+                                   R.z, S.tb, T1x, T0, live0, live1, live2, alwb0, m2b0);
+        sp = S1.y;
+        bool hb1 = tile_word<true>(sp ^ Xp1 ^ Jx1.y, sp ^ Nc1.x ^ Jx1.x, sp ^ Nn1.y ^ Jy1.y,
+                                   sp ^ Nm1.y ^ Jym1.y, sp ^ Nzp.y ^ Jz1.y, sp ^ Nc0.y ^ Jz0.y,
+                                   R.w, S.tb, T1x, T0, live0, live1, live2, alwb1, m2b1);
+        *reinterpret_cast<uint2 *>(upd + w0) = make_uint2(S0.x ^ alwa0, S0.y ^ alwa1);
+        *reinterpret_cast<uint2 *>(upd + w1) = make_uint2(S1.x ^ alwb0, S1.y ^ alwb1);
+        if (COUNT)
+            n_words += 4;
+        if (none_random)
+            continue;
+        if (COUNT)
+            n_calls += 1;
+        if (ha0)
+            q[atomicAdd(&S.qn[warp], 1)] = make_uint4((uint32_t)w0, S0.x, R.x, m2a0);
+        if (ha1)
+            q[atomicAdd(&S.qn[warp], 1)] = make_uint4((uint32_t)w0 + 1u, S0.y, R.y, m2a1);
+        if (hb0)
+            q[atomicAdd(&S.qn[warp], 1)] = make_uint4((uint32_t)w1, S1.x, R.z, m2b0);
+        if (hb1)
+            q[atomicAdd(&S.qn[warp], 1)] = make_uint4((uint32_t)w1 + 1u, S1.y, R.w, m2b1);
+        __syncwarp();
+        int q_n = S.qn[warp];
+        while (q_n >= 32) {  // rounds of one queued word per lane
+            q_n -= 32;
+            const uint4 e = q[q_n + lane];
+            const bool heavy = ((e.z & 0xFFC00u) <= T1x) | ((e.z & 0x3FFu) <= T0) | (always3 != 0u);
+            const uint32_t hv = __ballot_sync(0xffffffffu, heavy);
+            const int hn = S.hn[warp];
+            if (heavy)
+                hq[hn + __popc(hv & ((1u << lane) - 1u))] = e;
+            else {
+                unsigned int extra = 0;
+                stage_finish(S, e, upd, h, c1, c2m, c3, rk, extra);
+                if (COUNT)
+                    n_extra += extra;
+            }
+            __syncwarp();
+            if (lane == 0)
+                S.hn[warp] = hn + __popc(hv);
+            __syncwarp();
+            if (S.hn[warp] >= 32) {  // a round of the words with dE = 8 or 12 leads
+                const int k = S.hn[warp] - 32;
+                unsigned int extra = 0;
+                tile_finish<GL>(jb, S.tb, hq[k + lane], upd, nb, Jx, Jy, Jz, h, live0, live1,
+                                live2, always3, T1x, T0, c1, c2m, c3, rk, extra);
+                if (COUNT)
+                    n_extra += extra;
+                __syncwarp();
+                if (lane == 0)
+                    S.hn[warp] = k;
+                __syncwarp();
+            }
+        }
+        if (lane == 0)
+            S.qn[warp] = q_n;
+        __syncwarp();
+    }
+    // the words still queued in the block's four warps, pooled and shared out
+    __syncthreads();
+    int nq[5] = {0, 0, 0, 0, 0}, nh[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        nq[k + 1] = nq[k] + S.qn[k];
+        nh[k + 1] = nh[k] + S.hn[k];
+    }
+    for (int g = (int)threadIdx.x; g < nq[4] + nh[4]; g += kSweepThreads) {
+        unsigned int extra = 0;
+        if (g < nq[4]) {
+            const int wq = g < nq[1] ? 0 : g < nq[2] ? 1 : g < nq[3] ? 2 : 3;
+            const uint4 e = S.q[wq][g - nq[wq]];
+            const bool heavy = ((e.z & 0xFFC00u) <= T1x) | ((e.z & 0x3FFu) <= T0) | (always3 != 0u);
+            if (heavy)
+                tile_finish<GL>(jb, S.tb, e, upd, nb, Jx, Jy, Jz, h, live0, live1, live2, always3,
+                                T1x, T0, c1, c2m, c3, rk, extra);
+            else
+                stage_finish(S, e, upd, h, c1, c2m, c3, rk, extra);
+        } else {
+            const int gh = g - nq[4];
+            const int wq = gh < nh[1] ? 0 : gh < nh[2] ? 1 : gh < nh[3] ? 2 : 3;
+            tile_finish<GL>(jb, S.tb, S.hq[wq][gh - nh[wq]], upd, nb, Jx, Jy, Jz, h, live0, live1,
+                            live2, always3, T1x, T0, c1, c2m, c3, rk, extra);
+        }
         if (COUNT)
             n_extra += extra;
     }
@@ -1824,6 +2204,247 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Metropolis sweeps with the whole sample resident in shared memory: one block
+// per sample loads both areas and the three coupling arrays once, runs every
+// sweep of the launch (both half-steps, __syncthreads between them) out of
+// shared memory and writes the spins back at the end.  For samples small
+// enough to fit (side <= 64), where one sample is too little work to fill
+// the GPU for a single half-step, so that per-half-step launches would run at
+// launch latency.  Any side: the word lattice n0 x n1 x n2 and the lane
+// realignment at the wraps come from the geometry, as in metro_kernel.
+//   pass 1: a thread takes a quad of word-sites (x' even, x' + 1) x (z' even,
+//     z' + 1) at one y', draws the quad's main call, and writes each word
+//     with its outright flips unless the leading bits of its first draws might
+//     select a lane; such words go to a block queue (word-site, main bits);
+//   pass 2: the queued words are counted again from the neighbour area, which
+//     this half-step does not write, and finished exactly (finish_word).
+// The draws are those of every other Metropolis kernel, so a job's results do
+// not depend on the kernel that runs it.
+// ---------------------------------------------------------------------------
+constexpr int kResThreads = 256;
+
+struct ResGeo {
+    int n0, n1, n2, sz;
+    bool fix_x, fix_y;
+    Axis ax, ay, az;
+};
+
+// The bit-sliced count of the word at word-site w = (x, y, z) with spins s,
+// its neighbours in area nb and its bonds in Jx, Jy, Jz (all in shared memory).
+__device__ __forceinline__ Count res_count(const uint32_t *nb, const uint32_t *Jx,
+                                           const uint32_t *Jy, const uint32_t *Jz, uint32_t s,
+                                           int x, int y, int z, int w, const ResGeo &g)
+{
+    const bool exp_ = x + 1 == g.n0, exm = x == 0, eyp = y + 1 == g.n1, eym = y == 0;
+    const bool ezp = z + 1 == g.n2, ezm = z == 0;
+    const int wxp = exp_ ? w - (g.n0 - 1) : w + 1;
+    const int wxm = exm ? w + (g.n0 - 1) : w - 1;
+    const int wyp = eyp ? w - (g.n1 - 1) * g.n0 : w + g.n0;
+    const int wym = eym ? w + (g.n1 - 1) * g.n0 : w - g.n0;
+    const int wzp = ezp ? w - (g.n2 - 1) * g.sz : w + g.sz;
+    const int wzm = ezm ? w + (g.n2 - 1) * g.sz : w - g.sz;
+    uint32_t nxp = nb[wxp], nxm = nb[wxm], jxm = Jx[wxm];
+    uint32_t nyp = nb[wyp], nym = nb[wym], jym = Jy[wym];
+    uint32_t nzp = nb[wzp], nzm = nb[wzm], jzm = Jz[wzm];
+    if (g.fix_x) {
+        if (exp_)
+            nxp = fixup(nxp, g.ax, 0);
+        if (exm) {
+            nxm = fixup(nxm, g.ax, 1);
+            jxm = fixup(jxm, g.ax, 1);
+        }
+    }
+    if (g.fix_y) {
+        if (eyp)
+            nyp = fixup(nyp, g.ay, 0);
+        if (eym) {
+            nym = fixup(nym, g.ay, 1);
+            jym = fixup(jym, g.ay, 1);
+        }
+    }
+    if (ezp)
+        nzp = fixup(nzp, g.az, 0);
+    if (ezm) {
+        nzm = fixup(nzm, g.az, 1);
+        jzm = fixup(jzm, g.az, 1);
+    }
+    return count6(s ^ nxp ^ Jx[w], s ^ nxm ^ jxm, s ^ nyp ^ Jy[w], s ^ nym ^ jym, s ^ nzp ^ Jz[w],
+                  s ^ nzm ^ jzm);
+}
+
+// Dynamic shared memory of a resident block for a sample of W words per area:
+// areas 0 and 1, Jx, Jy, Jz, and the queue of up to W (word-site, main bits).
+__host__ __device__ constexpr size_t res_smem_bytes(int W)
+{
+    return (size_t)W * (5 * sizeof(uint32_t) + sizeof(uint2));
+}
+
+template <bool COUNT, int MAXJ>
+__global__ void __launch_bounds__(kResThreads, 1)
+    metro_res_kernel(const __grid_constant__ MetroParams<MAXJ> P, uint32_t n_sweeps,
+                     unsigned long long *counters)
+{
+    int j = 0;
+    {
+        int lo = 0, hi = P.n_jobs - 1;
+        const int b = (int)blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.block_begin[mid] <= b)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    const MetroJob &J = P.job[j];
+    const MetroGeo &G = P.geo[(J.meta >> 8) & 0xFFu];
+    const JobDev *__restrict__ jb = P.jobs_dev + j;
+    uint32_t rk[20];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = J.key0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = J.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    extern __shared__ __align__(16) uint32_t res_smem[];
+    __shared__ uint32_t s_gh[3][33];
+    __shared__ int s_qn;
+    const int W = (int)G.words;
+    uint32_t *const sJx = res_smem + 2 * W;
+    uint32_t *const sJy = sJx + W;
+    uint32_t *const sJz = sJy + W;
+    uint2 *const queue = reinterpret_cast<uint2 *>(res_smem + 5 * W);
+    for (int i = threadIdx.x; i < 3 * 33; i += blockDim.x) {
+        const int u = i / 33;
+        const uint32_t hi = (&jb->gC_hi[0][0])[i];
+        (&s_gh[0][0])[i] = u == 2 ? lead2(hi) : u == 1 ? lead1(hi) : lead0(hi);
+    }
+    const int s = (int)blockIdx.x - P.block_begin[j];
+    uint32_t *__restrict__ gsp = J.spins + (size_t)s * 2 * W;
+    const uint32_t *__restrict__ gJ = J.J + (size_t)s * 3 * W;
+    // W is a multiple of 8 (every side of the word lattice is even)
+    for (int i = threadIdx.x; i < W / 2; i += blockDim.x) {
+        reinterpret_cast<uint4 *>(res_smem)[i] = reinterpret_cast<const uint4 *>(gsp)[i];
+        if (i < 3 * W / 4)
+            reinterpret_cast<uint4 *>(sJx)[i] = reinterpret_cast<const uint4 *>(gJ)[i];
+    }
+    for (int i = W / 2 + threadIdx.x; i < 3 * W / 4; i += blockDim.x)
+        reinterpret_cast<uint4 *>(sJx)[i] = reinterpret_cast<const uint4 *>(gJ)[i];
+    if (threadIdx.x == 0)
+        s_qn = 0;
+    __syncthreads();
+
+    ResGeo g;
+    g.n0 = G.n0;
+    g.n1 = G.n1;
+    g.n2 = G.n2;
+    g.sz = G.n0 * G.n1;
+    g.fix_x = (G.fix & 1u) != 0;
+    g.fix_y = (G.fix & 2u) != 0;
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+        g.az.sA[dir] = G.zsA[dir];
+        g.az.sB[dir] = G.zsB[dir];
+        g.az.mA[dir] = G.zmA[dir];
+        g.az.mB[dir] = G.zmB[dir];
+    }
+    if (g.fix_x)
+        load_axis(g.ax, jb->geo, 0);
+    if (g.fix_y)
+        load_axis(g.ay, jb->geo, 1);
+    const uint32_t valid = G.valid;
+    const bool all_always = (J.meta >> 3) & 1u, none_random = (J.meta >> 4) & 1u;
+    const uint32_t live0 = 0u - (J.meta & 1u), live1 = 0u - ((J.meta >> 1) & 1u),
+                   live2 = 0u - ((J.meta >> 2) & 1u);
+    const uint32_t c3 = ((uint32_t)s + (J.meta >> 16)) / J.rng_group;
+    const int hx = g.n0 >> 1, quads = hx * g.n1 * (g.n2 >> 1);
+    unsigned int n_words = 0, n_calls = 0, n_extra = 0;
+
+    for (uint32_t k = 0; k < n_sweeps; ++k) {
+        const uint64_t t = jb->t + P.sweep_offset + k;
+        if (t >= jb->t_end)
+            break;  // the job stops here (uniform over the block)
+        const uint32_t c1 = (uint32_t)t;
+        const uint32_t c2m = dev::kStreamMetropolis | (((uint32_t)(t >> 32) & 0xFFFFu) << 12);
+        for (int h = 0; h < 2; ++h) {
+            uint32_t *const upd = h ? res_smem + W : res_smem;
+            const uint32_t *const nb = h ? res_smem : res_smem + W;
+            for (int qd = threadIdx.x; qd < quads; qd += kResThreads) {
+                const int xq = qd % hx, r = qd / hx;
+                const int y = r % g.n1, z0 = (r / g.n1) * 2, x0 = 2 * xq;
+                const int w0 = x0 + g.n0 * y + g.sz * z0;
+                const int ws[4] = {w0, w0 + 1, w0 + g.sz, w0 + g.sz + 1};
+                uint32_t sp[4], alw[4];
+                Classes kc[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    sp[q] = upd[ws[q]];
+                    const Count c = res_count(nb, sJx, sJy, sJz, sp[q], x0 + (q & 1), y,
+                                              z0 + (q >> 1), ws[q], g);
+                    alw[q] = c.b2 | (c.b1 & c.b0);
+                    kc[q] = classes(c, alw[q], valid, live0, live1, live2);
+                }
+                if (COUNT)
+                    n_words += 4;
+                if (all_always || none_random) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        upd[ws[q]] = sp[q] ^ ((all_always ? 0xffffffffu : alw[q]) & valid);
+                    continue;
+                }
+                // the quad's main call: its first word-site, the replica there
+                const uint32_t c2q = c2m | ((uint32_t)(h ^ (y & 1)) << 11);
+                const uint4 R = dev::philox10_rk(make_uint4((uint32_t)w0, c1, c2q, c3), rk);
+                if (COUNT)
+                    n_calls += 1;
+                const uint32_t M[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (class_hit(kc[q], M[q], s_gh))
+                        queue[atomicAdd(&s_qn, 1)] = make_uint2((uint32_t)ws[q], M[q]);
+                    else
+                        upd[ws[q]] = sp[q] ^ (alw[q] & valid);
+                }
+            }
+            __syncthreads();
+            const int nq = s_qn;
+            for (int i = threadIdx.x; i < nq; i += kResThreads) {
+                const uint2 e = queue[i];
+                const int w = (int)e.x;
+                const int x = w % g.n0, r = w / g.n0, y = r % g.n1, z = r / g.n1;
+                const uint32_t sw = upd[w];  // not written in pass 1
+                const Count c = res_count(nb, sJx, sJy, sJz, sw, x, y, z, w, g);
+                const uint32_t a = c.b2 | (c.b1 & c.b0);
+                const Classes kc = classes(c, a, valid, live0, live1, live2);
+                Pending p;
+                p.w = (uint32_t)w;
+                p.base = sw ^ (a & valid);
+                p.M0 = kc.M0;
+                p.M1 = kc.M1;
+                p.M2 = kc.M2;
+                p.c2 = c2m | ((uint32_t)(h ^ ((x + y + z) & 1)) << 11);
+                p.lead = e.y;
+                unsigned int extra = 0;
+                finish_word(jb, p, upd, valid, c1, c3, rk, extra);
+                if (COUNT)
+                    n_extra += extra;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0)
+                s_qn = 0;
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < W / 2; i += blockDim.x)
+        reinterpret_cast<uint4 *>(gsp)[i] = reinterpret_cast<const uint4 *>(res_smem)[i];
+    if (COUNT) {
+        atomicAdd(&counters[0], (unsigned long long)n_words);
+        atomicAdd(&counters[1], (unsigned long long)(n_calls + n_extra));
+        atomicAdd(&counters[2], (unsigned long long)n_extra);
+    }
+}
+
 __global__ void advance_time_kernel(JobDev *jobs, int n_jobs, uint64_t n)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1881,6 +2502,10 @@ void fill_job_layout(JobDev *jd, int cols_per_thread)
     jd->blocks_per_sample = (jd->cols + per_block - 1) / per_block;
 }
 
+// the bounded waits of the staged kernel (set_wait_policy)
+static std::atomic<uint32_t> g_wait_limit{1u << 22};
+static std::atomic<uint32_t> g_wait_mode{0u};
+
 static void metro_geo(MetroGeo &g, const JobDev &jd)
 {
     std::memset(&g, 0, sizeof(g));
@@ -1929,6 +2554,8 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
     p.jobs_dev = dev;
     p.n_jobs = cnt;
     p.block_begin[0] = 0;
+    p.wait_limit = g_wait_limit;
+    p.wait_mode = g_wait_mode;
     int n_geo = 0;
     int geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
     // tile kernels: rows per thread from the launch shape, halved (down to 2)
@@ -2019,6 +2646,29 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
                     metro_gtile_kernel<false, MAXJ, false>
                         <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
                 }
+            } else if constexpr (GL == 128) {
+                const bool staged = lowt && (host[0].variant & 1);
+                if (staged) {
+                    if (counters)
+                        metro_stage_kernel<true, MAXJ>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                    else
+                        metro_stage_kernel<false, MAXJ>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                } else if (counters) {
+                    if (lowt)
+                        metro_tile_kernel<true, MAXJ, GL, true>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                    else
+                        metro_tile_kernel<true, MAXJ, GL, false>
+                            <<<grid, kSweepThreads, 0, stream>>>(p, counters);
+                } else if (lowt) {
+                    metro_tile_kernel<false, MAXJ, GL, true>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                } else {
+                    metro_tile_kernel<false, MAXJ, GL, false>
+                        <<<grid, kSweepThreads, 0, stream>>>(p, nullptr);
+                }
             } else if constexpr (GL != 0) {
                 if (counters) {
                     if (lowt)
@@ -2042,6 +2692,66 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
             }
             count_launches(1);
         }
+}
+
+// The sample-resident kernel over jobs host[0..cnt): one block per sample, up
+// to kResSweepsPerLaunch sweeps per launch.
+template <bool COUNT, int MAXJ>
+static void res_launch(const MetroParams<MAXJ> &p, int grid, size_t smem, uint32_t sweeps,
+                       cudaStream_t stream, unsigned long long *counters)
+{
+    metro_res_kernel<COUNT, MAXJ><<<grid, kResThreads, smem, stream>>>(p, sweeps, counters);
+    count_launches(1);
+}
+
+template <bool COUNT, int MAXJ>
+static cudaError_t res_opt_in()
+{
+    return cudaFuncSetAttribute(metro_res_kernel<COUNT, MAXJ>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)res_smem_bytes(kResMaxL * kResMaxL * kResMaxL / 32));
+}
+
+template <int MAXJ>
+static void launch_res_chunk(const JobDev *host, const JobDev *dev, int cnt, uint64_t n,
+                             cudaStream_t stream, unsigned long long *counters)
+{
+    MetroParams<MAXJ> p;
+    std::memset(p.geo, 0, sizeof(p.geo));
+    p.jobs_dev = dev;
+    p.n_jobs = cnt;
+    p.h = 0;
+    p.wait_limit = g_wait_limit;
+    p.wait_mode = g_wait_mode;
+    p.block_begin[0] = 0;
+    int n_geo = 0, geo_L[kMetroMaxGeo], W_max = 0;
+    for (int i = 0; i < cnt; ++i) {
+        const JobDev &jd = host[i];
+        int gi = 0;
+        while (gi < n_geo && geo_L[gi] != jd.geo.L)
+            ++gi;
+        if (gi == n_geo) {
+            geo_L[gi] = jd.geo.L;
+            metro_geo(p.geo[gi], jd);
+            p.geo[gi].bps = 1;
+            ++n_geo;
+        }
+        metro_job(p.job[i], jd, gi);
+        p.block_begin[i + 1] = p.block_begin[i] + jd.n_samples;
+        W_max = std::max(W_max, jd.geo.words);
+    }
+    const int grid = p.block_begin[cnt];
+    if (grid == 0)
+        return;
+    const size_t smem = res_smem_bytes(W_max);
+    for (uint64_t done = 0; done < n; done += kResSweepsPerLaunch) {
+        p.sweep_offset = (uint32_t)done;
+        const uint32_t k = (uint32_t)std::min<uint64_t>(kResSweepsPerLaunch, n - done);
+        if (counters)
+            res_launch<true, MAXJ>(p, grid, smem, k, stream, counters);
+        else
+            res_launch<false, MAXJ>(p, grid, smem, k, stream, nullptr);
+    }
 }
 
 // Jobs host[0..cnt) of one run of the Metropolis table: side GLR (64 or 128,
@@ -2068,7 +2778,14 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
         }
         const JobDev *h = host + first;
         const JobDev *d = dev + first;
-        if (HEAT && GLR == 128) {
+        if (!HEAT && GLR == kResidentRun) {
+            if (c <= 8)
+                launch_res_chunk<8>(h, d, c, n, stream, counters);
+            else if (c <= 128)
+                launch_res_chunk<128>(h, d, c, n, stream, counters);
+            else
+                launch_res_chunk<kMetroMaxJobs>(h, d, c, n, stream, counters);
+        } else if (HEAT && GLR == 128) {
             if (c <= 8)
                 launch_metro_chunk<8, 128, true>(h, d, c, n, stream, counters);
             else
@@ -2126,24 +2843,28 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
     }
 }
 
-// A table read as runs, in this order: the jobs for the column kernels, then
-// (with `general`) those of the general tile kernel, then side 64, then side
-// 128 (their own tile kernels).  A table in any other order is one run for the
+// A table read as runs, in this order: (with `resident`) the jobs marked for
+// the sample-resident kernel, then those for the column kernels, then (with
+// `general`) those of the general tile kernel, then side 64, then side 128
+// (their own tile kernels).  A table in any other order is one run for the
 // column kernel.
 struct Run {
     int first, cnt, GLR;
 };
 
-static int split_runs(const JobDev *host, int n_jobs, bool general, Run runs[4])
+static int split_runs(const JobDev *host, int n_jobs, bool general, bool resident, Run runs[5])
 {
-    constexpr int kCode[4] = {0, kGeneralTile, 64, 128};
-    auto cls = [&](int L) {
-        return L == 64 ? 2 : L == 128 ? 3 : (general && general_tile_side(L)) ? 1 : 0;
+    constexpr int kCode[5] = {kResidentRun, 0, kGeneralTile, 64, 128};
+    auto cls = [&](const JobDev &jd) {
+        const int L = jd.geo.L;
+        if (resident && jd.resident)
+            return 0;
+        return L == 64 ? 3 : L == 128 ? 4 : (general && general_tile_side(L)) ? 2 : 1;
     };
-    int count[4] = {0, 0, 0, 0};
+    int count[5] = {0, 0, 0, 0, 0};
     int prev = 0;
     for (int i = 0; i < n_jobs; ++i) {
-        const int c = cls(host[i].geo.L);
+        const int c = cls(host[i]);
         if (c < prev) {  // not in run order
             runs[0] = {0, n_jobs, 0};
             return 1;
@@ -2152,7 +2873,7 @@ static int split_runs(const JobDev *host, int n_jobs, bool general, Run runs[4])
         ++count[c];
     }
     int n_runs = 0, first = 0;
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 5; ++c)
         if (count[c] > 0) {
             runs[n_runs++] = {first, count[c], kCode[c]};
             first += count[c];
@@ -2169,8 +2890,8 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
     // between them: given side streams, every run after the first is forked
     // from `stream` and joined back after its n sweeps, so the runs share the
     // GPU.  The heat-bath runs follow on `stream`.
-    Run runs[4];
-    const int n_runs = split_runs(host0, n_jobs0, true, runs);
+    Run runs[5];
+    const int n_runs = split_runs(host0, n_jobs0, true, true, runs);
     const bool fork = side != nullptr && n_runs > 1;
     if (fork) {
         cudaError_t err = cudaEventRecord(side->fork, stream);
@@ -2192,12 +2913,48 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
         if (err != cudaSuccess)
             return err;
     }
-    Run hruns[4];
-    const int n_hruns = split_runs(host1, n_jobs1, true, hruns);
+    Run hruns[5];
+    const int n_hruns = split_runs(host1, n_jobs1, true, false, hruns);
     for (int r = 0; r < n_hruns; ++r)
         launch_metro_run<true>(host1 + hruns[r].first, dev1 + hruns[r].first, hruns[r].cnt,
                                hruns[r].GLR, n, stream, counters);
     return cudaGetLastError();
+}
+
+void set_wait_policy(uint32_t limit, uint32_t mode)
+{
+    g_wait_limit = limit;
+    g_wait_mode = mode;
+}
+
+cudaError_t read_sweep_status(cudaStream_t stream, uint32_t *status)
+{
+    unsigned int v = 0u, zero = 0u;
+    cudaError_t err = cudaMemcpyFromSymbolAsync(&v, g_sweep_status, sizeof(v), 0,
+                                                cudaMemcpyDeviceToHost, stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyToSymbolAsync(g_sweep_status, &zero, sizeof(zero), 0,
+                                      cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(stream);
+    *status = v;
+    return err;
+}
+
+cudaError_t prepare_resident_kernels()
+{
+    cudaError_t err = cudaSuccess;
+    auto take = [&err](cudaError_t e) {
+        if (err == cudaSuccess)
+            err = e;
+    };
+    take(res_opt_in<false, 8>());
+    take(res_opt_in<true, 8>());
+    take(res_opt_in<false, 128>());
+    take(res_opt_in<true, 128>());
+    take(res_opt_in<false, kMetroMaxJobs>());
+    take(res_opt_in<true, kMetroMaxJobs>());
+    return err;
 }
 
 cudaError_t launch_advance_time(JobDev *jobs_dev, int n_jobs, uint64_t n, cudaStream_t stream)

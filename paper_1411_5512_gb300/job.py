@@ -75,6 +75,21 @@ def int_throughput(stream=None):
     return {"lop3": out[0], "imad": out[1], "philox": out[2]}
 
 
+def debug_set_wait(polls, wait_for_nothing=False):
+    """The bounded device waits: polls before giving up; wait_for_nothing (tests of
+    the timeout path only) makes every wait run out."""
+    _lib.check(_lib.load().ea_debug_set_wait(int(polls), 1 if wait_for_nothing else 0))
+
+
+def device_status(stream=None):
+    """Synchronise, read and clear the device status word (bit 0: a wait ran out)."""
+    v = ctypes.c_uint32()
+    rc = _lib.load().ea_device_status(_stream_handle(stream), ctypes.byref(v))
+    if rc not in (_lib.EA_OK, _lib.EA_ERR_TIMEOUT):
+        _lib.check(rc)
+    return v.value
+
+
 def geometry(L):
     out = (ctypes.c_int * 6)()
     _lib.check(_lib.load().ea_geometry(L, out))
@@ -292,6 +307,24 @@ class EABatch:
         a, b = ctypes.c_int(), ctypes.c_int()
         _lib.check(self.lib.ea_batch_get_config(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def set_resident(self, max_side):
+        """Metropolis members up to this side run sample-resident (0: never)."""
+        _lib.check(self.lib.ea_batch_set_resident(self.h, int(max_side)), batch=self.h)
+
+    def resident(self):
+        v = ctypes.c_int()
+        _lib.check(self.lib.ea_batch_get_resident(self.h, ctypes.byref(v)))
+        return v.value
+
+    def set_variant(self, variant):
+        """Side-128 Metropolis members: 1 the staged kernel, 0 the tile kernel."""
+        _lib.check(self.lib.ea_batch_set_variant(self.h, int(variant)), batch=self.h)
+
+    def variant(self):
+        v = ctypes.c_int()
+        _lib.check(self.lib.ea_batch_get_variant(self.h, ctypes.byref(v)))
+        return v.value
 
     def autotune(self, trial_sweeps=8):
         _lib.check(self.lib.ea_batch_autotune(self.h, int(trial_sweeps)), batch=self.h)

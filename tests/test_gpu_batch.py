@@ -71,14 +71,18 @@ def alone(J, n):
     return res
 
 
-@pytest.mark.parametrize("cpt,graph", [(0, 0), (1, 0), (2, 4), (4, 16), (1, 7)])
-def test_batch_equals_alone(J, cpt, graph):
+@pytest.mark.parametrize("cpt,graph,res", [(0, 0, 64), (1, 0, 0), (2, 4, 64), (4, 16, 0),
+                                           (1, 7, 64), (2, 0, 32)])
+def test_batch_equals_alone(J, cpt, graph, res):
+    """A job alone (sample-resident where its side allows) equals the same job in a
+    mixed batch under every launch shape, graph length and resident limit."""
     import torch
     n = 21
     ref = alone(J, n)
     stream = torch.cuda.Stream()
     b = J.EABatch(stream=stream)
     b.configure(cpt, graph)
+    b.set_resident(res)
     jobs = [make(J, spec, stream=stream) for spec in MIX]
     for j in jobs:
         b.add(j)
@@ -191,24 +195,34 @@ def test_profile_counts_words_and_restores_state(J, L):
 
 
 def test_launch_count(J):
-    """The library's launch counter: two half-step launches per plain sweep; a batch
-    adds one time-advance kernel per enqueue, and a graph of K sweeps, replayed,
-    counts its 2K half-steps and its time advance."""
+    """The library's launch counter: two half-step launches per sweep, or one
+    sample-resident launch for up to 1024 sweeps; a batch adds one time-advance kernel
+    per enqueue, and a graph of K sweeps, replayed, counts the kernels it holds and its
+    time advance."""
     import torch
     j = make(J, (16, 0.5, 3, 1, 0.7, 0, [], []))
     n0 = J.launch_count()
-    j.sweep(5)
-    assert J.launch_count() - n0 == 10
+    j.sweep(5)  # side 16 swept on its own: sample-resident
+    assert J.launch_count() - n0 == 1
+    n0 = J.launch_count()
+    j.sweep(1500)
+    assert J.launch_count() - n0 == 2
     b = J.EABatch()  # default stream: direct launches, no graph
     b.configure(1, 4)
+    b.set_resident(0)
     b.add(j)
     n0 = J.launch_count()
     b.sweep(8)
     assert J.launch_count() - n0 == 2 * 8 + 1
+    b.set_resident(64)
+    n0 = J.launch_count()
+    b.sweep(8)
+    assert J.launch_count() - n0 == 1 + 1
     b.close()
     stream = torch.cuda.Stream()
     b = J.EABatch(stream=stream)
     b.configure(1, 4)
+    b.set_resident(0)
     b.add(j)
     b.sweep(4)  # captures the graph (capturing counts nothing) and replays it once
     n0 = J.launch_count()

@@ -119,3 +119,39 @@ def test_library_job_continues_from_its_checkpoint(J, tmp_path):
     res = recovery.run_jobs([spec, dict(spec, seed=6, rule=1)], 0, 1, dist.HashStore(),
                             str(tmp_path / "all"), chunk=7)
     assert sorted(res) == [0, 1] and res[0] == fresh
+
+
+def test_bounded_wait_runs_out_cleanly(J):
+    """A bounded device wait that runs out: the staged side-128 kernel waits on a
+    barrier that nothing completes (a test mode), gives up after a few polls, waits
+    for its own copies in flight and returns; the status word reports it, and the
+    context stays usable: with the normal policy back, a fresh job matches the
+    oracle bit for bit."""
+    import oracle as ora
+    L, p_neg, seed, T = 128, 0.5, 13, 0.7
+    j = J.EAJob(L, p_neg, seed, 2)
+    j.quench(T)
+    b = J.EABatch()
+    b.set_variant(1)
+    b.add(j)
+    assert J.device_status() == 0
+    try:
+        J.debug_set_wait(16, wait_for_nothing=True)
+        b.sweep(1)
+        assert J.device_status() & 1
+    finally:
+        J.debug_set_wait(1 << 22, wait_for_nothing=False)
+    assert J.device_status() == 0
+    b.close()
+    j.close()
+    j = J.EAJob(L, p_neg, seed, 2)
+    j.quench(T)
+    b = J.EABatch()
+    b.set_variant(1)
+    b.add(j)
+    b.sweep(2)
+    assert J.device_status() == 0
+    ref = ora.run_job(L, p_neg, seed, 2, T, 0, [], [], 2, samples=[1], keep_spins=True)
+    assert np.array_equal(j.all_spins(1), ref["spins"][0])
+    b.close()
+    j.close()

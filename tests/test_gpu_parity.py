@@ -114,12 +114,66 @@ SWEEP_CASES = [
 
 @pytest.mark.parametrize("L,p_neg,T,rule,G,S,n", SWEEP_CASES)
 def test_sweeps_bit_exact(J, L, p_neg, T, rule, G, S, n):
+    """Swept on its own: Metropolis samples of side up to 64 run sample-resident."""
     seed = 7 + L
     j = gpu_run(J, L, p_neg, seed, S, T, rule, [], [], n, G=G)
     ref = ora.run_job(L, p_neg, seed, S, T, rule, [], [], n, keep_spins=True, rng_group=G)
     for s in range(S):
         assert np.array_equal(j.all_spins(s), ref["spins"][s]), s
     j.close()
+
+
+@pytest.mark.parametrize("L,p_neg,T,rule,G,S,n",
+                         [c for c in SWEEP_CASES if c[3] == 0 and c[0] <= 64])
+def test_sweeps_bit_exact_per_half_step(J, L, p_neg, T, rule, G, S, n):
+    """The same Metropolis cases through a batch that keeps them off the sample-resident
+    kernel: one launch per half-step (column, general-tile and side-64 kernels)."""
+    seed = 7 + L
+    j = J.EAJob(L, p_neg, seed, S, rng_group=G)
+    j.quench(T, rule)
+    b = J.EABatch()
+    b.set_resident(0)
+    b.add(j)
+    b.sweep(n)
+    b.close()
+    ref = ora.run_job(L, p_neg, seed, S, T, rule, [], [], n, keep_spins=True, rng_group=G)
+    for s in range(S):
+        assert np.array_equal(j.all_spins(s), ref["spins"][s]), s
+    j.close()
+
+
+# the sample-resident kernel: several jobs of different sides in one launch, sweeps
+# beyond one launch, the temperature limits, shared random numbers, many rare paths
+RESIDENT_JOBS = [
+    # tuples of (L, p_neg, T, G, S) swept together, sweeps
+    ([(64, 0.5, 0.7, 1, 2), (16, 0.3, 1.1, 1, 3), (6, 0.5, 0.7, 1, 2)], 6),
+    ([(32, 0.5, 0.6, 1, 4), (48, 0.2, 0.8, 2, 4)], 5),
+    ([(8, 0.5, 0.7, 1, 2), (4, 0.5, 2.0, 1, 2), (2, 0.5, 1.0, 1, 2)], 1100),
+    ([(24, 0.5, 5.0, 1, 2), (16, 0.5, float("inf"), 1, 2), (16, 0.0, 0.0, 1, 2)], 4),
+    ([(64, 0.5, 1e17, 1, 1), (12, 0.5, 0.7, 2, 4)], 3),
+]
+
+
+@pytest.mark.parametrize("jobs,n", RESIDENT_JOBS)
+def test_resident_kernel_bit_exact(J, jobs, n):
+    handles = []
+    b = J.EABatch()
+    b.set_resident(64)
+    for k, (L, p_neg, T, G, S) in enumerate(jobs):
+        j = J.EAJob(L, p_neg, 900 + k + L, S, rng_group=G)
+        j.quench(T)
+        b.add(j)
+        handles.append(j)
+    b.sweep(n)
+    b.close()
+    for k, ((L, p_neg, T, G, S), j) in enumerate(zip(jobs, handles)):
+        assert j.time == n
+        pick = [0, S - 1] if S > 1 else [0]
+        ref = ora.run_job(L, p_neg, 900 + k + L, S, T, 0, [], [], n, samples=pick,
+                          keep_spins=True, rng_group=G)
+        for i, s in enumerate(pick):
+            assert np.array_equal(j.all_spins(s), ref["spins"][i]), (L, s)
+        j.close()
 
 
 # the side-64/128 kernel (2 x 2 word tiles, rows along y) under each segment length,
@@ -141,13 +195,20 @@ TILE_CASES = [
 ]
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("L,p_neg,T,cpt,S,n", TILE_CASES)
-def test_tile_kernel_bit_exact(J, L, p_neg, T, cpt, S, n):
+def test_tile_kernel_bit_exact(J, L, p_neg, T, cpt, S, n, variant):
+    """Sides 64 and 128 on the register-window tile kernel (variant 0) and, at side
+    128 where the tables allow, the staged kernel (variant 1)."""
+    if variant == 1 and L != 128:
+        pytest.skip("the staged kernel is for side 128")
     seed = 500 + L + cpt
     j = J.EAJob(L, p_neg, seed, S)
     j.quench(T)
     b = J.EABatch()
     b.configure(cpt, 0)
+    b.set_resident(0)  # side 64 on its tile kernel
+    b.set_variant(variant)
     b.add(j)
     b.sweep(n)
     pick = [0, S - 1] if S > 1 else [0]
@@ -159,8 +220,10 @@ def test_tile_kernel_bit_exact(J, L, p_neg, T, cpt, S, n):
 
 
 @pytest.mark.parametrize("t0", [(1 << 32) - 1, (1 << 44) + 77])
-def test_tile_kernel_late_time(J, t0):
-    """The high bits of the sweep counter in the tile kernel's draws."""
+@pytest.mark.parametrize("resident", [0, 64])
+def test_tile_kernel_late_time(J, t0, resident):
+    """The high bits of the sweep counter in the draws of the side-64 tile kernel and
+    of the sample-resident kernel."""
     L, seed, p_neg, T = 64, 41, 0.5, 0.9
     Jc = ora.init_couplings(L, p_neg, seed, 0)
     S0 = ora.init_spins(L, seed, 0)
@@ -169,7 +232,11 @@ def test_tile_kernel_late_time(J, t0):
     j = J.EAJob(L, p_neg, seed, 1)
     j.quench(T)
     j.set_time(t0)
-    j.sweep(3)
+    b = J.EABatch()
+    b.set_resident(resident)
+    b.add(j)
+    b.sweep(3)
+    b.close()
     assert np.array_equal(j.all_spins(0), ref)
     j.close()
 
@@ -195,6 +262,7 @@ def test_general_tile_kernel_bit_exact(J, L, p_neg, T, cpt, S, n):
     j.quench(T)
     b = J.EABatch()
     b.configure(cpt, 0)
+    b.set_resident(0)  # sides 32 and 48 on the general tiles
     b.add(j)
     b.sweep(n)
     pick = [0, S - 1] if S > 1 else [0]
@@ -237,14 +305,17 @@ def test_heat_bath_batch_bit_exact(J, L, p_neg, T, cpt, S, n):
     j.close()
 
 
-@pytest.mark.parametrize("L,rule,S", [(64, 0, 4), (64, 1, 4), (48, 0, 3), (96, 1, 2), (128, 0, 2)])
-def test_shared_random_numbers_on_the_tiles(J, L, rule, S):
+@pytest.mark.parametrize("L,rule,S,resident", [(64, 0, 4, 0), (64, 0, 4, 64), (64, 1, 4, 0),
+                                                (48, 0, 3, 0), (96, 1, 2, 0), (128, 0, 2, 0)])
+def test_shared_random_numbers_on_the_tiles(J, L, rule, S, resident):
     """Pairs of samples sharing their random numbers (G = 2) through the tile kernels of
-    both rules: every sample against the oracle with the same share groups."""
+    both rules and the sample-resident kernel: every sample against the oracle with the
+    same share groups."""
     seed, p_neg, T, n = 40 + L, 0.5, 0.8, 3
     j = J.EAJob(L, p_neg, seed, S, rng_group=2)
     j.quench(T, rule)
     b = J.EABatch()
+    b.set_resident(resident)
     b.add(j)
     b.sweep(n)
     b.close()
