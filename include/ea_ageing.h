@@ -232,6 +232,30 @@ int ea_quench(ea_ctx *ctx, double T, int rule);
  * EA_ERR_INVALID_ARG (time would pass 2^48), EA_ERR_CUDA. */
 int ea_sweep(ea_ctx *ctx, uint64_t n);
 
+/* One lattice split over ranks (y-slabs, the single-lattice decomposition
+ * over several GPUs that Sec. III sketches for lattices larger than one
+ * GPU).  Sides 64 and 128, whose word lattice has every lane along z, so that
+ * a row y' of the word lattice is the lattice row y:
+ *   ea_set_row_range: sweeps of this context update only the rows [y_lo,
+ *     y_hi); the other rows are read as neighbours and must be kept current
+ *     by the caller.  Needs a context with no measurement schedule that is not
+ *     in a batch (EA_ERR_STATE).  EA_ERR_INVALID_ARG for other sides or rows.
+ *     Not saved by ea_checkpoint.
+ *   ea_half_sweep: the next half-step of the current sweep (h = 0, then
+ *     h = 1, after which the time advances by one), so that the halo rows can
+ *     be exchanged between the two.  Needs a context with no schedule.
+ *   ea_get_rows / ea_set_rows: rows y .. y + n_rows - 1 of spin area `area`
+ *     (0 or 1: half-step h updates area h and reads area 1 - h) of every
+ *     sample, to or from host words laid out [sample][z'][row][x'];
+ *     synchronises the stream.
+ * A rank owning rows [lo, hi) sends its rows lo and hi - 1 of area 1 - h
+ * before half-step h and receives rows lo - 1 and hi (periodic); the result
+ * is bit-identical to the undivided lattice. */
+int ea_set_row_range(ea_ctx *ctx, int y_lo, int y_hi);
+int ea_half_sweep(ea_ctx *ctx);
+int ea_get_rows(ea_ctx *ctx, int area, int y, int n_rows, uint32_t *host_words);
+int ea_set_rows(ea_ctx *ctx, int area, int y, int n_rows, const uint32_t *host_words);
+
 /* Current time (sweeps done since the quench, counting sweeps still enqueued)
  * into *t.  Host only.  Errors: EA_ERR_INVALID_ARG (NULL). */
 int ea_time(const ea_ctx *ctx, uint64_t *t);

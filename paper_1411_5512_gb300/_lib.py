@@ -81,6 +81,10 @@ SIGNATURES = {
     "ea_set_schedule": (ctypes.c_int, [vp, u64p, ctypes.c_int, u64p, ctypes.c_int]),
     "ea_quench": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
     "ea_sweep": (ctypes.c_int, [vp, ctypes.c_uint64]),
+    "ea_set_row_range": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+    "ea_half_sweep": (ctypes.c_int, [vp]),
+    "ea_get_rows": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p]),
+    "ea_set_rows": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p]),
     "ea_time": (ctypes.c_int, [vp, u64p]),
     "ea_measure": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.POINTER(EaObs)]),

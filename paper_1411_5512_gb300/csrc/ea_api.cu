@@ -253,6 +253,7 @@ struct ea_ctx {
     int S = 0;
     int first = 0;  // the job-local index of sample 0 (ea_create_samples_range)
     int G = 1;
+    int half = 0;   // 1 between the two half-steps of a sweep (ea_half_sweep)
     cudaStream_t stream = nullptr;
     Geo geo;
 
@@ -614,6 +615,8 @@ int ea_create_samples_range(ea_ctx **out, int L, double p_neg, uint64_t seed, in
     c->jd.geo = g;
     c->jd.n_samples = n_samples;
     c->jd.first_sample = first_sample;
+    c->jd.row_lo = 0;
+    c->jd.row_hi = g.n[1];
     c->jd.resident = L <= ea::kResDefaultMaxL && ea::res_side_fits(L) ? 1 : 0;
     c->jd.variant = 0;  // side 128: the register-window tile kernel
     if (c->jd.resident) {
@@ -731,6 +734,8 @@ int ea_sweep(ea_ctx *c, uint64_t n)
         return fail(c, EA_ERR_STATE, "ea_sweep before ea_quench");
     if (n > ea::kMaxTime || c->t + n > ea::kMaxTime)
         return fail(c, EA_ERR_INVALID_ARG, "time would pass 2^48");
+    if (c->half != 0)
+        return fail(c, EA_ERR_STATE, "ea_sweep between the half-steps of ea_half_sweep");
     const uint64_t target = c->t + n;
     while (c->t < target) {
         auto it = std::upper_bound(c->meas.begin(), c->meas.end(), c->t);
@@ -747,6 +752,92 @@ int ea_sweep(ea_ctx *c, uint64_t n)
             return rc;
     }
     return EA_OK;
+}
+
+int ea_set_row_range(ea_ctx *c, int y_lo, int y_hi)
+{
+    if (check_ctx(c))
+        return EA_ERR_INVALID_ARG;
+    if (c->L != 64 && c->L != 128)
+        return fail(c, EA_ERR_INVALID_ARG, "ea_set_row_range: sides 64 and 128 only");
+    if (y_lo < 0 || y_hi > c->geo.n[1] || y_lo >= y_hi)
+        return fail(c, EA_ERR_INVALID_ARG, "ea_set_row_range: need 0 <= y_lo < y_hi <= L");
+    if (!c->tw.empty() || !c->tt.empty())
+        return fail(c, EA_ERR_STATE, "ea_set_row_range on a context with a measurement schedule");
+    if (c->batch)
+        return fail(c, EA_ERR_STATE, "ea_set_row_range on a member of a batch");
+    c->jd.row_lo = y_lo;
+    c->jd.row_hi = y_hi;
+    return EA_OK;
+}
+
+int ea_half_sweep(ea_ctx *c)
+{
+    NvtxRange nvtx_range("ea_half_sweep");
+    if (check_ctx(c))
+        return EA_ERR_INVALID_ARG;
+    if (!c->quenched)
+        return fail(c, EA_ERR_STATE, "ea_half_sweep before ea_quench");
+    if (!c->meas.empty())
+        return fail(c, EA_ERR_STATE, "ea_half_sweep on a context with a measurement schedule");
+    if (c->batch)
+        return fail(c, EA_ERR_STATE, "ea_half_sweep on a member of a batch");
+    if (c->t + 1 > ea::kMaxTime)
+        return fail(c, EA_ERR_INVALID_ARG, "time would pass 2^48");
+    if (c->half == 0) {
+        const int rc = upload_time(c, c->t + 1);
+        if (rc != EA_OK)
+            return rc;
+    }
+    const bool heat = c->rule == EA_RULE_HEATBATH;
+    EA_CUDA(c, ea::launch_sweep_table(heat ? nullptr : &c->jd, heat ? nullptr : c->jd_dev,
+                                      heat ? 0 : 1, heat ? &c->jd : nullptr,
+                                      heat ? c->jd_dev : nullptr, heat ? 1 : 0, 1, c->stream,
+                                      nullptr, nullptr, c->half));
+    if (c->half == 1) {
+        c->half = 0;
+        c->t += 1;
+    } else {
+        c->half = 1;
+    }
+    return EA_OK;
+}
+
+// Rows y .. y + n_rows - 1 of one area of every sample, host layout
+// [sample][z'][row][x'] (word-lattice words).
+static int copy_rows(ea_ctx *c, int area, int y, int n_rows, uint32_t *host, bool to_host)
+{
+    if (check_ctx(c) || !host || (area != 0 && area != 1) || n_rows < 1 || y < 0 ||
+        y + n_rows > c->geo.n[1])
+        return EA_ERR_INVALID_ARG;
+    const size_t n0 = (size_t)c->geo.n[0], n2 = (size_t)c->geo.n[2];
+    const size_t sz = n0 * (size_t)c->geo.n[1], W = (size_t)c->geo.words;
+    const size_t width = (size_t)n_rows * n0 * sizeof(uint32_t);
+    for (int s = 0; s < c->S; ++s) {
+        uint32_t *dev = c->spins + ((size_t)s * 2 + area) * W + (size_t)y * n0;
+        uint32_t *h = host + (size_t)s * n2 * n_rows * n0;
+        const cudaError_t e =
+            to_host ? cudaMemcpy2DAsync(h, width, dev, sz * sizeof(uint32_t), width, n2,
+                                        cudaMemcpyDeviceToHost, c->stream)
+                    : cudaMemcpy2DAsync(dev, sz * sizeof(uint32_t), h, width, width, n2,
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, to_host ? "ea_get_rows" : "ea_set_rows");
+    }
+    EA_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!to_host)
+        ++c->res_gen;
+    return EA_OK;
+}
+
+int ea_get_rows(ea_ctx *c, int area, int y, int n_rows, uint32_t *host_words)
+{
+    return copy_rows(c, area, y, n_rows, host_words, true);
+}
+
+int ea_set_rows(ea_ctx *c, int area, int y, int n_rows, const uint32_t *host_words)
+{
+    return copy_rows(c, area, y, n_rows, const_cast<uint32_t *>(host_words), false);
 }
 
 int ea_time(const ea_ctx *c, uint64_t *t)
@@ -1453,6 +1544,7 @@ uint64_t table_signature(const std::vector<ea::JobDev> (&tab)[2])
             mix(((uint64_t)(uint32_t)jd.all_always << 32) | (uint32_t)jd.none_random);
             mix(((uint64_t)jd.gC_hi[1][32] << 32) | jd.gC_hi[0][32]);
             mix(((uint64_t)(uint32_t)jd.resident << 32) | (uint32_t)jd.variant);
+            mix(((uint64_t)(uint32_t)jd.row_lo << 32) | (uint32_t)jd.row_hi);
         }
     }
     return h;
@@ -1476,7 +1568,10 @@ int upload_tables(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limits =
         jd.t_end = m->t + allow;
         if (b->cpt > 0)
             ea::fill_job_layout(&jd, b->cpt);
-        jd.resident = (r == 0 && jd.geo.L <= b->res_max_L && ea::res_side_fits(jd.geo.L)) ? 1 : 0;
+        jd.resident = (r == 0 && jd.geo.L <= b->res_max_L && ea::res_side_fits(jd.geo.L) &&
+                       jd.row_lo == 0 && jd.row_hi == jd.geo.n[1])
+                          ? 1
+                          : 0;
         jd.variant = b->variant;
         b->tab_host[r].push_back(jd);
     }

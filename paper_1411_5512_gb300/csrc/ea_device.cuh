@@ -133,6 +133,22 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Four independent Philox4x32-10 calls advanced round by round together: each
+// round key serves four calls, and the four multiply chains overlap.
+__device__ __forceinline__ void philox10_rk_x4(uint4 (&c)[4], const uint32_t (&rk)[20])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t p0 = (uint64_t)0xD2511F53u * c[k].x;
+            const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[k].z;
+            c[k] = make_uint4((uint32_t)(p1 >> 32) ^ c[k].y ^ rk[2 * r], (uint32_t)p1,
+                              (uint32_t)(p0 >> 32) ^ c[k].w ^ rk[2 * r + 1], (uint32_t)p0);
+        }
+    }
+}
+
 constexpr uint32_t kStreamCouplings = 0u << 30;
 constexpr uint32_t kStreamSpins = 1u << 30;
 constexpr uint32_t kStreamHeat = 2u << 30;         // heat-bath coin words and gaps

@@ -92,7 +92,9 @@ struct alignas(16) JobDev {
     int resident;             // Metropolis: run every sweep of a launch out of shared
                               // memory, one block per sample (res_side_fits)
     int variant;              // bit 0: Metropolis side 128 on the staged kernel
-    int pad_;
+    int row_lo, row_hi;       // sides 64 and 128: the rows [row_lo, row_hi) of the word
+                              // lattice that sweeps update (ea_set_row_range)
+    int pad_[3];
 };
 
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev tables are arrays of 16-byte aligned rows");
@@ -113,6 +115,8 @@ struct MetroGeo {
     int n0, n1, n2, cols;
     int bps, cpt;          // blocks per sample, word columns per thread
     int seg;               // rows per thread of the tile kernels
+    int row0;              // the first row the tile kernels update (sides 64, 128)
+    int row_n;             // and how many: threads past them update nothing
     uint32_t words;        // words per area
     uint32_t valid, magic;
     int dshift;
@@ -211,11 +215,13 @@ struct SideStreams {
 // and run (tables of more than kMetroMaxJobs jobs take several).  host0/dev0
 // are the host and device copies of the Metropolis rows, host1/dev1 those of
 // the heat-bath rows.
+// half = 0 or 1: only that half-step of one sweep (n must be 1), for a
+// lattice split over ranks whose halo rows are exchanged between half-steps.
 cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
                                const JobDev *host1, const JobDev *dev1, int n_jobs1,
                                uint64_t n, cudaStream_t stream,
                                unsigned long long *counters = nullptr,
-                               const SideStreams *side = nullptr);
+                               const SideStreams *side = nullptr, int half = -1);
 
 // Four-point sums over every displacement vector (ea_c4full.cu), by an exact
 // transform modulo a prime p = cL + 1 > 2N + 1 below 2^31.

@@ -797,7 +797,11 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
     const int tl = (local - s * G.bps) * kSweepThreads + (int)threadIdx.x;
     const int x0 = 2 * (tl & (XP - 1));
     const int z0 = 2 * ((tl >> XPLOG) & (ZP - 1));  // uniform over a warp (XP >= 32)
-    const int y0 = (tl >> XPLOG) / ZP * Y;
+    // threads past the last segment of a row range (ea_set_row_range) run no
+    // row; a warp is wholly in or out (a row of tiles is a whole number of warps)
+    const bool act = (tl >> XPLOG) / ZP * Y < G.row_n;
+    const int y0 = G.row0 + (act ? (tl >> XPLOG) / ZP * Y : 0);
+    const int Yrun = act ? Y : 0;
     const bool all_always = (J.meta >> 3) & 1u, none_random = (J.meta >> 4) & 1u;
     const uint32_t live0 = 0u - (J.meta & 1u), live1 = 0u - ((J.meta >> 1) & 1u),
                    live2 = 0u - ((J.meta >> 2) & 1u);
@@ -823,7 +827,7 @@ __global__ void __launch_bounds__(kSweepThreads, 9)
     uint2 Nm0 = ld2(nb, x0 + rym + oz0), Nm1 = ld2(nb, x0 + rym + oz1);
     uint2 Jym0 = ld2(Jy, x0 + rym + oz0), Jym1 = ld2(Jy, x0 + rym + oz1);
     uint2 Nc0 = ld2(nb, x0 + y0 * GL + oz0), Nc1 = ld2(nb, x0 + y0 * GL + oz1);
-    for (int i = 0; i < Y; ++i) {
+    for (int i = 0; i < Yrun; ++i) {
         const int y = y0 + i;
         const int ry = y * GL, ryp = ((y + 1) & (GL - 1)) * GL;
         const int w0 = x0 + ry + oz0, w1 = x0 + ry + oz1;  // the even-x words at z0, z0 + 1
@@ -1065,7 +1069,7 @@ __global__ void __launch_bounds__(kSweepThreads, 5)
     const int Y = G.seg;
     const int local = (int)blockIdx.x - P.block_begin[j];
     const int s = local / G.bps;
-    const int y0 = (local - s * G.bps) * Y;
+    const int y0 = G.row0 + (local - s * G.bps) * Y;
     uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
     const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
     const uint32_t *__restrict__ Jx = J.J + (size_t)s * 3 * W;
@@ -2021,9 +2025,14 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
         z0 = 2 * ((tl / xp) % zp);
         y0 = tl / xp / zp * Y;
     } else {
+        // threads past the last segment of a row range run on a valid tile and
+        // write nothing
+        act = (tl >> XPLOG) / ZP * Y < G.row_n;
+        if (!act)
+            tl = 0;
         x0 = 2 * (tl & (XP - 1));
         z0 = 2 * ((tl >> XPLOG) & (ZP - 1));  // uniform over a warp (XP >= 32)
-        y0 = (tl >> XPLOG) / ZP * Y;
+        y0 = G.row0 + (tl >> XPLOG) / ZP * Y;
     }
     uint32_t *__restrict__ upd = J.spins + ((size_t)s * 2 + h) * W;
     const uint32_t *__restrict__ nb = J.spins + ((size_t)s * 2 + (h ^ 1)) * W;
@@ -2547,7 +2556,7 @@ static void metro_job(MetroJob &m, const JobDev &jd, int geo_index)
 // kMetroMaxGeo (side, layout) geometries.
 template <int MAXJ, int GL, bool HEAT = false>
 static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, uint64_t n,
-                               cudaStream_t stream, unsigned long long *counters)
+                               cudaStream_t stream, unsigned long long *counters, int half)
 {
     MetroParams<MAXJ> p;
     std::memset(p.geo, 0, sizeof(p.geo));
@@ -2557,7 +2566,11 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
     p.wait_limit = g_wait_limit;
     p.wait_mode = g_wait_mode;
     int n_geo = 0;
-    int geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
+    int geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo], geo_lo[kMetroMaxGeo], geo_hi[kMetroMaxGeo];
+    // the rows a job's tile launch updates: all, or its row range (sides 64, 128)
+    auto rows_of = [](const JobDev &jd) {
+        return (GL == 64 || GL == 128) ? jd.row_hi - jd.row_lo : jd.geo.n[1];
+    };
     // tile kernels: rows per thread from the launch shape, halved (down to 2)
     // while the launch would hold fewer than four blocks per SM
     int y_max = 16;
@@ -2565,7 +2578,7 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
         long tiles = 0;  // tiles of one row, 2 x 2 word-sites each
         for (int i = 0; i < cnt; ++i)
             tiles += (long)host[i].n_samples * (host[i].geo.n[0] / 2) * (host[i].geo.n[2] / 2) *
-                     host[i].geo.n[1];
+                     rows_of(host[i]);
         while (y_max > 2 && tiles / y_max / kSweepThreads < 4L * kTileMinSMs)
             y_max >>= 1;
         // a launch that would not even give every SM a block takes single rows:
@@ -2576,21 +2589,30 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
     for (int i = 0; i < cnt; ++i) {
         const JobDev &jd = host[i];
         int gi = 0;
-        while (gi < n_geo && !(geo_L[gi] == jd.geo.L && geo_cpt[gi] == jd.cols_per_thread))
+        const bool ranged = GL == 64 || GL == 128;
+        while (gi < n_geo &&
+               !(geo_L[gi] == jd.geo.L && geo_cpt[gi] == jd.cols_per_thread &&
+                 (!ranged || (geo_lo[gi] == jd.row_lo && geo_hi[gi] == jd.row_hi))))
             ++gi;
         if (gi == n_geo) {
             geo_L[gi] = jd.geo.L;
             geo_cpt[gi] = jd.cols_per_thread;
+            geo_lo[gi] = jd.row_lo;
+            geo_hi[gi] = jd.row_hi;
             metro_geo(p.geo[gi], jd);
             if (GL != 0) {
                 // tiles of 2 x 2 word-sites times a segment of Y = 4, 8 or 16 rows
-                // (fewer where the row count n1 of the word lattice needs it)
+                // (fewer where the row count of the word lattice, or of the job's
+                // row range, needs it)
+                const int n_rows = rows_of(jd);
                 int Y = std::min(y_max,
                                  jd.cols_per_thread >= 4 ? 16 : jd.cols_per_thread >= 2 ? 8 : 4);
-                while (jd.geo.n[1] % Y != 0)
+                while (n_rows % Y != 0)
                     Y >>= 1;
-                const int threads = (jd.geo.n[0] / 2) * (jd.geo.n[2] / 2) * (jd.geo.n[1] / Y);
+                const int threads = (jd.geo.n[0] / 2) * (jd.geo.n[2] / 2) * (n_rows / Y);
                 p.geo[gi].seg = Y;
+                p.geo[gi].row0 = ranged ? jd.row_lo : 0;
+                p.geo[gi].row_n = n_rows;
                 p.geo[gi].bps = (threads + kSweepThreads - 1) / kSweepThreads;
             }
             ++n_geo;
@@ -2609,6 +2631,8 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
                (host[i].always_u & 7u) == 0u;
     for (uint64_t k = 0; k < n; ++k)
         for (int h = 0; h < 2; ++h) {
+            if (half >= 0 && h != half)
+                continue;
             p.h = h;
             p.sweep_offset = (uint32_t)k;
             if constexpr (HEAT && GL != 0) {
@@ -2759,20 +2783,25 @@ static void launch_res_chunk(const JobDev *host, const JobDev *dev, int cnt, uin
 // most kMetroMaxJobs jobs and kMetroMaxGeo geometries per launch.
 template <bool HEAT = false>
 static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int GLR, uint64_t n,
-                             cudaStream_t stream, unsigned long long *counters)
+                             cudaStream_t stream, unsigned long long *counters, int half)
 {
     for (int first = 0, c = 0; first < cnt; first += c) {
-        int n_geo = 0, geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo];
+        int n_geo = 0, geo_L[kMetroMaxGeo], geo_cpt[kMetroMaxGeo], geo_lo[kMetroMaxGeo],
+            geo_hi[kMetroMaxGeo];
         for (c = 0; first + c < cnt && c < kMetroMaxJobs; ++c) {
             const JobDev &jd = host[first + c];
             int gi = 0;
-            while (gi < n_geo && !(geo_L[gi] == jd.geo.L && geo_cpt[gi] == jd.cols_per_thread))
+            while (gi < n_geo &&
+                   !(geo_L[gi] == jd.geo.L && geo_cpt[gi] == jd.cols_per_thread &&
+                     geo_lo[gi] == jd.row_lo && geo_hi[gi] == jd.row_hi))
                 ++gi;
             if (gi == n_geo) {
                 if (n_geo == kMetroMaxGeo)
                     break;
                 geo_L[gi] = jd.geo.L;
                 geo_cpt[gi] = jd.cols_per_thread;
+                geo_lo[gi] = jd.row_lo;
+                geo_hi[gi] = jd.row_hi;
                 ++n_geo;
             }
         }
@@ -2787,58 +2816,58 @@ static void launch_metro_run(const JobDev *host, const JobDev *dev, int cnt, int
                 launch_res_chunk<kMetroMaxJobs>(h, d, c, n, stream, counters);
         } else if (HEAT && GLR == 128) {
             if (c <= 8)
-                launch_metro_chunk<8, 128, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<8, 128, true>(h, d, c, n, stream, counters, half);
             else
-                launch_metro_chunk<kMetroMaxJobs, 128, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<kMetroMaxJobs, 128, true>(h, d, c, n, stream, counters, half);
         } else if (HEAT && GLR == kGeneralTile) {
             if (c <= 8)
-                launch_metro_chunk<8, kGeneralTile, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<8, kGeneralTile, true>(h, d, c, n, stream, counters, half);
             else if (c <= 128)
-                launch_metro_chunk<128, kGeneralTile, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<128, kGeneralTile, true>(h, d, c, n, stream, counters, half);
             else
                 launch_metro_chunk<kMetroMaxJobs, kGeneralTile, true>(h, d, c, n, stream,
-                                                                      counters);
+                                                                      counters, half);
         } else if (HEAT && GLR == 64) {
             if (c <= 8)
-                launch_metro_chunk<8, 64, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<8, 64, true>(h, d, c, n, stream, counters, half);
             else
-                launch_metro_chunk<kMetroMaxJobs, 64, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<kMetroMaxJobs, 64, true>(h, d, c, n, stream, counters, half);
         } else if (HEAT) {
             if (c <= 1)
-                launch_metro_chunk<1, 0, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<1, 0, true>(h, d, c, n, stream, counters, half);
             else if (c <= 8)
-                launch_metro_chunk<8, 0, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<8, 0, true>(h, d, c, n, stream, counters, half);
             else if (c <= 128)
-                launch_metro_chunk<128, 0, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<128, 0, true>(h, d, c, n, stream, counters, half);
             else
-                launch_metro_chunk<kMetroMaxJobs, 0, true>(h, d, c, n, stream, counters);
+                launch_metro_chunk<kMetroMaxJobs, 0, true>(h, d, c, n, stream, counters, half);
         } else if (GLR == kGeneralTile) {
             if (c <= 8)
-                launch_metro_chunk<8, kGeneralTile>(h, d, c, n, stream, counters);
+                launch_metro_chunk<8, kGeneralTile>(h, d, c, n, stream, counters, half);
             else if (c <= 128)
-                launch_metro_chunk<128, kGeneralTile>(h, d, c, n, stream, counters);
+                launch_metro_chunk<128, kGeneralTile>(h, d, c, n, stream, counters, half);
             else
-                launch_metro_chunk<kMetroMaxJobs, kGeneralTile>(h, d, c, n, stream, counters);
+                launch_metro_chunk<kMetroMaxJobs, kGeneralTile>(h, d, c, n, stream, counters, half);
         } else if (GLR == 128) {
             if (c <= 8)
-                launch_metro_chunk<8, 128>(h, d, c, n, stream, counters);
+                launch_metro_chunk<8, 128>(h, d, c, n, stream, counters, half);
             else
-                launch_metro_chunk<kMetroMaxJobs, 128>(h, d, c, n, stream, counters);
+                launch_metro_chunk<kMetroMaxJobs, 128>(h, d, c, n, stream, counters, half);
         } else if (GLR == 64) {
             if (c <= 8)
-                launch_metro_chunk<8, 64>(h, d, c, n, stream, counters);
+                launch_metro_chunk<8, 64>(h, d, c, n, stream, counters, half);
             else
-                launch_metro_chunk<kMetroMaxJobs, 64>(h, d, c, n, stream, counters);
+                launch_metro_chunk<kMetroMaxJobs, 64>(h, d, c, n, stream, counters, half);
         } else if (c <= 1) {
-            launch_metro_chunk<1, 0>(h, d, c, n, stream, counters);
+            launch_metro_chunk<1, 0>(h, d, c, n, stream, counters, half);
         } else if (c <= 8) {
-            launch_metro_chunk<8, 0>(h, d, c, n, stream, counters);
+            launch_metro_chunk<8, 0>(h, d, c, n, stream, counters, half);
         } else if (c <= 32) {
-            launch_metro_chunk<32, 0>(h, d, c, n, stream, counters);
+            launch_metro_chunk<32, 0>(h, d, c, n, stream, counters, half);
         } else if (c <= 128) {
-            launch_metro_chunk<128, 0>(h, d, c, n, stream, counters);
+            launch_metro_chunk<128, 0>(h, d, c, n, stream, counters, half);
         } else {
-            launch_metro_chunk<kMetroMaxJobs, 0>(h, d, c, n, stream, counters);
+            launch_metro_chunk<kMetroMaxJobs, 0>(h, d, c, n, stream, counters, half);
         }
     }
 }
@@ -2884,14 +2913,15 @@ static int split_runs(const JobDev *host, int n_jobs, bool general, bool residen
 cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
                                const JobDev *host1, const JobDev *dev1, int n_jobs1,
                                uint64_t n, cudaStream_t stream, unsigned long long *counters,
-                               const SideStreams *side)
+                               const SideStreams *side, int half)
 {
     // Runs of the Metropolis table hold different jobs, so they need no order
     // between them: given side streams, every run after the first is forked
     // from `stream` and joined back after its n sweeps, so the runs share the
     // GPU.  The heat-bath runs follow on `stream`.
     Run runs[5];
-    const int n_runs = split_runs(host0, n_jobs0, true, true, runs);
+    // the sample-resident kernel runs whole sweeps only
+    const int n_runs = split_runs(host0, n_jobs0, true, half < 0, runs);
     const bool fork = side != nullptr && n_runs > 1;
     if (fork) {
         cudaError_t err = cudaEventRecord(side->fork, stream);
@@ -2902,7 +2932,7 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
     }
     for (int r = 0; r < n_runs; ++r)
         launch_metro_run(host0 + runs[r].first, dev0 + runs[r].first, runs[r].cnt, runs[r].GLR, n,
-                         fork && r > 0 ? side->stream[r - 1] : stream, counters);
+                         fork && r > 0 ? side->stream[r - 1] : stream, counters, half);
     if (fork) {
         cudaError_t err = cudaSuccess;
         for (int r = 1; r < n_runs && err == cudaSuccess; ++r) {
@@ -2917,7 +2947,7 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
     const int n_hruns = split_runs(host1, n_jobs1, true, false, hruns);
     for (int r = 0; r < n_hruns; ++r)
         launch_metro_run<true>(host1 + hruns[r].first, dev1 + hruns[r].first, hruns[r].cnt,
-                               hruns[r].GLR, n, stream, counters);
+                               hruns[r].GLR, n, stream, counters, half);
     return cudaGetLastError();
 }
 

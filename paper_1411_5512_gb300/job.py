@@ -152,6 +152,27 @@ class EAJob:
     def sweep(self, n):
         _lib.check(self.lib.ea_sweep(self.h, int(n)), self.h)
 
+    def set_row_range(self, y_lo, y_hi):
+        """Sweeps update only the rows [y_lo, y_hi) (sides 64, 128; see domain.py)."""
+        _lib.check(self.lib.ea_set_row_range(self.h, int(y_lo), int(y_hi)), self.h)
+
+    def half_sweep(self):
+        """The next half-step of the current sweep (h = 0, then h = 1)."""
+        _lib.check(self.lib.ea_half_sweep(self.h), self.h)
+
+    def get_rows(self, area, y, n_rows):
+        """Rows y .. y + n_rows - 1 of spin area `area`, uint32 [S][n2][n_rows][n0]."""
+        g = geometry(self.L)
+        out = np.zeros((self.n_samples, g[5], n_rows, g[3]), dtype=np.uint32)
+        _lib.check(self.lib.ea_get_rows(self.h, int(area), int(y), int(n_rows),
+                                        out.ctypes.data_as(_lib.u32p)), self.h)
+        return out
+
+    def set_rows(self, area, y, words):
+        arr = np.ascontiguousarray(words, dtype=np.uint32)
+        _lib.check(self.lib.ea_set_rows(self.h, int(area), int(y), int(arr.shape[2]),
+                                        arr.ctypes.data_as(_lib.u32p)), self.h)
+
     @property
     def time(self):
         t = ctypes.c_uint64()

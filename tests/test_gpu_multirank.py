@@ -84,3 +84,52 @@ def test_two_ranks_on_the_library_sum_to_single_process():
             assert np.array_equal(spins[i], ref_spins[s]), (rank, s)
             covered.append(s)
     assert sorted(covered) == list(range(JOB["n_samples"]))
+
+
+def _slab_rank(rank, world, port, q, L, rule):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1411_5512_gb300 import domain
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    j = domain.run_slab(L, 0.5, 77, 2, 0.8, rule, 3, rank, world)
+    lo, hi = domain.slab(L, rank, world)
+    q.put((rank, lo, hi, [j.get_rows(a, lo, hi - lo) for a in (0, 1)], j.time))
+    j.close()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("L,world,rule", [(128, 2, 0), (64, 3, 1)])
+def test_ranks_split_one_lattice(L, world, rule):
+    """One lattice in y-slabs over ranks (processes sharing the one GPU) with the halo
+    rows exchanged by gloo between the half-steps: every slab equals those rows of the
+    undivided lattice, bit for bit."""
+    from paper_1411_5512_gb300 import build, job
+    build.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_rank, args=(r, world, port, q, L, rule))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=600) for _ in procs]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    whole = job.EAJob(L, 0.5, 77, 2)
+    whole.quench(0.8, rule)
+    whole.sweep(3)
+    ref = [whole.get_rows(a, 0, L) for a in (0, 1)]
+    covered = []
+    for rank, lo, hi, areas, t in got:
+        assert t == 3
+        for a in (0, 1):
+            assert np.array_equal(areas[a], ref[a][:, :, lo:hi, :]), (rank, a)
+        covered += list(range(lo, hi))
+    assert sorted(covered) == list(range(L))
+    whole.close()

@@ -85,3 +85,22 @@ def test_two_gloo_ranks_sum_to_single_process():
     ref = _sums(full, JOB["n_samples"], list(range(JOB["n_samples"])))
     assert np.array_equal(total, ref)
     assert tmax == 2.0
+
+
+@pytest.mark.parametrize("L", [64, 128])
+@pytest.mark.parametrize("world", [1, 2, 3, 5])
+def test_slabs_and_halo_sources(L, world):
+    """The y-slabs of one lattice cover every row once; the row below a slab is the
+    previous rank's last row and the row above it the next rank's first (periodic)."""
+    from paper_1411_5512_gb300 import domain
+    rows = []
+    for r in range(world):
+        lo, hi = domain.slab(L, r, world)
+        assert hi > lo
+        rows += list(range(lo, hi))
+        (pr, prow), (nr, nrow) = domain.halo_sources(L, r, world)
+        assert prow == (lo - 1) % L and nrow == hi % L
+        plo, phi = domain.slab(L, pr, world)
+        nlo, nhi = domain.slab(L, nr, world)
+        assert plo <= prow < phi and nlo <= nrow < nhi
+    assert rows == list(range(L))
