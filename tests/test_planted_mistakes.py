@@ -37,7 +37,7 @@ MUTANTS = [
     # word-site geometry
     ("geometry_kz_cap", "ea_oracle.c", "int kz = p2 < 32 ? p2 : 32;", "int kz = p2 < 16 ? p2 : 16;"),
     ("geometry_block_origin", "ea_oracle.c", "sy[b] = ((b / kx) % ky) * Ly + yw;",
-     "sy[b] = ((b / kx) % ky) * Ly + yw + 1;"),
+     "sy[b] = (((b / kx) % ky) * Ly + yw + 1) % L;"),
     # Eq. 9 and the heat-bath rule
     ("metropolis_sign", "ea_oracle.c", "P = exp(-(double)dE / T);", "P = exp((double)dE / T);"),
     ("metropolis_temperature_scale", "ea_oracle.c", "P = exp(-(double)dE / T);",
