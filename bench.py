@@ -487,6 +487,9 @@ def run_ours(args, world, rank, local):
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed(args, job, workloads, stream, flush)
+    side32 = None
+    if not args.no_mixed:
+        side32 = run_side32(args, job, workloads, stream, flush)
     heat = None
     if not args.no_heat:
         heat = run_heat(args, job, workloads, stream, flush)
@@ -529,6 +532,8 @@ def run_ours(args, world, rank, local):
         line["serving"] = serving
     if mixed is not None:
         line["mixed_l"] = mixed
+    if side32 is not None:
+        line["side32"] = side32
     if heat is not None:
         line["heat_bath"] = heat
     if c4r is not None:
@@ -574,6 +579,35 @@ def run_plain_single(args, job, workloads, stream, flush, t_w, t_lag, t_now):
     m = statistics.median(ms)
     return {"value": flips / (m * 1e6), "unit": UNIT, "ms_per_step": m,
             "path": "one sample per launch sequence (80 contexts), 2 launches per sweep each"}
+
+
+def run_side32(args, job, workloads, stream, flush):
+    """The side-32 configuration (two jobs of 64 samples, T = 0.6 and 0.8) in one
+    batch: sample-resident (one block per sample in shared memory, up to 1024 sweeps
+    per launch) against one launch per half-step, median of three steps."""
+    specs = workloads.SMALL
+    jobs = []
+    for w in specs:
+        j = job.EAJob(w["L"], w["p_neg"], w["seed"], w["n_samples"], stream=stream)
+        j.quench(w["T"])
+        jobs.append(j)
+    flips = args.side32_sweeps * sum(2 * w["n_samples"] * w["L"] ** 3 for w in specs)
+    out = {"workload": "L32_S64x2_T0.6,0.8", "sweeps": args.side32_sweeps}
+    for name, res in (("resident", 32), ("per_half_step", 0)):
+        b = job.EABatch(stream=stream)
+        for j in jobs:
+            b.add(j)
+        b.configure(0, 16)
+        b.set_resident(res)
+        b.sweep(4)
+        ms = timed_steps(stream, 3, lambda: b.sweep(args.side32_sweeps), flush)
+        b.close()
+        m = statistics.median(ms)
+        out[name] = {"value": flips / (m * 1e6), "unit": UNIT, "ms": m}
+    for j in jobs:
+        j.close()
+    out["resident_over_per_half_step"] = out["resident"]["value"] / out["per_half_step"]["value"]
+    return out
 
 
 def run_mixed(args, job, workloads, stream, flush):
@@ -858,6 +892,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-heat", action="store_true")
     ap.add_argument("--mixed-sweeps", type=int, default=64)
+    ap.add_argument("--side32-sweeps", type=int, default=512)
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-chunk", type=int, default=1024)
     ap.add_argument("--serve-budget-gb", type=int, default=64)

@@ -2129,12 +2129,19 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
         Jym1 = Jy1;
         uint32_t out[4];
         bool hit[4];
+        // the four words' main calls advance round by round together: each
+        // round key serves four calls and the four multiply chains overlap
+        uint4 RR[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            RR[k] = make_uint4(wd[k], c1, c2w[k], c3);
+        dev::philox10_rk_x4(RR, rk);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t v = sp[k];
             const Count c = count6(v ^ in[k][0], v ^ in[k][1], v ^ in[k][2], v ^ in[k][3],
                                    v ^ in[k][4], v ^ in[k][5]);
-            const uint4 R = dev::philox10_rk(make_uint4(wd[k], c1, c2w[k], c3), rk);
+            const uint4 R = RR[k];
             uint32_t m3;
             if (LOWT) {
                 // the pairs (1, 5) and (0, 6) against their 32-lane bounds: a superset
