@@ -846,7 +846,9 @@ def run_case(args):
 
     torch.cuda.set_device(0)
     j = job.EAJob(args.case_L, 0.5, 100, args.case_samples)
-    if args.case_c4_radial:
+    if args.case_measure:
+        j.set_schedule([0, 1, 2, 4], [0, 1, 2, 4])
+    elif args.case_c4_radial:
         j.set_schedule([args.case_sweeps], [0])
     j.quench(args.case_T, args.case_rule)
     if args.case_plain:
@@ -906,6 +908,8 @@ def main():
     ap.add_argument("--case-T", type=float, default=0.7)
     ap.add_argument("--case-plain", action="store_true")
     ap.add_argument("--case-c4-radial", action="store_true")
+    ap.add_argument("--case-measure", action="store_true",
+                    help="schedule t_w = t = {0, 1, 2, 4} (the observable kernels fire)")
     ap.add_argument("--case-variant", type=int, default=-1,
                     help="side-128 Metropolis kernel: 0 tile, 1 staged (-1: the default)")
     ap.add_argument("--case-resident", type=int, default=-1,

@@ -106,6 +106,25 @@ def test_noalloc_matches_allocating_entry_point(J, L, S, n):
     j.close()
 
 
+def test_noalloc_matches_the_oracle(J):
+    """Directly against the oracle's brute force over every displacement vector, on the
+    oracle's own spins (side 16, two samples)."""
+    import oracle as ora
+    L, S, n, seed = 16, 2, 4, 71
+    j = J.EAJob(L, 0.5, seed, S)
+    j.set_schedule([n], [0])
+    j.quench(0.7)
+    j.sweep(n)
+    rc, sums, counts, _, _ = _call(j.lib, "ea_c4_radial_noalloc", j, n)
+    assert rc == 0, j.lib.ea_last_error(j.h)
+    ref = ora.run_job(L, 0.5, seed, S, 0.7, 0, [], [], n, keep_spins=True)
+    for s in range(S):
+        want, want_counts = ora.c4_radial_sums(ora.c4_full_sums(ref["spins"][s]))
+        assert np.array_equal(counts, want_counts)
+        assert np.array_equal(sums[s], want), s
+    j.close()
+
+
 def test_noalloc_rejects_sides_above_its_scratch(J):
     j = J.EAJob(130, 0.5, 3, 1)
     j.set_schedule([0], [0])
