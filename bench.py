@@ -290,6 +290,11 @@ def run_reference(args, world, rank):
 #   two wide multiplies, two three-input XORs and the key schedule), with the
 #   calls per word counted on the live state; every op is priced at the measured
 #   lop3.b32 rate of this GPU (ea_int_throughput).
+# Thread instructions the side-128 tile kernel executes per attempted flip, from
+# the ncu capture of profiles/metro_tile_kernel_L128_S128.md
+# (sass__thread_inst_executed_true_per_opcode total 825.3 M over 268.4 M flips):
+# what the kernel spends against the algorithmic ops of the ALU roof.
+NCU_THREAD_INST_PER_FLIP = 825.3e6 / (128 * 128 ** 3)
 BYTES_PER_FLIP = 7.0 / 16.0
 BYTES_PER_FLIP_HALF_STEPS = 12.0 / 16.0
 OPS_LOGIC_PER_WORD = 20
@@ -300,9 +305,9 @@ OPS_PER_PHILOX = 90
 # dram__bytes_write.sum, one pass, caches flushed before each captured launch;
 # mean of three launches).  Take them again (or set None) when the kernel
 # changes.
-TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.12e6, 2: 108.77e6 + 3.54e6, 4: 110.37e6 + 5.53e6}
-# The same for the heat-bath tile kernel on the heat-bath leg, shapes 1 and 2.
-HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.16e6, 2: 106.33e6 + 3.12e6}
+TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.40e6, 2: 108.47e6 + 3.65e6, 4: 110.29e6 + 5.76e6}
+# The same for the heat-bath tile kernel on the heat-bath leg (shape 1 measured).
+HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.77e6}
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
@@ -355,6 +360,7 @@ def roofline(per_launch, ops_per_flip, ipk, traffic, calls_per_word):
     alu = {"bound": "alu", "achieved": rate * ops_per_flip / 1e12, "peak": alu_peak / 1e12,
            "unit": "Tops/s", "frac": rate / alu_roof, "roof_flips_per_ns": alu_roof / 1e9,
            "ops_per_flip": ops_per_flip, "philox_calls_per_word": calls_per_word,
+           "ncu_thread_inst_per_flip": NCU_THREAD_INST_PER_FLIP,
            "peak_kind": "measured lop3.b32 rate of this GPU (ea_int_throughput)",
            "measured_rates": {"lop3_tops": ipk["lop3"] / 1e12, "imad_tops": ipk["imad"] / 1e12,
                               "philox_gcalls": ipk["philox"] / 1e9}}
