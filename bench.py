@@ -306,8 +306,8 @@ OPS_PER_PHILOX = 90
 # mean of three launches).  Take them again (or set None) when the kernel
 # changes.
 TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.40e6, 2: 108.47e6 + 3.65e6, 4: 110.29e6 + 5.76e6}
-# The same for the heat-bath tile kernel on the heat-bath leg (shape 1 measured).
-HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.77e6}
+# The same for the heat-bath tile kernel on the heat-bath leg, shapes 1 and 2.
+HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.77e6, 2: 107.60e6 + 5.08e6}
 
 
 def timed_steps(stream, n_steps, step_fn, flush):

@@ -560,6 +560,32 @@ def test_infinite_temperature_full_size(J):
     j.close()
 
 
+def test_largest_side(J):
+    """The largest side the library takes (1024: 2^30 sites, 671 MB of state per
+    sample, the general tile kernel), by properties that hold at any size: at T = inf
+    every spin flips every sweep; the ferromagnet at T = 0 from all spins up stays put;
+    the overlap and energy sums agree with the spins read back."""
+    L = 1024
+    j = J.EAJob(L, 0.5, 8, 1)
+    j.set_schedule([0, 1], [0])
+    j.quench(float("inf"))
+    s0 = j.spins(0, 0)
+    j.sweep(1)
+    assert np.array_equal(j.spins(0, 0), -s0)
+    m = j.measure(1, 0)
+    assert m["Q"][0] == int(np.sum(j.spins(0, 0) * j.spins(0, 1), dtype=np.int64))
+    assert m["A"][0, 0] == L ** 3  # C(t_w, t_w) = 1
+    j.close()
+    f = J.EAJob(L, 0.0, 9, 1)
+    f.quench(0.0)
+    up = np.ones((L, L, L), dtype=np.int8)
+    f.set_spins(0, 0, up)
+    f.set_spins(0, 1, up)
+    f.sweep(1)
+    assert np.array_equal(f.spins(0, 0), up) and np.array_equal(f.spins(0, 1), up)
+    f.close()
+
+
 # ----------------------------------------------------------------------------------
 # state handling and errors
 # ----------------------------------------------------------------------------------
