@@ -2240,7 +2240,7 @@ __global__ void __launch_bounds__(kSweepThreads, 7)
 // ---------------------------------------------------------------------------
 // 512 threads: half the work between the barriers of a half-step, and twice
 // the warps to cover shared-memory latency, against 256 (sides 48 and 64 run
-// up to 30% faster, side 32 the same).
+// 17-28% faster, side 32 the same).
 constexpr int kResThreads = 512;
 
 // The lane realignment of the resident kernel: z (every side: a z wrap of a
