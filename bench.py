@@ -299,15 +299,18 @@ BYTES_PER_FLIP = 7.0 / 16.0
 BYTES_PER_FLIP_HALF_STEPS = 12.0 / 16.0
 OPS_LOGIC_PER_WORD = 20
 OPS_PER_PHILOX = 90
-# DRAM bytes (read + write) of one batched half-step launch of this workload
-# per launch shape (rows per thread 4, 8, 16 <-> --cpt 1, 2, 4), from an ncu
-# capture of this command with that fixed shape (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass, caches flushed before each captured launch;
-# mean of three launches).  Take them again (or set None) when the kernel
-# changes.
-TRAFFIC_BYTES_PER_LAUNCH = {1: 104.92e6 + 2.40e6, 2: 108.47e6 + 3.65e6, 4: 110.29e6 + 5.76e6}
-# The same for the heat-bath tile kernel on the heat-bath leg, shapes 1 and 2.
-HEAT_TRAFFIC_BYTES_PER_LAUNCH = {1: 104.93e6 + 3.77e6, 2: 107.60e6 + 5.08e6}
+# DRAM bytes (read + write) of one batched half-step of this workload (the sum
+# over its launches, one per stream group), keyed by (launch shape, streams):
+# rows per thread 4, 8, 16 <-> --cpt 1, 2, 4.  From an ncu capture of this
+# command with that fixed shape and stream count, taken with the caches warm as
+# they are inside a step (--cache-control none, one pass: dram__bytes_read.sum +
+# dram__bytes_write.sum, mean over consecutive half-steps).  Take them again
+# (or drop the entry) when the kernel changes.
+TRAFFIC_BYTES_PER_HALF_STEP = {(1, 1): 76.7e6 + 22.3e6, (2, 1): 80.0e6 + 25.5e6,
+                               (4, 1): 83.8e6 + 29.2e6, (1, 3): 38.19e6 + 0.01e6,
+                               (2, 3): 38.18e6 + 0.01e6}
+# The same for the heat-bath tile kernel on the heat-bath leg.
+HEAT_TRAFFIC_BYTES_PER_HALF_STEP = {(1, 1): 78.7e6 + 26.6e6, (2, 1): 79.3e6 + 26.4e6}
 
 
 def timed_steps(stream, n_steps, step_fn, flush):
@@ -340,7 +343,7 @@ def value_per_launch(flips_per_launch, kernel_ms):
 def traffic_bytes(args, batch_cfg):
     if args.traffic_bytes is not None:
         return args.traffic_bytes
-    return TRAFFIC_BYTES_PER_LAUNCH.get(batch_cfg[0])
+    return TRAFFIC_BYTES_PER_HALF_STEP.get((batch_cfg[0], batch_cfg[2]))
 
 
 def roofline(per_launch, ops_per_flip, ipk, traffic, calls_per_word):
@@ -422,9 +425,11 @@ def run_ours(args, world, rank, local):
         batch.add(j)
     if args.cpt:
         batch.configure(args.cpt, args.graph_sweeps)
-        batch_cfg = (args.cpt, args.graph_sweeps)
+        if args.streams:
+            batch.set_streams(args.streams)
+        batch_cfg = (args.cpt, args.graph_sweeps, batch.streams())
     else:
-        batch_cfg = batch.autotune(trial_sweeps=8)
+        batch_cfg = tuple(batch.autotune(trial_sweeps=8)) + (batch.streams(),)
 
     def batched_step():
         batch.sweep(sps)
@@ -452,7 +457,8 @@ def run_ours(args, world, rank, local):
     sampler.stop()
     t_ms = shard.max_over_ranks(sum(step_ms), device="cuda")
     value = world * flips_per_step * args.steps / (t_ms * 1e6)
-    launches = args.steps * 2 * sps  # sweep launches: one per half-step covers all 80 samples
+    # batched half-steps: each covers all 80 samples, in one launch per stream group
+    launches = args.steps * 2 * sps
     kernel_ms = t_ms / launches  # incl. the rare observable and time-advance kernels
 
     # plain: the same work as separate per-job launch sequences (the paper's two
@@ -517,9 +523,12 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD, "L": L,
                        "jobs": [w["p_neg"] for w in specs], "samples": samples, "replicas": 2,
                        "sweeps_per_step": sps, "rule": "metropolis", "rng_group": 1,
-                       "path": "batched (one launch per half-step for all 5 jobs)",
+                       "path": "batched: each half-step of all 5 jobs is one launch per "
+                               "stream group (the jobs split into batch_config.streams groups "
+                               "on streams of their own)",
                        "batch_config": {"cols_per_thread": batch_cfg[0],
-                                        "graph_sweeps": batch_cfg[1]},
+                                        "graph_sweeps": batch_cfg[1],
+                                        "streams": batch_cfg[2]},
                        "l2": "flushed between steps (256 MiB write); inside a step nothing is "
                              "flushed, and a half-step still re-reads most of the 105 MB state "
                              "from DRAM (warm L2 sector hit rate 44%)"},
@@ -633,6 +642,7 @@ def run_mixed(args, job, workloads, stream, flush):
     for j in jobs:
         b.add(j)
     cfg = b.autotune(trial_sweeps=8)
+    b_streams = b.streams()
     n_b = args.mixed_sweeps
     b.sweep(4)
     ms_b = timed_steps(stream, 3, lambda: b.sweep(n_b), flush)
@@ -653,7 +663,8 @@ def run_mixed(args, job, workloads, stream, flush):
     return {"workload": workloads.MIXED_L["name"], "jobs": len(specs),
             "flips_per_sweep": flips_per_sweep,
             "batched": {"value": vb, "unit": UNIT, "sweeps": n_b, "ms": mb,
-                        "cols_per_thread": cfg[0], "graph_sweeps": cfg[1]},
+                        "cols_per_thread": cfg[0], "graph_sweeps": cfg[1],
+                        "streams": b_streams},
             "plain": {"value": vp, "unit": UNIT, "sweeps": n_p, "ms": mp},
             "batched_over_plain": vb / vp}
 
@@ -672,9 +683,11 @@ def run_heat(args, job, workloads, stream, flush):
         b.add(j)
     if args.cpt:  # a fixed launch shape (for a traffic capture of that shape)
         b.configure(args.cpt, args.graph_sweeps)
-        cfg = (args.cpt, args.graph_sweeps)
+        if args.streams:
+            b.set_streams(args.streams)
+        cfg = (args.cpt, args.graph_sweeps, b.streams())
     else:
-        cfg = b.autotune(trial_sweeps=8)
+        cfg = tuple(b.autotune(trial_sweeps=8)) + (b.streams(),)
     prof = b.profile(sweeps=4)
     n = args.sweeps_per_step
     b.sweep(n)
@@ -686,10 +699,12 @@ def run_heat(args, job, workloads, stream, flush):
     m = statistics.median(ms)
     return {"workload": "L128_p0.5-0.1_S16x5_T0.7 heat bath", "value": flips / (m * 1e6),
             "unit": UNIT, "ms_per_step": m, "cols_per_thread": cfg[0], "graph_sweeps": cfg[1],
+            "streams": cfg[2],
             "philox_calls_per_word": prof["philox_calls"] / max(prof["words"], 1),
             "hbm_frac_of_measured": flips / (m * 1e6) * 0.75 / peaks()[0]["hbm_gbs"],
-            "traffic_per_launch": HEAT_TRAFFIC_BYTES_PER_LAUNCH.get(cfg[0]),
-            "algorithmic_bytes_per_launch": 0.75 * sum(w["n_samples"] * w["L"] ** 3 for w in specs)}
+            "traffic_per_half_step": HEAT_TRAFFIC_BYTES_PER_HALF_STEP.get((cfg[0], cfg[2])),
+            "algorithmic_bytes_per_half_step":
+                0.75 * sum(w["n_samples"] * w["L"] ** 3 for w in specs)}
 
 
 def run_c4_radial(args, job, workloads, stream):
@@ -895,6 +910,8 @@ def main():
     ap.add_argument("--cpt", type=int, default=0, choices=[0, 1, 2, 4],
                     help="fixed launch shape of the batched path instead of the autotuned one")
     ap.add_argument("--graph-sweeps", type=int, default=8)
+    ap.add_argument("--streams", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
+                    help="with --cpt: the batch's stream groups (0: the library's default)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per half-step launch from an ncu capture of this command")
     ap.add_argument("--no-serve", action="store_true")

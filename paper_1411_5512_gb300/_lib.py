@@ -114,6 +114,8 @@ SIGNATURES = {
     "ea_batch_get_resident": (ctypes.c_int, [vp, intp]),
     "ea_batch_set_variant": (ctypes.c_int, [vp, ctypes.c_int]),
     "ea_batch_get_variant": (ctypes.c_int, [vp, intp]),
+    "ea_batch_set_streams": (ctypes.c_int, [vp, ctypes.c_int]),
+    "ea_batch_get_streams": (ctypes.c_int, [vp, intp]),
     "ea_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int]),
     "ea_batch_profile": (ctypes.c_int, [vp, ctypes.c_int, u64p]),
     "ea_batch_sweep": (ctypes.c_int, [vp, ctypes.c_uint64]),

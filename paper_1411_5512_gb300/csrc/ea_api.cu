@@ -1472,6 +1472,8 @@ struct ea_batch {
     int graph_sweeps = 0;  // sweeps per captured graph (0 = direct launches)
     int res_max_L = ea::kResDefaultMaxL;  // Metropolis sides up to this run sample-resident
     int variant = 0;                      // bit 0: side 128 on the staged kernel
+    // a table of one kernel's jobs is split over this many streams (1 .. 5)
+    int streams = ea::kDefaultStreams;
     // device job tables, one per update rule
     ea::JobDev *tab_dev[2] = {nullptr, nullptr};
     size_t cap[2] = {0, 0};
@@ -1484,6 +1486,7 @@ struct ea_batch {
     uint64_t graph_kernels = 0;  // kernels per replay
     const void *graph_key[2] = {nullptr, nullptr};
     uint64_t graph_sig = 0;
+    int graph_streams = 0;
     // side streams: the runs of a mixed table (column kernel, general tiles,
     // side 64, side 128) are enqueued concurrently
     ea::SideStreams side{};
@@ -1616,7 +1619,8 @@ int enqueue_direct(ea_batch *b, uint64_t n, unsigned long long *counters = nullp
 {
     EA_BCUDA(b, ea::launch_sweep_table(b->tab_host[0].data(), b->tab_dev[0], b->n_jobs[0],
                                        b->tab_host[1].data(), b->tab_dev[1], b->n_jobs[1], n,
-                                       b->stream, counters, b->have_side ? &b->side : nullptr));
+                                       b->stream, counters, b->have_side ? &b->side : nullptr,
+                                       -1, b->streams));
     for (int r = 0; r < 2; ++r)
         EA_BCUDA(b, ea::launch_advance_time(b->tab_dev[r], b->n_jobs[r], n, b->stream));
     return EA_OK;
@@ -1626,7 +1630,8 @@ int ensure_graph(ea_batch *b)
 {
     const int K = b->graph_sweeps;
     if (b->graph && b->graph_K == K && b->graph_key[0] == b->tab_dev[0] &&
-        b->graph_key[1] == b->tab_dev[1] && b->graph_sig == b->tab_sig)
+        b->graph_key[1] == b->tab_dev[1] && b->graph_sig == b->tab_sig &&
+        b->graph_streams == b->streams)
         return EA_OK;
     drop_graph(b);
     cudaGraph_t g = nullptr;
@@ -1653,6 +1658,7 @@ int ensure_graph(ea_batch *b)
     b->graph_key[0] = b->tab_dev[0];
     b->graph_key[1] = b->tab_dev[1];
     b->graph_sig = b->tab_sig;
+    b->graph_streams = b->streams;
     return EA_OK;
 }
 
@@ -1922,6 +1928,23 @@ int ea_batch_profile(ea_batch *b, int sweeps, uint64_t out[4])
     return EA_OK;
 }
 
+int ea_batch_set_streams(ea_batch *b, int streams)
+{
+    if (!b || streams < 1 || streams > 1 + ea::kSideStreams)
+        return EA_ERR_INVALID_ARG;
+    b->streams = streams;
+    drop_graph(b);
+    return EA_OK;
+}
+
+int ea_batch_get_streams(const ea_batch *b, int *streams)
+{
+    if (!b || !streams)
+        return EA_ERR_INVALID_ARG;
+    *streams = b->streams;
+    return EA_OK;
+}
+
 int ea_batch_set_resident(ea_batch *b, int max_side)
 {
     if (!b || max_side < 0)
@@ -1980,12 +2003,16 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
         any_128 = any_128 || (m->rule == EA_RULE_METROPOLIS && m->L == 128);
     const int var_opts[2] = {0, 1};
     const int n_var = any_128 ? 2 : 1;
+    // and the number of streams, given side streams and two or more members
+    const int str_opts[4] = {1, 2, 3, 4};
+    const int n_str = b->have_side && b->members.size() >= 2 ? 4 : 1;
     float best = 1e30f;
     int best_cpt = b->cpt, best_graph = b->graph_sweeps, best_res = b->res_max_L;
-    int best_var = b->variant;
+    int best_var = b->variant, best_str = b->streams;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == EA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         rc = bfail(b, EA_ERR_CUDA, "event creation failed");
+    for (int si = 0; si < n_str && rc == EA_OK; ++si)
     for (int vi = 0; vi < n_var && rc == EA_OK; ++vi)
     for (int ri = 0; ri < n_res && rc == EA_OK; ++ri)
     for (int ci = 0; ci < 3 && rc == EA_OK; ++ci) {
@@ -1994,6 +2021,7 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
                 continue;
             b->res_max_L = any_res ? res_opts[ri] : b->res_max_L;
             b->variant = any_128 ? var_opts[vi] : b->variant;
+            b->streams = n_str > 1 ? str_opts[si] : b->streams;
             b->cpt = cpts[ci];
             b->graph_sweeps = graphs[gi] > 0 ? std::min(graphs[gi], trial_sweeps) : 0;
             rc = upload_tables(b, ea::kMaxTime);
@@ -2016,6 +2044,7 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
                 best_graph = b->graph_sweeps;
                 best_res = b->res_max_L;
                 best_var = b->variant;
+                best_str = b->streams;
             }
         }
     }
@@ -2028,6 +2057,7 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
     b->graph_sweeps = best_graph;
     b->res_max_L = best_res;
     b->variant = best_var;
+    b->streams = best_str;
     drop_graph(b);
     return rc;
 }

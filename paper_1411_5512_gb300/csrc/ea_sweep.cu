@@ -2945,29 +2945,65 @@ static int split_runs(const JobDev *host, int n_jobs, bool general, bool residen
 cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
                                const JobDev *host1, const JobDev *dev1, int n_jobs1,
                                uint64_t n, cudaStream_t stream, unsigned long long *counters,
-                               const SideStreams *side, int half)
+                               const SideStreams *side, int half, int streams)
 {
-    // Runs of the Metropolis table hold different jobs, so they need no order
-    // between them: given side streams, every run after the first is forked
-    // from `stream` and joined back after its n sweeps, so the runs share the
-    // GPU.  The heat-bath runs follow on `stream`.
+    // Every run holds jobs of its own, so the runs need no order between them:
+    // given side streams, run r goes to lane r mod (number of lanes), lane 0
+    // being `stream` and the others side streams forked from it and joined
+    // back after their n sweeps, so the runs share the GPU.  A table of a
+    // single run (one kernel for every job) is split into `streams` runs of
+    // whole jobs first: the blocks of one run's launches then fill the SMs that
+    // another run's last wave leaves idle.
+    struct Item {
+        Run run;
+        bool heat;
+    };
+    Item items[10];
+    int n_items = 0;
     Run runs[5];
     // the sample-resident kernel runs whole sweeps only
-    const int n_runs = split_runs(host0, n_jobs0, true, half < 0, runs);
-    const bool fork = side != nullptr && n_runs > 1;
+    int nr = split_runs(host0, n_jobs0, true, half < 0, runs);
+    for (int r = 0; r < nr; ++r)
+        items[n_items++] = {runs[r], false};
+    nr = split_runs(host1, n_jobs1, true, false, runs);
+    for (int r = 0; r < nr; ++r)
+        items[n_items++] = {runs[r], true};
+    const int lanes = side != nullptr ? 1 + kSideStreams : 1;
+    const int want = std::min(std::max(streams, 1), lanes);
+    if (n_items == 1 && want > 1 && items[0].run.cnt >= 2) {
+        const Item whole = items[0];
+        const int parts = std::min(want, whole.run.cnt);
+        int first = whole.run.first;
+        for (int q = 0; q < parts; ++q) {
+            const int c = whole.run.cnt / parts + (q < whole.run.cnt % parts ? 1 : 0);
+            items[q] = {{first, c, whole.run.GLR}, whole.heat};
+            first += c;
+        }
+        n_items = parts;
+    }
+    const int used = std::min(n_items, lanes);
+    const bool fork = used > 1;
     if (fork) {
         cudaError_t err = cudaEventRecord(side->fork, stream);
-        for (int r = 1; r < n_runs && err == cudaSuccess; ++r)
+        for (int r = 1; r < used && err == cudaSuccess; ++r)
             err = cudaStreamWaitEvent(side->stream[r - 1], side->fork, 0);
         if (err != cudaSuccess)
             return err;
     }
-    for (int r = 0; r < n_runs; ++r)
-        launch_metro_run(host0 + runs[r].first, dev0 + runs[r].first, runs[r].cnt, runs[r].GLR, n,
-                         fork && r > 0 ? side->stream[r - 1] : stream, counters, half);
+    for (int i = 0; i < n_items; ++i) {
+        const int lane = i % used;
+        cudaStream_t s = lane == 0 ? stream : side->stream[lane - 1];
+        const Run &r = items[i].run;
+        if (items[i].heat)
+            launch_metro_run<true>(host1 + r.first, dev1 + r.first, r.cnt, r.GLR, n, s,
+                                   counters, half);
+        else
+            launch_metro_run(host0 + r.first, dev0 + r.first, r.cnt, r.GLR, n, s, counters,
+                             half);
+    }
     if (fork) {
         cudaError_t err = cudaSuccess;
-        for (int r = 1; r < n_runs && err == cudaSuccess; ++r) {
+        for (int r = 1; r < used && err == cudaSuccess; ++r) {
             err = cudaEventRecord(side->join[r - 1], side->stream[r - 1]);
             if (err == cudaSuccess)
                 err = cudaStreamWaitEvent(stream, side->join[r - 1], 0);
@@ -2975,11 +3011,6 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
         if (err != cudaSuccess)
             return err;
     }
-    Run hruns[5];
-    const int n_hruns = split_runs(host1, n_jobs1, true, false, hruns);
-    for (int r = 0; r < n_hruns; ++r)
-        launch_metro_run<true>(host1 + hruns[r].first, dev1 + hruns[r].first, hruns[r].cnt,
-                               hruns[r].GLR, n, stream, counters, half);
     return cudaGetLastError();
 }
 

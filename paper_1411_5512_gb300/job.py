@@ -347,6 +347,16 @@ class EABatch:
         _lib.check(self.lib.ea_batch_get_variant(self.h, ctypes.byref(v)))
         return v.value
 
+    def set_streams(self, streams):
+        """Members on one kernel are split into this many groups of whole jobs, each
+        swept on a stream of its own (1 .. 5; 1: one launch per half-step for all)."""
+        _lib.check(self.lib.ea_batch_set_streams(self.h, int(streams)), batch=self.h)
+
+    def streams(self):
+        v = ctypes.c_int()
+        _lib.check(self.lib.ea_batch_get_streams(self.h, ctypes.byref(v)))
+        return v.value
+
     def autotune(self, trial_sweeps=8):
         _lib.check(self.lib.ea_batch_autotune(self.h, int(trial_sweeps)), batch=self.h)
         return self.config()

@@ -265,3 +265,63 @@ def test_graph_follows_member_swaps_and_requench(J):
     assert a.time == 8 and c.time == 8
     for j in (a, c, ra, rc):
         j.close()
+
+
+# Batches whose members all run on one kernel, so that the batch splits them
+# into groups of whole jobs over its streams: side 128 (tile kernel), side 96
+# (general tiles), side 64 heat bath, side 24 (column kernel, not resident here)
+ONE_KERNEL = {
+    "tile128": [(128, p, 30 + i, 1, 0.7, 0, [0, 2], [0, 4])
+                for i, p in enumerate((0.5, 0.4, 0.3, 0.2, 0.1))],
+    "gtile96": [(96, 0.5, 40 + i, 1, 0.8, 0, [0, 4], [0, 2]) for i in range(3)],
+    "heat64": [(64, 0.5, 50 + i, 1, 0.8, 1, [0, 4], [0, 8]) for i in range(4)],
+    "column24": [(24, 0.3, 60 + i, 2, 0.7, 0, [0], [0, 2, 8]) for i in range(6)],
+}
+
+
+@pytest.mark.parametrize("streams", [1, 2, 3, 5])
+@pytest.mark.parametrize("case", sorted(ONE_KERNEL))
+def test_streams_split_changes_nothing(J, case, streams):
+    """A batch of jobs on one kernel, split into 1, 2, 3 or 5 groups on streams of
+    their own, gives every job exactly what it gives alone; the side-64 heat-bath and
+    side-24 groups are also checked against the oracle."""
+    import torch
+    specs = ONE_KERNEL[case]
+    n = 21
+    ref = []
+    for spec in specs:
+        j = make(J, spec)
+        j.sweep(n)
+        ref.append(snapshot(j, spec, n))
+        j.close()
+    stream = torch.cuda.Stream()
+    b = J.EABatch(stream=stream)
+    b.configure(2, 4)
+    b.set_resident(0)
+    b.set_streams(streams)
+    assert b.streams() == streams
+    jobs = [make(J, spec, stream=stream) for spec in specs]
+    for j in jobs:
+        b.add(j)
+    b.sweep(5)
+    b.sweep(16)
+    for j, spec, r in zip(jobs, specs, ref):
+        assert same(snapshot(j, spec, n), r), (case, streams, spec)
+    if case in ("heat64", "column24") and streams == 3:
+        for j, spec in zip(jobs[:2], specs[:2]):
+            L, p, seed, S, T, rule, tw, tt = spec
+            out = ora.run_job(L, p, seed, S, T, rule, tw, tt, n, keep_spins=True)
+            for s in range(S):
+                assert np.array_equal(j.all_spins(s), out["spins"][s])
+    b.close()
+    for j in jobs:
+        j.close()
+
+
+def test_streams_rejects_bad_counts(J):
+    b = J.EABatch()
+    for bad in (0, 6, -1):
+        with pytest.raises(Exception):
+            b.set_streams(bad)
+    assert b.streams() == 3
+    b.close()
