@@ -420,14 +420,14 @@ int ea_batch_set_variant(ea_batch *b, int variant);
 int ea_batch_get_variant(const ea_batch *b, int *variant);
 
 /* The streams a batch spreads its sweep launches over, 1 .. 5 (default 3).
- * When every member runs on the same kernel (one side range, one rule), the
- * members are split into that many groups of whole jobs, and each group's
- * half-step launches go to a stream of its own, forked from the batch's
- * stream and joined back after the sweeps; a mixed table already spreads its
- * kernels' groups over the streams.  One group's launches fill the SMs that
- * another group's last wave leaves idle.  Jobs are independent, so the
- * results do not depend on the setting; 1 runs one launch per half-step for
- * all members.  The autotuner chooses among 1 .. 4.  get reads it back.
+ * The members form one group per kernel (side range and rule); while there
+ * are fewer groups than streams, the group of most jobs is halved (whole
+ * jobs).  Each group's half-step launches go to a stream of its own, forked
+ * from the batch's stream and joined back after the sweeps, so one group's
+ * launches fill the SMs that another group's last wave leaves idle.  Jobs are
+ * independent, so the results do not depend on the setting; with 1 a
+ * one-kernel batch runs one launch per half-step for all its members.  The
+ * autotuner chooses among 1 .. 4.  get reads it back.
  * Errors: EA_ERR_INVALID_ARG (NULL, streams outside 1 .. 5). */
 int ea_batch_set_streams(ea_batch *b, int streams);
 int ea_batch_get_streams(const ea_batch *b, int *streams);

@@ -222,8 +222,8 @@ struct SideStreams {
 // half = 0 or 1: only that half-step of one sweep (n must be 1), for a
 // lattice split over ranks whose halo rows are exchanged between half-steps.
 // Given side streams, the runs (the rows of one kernel) are spread over
-// `stream` and the side streams, and a table of a single run is first split
-// into up to `streams` runs of whole jobs (1 .. 1 + kSideStreams).
+// `stream` and the side streams, after the largest runs are halved (whole
+// jobs) until there are `streams` runs (1 .. 1 + kSideStreams) or none splits.
 cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jobs0,
                                const JobDev *host1, const JobDev *dev1, int n_jobs1,
                                uint64_t n, cudaStream_t stream,

@@ -2950,10 +2950,10 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
     // Every run holds jobs of its own, so the runs need no order between them:
     // given side streams, run r goes to lane r mod (number of lanes), lane 0
     // being `stream` and the others side streams forked from it and joined
-    // back after their n sweeps, so the runs share the GPU.  A table of a
-    // single run (one kernel for every job) is split into `streams` runs of
-    // whole jobs first: the blocks of one run's launches then fill the SMs that
-    // another run's last wave leaves idle.
+    // back after their n sweeps, so the runs share the GPU.  With fewer runs
+    // than `streams`, runs are first split into runs of whole jobs: the blocks
+    // of one run's launches then fill the SMs that another run's last wave
+    // leaves idle.
     struct Item {
         Run run;
         bool heat;
@@ -2970,16 +2970,22 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
         items[n_items++] = {runs[r], true};
     const int lanes = side != nullptr ? 1 + kSideStreams : 1;
     const int want = std::min(std::max(streams, 1), lanes);
-    if (n_items == 1 && want > 1 && items[0].run.cnt >= 2) {
-        const Item whole = items[0];
-        const int parts = std::min(want, whole.run.cnt);
-        int first = whole.run.first;
-        for (int q = 0; q < parts; ++q) {
-            const int c = whole.run.cnt / parts + (q < whole.run.cnt % parts ? 1 : 0);
-            items[q] = {{first, c, whole.run.GLR}, whole.heat};
-            first += c;
-        }
-        n_items = parts;
+    // fewer runs than streams: halve the run of most jobs (whole jobs, the
+    // first half keeps the larger share) until there are enough or none splits
+    while (n_items < want) {
+        int big = -1;
+        for (int i = 0; i < n_items; ++i)
+            if (items[i].run.cnt >= 2 && (big < 0 || items[i].run.cnt > items[big].run.cnt))
+                big = i;
+        if (big < 0)
+            break;
+        for (int i = n_items; i > big + 1; --i)
+            items[i] = items[i - 1];
+        const Run r = items[big].run;
+        const int c0 = (r.cnt + 1) / 2;
+        items[big].run = {r.first, c0, r.GLR};
+        items[big + 1] = {{r.first + c0, r.cnt - c0, r.GLR}, items[big].heat};
+        ++n_items;
     }
     const int used = std::min(n_items, lanes);
     const bool fork = used > 1;
