@@ -289,8 +289,7 @@ __global__ void __launch_bounds__(kObsThreads)
 #pragma unroll
     for (int i = 0; i < kAcc; ++i) {
         if (i < n_acc) {
-            // a warp's sum fits 32 bits: at most 96 per word, four words per thread
-            unsigned int v = acc[i];
+            unsigned long long v = acc[i];
             for (int o = 16; o > 0; o >>= 1)
                 v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0)
@@ -617,8 +616,6 @@ cudaError_t launch_init_spins(uint32_t *spins, const Geo &g, int first_sample, i
 cudaError_t launch_obs_time(const ObsTimeParams &p, const Geo &g, int n_samples,
                             cudaStream_t stream)
 {
-    // four words per thread: one word per thread measured 16% slower (four
-    // times the blocks, each with its reduction and atomics)
     const unsigned bx = (unsigned)std::max(1, (g.words + 4 * kObsThreads - 1) / (4 * kObsThreads));
     obs_time_kernel<<<dim3(bx, (unsigned)n_samples), kObsThreads, 0, stream>>>(p, g);
     count_launches(1);
