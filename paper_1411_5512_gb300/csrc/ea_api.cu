@@ -411,7 +411,7 @@ int launch_plain(ea_ctx *c, uint64_t n)
 }
 
 // Measurements due at the current time c->t (if it is a scheduled time).
-int fire_measurements(ea_ctx *c)
+int fire_measurements(ea_ctx *c, cudaStream_t stream)
 {
     const int mi = idx_of(c->meas, c->t);
     if (mi < 0)
@@ -422,9 +422,9 @@ int fire_measurements(ea_ctx *c)
     const int ti = idx_of(c->tw, c->t);
     if (ti >= 0) {
         EA_CUDA(c, cudaMemcpyAsync(c->snaps + ti * area, c->spins, area * sizeof(uint32_t),
-                                   cudaMemcpyDeviceToDevice, c->stream));
+                                   cudaMemcpyDeviceToDevice, stream));
         EA_CUDA(c, ea::launch_obs_c4(c->spins, c->geo, c->S, c->res + c->off_g + ti * S * 3 * R,
-                                     c->stream));
+                                     stream));
     }
     // the state sums and every autocorrelation due at this time, one pass over
     // the state per launch of up to kObsMaxSnaps snapshots
@@ -441,14 +441,14 @@ int fire_measurements(ea_ctx *c)
         p.snap[p.n_snap] = c->snaps + i * area;
         p.a_pop[p.n_snap] = c->res + c->off_a + (i * c->tt.size() + (size_t)j) * S * 2;
         if (++p.n_snap == ea::kObsMaxSnaps) {
-            EA_CUDA(c, ea::launch_obs_time(p, c->geo, c->S, c->stream));
+            EA_CUDA(c, ea::launch_obs_time(p, c->geo, c->S, stream));
             p.q_pop = nullptr;  // the state sums went with the first launch
             p.u_pop = nullptr;
             p.n_snap = 0;
         }
     }
     if (p.n_snap > 0 || p.q_pop != nullptr)
-        EA_CUDA(c, ea::launch_obs_time(p, c->geo, c->S, c->stream));
+        EA_CUDA(c, ea::launch_obs_time(p, c->geo, c->S, stream));
     return EA_OK;
 }
 
@@ -722,7 +722,7 @@ int ea_quench(ea_ctx *c, double T, int rule)
     int rc = upload_job(c);
     if (rc != EA_OK)
         return rc;
-    return fire_measurements(c);
+    return fire_measurements(c, c->stream);
 }
 
 int ea_sweep(ea_ctx *c, uint64_t n)
@@ -747,7 +747,7 @@ int ea_sweep(ea_ctx *c, uint64_t n)
         if (rc0 != EA_OK)
             return rc0;
         c->t = stop;
-        const int rc = fire_measurements(c);
+        const int rc = fire_measurements(c, c->stream);
         if (rc != EA_OK)
             return rc;
     }
@@ -1815,15 +1815,39 @@ int batch_sweep_impl(ea_batch *b, uint64_t n, const std::vector<uint64_t> *limit
         rc = run_sweeps(b, step);
         if (rc != EA_OK)
             return rc;
+        std::vector<ea_ctx *> due;
         for (size_t i = 0; i < b->members.size(); ++i) {
             ea_ctx *m = b->members[i];
             const uint64_t adv = std::min<uint64_t>(step, end[i] - m->t);
             if (adv == 0)
                 continue;
             m->t += adv;
-            rc = fire_measurements(m);
+            if (idx_of(m->meas, m->t) >= 0)
+                due.push_back(m);
+        }
+        // each member's measurements read the state the sweeps left and write
+        // the member's own sums only: given side streams, they run side by
+        // side, forked from the batch stream and joined back before the next
+        // sweeps
+        const int lanes = b->have_side && due.size() >= 2
+                              ? (int)std::min<size_t>(due.size(), 1 + ea::kSideStreams)
+                              : 1;
+        if (lanes > 1) {
+            EA_BCUDA(b, cudaEventRecord(b->side.fork, b->stream));
+            for (int r = 1; r < lanes; ++r)
+                EA_BCUDA(b, cudaStreamWaitEvent(b->side.stream[r - 1], b->side.fork, 0));
+        }
+        for (size_t k = 0; k < due.size(); ++k) {
+            const int lane = (int)(k % (size_t)lanes);
+            rc = fire_measurements(due[k], lane == 0 ? b->stream : b->side.stream[lane - 1]);
             if (rc != EA_OK)
-                return bfail(b, rc, "measurement failed: " + m->err);
+                return bfail(b, rc, "measurement failed: " + due[k]->err);
+        }
+        if (lanes > 1) {
+            for (int r = 1; r < lanes; ++r) {
+                EA_BCUDA(b, cudaEventRecord(b->side.join[r - 1], b->side.stream[r - 1]));
+                EA_BCUDA(b, cudaStreamWaitEvent(b->stream, b->side.join[r - 1], 0));
+            }
         }
         remaining -= step;
     }
