@@ -2584,6 +2584,10 @@ static void metro_job(MetroJob &m, const JobDev &jd, int geo_index)
              ((uint32_t)geo_index << 8) | ((uint32_t)jd.first_sample << 16);
 }
 
+// Tiles (2 x 2 word-sites of one row) of all tile-kernel runs that
+// launch_sweep_table spreads over streams at once, 0 outside such a set.
+static thread_local long t_tiles_shared = 0;
+
 // Jobs host[0..cnt) in one launch sequence; all of them share at most
 // kMetroMaxGeo (side, layout) geometries.
 template <int MAXJ, int GL, bool HEAT = false>
@@ -2604,13 +2608,17 @@ static void launch_metro_chunk(const JobDev *host, const JobDev *dev, int cnt, u
         return (GL == 64 || GL == 128) ? jd.row_hi - jd.row_lo : jd.geo.n[1];
     };
     // tile kernels: rows per thread from the launch shape, halved (down to 2)
-    // while the launch would hold fewer than four blocks per SM
+    // while the launch would hold fewer than four blocks per SM.  Runs that
+    // share the GPU on streams count the tiles of all of them (t_tiles_shared):
+    // the GPU is full as long as the set is, so a small run of the set need not
+    // take shorter rows
     int y_max = 16;
     if (GL != 0) {
         long tiles = 0;  // tiles of one row, 2 x 2 word-sites each
         for (int i = 0; i < cnt; ++i)
             tiles += (long)host[i].n_samples * (host[i].geo.n[0] / 2) * (host[i].geo.n[2] / 2) *
                      rows_of(host[i]);
+        tiles = std::max(tiles, t_tiles_shared);
         while (y_max > 2 && tiles / y_max / kSweepThreads < 4L * kTileMinSMs)
             y_max >>= 1;
         // a launch that would not even give every SM a block takes single rows:
@@ -2989,6 +2997,19 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
     }
     const int used = std::min(n_items, lanes);
     const bool fork = used > 1;
+    long shared = 0;
+    if (fork)
+        for (int i = 0; i < n_items; ++i) {
+            const Run &r = items[i].run;
+            if (r.GLR != 128 && r.GLR != 64 && r.GLR != kGeneralTile)
+                continue;
+            const JobDev *h = (items[i].heat ? host1 : host0) + r.first;
+            for (int k = 0; k < r.cnt; ++k) {
+                const int rows = (r.GLR == 64 || r.GLR == 128) ? h[k].row_hi - h[k].row_lo
+                                                                : h[k].geo.n[1];
+                shared += (long)h[k].n_samples * (h[k].geo.n[0] / 2) * (h[k].geo.n[2] / 2) * rows;
+            }
+        }
     if (fork) {
         cudaError_t err = cudaEventRecord(side->fork, stream);
         for (int r = 1; r < used && err == cudaSuccess; ++r)
@@ -2996,6 +3017,7 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
         if (err != cudaSuccess)
             return err;
     }
+    t_tiles_shared = shared;
     for (int i = 0; i < n_items; ++i) {
         const int lane = i % used;
         cudaStream_t s = lane == 0 ? stream : side->stream[lane - 1];
@@ -3007,6 +3029,7 @@ cudaError_t launch_sweep_table(const JobDev *host0, const JobDev *dev0, int n_jo
             launch_metro_run(host0 + r.first, dev0 + r.first, r.cnt, r.GLR, n, s, counters,
                              half);
     }
+    t_tiles_shared = 0;
     if (fork) {
         cudaError_t err = cudaSuccess;
         for (int r = 1; r < used && err == cudaSuccess; ++r) {
