@@ -432,9 +432,12 @@ int ea_batch_get_variant(const ea_batch *b, int *variant);
 int ea_batch_set_streams(ea_batch *b, int streams);
 int ea_batch_get_streams(const ea_batch *b, int *streams);
 
-/* Try the launch shapes on the members' current state for trial_sweeps sweeps
- * each, keep the fastest and put the state back as it was (time, spins): the
- * tuning leaves every result unchanged.  Synchronises the batch stream. */
+/* Try the launch configurations on the members' current state for
+ * trial_sweeps sweeps each: word columns per thread {1, 2, 4}, graphs {none,
+ * 16 sweeps}, and where they apply the resident limit {32, 64, 0}, the
+ * side-128 kernel {0, 1} and the streams {1, 2, 3, 4}.  Keeps the fastest and
+ * puts the state back as it was (time, spins): the tuning leaves every result
+ * unchanged.  Synchronises the batch stream. */
 int ea_batch_autotune(ea_batch *b, int trial_sweeps);
 
 /* Work counts of the update, for the integer-op roofline: runs `sweeps`
