@@ -503,7 +503,7 @@ def run_ours(args, world, rank, local):
         side32 = run_side32(args, job, workloads, stream, flush)
     heat = None
     if not args.no_heat:
-        heat = run_heat(args, job, workloads, stream, flush)
+        heat = run_heat(args, job, workloads, stream, flush, ipk)
     c4r = None
     if not args.no_heat:
         c4r = run_c4_radial(args, job, workloads, stream)
@@ -668,9 +668,20 @@ def run_mixed(args, job, workloads, stream, flush):
             "batched_over_plain": vb / vp}
 
 
-def run_heat(args, job, workloads, stream, flush):
+def heat_alu_roof(value, prof, ipk):
+    c = prof["philox_calls"] / max(prof["words"], 1)
+    ops = (OPS_LOGIC_PER_WORD + OPS_PER_PHILOX * c) / 32.0
+    roof = ipk["lop3"] / ops / 1e9  # flips/ns
+    return {"ops_per_flip": ops, "roof_flips_per_ns": roof, "frac": value / roof,
+            "peak_kind": "measured lop3.b32 rate of this GPU (ea_int_throughput)"}
+
+
+def run_heat(args, job, workloads, stream, flush, ipk):
     """The heat-bath variant on the paper-scale workload (side 128, five jobs of 16
-    samples, T = 0.7): batched, median of 3 steps of 64 sweeps, L2 flushed between."""
+    samples, T = 0.7): batched, median of 3 steps of 64 sweeps, L2 flushed between.
+    Its integer-ALU roof takes the same (20 + 90 c) / 32 ops per flip as the
+    Metropolis one, with c its own Philox calls per word (one main call per word
+    where the Metropolis path shares one per four)."""
     specs = workloads.PAPER_SCALE
     jobs = []
     for w in specs:
@@ -700,6 +711,7 @@ def run_heat(args, job, workloads, stream, flush):
             "unit": UNIT, "ms_per_step": m, "cols_per_thread": cfg[0], "graph_sweeps": cfg[1],
             "streams": cfg[2],
             "philox_calls_per_word": prof["philox_calls"] / max(prof["words"], 1),
+            "alu_roof": heat_alu_roof(flips / (m * 1e6), prof, ipk),
             "hbm_frac_of_measured": flips / (m * 1e6) * 0.75 / peaks()[0]["hbm_gbs"],
             "traffic_per_half_step": HEAT_TRAFFIC_BYTES_PER_HALF_STEP.get((cfg[0], cfg[2])),
             "algorithmic_bytes_per_half_step":

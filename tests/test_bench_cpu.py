@@ -46,3 +46,17 @@ def test_roofline_reports_the_lower_roof():
     assert r["other"]["bound"] != r["bound"]
     assert abs(r["half_step_traffic"]["bytes_per_flip"] - 0.75) < 1e-15
     assert abs(bench.BYTES_PER_FLIP - 0.4375) < 1e-15
+
+
+def test_heat_bath_alu_roof():
+    """(20 + 90 c) / 32 ops per flip with the heat bath's own Philox calls per word c,
+    priced at the measured lop3 rate."""
+    sys.path.insert(0, ROOT)
+    import bench
+    ipk = {"lop3": 19.7e12, "imad": 19.9e12, "philox": 4.4e11}
+    prof = {"words": 1000, "philox_calls": 1110}
+    r = bench.heat_alu_roof(4633.0, prof, ipk)
+    ops = (20 + 90 * 1.11) / 32
+    assert abs(r["ops_per_flip"] - ops) < 1e-12
+    assert abs(r["roof_flips_per_ns"] - 19.7e12 / ops / 1e9) < 1e-9
+    assert abs(r["frac"] - 4633.0 / r["roof_flips_per_ns"]) < 1e-12
