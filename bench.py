@@ -428,7 +428,7 @@ def run_ours(args, world, rank, local):
             batch.set_streams(args.streams)
         batch_cfg = (args.cpt, args.graph_sweeps, batch.streams())
     else:
-        batch_cfg = tuple(batch.autotune(trial_sweeps=8)) + (batch.streams(),)
+        batch_cfg = tuple(batch.autotune(trial_sweeps=64)) + (batch.streams(),)
 
     def batched_step():
         batch.sweep(sps)
@@ -640,7 +640,7 @@ def run_mixed(args, job, workloads, stream, flush):
     b = job.EABatch(stream=stream)
     for j in jobs:
         b.add(j)
-    cfg = b.autotune(trial_sweeps=8)
+    cfg = b.autotune(trial_sweeps=64)
     b_streams = b.streams()
     n_b = args.mixed_sweeps
     b.sweep(4)
@@ -697,7 +697,7 @@ def run_heat(args, job, workloads, stream, flush, ipk):
             b.set_streams(args.streams)
         cfg = (args.cpt, args.graph_sweeps, b.streams())
     else:
-        cfg = tuple(b.autotune(trial_sweeps=8)) + (b.streams(),)
+        cfg = tuple(b.autotune(trial_sweeps=64)) + (b.streams(),)
     prof = b.profile(sweeps=4)
     n = args.sweeps_per_step
     b.sweep(n)

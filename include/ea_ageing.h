@@ -434,7 +434,7 @@ int ea_batch_get_streams(const ea_batch *b, int *streams);
 
 /* Try the launch configurations on the members' current state for
  * trial_sweeps sweeps each: word columns per thread {1, 2, 4}, graphs {none,
- * 16 sweeps}, and where they apply the resident limit {32, 64, 0}, the
+ * 16, 64 sweeps} (at most trial_sweeps), and where they apply the resident limit {32, 64, 0}, the
  * side-128 kernel {0, 1} and the streams {1, 2, 3, 4}.  Keeps the fastest and
  * puts the state back as it was (time, spins): the tuning leaves every result
  * unchanged.  Synchronises the batch stream. */

@@ -2014,7 +2014,7 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
     SavedState st;
     int rc = save_state(b, st);
     const int cpts[3] = {1, 2, 4};
-    const int graphs[2] = {0, 16};
+    const int graphs[3] = {0, 16, 64};
     // the sample-resident kernel is a candidate when a Metropolis member fits
     bool any_res = false;
     for (ea_ctx *m : b->members)
@@ -2040,7 +2040,7 @@ int ea_batch_autotune(ea_batch *b, int trial_sweeps)
     for (int vi = 0; vi < n_var && rc == EA_OK; ++vi)
     for (int ri = 0; ri < n_res && rc == EA_OK; ++ri)
     for (int ci = 0; ci < 3 && rc == EA_OK; ++ci) {
-        for (int gi = 0; gi < 2 && rc == EA_OK; ++gi) {
+        for (int gi = 0; gi < 3 && rc == EA_OK; ++gi) {
             if (graphs[gi] > 0 && b->stream == nullptr)
                 continue;
             b->res_max_L = any_res ? res_opts[ri] : b->res_max_L;
