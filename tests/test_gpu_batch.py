@@ -161,7 +161,8 @@ def test_autotune_changes_nothing(J):
         b.add(j)
     b.sweep(4)
     cfg = b.autotune(trial_sweeps=6)
-    assert cfg[0] in (1, 2, 4) and cfg[1] >= 0
+    assert cfg[0] in (1, 2, 4) and 0 <= cfg[1] <= 6
+    assert 1 <= b.streams() <= 4 and b.resident() in (32, 64, 0)
     b.sweep(n - 4)
     for j, spec, r in zip(jobs, MIX, ref):
         assert same(snapshot(j, spec, n), r), spec
