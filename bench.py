@@ -493,7 +493,7 @@ def run_ours(args, world, rank, local):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, job, workloads, stream, rank, world)
+        e2e = run_e2e(args, job, workloads, stream, rank, world, batch_cfg)
     serving = None
     if not args.no_serve:
         serving = run_serving(args, job, workloads, stream)
@@ -801,7 +801,7 @@ def run_serving(args, job, workloads, stream):
             "flips": int(flips), "wall_s": wall, "value": flips / (wall * 1e9), "unit": UNIT}
 
 
-def run_e2e(args, job, workloads, stream, rank, world):
+def run_e2e(args, job, workloads, stream, rank, world, batch_cfg):
     """Whole jobs through the public API with their inputs from host memory: create,
     the couplings of every sample uploaded from a pinned host buffer (the packed
     layout), the schedule from host arrays, quench, sweeps of all five jobs together
@@ -839,7 +839,9 @@ def run_e2e(args, job, workloads, stream, rank, world):
             j.quench(w["T"])
             jobs.append(j)
         b = job.EABatch(stream=stream)  # the jobs' sweeps share launches
-        b.configure(0, 8)
+        # the launch configuration the batched leg's autotuner found for these jobs
+        b.configure(batch_cfg[0], batch_cfg[1])
+        b.set_streams(batch_cfg[2])
         for j in jobs:
             b.add(j)
         b.sweep(n)
