@@ -336,9 +336,10 @@ def pct(v, q):
     return v[i]
 
 
-def value_per_launch(flips_per_launch, kernel_ms):
-    """flips per launch and seconds per launch of the timed half-step kernel."""
-    return flips_per_launch, kernel_ms * 1e-3
+def value_per_half_step(flips_per_half_step, kernel_ms):
+    """flips and seconds per batched half-step (all samples; one launch per stream
+    group, the groups side by side)."""
+    return flips_per_half_step, kernel_ms * 1e-3
 
 
 def traffic_bytes(args, batch_cfg):
@@ -347,11 +348,11 @@ def traffic_bytes(args, batch_cfg):
     return TRAFFIC_BYTES_PER_HALF_STEP.get((batch_cfg[0], batch_cfg[2]))
 
 
-def roofline(per_launch, ops_per_flip, ipk, traffic, calls_per_word):
+def roofline(per_half_step, ops_per_flip, ipk, traffic, calls_per_word):
     """The binding roof of the half-step kernel and the others beside it.  HBM at the
     algorithmic 0.4375 B/flip against the measured copy bandwidth; integer ALU at
     the algorithmic ops per flip against the measured lop3.b32 rate."""
-    flips, launch_s = per_launch
+    flips, launch_s = per_half_step
     pk, pk_kind = peaks()
     rate = flips / launch_s  # flips/s
     hbm_roof = pk["hbm_gbs"] * 1e9 / BYTES_PER_FLIP
@@ -375,7 +376,7 @@ def roofline(per_launch, ops_per_flip, ipk, traffic, calls_per_word):
             "what": "the traffic of a pair of half-step kernels, for comparison"}
     primary, other = (hbm, alu) if hbm_roof <= alu_roof else (alu, hbm)
     roof = dict(primary)
-    roof.update({"kernel": "metro_tile_kernel", "flips_per_launch": flips,
+    roof.update({"kernel": "metro_tile_kernel", "flips_per_half_step": flips,
                  "traffic": traffic,
                  "traffic_over_algorithmic": (None if traffic is None else
                                               traffic / (flips * BYTES_PER_FLIP)),
@@ -480,9 +481,10 @@ def run_ours(args, world, rank, local):
     calls_per_word = prof["philox_calls"] / max(1, prof["words"])
     ops_per_flip = (OPS_LOGIC_PER_WORD + OPS_PER_PHILOX * calls_per_word) / 32.0
     ipk = job.int_throughput(stream)  # measured integer rates of this GPU
-    roof = roofline(value_per_launch(samples * N, kernel_ms), ops_per_flip, ipk,
+    roof = roofline(value_per_half_step(samples * N, kernel_ms), ops_per_flip, ipk,
                     traffic_bytes(args, batch_cfg), calls_per_word)
-    roof["kernel_us_per_launch"] = kernel_ms * 1e3
+    roof["us_per_half_step"] = kernel_ms * 1e3
+    roof["launches_per_half_step"] = min(batch_cfg[2], len(jobs))  # one per stream group
 
     # the paper's plain path: one sample per launch sequence, two launches per
     # sweep, over every sample of the workload
