@@ -515,7 +515,7 @@ int ea_server_create(ea_server **out, size_t budget_bytes, int max_running, uint
 int ea_server_submit(ea_server *srv, const ea_job_spec *spec, int64_t *job_id);
 
 /* One round: admit, run one chunk, retire.  *n_finished (may be NULL)
- * receives the number of jobs retired in this round.  Asynchronous apart from
+ * receives the number of jobs retired in this step.  Asynchronous apart from
  * the admission of new jobs; a retired job's results are read with
  * ea_measure on its context (ea_server_job), which synchronises. */
 int ea_server_step(ea_server *srv, int *n_finished);
