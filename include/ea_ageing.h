@@ -514,7 +514,7 @@ int ea_server_create(ea_server **out, size_t budget_bytes, int max_running, uint
  * whole budget). */
 int ea_server_submit(ea_server *srv, const ea_job_spec *spec, int64_t *job_id);
 
-/* One round: admit, run one chunk, retire.  *n_finished (may be NULL)
+/* One step: admit, run one chunk, retire.  *n_finished (may be NULL)
  * receives the number of jobs retired in this step.  Asynchronous apart from
  * the admission of new jobs; a retired job's results are read with
  * ea_measure on its context (ea_server_job), which synchronises. */
